@@ -1,0 +1,184 @@
+"""FP64 CPU oracle for the coherent-dedispersion filterbank (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  The GPU library never uses it.  The arithmetic lives in
+``cdmt_oracle.c`` (plain C, double precision, its own radix-2 FFT); this module
+compiles it with gcc on first use and marshals numpy arrays through ctypes.
+
+Every function states the passage of Bassa, Pleunis & Hessels (2016) that it
+follows; the C file's header lists the steps and the readings taken where the
+paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cdmt_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+D_CONST = 4.148808e3  # MHz^2 pc^-1 cm^3 s (dispersion constant reading)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle to ``liboracle.so`` (gcc -O2, no fast-math, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            fp = ctypes.POINTER(ctypes.c_float)
+            i64 = ctypes.c_int64
+            lib.orc_sweep.restype = ctypes.c_double
+            lib.orc_sweep.argtypes = [ctypes.c_double] * 3
+            lib.orc_subband_centre.restype = ctypes.c_double
+            lib.orc_subband_centre.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            lib.orc_channel_centre.restype = ctypes.c_double
+            lib.orc_channel_centre.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            lib.orc_overlap.restype = i64
+            lib.orc_overlap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, i64]
+            lib.orc_fft.restype = None
+            lib.orc_fft.argtypes = [dp, i64, ctypes.c_int]
+            lib.orc_dft.restype = None
+            lib.orc_dft.argtypes = [dp, dp, i64, ctypes.c_int]
+            lib.orc_segment_channels.restype = None
+            lib.orc_segment_channels.argtypes = [dp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, dp]
+            lib.orc_grid.restype = ctypes.c_int
+            lib.orc_grid.argtypes = [i64, i64, ctypes.c_int, i64, ctypes.c_int,
+                                     ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            lib.orc_filterbank.restype = ctypes.c_int
+            lib.orc_filterbank.argtypes = [fp, ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, dp,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, dp, ctypes.c_int]
+            lib.orc_tiles.restype = ctypes.c_int
+            lib.orc_tiles.argtypes = [fp, ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, dp,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
+                                      ctypes.POINTER(ctypes.c_int), dp, ctypes.c_int]
+            lib.orc_max_threads.restype = ctypes.c_int
+            lib.orc_max_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def sweep(nu_min: float, nu_max: float, dm: float) -> float:
+    """Dispersion sweep t_d (s) across [nu_min, nu_max] MHz (Eq. 2)."""
+    return _load().orc_sweep(nu_min, nu_max, dm)
+
+
+def subband_centre(nsub: int, f_centre: float, bw: float, s: int) -> float:
+    """Centre (MHz) of subband s of a contiguous band centred on f_centre (Sec. 3 input model)."""
+    return _load().orc_subband_centre(nsub, f_centre, bw, s)
+
+
+def channel_centre(nu_s: float, bw: float, nchan: int, c: int) -> float:
+    """Centre (MHz) of channel c of a subband centred on nu_s (Sec. 2, nu_0 of a channel)."""
+    return _load().orc_channel_centre(nu_s, bw, nchan, c)
+
+
+def overlap(nsub, f_centre, bw, dm_list, nchan, nint, nbin) -> int:
+    """Overlap nd of Sec. 2 (nd = r t_d / n_c, t_d of Eq. 2 for the lowest channel)."""
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    return int(_load().orc_overlap(nsub, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin))
+
+
+def grid(nsamp, nbin, nchan, nd, nint):
+    """(S, nseg, nout) of the overlap-save grid (Sec. 2, Fig. 2; Sec. 3 block loop)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = _load().orc_grid(nsamp, nbin, nchan, nd, nint, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc:
+        raise ValueError("invalid overlap-save grid")
+    return a.value, b.value, c.value
+
+
+def fft(x, sign: int) -> np.ndarray:
+    """Unnormalised radix-2 FFT with kernel exp(sign 2 pi i nk/n) (the oracle's own)."""
+    a = np.ascontiguousarray(x, dtype=np.complex128).copy()
+    _load().orc_fft(_dp(a.view(np.float64)), len(a), sign)
+    return a
+
+
+def dft(x, sign: int) -> np.ndarray:
+    """Naive O(n^2) DFT with kernel exp(sign 2 pi i nk/n)."""
+    a = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.empty_like(a)
+    _load().orc_dft(_dp(a.view(np.float64)), _dp(y.view(np.float64)), len(a), sign)
+    return y
+
+
+def segment_channels(x, nchan: int, nu_s: float, bw: float, dm: float) -> np.ndarray:
+    """Channelised, dedispersed complex series [nchan][M] of one polarisation of
+    one segment, before the overlap is discarded (Sec. 2 steps 3-5 of Fig. 2)."""
+    a = np.ascontiguousarray(x, dtype=np.complex128)
+    n = len(a)
+    y = np.empty((nchan, n // nchan), dtype=np.complex128)
+    _load().orc_segment_channels(_dp(a.view(np.float64)), n, nchan, nu_s, bw, dm, _dp(y.view(np.float64)))
+    return y
+
+
+def filterbank(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, nthreads: int = 0) -> np.ndarray:
+    """Whole DM x channel x time filterbank (Algorithm 1 up to detection, plus
+    integration over nint).  x: float32 [nsub][nsamp][4]; returns float64
+    [ndm][nsub*nchan][nout]."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    nsub, nsamp = x.shape[0], x.shape[1]
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    _, _, nout = grid(nsamp, nbin, nchan, nd, nint)
+    out = np.zeros((len(dm), nsub * nchan, nout), dtype=np.float64)
+    rc = _load().orc_filterbank(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint,
+                                nbin, nd, _dp(out), nthreads)
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthreads: int = 0) -> np.ndarray:
+    """Filterbank samples of the listed (subband, segment, DM index) tiles:
+    float64 [ntile][nchan][(M - nd)/nint].  Equal to the matching slice of
+    :func:`filterbank` (each segment is independent given its own input)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    nsub, nsamp = x.shape[0], x.shape[1]
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    sub = np.ascontiguousarray(sub, dtype=np.int32)
+    seg = np.ascontiguousarray(seg, dtype=np.int64)
+    dmi = np.ascontiguousarray(dmi, dtype=np.int32)
+    m = nbin // nchan
+    out = np.zeros((len(sub), nchan, (m - nd) // nint), dtype=np.float64)
+    rc = _load().orc_tiles(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin, nd,
+                           len(sub), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                           seg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           dmi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out), nthreads)
+    if rc:
+        raise ValueError("oracle rejected the tile list")
+    return out
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle uses by default."""
+    return int(_load().orc_max_threads())

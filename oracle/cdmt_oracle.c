@@ -1,0 +1,320 @@
+/*
+ * FP64 CPU oracle for coherent dedispersion with a convolving synthetic
+ * filterbank (Bassa, Pleunis & Hessels 2016, "cdmt").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is read, built and run by the test
+ * suite, by the smoke check and by the CPU-baseline leg of the benchmark.
+ * The GPU library never links, includes or calls it, and it shares no code
+ * (kernels, headers, tables, constants generators) with the GPU library.
+ *
+ * What it computes, per subband s, overlap-save segment k, DM trial and
+ * polarisation (paper Sec. 2, Eq. 1, Eq. 2, Fig. 2; Sec. 3, Algorithm 1):
+ *   1. x_n = in[s][k*S + n][pol], n < N  (S = N - nd*nchan valid samples)
+ *   2. X = unitary forward DFT_N(x) (e^{-2 pi i}/sqrt(N)), halves swapped so
+ *      bins run in increasing frequency (Sec. 3, "swap halves per subband").
+ *   3. channel c takes bins [c*M, (c+1)*M), M = N/nchan, and multiplies them
+ *      by the conjugate of Eq. 1 evaluated at the channel centre nu_c with
+ *      offset nu = (j - M/2) * bw / N  (Sec. 2: each channel gets its own
+ *      transfer function; Sec. 3: "complex multiplication with transfer
+ *      function").  Dedispersion is the convolution with the INVERSE of the
+ *      ISM transfer function (Sec. 1, Sec. 2), i.e. multiplication by
+ *      exp(-2 pi i phi), phi = 1e6 * D * DM * nu^2 / (nu_c^2 (nu_c + nu)).
+ *   4. halves of each channel swapped back, unitary inverse DFT_M
+ *      (e^{+2 pi i}/sqrt(M)) (Sec. 3, "backward FFT").
+ *   5. nd/2 samples dropped at each edge, |y_X|^2 + |y_Y|^2 (Stokes I)
+ *      (Sec. 3, "transpose, unpad and detect").
+ *   6. nint consecutive samples summed into out[dm][s*nchan + c][t].
+ *
+ * Readings where the paper is silent: D = 4.148808e3 MHz^2 pc^-1 cm^3 s
+ * (the paper quotes 1/2.41e-4); transforms unitary; channel index increases
+ * with frequency; nd = the smallest even integer >= r*t_d/nchan (Eq. 2 for the
+ * lowest channel at the largest |DM|) with (M - nd) divisible by nint.
+ *
+ * The FFT is an iterative radix-2 Cooley-Tukey transform with each twiddle
+ * evaluated directly from cos/sin (no recurrences).  A naive O(N^2) DFT is
+ * provided for the tests that pin the FFT.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_D 4.148808e3 /* MHz^2 pc^-1 cm^3 s */
+#define ORC_PI 3.14159265358979323846
+
+typedef double complex cplx;
+
+/* Eq. 2: dispersion sweep across [nu_min, nu_max] (MHz) at the given DM. */
+double orc_sweep(double nu_min, double nu_max, double dm)
+{
+    return ORC_D * (1.0 / (nu_min * nu_min) - 1.0 / (nu_max * nu_max)) * dm;
+}
+
+/* Centre frequency (MHz) of subband s: the band is contiguous and f_centre is
+ * the centre of the whole band. */
+double orc_subband_centre(int nsub, double f_centre, double bw, int s)
+{
+    return f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
+}
+
+/* Centre frequency (MHz) of channel c of a subband centred on nu_s. */
+double orc_channel_centre(double nu_s, double bw, int nchan, int c)
+{
+    return nu_s - 0.5 * bw + ((double)c + 0.5) * bw / (double)nchan;
+}
+
+/* Overlap rule of Sec. 2: nd = r t_d / nchan with t_d (Eq. 2) for the lowest
+ * channel, at the largest |DM| of the list.  Rounded up to an even integer
+ * and then up until (M - nd) is a multiple of nint.  Returns -1 if no nd < M
+ * exists. */
+int64_t orc_overlap(int nsub, double f_centre, double bw, const double *dm,
+                    int ndm, int nchan, int nint, int64_t nbin)
+{
+    double dmax = 0.0;
+    for (int i = 0; i < ndm; i++)
+        if (fabs(dm[i]) > dmax) dmax = fabs(dm[i]);
+    double nu_s0 = orc_subband_centre(nsub, f_centre, bw, 0);
+    double lo = nu_s0 - 0.5 * bw;
+    double hi = lo + bw / (double)nchan;
+    double td = orc_sweep(lo, hi, dmax);
+    double r = bw * 1e6;
+    double want = r * td / (double)nchan;
+    int64_t nd = (int64_t)ceil(want);
+    if (nd % 2) nd++;
+    int64_t m = nbin / nchan;
+    while (nd < m && (m - nd) % nint != 0) nd += 2;
+    if (nd >= m) return -1;
+    return nd;
+}
+
+/* In-place iterative radix-2 FFT, unnormalised, kernel exp(sign*2*pi*i*nk/n). */
+void orc_fft(cplx *x, int64_t n, int sign)
+{
+    for (int64_t i = 1, j = 0; i < n; i++) {
+        int64_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            cplx t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    for (int64_t len = 2; len <= n; len <<= 1) {
+        int64_t h = len >> 1;
+        for (int64_t k = 0; k < h; k++) {
+            double ang = (double)sign * 2.0 * ORC_PI * (double)k / (double)len;
+            cplx w = cos(ang) + I * sin(ang);
+            for (int64_t i = 0; i < n; i += len) {
+                cplx u = x[i + k];
+                cplx v = x[i + k + h] * w;
+                x[i + k] = u + v;
+                x[i + k + h] = u - v;
+            }
+        }
+    }
+}
+
+/* Naive O(n^2) DFT, unnormalised: y[k] = sum_n x[n] exp(sign*2*pi*i*n*k/n). */
+void orc_dft(const cplx *x, cplx *y, int64_t n, int sign)
+{
+    for (int64_t k = 0; k < n; k++) {
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            int64_t p = (j * k) % n; /* exact reduction of the angle */
+            double ang = (double)sign * 2.0 * ORC_PI * (double)p / (double)n;
+            acc += x[j] * (cos(ang) + I * sin(ang));
+        }
+        y[k] = acc;
+    }
+}
+
+/* Forward spectrum of one segment (step 2): unitary DFT_N with halves swapped
+ * so that output bin i has frequency offset (i - N/2) * bw / N. */
+static void spectrum(const cplx *x, cplx *xs, cplx *tmp, int64_t n)
+{
+    memcpy(tmp, x, sizeof(cplx) * (size_t)n);
+    orc_fft(tmp, n, -1);
+    double sc = 1.0 / sqrt((double)n);
+    for (int64_t i = 0; i < n; i++) xs[i] = tmp[(i + n / 2) % n] * sc;
+}
+
+/* Steps 3-4 for one channel: chirp multiply, swap halves back, unitary inverse
+ * DFT_M.  xs: the swapped forward spectrum of the segment (length N). */
+static void channel_series(const cplx *xs, int64_t n, int nchan, int c,
+                           double nu_c, double bw, double dm, cplx *y, cplx *w)
+{
+    int64_t m = n / nchan;
+    for (int64_t j = 0; j < m; j++) {
+        double nu = ((double)j - 0.5 * (double)m) * bw / (double)n;
+        double phi = 1e6 * ORC_D * dm * nu * nu / (nu_c * nu_c * (nu_c + nu));
+        cplx h = cos(2.0 * ORC_PI * phi) - I * sin(2.0 * ORC_PI * phi); /* exp(-2 pi i phi) */
+        y[j] = xs[(int64_t)c * m + j] * h;
+    }
+    for (int64_t j = 0; j < m; j++) w[j] = y[(j + m / 2) % m];
+    orc_fft(w, m, +1);
+    double sc = 1.0 / sqrt((double)m);
+    for (int64_t j = 0; j < m; j++) y[j] = w[j] * sc;
+}
+
+/* Complex channelised, dedispersed time series of ONE polarisation of ONE
+ * segment, before any samples are discarded (steps 2-4).
+ * x: N complex samples; y: [nchan][M] complex output. */
+void orc_segment_channels(const cplx *x, int64_t n, int nchan, double nu_s,
+                          double bw, double dm, cplx *y)
+{
+    int64_t m = n / nchan;
+    cplx *xs = malloc(sizeof(cplx) * (size_t)n);
+    cplx *tmp = malloc(sizeof(cplx) * (size_t)n);
+    spectrum(x, xs, tmp, n);
+    for (int c = 0; c < nchan; c++) {
+        double nu_c = orc_channel_centre(nu_s, bw, nchan, c);
+        channel_series(xs, n, nchan, c, nu_c, bw, dm, y + (int64_t)c * m, tmp);
+    }
+    free(xs);
+    free(tmp);
+}
+
+/* Plan quantities (overlap-save segment grid). Returns 0 on success. */
+int orc_grid(int64_t nsamp, int64_t nbin, int nchan, int64_t nd, int nint,
+             int64_t *nvalid, int64_t *nseg, int64_t *nout)
+{
+    int64_t m = nbin / nchan;
+    int64_t s = nbin - nd * nchan;
+    if (s <= 0 || nsamp < nbin || (m - nd) % nint != 0) return -1;
+    *nvalid = s;
+    *nseg = (nsamp - nbin) / s + 1;
+    *nout = *nseg * (m - nd) / nint;
+    return 0;
+}
+
+/* Filterbank rows of one (subband s, segment k) for the DM trials listed in
+ * dm_idx.  in: float32 [nsub][nsamp][4] = (Xre, Xim, Yre, Yim) per sample.
+ * out: double [ndm_total][nsub*nchan][nout]; only the samples of segment k
+ * in rows of subband s and the listed DMs are written. */
+static void segment_rows(const float *in, int nsub, int64_t nsamp, double f_centre,
+                         double bw, const double *dm, int ndm_total,
+                         const int *dm_idx, int ndm_sel, int nchan, int nint,
+                         int64_t nbin, int64_t nd, int s, int64_t k, double *out,
+                         int64_t nout)
+{
+    int64_t m = nbin / nchan;
+    int64_t sv = nbin - nd * nchan;
+    int64_t l = (m - nd) / nint;
+    double nu_s = orc_subband_centre(nsub, f_centre, bw, s);
+    cplx *x = malloc(sizeof(cplx) * (size_t)nbin);
+    cplx *xs[2];
+    cplx *tmp = malloc(sizeof(cplx) * (size_t)nbin);
+    cplx *y = malloc(sizeof(cplx) * (size_t)m);
+    double *pw = malloc(sizeof(double) * (size_t)m);
+    for (int p = 0; p < 2; p++) {
+        xs[p] = malloc(sizeof(cplx) * (size_t)nbin);
+        const float *src = in + ((size_t)s * (size_t)nsamp + (size_t)(k * sv)) * 4;
+        for (int64_t i = 0; i < nbin; i++)
+            x[i] = (double)src[i * 4 + 2 * p] + I * (double)src[i * 4 + 2 * p + 1];
+        spectrum(x, xs[p], tmp, nbin);
+    }
+    (void)ndm_total;
+    for (int q = 0; q < ndm_sel; q++) {
+        int idm = dm_idx[q];
+        for (int c = 0; c < nchan; c++) {
+            double nu_c = orc_channel_centre(nu_s, bw, nchan, c);
+            for (int64_t i = 0; i < m; i++) pw[i] = 0.0;
+            for (int p = 0; p < 2; p++) {
+                channel_series(xs[p], nbin, nchan, c, nu_c, bw, dm[idm], y, tmp);
+                for (int64_t i = 0; i < m; i++) {
+                    double re = creal(y[i]), im = cimag(y[i]);
+                    pw[i] += re * re + im * im;
+                }
+            }
+            double *row = out + ((size_t)idm * (size_t)nsub * (size_t)nchan +
+                                 (size_t)s * (size_t)nchan + (size_t)c) * (size_t)nout;
+            for (int64_t u = 0; u < l; u++) {
+                double acc = 0.0;
+                for (int qq = 0; qq < nint; qq++) acc += pw[nd / 2 + u * nint + qq];
+                row[k * l + u] = acc;
+            }
+        }
+    }
+    for (int p = 0; p < 2; p++) free(xs[p]);
+    free(x);
+    free(tmp);
+    free(y);
+    free(pw);
+}
+
+/* Whole filterbank: out double [ndm][nsub*nchan][nout]. nthreads <= 0 means
+ * the OpenMP default.  Returns 0 on success, -1 on bad arguments. */
+int orc_filterbank(const float *in, int nsub, int64_t nsamp, double f_centre,
+                   double bw, const double *dm, int ndm, int nchan, int nint,
+                   int64_t nbin, int64_t nd, double *out, int nthreads)
+{
+    int64_t sv, nseg, nout;
+    if (nbin % nchan || orc_grid(nsamp, nbin, nchan, nd, nint, &sv, &nseg, &nout))
+        return -1;
+    int *idx = malloc(sizeof(int) * (size_t)ndm);
+    for (int i = 0; i < ndm; i++) idx[i] = i;
+    int64_t npair = (int64_t)nsub * nseg;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t pr = 0; pr < npair; pr++) {
+        int s = (int)(pr / nseg);
+        int64_t k = pr % nseg;
+        segment_rows(in, nsub, nsamp, f_centre, bw, dm, ndm, idx, ndm, nchan, nint,
+                     nbin, nd, s, k, out, nout);
+    }
+    free(idx);
+    return 0;
+}
+
+/* Sampled tiles: for each tile t, the filterbank samples of segment seg[t] in
+ * the rows of subband sub[t] and DM index dmi[t], written to
+ * out[t][nchan][(M - nd)/nint].  Each tile depends only on its own segment of
+ * input, so this reproduces the corresponding slice of orc_filterbank. */
+int orc_tiles(const float *in, int nsub, int64_t nsamp, double f_centre, double bw,
+              const double *dm, int ndm, int nchan, int nint, int64_t nbin,
+              int64_t nd, int ntile, const int *sub, const int64_t *seg,
+              const int *dmi, double *out, int nthreads)
+{
+    int64_t sv, nseg, nout;
+    if (nbin % nchan || orc_grid(nsamp, nbin, nchan, nd, nint, &sv, &nseg, &nout))
+        return -1;
+    int64_t l = (nbin / nchan - nd) / nint;
+    for (int t = 0; t < ntile; t++)
+        if (sub[t] < 0 || sub[t] >= nsub || seg[t] < 0 || seg[t] >= nseg ||
+            dmi[t] < 0 || dmi[t] >= ndm)
+            return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int t = 0; t < ntile; t++) {
+        /* a private one-subband, one-DM view: rows land in a scratch filterbank
+         * whose time axis is the segment's own l samples */
+        double *scratch = malloc(sizeof(double) * (size_t)nchan * (size_t)l);
+        const float *src = in + (size_t)sub[t] * (size_t)nsamp * 4 +
+                           (size_t)(seg[t] * sv) * 4;
+        segment_rows(src, 1, nbin, orc_subband_centre(nsub, f_centre, bw, sub[t]),
+                     bw, dm + dmi[t], 1, (const int[]){0}, 1, nchan, nint, nbin, nd,
+                     0, 0, scratch, l);
+        memcpy(out + (size_t)t * (size_t)nchan * (size_t)l, scratch,
+               sizeof(double) * (size_t)nchan * (size_t)l);
+        free(scratch);
+    }
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

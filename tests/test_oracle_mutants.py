@@ -1,0 +1,82 @@
+"""Planted mistakes: each mutant of the oracle must fail at least one pin.
+
+The mutants are textual edits of a COPY of oracle/cdmt_oracle.c, compiled into
+a temporary directory on the CPU; the oracle itself is never modified.  Every
+edit is a plausible slip (a flipped sign, a dropped term, a wrong index or
+centre); the pins in test_oracle_pins.py must reject each one.
+"""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+import test_oracle_pins as pins
+
+ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+
+# (name, original text, replacement, occurrence index or None for all)
+MUTANTS = [
+    ("chirp_sign", "- I * sin(2.0 * ORC_PI * phi)", "+ I * sin(2.0 * ORC_PI * phi)", None),
+    ("subband_not_channel_centre", "double nu_c = orc_channel_centre(nu_s, bw, nchan, c);",
+     "double nu_c = nu_s;", None),
+    ("channel_centre_half_off", "((double)c + 0.5) * bw", "((double)c) * bw", None),
+    ("no_forward_swap", "xs[i] = tmp[(i + n / 2) % n] * sc;", "xs[i] = tmp[i] * sc;", None),
+    ("forward_sign", "orc_fft(tmp, n, -1);", "orc_fft(tmp, n, +1);", None),
+    ("fft_twiddle_sign", "double ang = (double)sign * 2.0 * ORC_PI * (double)k / (double)len;",
+     "double ang = -(double)sign * 2.0 * ORC_PI * (double)k / (double)len;", None),
+    ("inverse_norm", "double sc = 1.0 / sqrt((double)m);", "double sc = 1.0 / (double)m;", None),
+    ("bin_grid_half_off", "((double)j - 0.5 * (double)m) * bw", "((double)j - 0.5 * (double)m + 0.5) * bw", None),
+    ("linear_not_quadratic", "dm * nu * nu /", "dm * nu /", None),
+    ("no_unpad_offset", "pw[nd / 2 + u * nint + qq]", "pw[u * nint + qq]", None),
+    ("one_pol_detected", "for (int p = 0; p < 2; p++) {\n                channel_series",
+     "for (int p = 0; p < 1; p++) {\n                channel_series", None),
+    ("short_integration", "for (int qq = 0; qq < nint; qq++)", "for (int qq = 0; qq < nint - 1; qq++)", None),
+    ("eq2_reversed", "(1.0 / (nu_min * nu_min) - 1.0 / (nu_max * nu_max))",
+     "(1.0 / (nu_max * nu_max) - 1.0 / (nu_min * nu_min))", None),
+    ("overlap_uses_top_channel", "double lo = nu_s0 - 0.5 * bw;", "double lo = nu_s0 + 0.5 * bw - bw / (double)nchan;",
+     None),
+    ("segment_stride_wrong", "(size_t)(k * sv)) * 4;", "(size_t)(k * nbin)) * 4;", None),
+]
+
+PIN_CALLS = [
+    lambda o: pins.test_fft_matches_naive_dft(o, 16, -1),
+    lambda o: pins.test_fft_matches_naive_dft(o, 16, +1),
+    lambda o: pins.test_eq2_worked_values(o),
+    lambda o: pins.test_lofar_channelisation_and_volume(o),
+    lambda o: pins.test_tone_at_channel_centre_is_dm_invariant(o, 3),
+    lambda o: pins.test_impulse_lands_in_one_sample_per_channel(o),
+    lambda o: pins.test_parseval_per_segment(o),
+    lambda o: pins.test_physical_impulse_recovered_at_true_dm(o),
+    lambda o: pins.test_brute_force_dense_matrices(o),
+    lambda o: pins.test_noise_mean_and_variance(o),
+    lambda o: pins.test_overlap_rule_values(o),
+    lambda o: pins.test_overlap_covers_every_channel_and_is_minimal(o),
+]
+
+
+def _load_mutant(tmp_path, name, old, new):
+    src = open(os.path.join(ORACLE_DIR, "cdmt_oracle.c")).read()
+    assert old in src, f"mutation anchor for {name} not found"
+    d = tmp_path / f"oracle_{name}"
+    d.mkdir()
+    shutil.copy(os.path.join(ORACLE_DIR, "__init__.py"), d / "__init__.py")
+    (d / "cdmt_oracle.c").write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location(f"oracle_{name}", d / "__init__.py",
+                                                  submodule_search_locations=[str(d)])
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    return mod
+
+
+@pytest.mark.parametrize("name,old,new,occ", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new, occ):
+    mod = _load_mutant(tmp_path, name, old, new)
+    caught = []
+    for i, call in enumerate(PIN_CALLS):
+        try:
+            call(mod)
+        except (AssertionError, ValueError, IndexError):
+            caught.append(i)
+    assert caught, f"mutant {name} passed every pin"

@@ -1,0 +1,320 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (golden files under tests/golden/), closed forms derived from
+Eq. 1 and the unitary transforms, an independent library FFT, a brute-force
+dense-matrix evaluation on tiny inputs, and the physics of a pulse dispersed
+with the subband-wide transfer function.  No GPU is needed.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BW = 0.1953125
+D = 4.148808e3
+
+
+def _read_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------- FFT
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64, 128, 256])
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_fft_matches_naive_dft(orc, n, sign):
+    g = np.random.default_rng(n)
+    x = g.standard_normal(n) + 1j * g.standard_normal(n)
+    a, b = orc.fft(x, sign), orc.dft(x, sign)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.sqrt(n) * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("n", [2 ** 10, 2 ** 14, 2 ** 16])
+def test_fft_matches_numpy(orc, n):
+    g = np.random.default_rng(n)
+    x = g.standard_normal(n) + 1j * g.standard_normal(n)
+    assert np.allclose(orc.fft(x, -1), np.fft.fft(x), rtol=0, atol=1e-10 * np.sqrt(n))
+    assert np.allclose(orc.fft(x, +1), np.fft.ifft(x) * n, rtol=0, atol=1e-10 * np.sqrt(n))
+
+
+def test_naive_dft_on_unit_vectors(orc):
+    # the DFT of e_p is the p-th column of the DFT matrix: exp(-2 pi i p k / n)
+    n = 12
+    for p in range(n):
+        e = np.zeros(n, complex)
+        e[p] = 1.0
+        k = np.arange(n)
+        assert np.allclose(orc.dft(e, -1), np.cos(2 * np.pi * p * k / n) - 1j * np.sin(2 * np.pi * p * k / n),
+                           atol=1e-13)
+
+
+# ------------------------------------------------------- printed numbers
+
+
+def test_eq2_worked_values(orc):
+    for nu, dnu, dm, td_ms, dec in _read_table("eq2_worked_values.txt"):
+        nu, dnu, dm, td_ms = float(nu), float(dnu), float(dm), float(td_ms)
+        got = orc.sweep(nu - dnu / 2, nu + dnu / 2, dm) * 1e3
+        assert round(got, int(dec)) == td_ms, (dm, got)
+
+
+def test_lofar_channelisation_and_volume(orc):
+    t = {r[0]: r[1] for r in _read_table("lofar_setup.txt")[1:]}
+    bw, nch = float(t["subband_mhz"]), int(t["nchan"])
+    nu_s = 135.0
+    c0, c1 = orc.channel_centre(nu_s, bw, nch, 0), orc.channel_centre(nu_s, bw, nch, 1)
+    assert round((c1 - c0) * 1e3, 2) == float(t["chan_khz_printed"])
+    assert round(nch / (bw * 1e6) * 1e6, 2) == float(t["tsamp_us_printed"])
+    assert int(t["nbin"]) // nch == int(t["mbin"])
+    nsamp = int(float(t["seconds_perf"]) * bw * 1e6)
+    _, _, nout = orc.grid(nsamp, int(t["nbin"]), nch, int(t["nd"]), 1)
+    gib = nout * nch * int(t["nsub_perf"]) / 2 ** 30
+    assert round(gib, 1) == float(t["out_gib_per_dm"]), gib
+
+
+def test_paper_overlap_covers_rule(orc):
+    # Sec. 5: N_bin 65536, n_d 2048, n_c 8 for subbands 114.93-116.88 MHz up to DM 80.
+    # The rule's n_d (lowest channel, Eq. 2) must not exceed the n_d the paper used.
+    nd = orc.overlap(10, (114.93 + 116.88) / 2, BW, [80.0], 8, 1, 65536)
+    assert 0 < nd <= 2048
+
+
+# ------------------------------------------------ closed forms from Eq. 1
+
+
+def _fb(orc, x, dms, nchan, nint, nbin, nd, fc=135.0):
+    return orc.filterbank(x, fc, BW, dms, nchan, nint, nbin, nd)
+
+
+@pytest.mark.parametrize("c", [0, 3, 5, 7])
+def test_tone_at_channel_centre_is_dm_invariant(orc, c):
+    # A tone at exactly nu_c sits on bin j = M/2 of channel c, where Eq. 1 is 1 at
+    # every DM; unitary transforms give |y|^2 = n_c |A|^2 per polarisation.
+    nchan, nint, nbin, nd = 8, 4, 1024, 16
+    m = nbin // nchan
+    off = (c * m + m // 2 - nbin // 2) * BW / nbin
+    ax, ay = 0.7 - 0.2j, 0.3 + 0.4j
+    x = synth.tone(3 * nbin, off, BW, ax, ay)
+    fb = _fb(orc, x, [0.0, 7.3, 50.0], nchan, nint, nbin, nd)
+    want = nint * nchan * (abs(ax) ** 2 + abs(ay) ** 2)
+    # the voltages are float32, so the tone carries ~1e-8 relative rounding noise
+    assert np.allclose(fb[:, c, :], want, rtol=1e-6, atol=0)
+    others = np.delete(fb, c, axis=1)
+    assert np.max(np.abs(others)) < 1e-6 * want
+
+
+def test_impulse_lands_in_one_sample_per_channel(orc):
+    # An impulse A at input n0 = k S + n_c m0 (inside segment k's kept region) at
+    # DM 0 gives |y|^2 = |A|^2 / n_c in every channel at output m0 - nd/2 of that
+    # segment, and zero elsewhere.
+    nchan, nint, nbin, nd = 8, 1, 512, 8
+    m = nbin // nchan
+    s_valid = nbin - nd * nchan
+    x = np.zeros((1, 3 * nbin, 4), np.float32)
+    k, m0 = 1, 20
+    n0 = k * s_valid + nchan * m0
+    x[0, n0, 0], x[0, n0, 1] = 1.5, -0.5
+    fb = _fb(orc, x, [0.0], nchan, nint, nbin, nd)[0]
+    t = k * (m - nd) + m0 - nd // 2
+    want = (1.5 ** 2 + 0.5 ** 2) / nchan
+    assert np.allclose(fb[:, t], want, rtol=1e-12)
+    fb[:, t] = 0
+    assert np.max(np.abs(fb)) < 1e-12
+    # moving the impulse by n_c input samples moves the output by exactly one sample
+    x2 = np.zeros_like(x)
+    x2[0, n0 + nchan, 0] = 1.0
+    fb2 = _fb(orc, x2, [0.0], nchan, nint, nbin, nd)[0]
+    assert np.all(np.argmax(fb2, axis=1) == t + 1)
+
+
+def test_parseval_per_segment(orc):
+    # |H| = 1 and both transforms are unitary, so energy is conserved before the
+    # overlap is discarded, at any DM.
+    g = np.random.default_rng(5)
+    n, nchan = 4096, 16
+    xx = g.standard_normal(n) + 1j * g.standard_normal(n)
+    for dm in (0.0, 30.0):
+        y = orc.segment_channels(xx, nchan, 120.0, BW, dm)
+        assert np.isclose(np.sum(np.abs(y) ** 2), np.sum(np.abs(xx) ** 2), rtol=1e-12)
+
+
+def test_channel_chirp_inverts_in_segment_dispersion(orc):
+    # Disperse one segment's impulse by the inverse of the dedispersion chirp of
+    # each channel (the oracle-internal closed form) and dedisperse at DM_true:
+    # the result equals the undispersed impulse; other trials do not.
+    nchan, n = 8, 2048
+    m = n // nchan
+    nu_s, dm_true = 120.0, 40.0
+    x = np.zeros(n, complex)
+    x[nchan * 100] = 1.0
+    ref = orc.segment_channels(x, nchan, nu_s, BW, 0.0)
+    X = np.fft.fftshift(np.fft.fft(x))
+    nu = (np.arange(m) - m / 2) * BW / n
+    for c in range(nchan):
+        nuc = nu_s - BW / 2 + (c + 0.5) * BW / nchan
+        X[c * m:(c + 1) * m] *= np.exp(2j * np.pi * 1e6 * D * dm_true * nu ** 2 / (nuc ** 2 * (nuc + nu)))
+    xd = np.fft.ifft(np.fft.ifftshift(X))
+    y = orc.segment_channels(xd, nchan, nu_s, BW, dm_true)
+    assert np.max(np.abs(y - ref)) < 1e-10
+    y2 = orc.segment_channels(xd, nchan, nu_s, BW, dm_true - 10.0)
+    assert np.max(np.abs(np.abs(y2) - np.abs(ref))) > 0.1
+
+
+def _physical_impulse(nsamp, fc, dm, t0_samp):
+    # a one-sample impulse at time t0 (subband centre), dispersed with the
+    # subband-wide transfer function: the independent physical forward model
+    x = np.zeros(nsamp, complex)
+    x[t0_samp] = 1.0
+    f = np.fft.fftfreq(nsamp, d=1.0 / (BW * 1e6)) / 1e6
+    h = np.exp(2j * np.pi * 1e6 * D * dm * f ** 2 / (fc ** 2 * (fc + f)))
+    xd = np.fft.ifft(np.fft.fft(x) * h)
+    out = np.zeros((1, nsamp, 4), np.float32)
+    out[0, :, 0], out[0, :, 1] = xd.real, xd.imag
+    return out
+
+
+def test_physical_impulse_recovered_at_true_dm(orc):
+    # At the true DM, channel c holds the pulse at the closed-form inter-channel
+    # delay D DM (nu_c^-2 - nu_s^-2) (Eq. 1 per channel minus Eq. 1 per subband is
+    # a pure delay), concentrated in the two nearest samples; at the DM = 0 trial
+    # the pulse is smeared and arrives earlier in higher channels.
+    fc, dm_true, nchan, nbin, nd = 135.0, 10.0, 8, 1 << 14, 32
+    nsamp = 1 << 15
+    r = BW * 1e6
+    t0 = 20000
+    x = _physical_impulse(nsamp, fc, dm_true, t0)
+    dms = [0.0, 5.0, 10.0, 15.0]
+    fb = _fb(orc, x, dms, nchan, 1, nbin, nd, fc)
+    m = nbin // nchan
+    sv = nbin - nd * nchan
+    for c in range(nchan):
+        nuc = fc - BW / 2 + (c + 0.5) * BW / nchan
+        delay = D * dm_true * (1 / nuc ** 2 - 1 / fc ** 2) * r / nchan   # output samples
+        t_exp = t0 / nchan + delay - nd / 2     # global output index (segments tile seamlessly)
+        row = fb[2, c]
+        e = np.sum(row)
+        i0 = int(np.floor(t_exp))
+        frac = (row[i0] + row[i0 + 1]) / e
+        assert abs(np.argmax(row) - t_exp) <= 1.0, (c, np.argmax(row), t_exp)
+        assert frac >= 0.8, (c, frac)
+        for idm in (0, 1, 3):
+            other = fb[idm, c]
+            j = int(np.argmax(other))
+            assert (other[j] + max(other[j - 1], other[j + 1])) / np.sum(other) < 0.6
+    # sign pin: at DM 0 the dispersed pulse's centroid is earlier in higher channels
+    cen = [np.sum(np.arange(fb.shape[2]) * fb[0, c]) / np.sum(fb[0, c]) for c in range(nchan)]
+    assert np.all(np.diff(cen) < 0)
+    assert sv * 2 <= nsamp  # the pulse sits inside the segment grid
+
+
+def test_brute_force_dense_matrices(orc):
+    # Tiny sizes: the whole filterbank written with dense DFT matrices and
+    # explicit loops (no FFT), nsamp 256, N 64, n_c 4, nd 4, 2 DMs.
+    g = np.random.default_rng(11)
+    nsamp, nbin, nchan, nd, nint = 256, 64, 4, 4, 2
+    fc = 60.0
+    dms = [3.0, 17.0]
+    x = (g.standard_normal((1, nsamp, 4)) * 0.7).astype(np.float32)
+    fb = _fb(orc, x, dms, nchan, nint, nbin, nd, fc)
+    m = nbin // nchan
+    sv = nbin - nd * nchan
+    nseg = (nsamp - nbin) // sv + 1
+    n = np.arange(nbin)
+    FN = np.exp(-2j * np.pi * np.outer(n, n) / nbin) / np.sqrt(nbin)
+    jj = np.arange(m)
+    FMi = np.exp(2j * np.pi * np.outer(jj, jj) / m) / np.sqrt(m)
+    L = (m - nd) // nint
+    want = np.zeros((len(dms), nchan, nseg * L))
+    for k in range(nseg):
+        pw = np.zeros((len(dms), nchan, m))
+        for p in range(2):
+            seg = x[0, k * sv:k * sv + nbin, 2 * p] + 1j * x[0, k * sv:k * sv + nbin, 2 * p + 1]
+            spec = FN @ seg.astype(complex)
+            spec = np.concatenate([spec[nbin // 2:], spec[:nbin // 2]])
+            for a, dm in enumerate(dms):
+                for c in range(nchan):
+                    nuc = fc - BW / 2 + (c + 0.5) * BW / nchan
+                    nu = (jj - m / 2) * BW / nbin
+                    ch = spec[c * m:(c + 1) * m] * np.exp(-2j * np.pi * 1e6 * D * dm * nu ** 2 / (nuc ** 2 * (nuc + nu)))
+                    ch = np.concatenate([ch[m // 2:], ch[:m // 2]])
+                    pw[a, c] += np.abs(FMi @ ch) ** 2
+        kept = pw[:, :, nd // 2:m - nd // 2]
+        want[:, :, k * L:(k + 1) * L] = kept.reshape(len(dms), nchan, L, nint).sum(-1)
+    assert np.allclose(fb, want, rtol=1e-11, atol=1e-12)
+
+
+def test_noise_mean_and_variance(orc):
+    # Complex white noise with E|x|^2 = sigma2 per pol stays white under unitary
+    # maps, so each output is Gamma(2 nint, sigma2): mean 2 sigma2 nint, variance
+    # 2 nint sigma2^2.
+    sigma2, nint, nchan, nbin = 1.0, 4, 8, 4096
+    x = synth.noise(7, 1, 1 << 16, sigma2)
+    fb = _fb(orc, x, [0.0, 20.0], nchan, nint, nbin, 16)
+    v = fb.ravel()
+    mu, se = v.mean(), v.std() / np.sqrt(v.size)
+    assert abs(mu - 2 * sigma2 * nint) < 3 * se + 0.0
+    var_want = 2 * nint * sigma2 ** 2
+    # standard error of a sample variance for a Gamma(k) variable: var * sqrt((2 + 6/k)/n)
+    se_var = var_want * np.sqrt((2 + 6 / (2 * nint)) / v.size)
+    assert abs(v.var() - var_want) < 4 * se_var
+
+
+def test_tiles_reproduce_filterbank(orc):
+    w = synth.tiny()
+    x = w.voltages()[:, :1 << 16]
+    nd = 32
+    fb = orc.filterbank(x, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin, nd)
+    sub, seg, dmi = [0, 0, 0], [0, 2, 3], [1, 3, 0]
+    t = orc.tiles(x, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin, nd, sub, seg, dmi)
+    L = (w.nbin // w.nchan - nd) // w.nint
+    for i in range(3):
+        assert np.array_equal(t[i], fb[dmi[i], :, seg[i] * L:(seg[i] + 1) * L])
+
+
+def test_overlap_rule_values(orc):
+    # tiny workload: lowest channel 134.9023-134.9268 MHz, DM 15 -> r t_d / n_c = 30.2 -> 32
+    assert orc.overlap(1, 135.0, BW, [0, 5, 10, 15], 8, 4, 1 << 14) == 32
+    # 64 subbands 128.75-141.25 MHz, DM 63.5, n_c 16 -> 36.8 -> 38, (4096-38) % 8 != 0 -> 40
+    assert orc.overlap(64, 135.0, BW, [0.5 * i for i in range(128)], 16, 8, 1 << 16) == 40
+    # no dispersion at all needs no overlap
+    assert orc.overlap(1, 135.0, BW, [0.0], 8, 4, 1 << 14) == 0
+
+
+def test_grid_rejects_bad_shapes(orc):
+    with pytest.raises(ValueError):
+        orc.grid(100, 1024, 8, 8, 4)        # nsamp < N
+    with pytest.raises(ValueError):
+        orc.grid(4096, 1024, 8, 128, 4)     # S <= 0
+    assert orc.grid(4096, 1024, 8, 8, 4) == (960, 4, 4 * 120 // 4)
+
+
+def test_overlap_covers_every_channel_and_is_minimal(orc):
+    # Sec. 2: the overlap must hold the chirp of the channel with the largest sweep
+    # (the lowest one).  Invariant: nd >= r t_d(c) / n_c for every channel of every
+    # subband (t_d from Eq. 2, pinned above), and nd - 2 fails that or the
+    # divisibility of (M - nd) by nint.  A low, wide band makes channels differ.
+    nsub, fc, nchan, nint, nbin = 4, 60.0, 4, 2, 1 << 16
+    dms = [0.0, 37.0, 100.0]
+    nd = orc.overlap(nsub, fc, BW, dms, nchan, nint, nbin)
+    r = BW * 1e6
+    need = 0.0
+    for s in range(nsub):
+        nus = orc.subband_centre(nsub, fc, BW, s)
+        for c in range(nchan):
+            nuc = orc.channel_centre(nus, BW, nchan, c)
+            lo, hi = nuc - BW / nchan / 2, nuc + BW / nchan / 2
+            need = max(need, r * orc.sweep(lo, hi, max(dms)) / nchan)
+    m = nbin // nchan
+    assert nd >= need and nd % 2 == 0 and (m - nd) % nint == 0
+    assert nd - 2 < need or (m - nd + 2) % nint != 0
