@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Throughput of the coherent-dedispersion hot path on GB300.
+
+One step = the whole filterbank of the 64-subband LOFAR-shaped workload
+(64 x 195.3125 kHz subbands 128.75-141.25 MHz, 2^22 complex dual-pol samples
+each with 5 dispersed pulses, N_bin 2^16, 128 DM trials 0..63.5, 16 channels,
+nint 8): forward FFTs of every overlap-save segment, then chirp, backward FFTs,
+detection and integration for every DM.  The metric is DM-trial x input samples
+per second (units = ndm * nsub * nseg * S).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cdmt|reference]
+
+Timing: W untimed steps, then K steps between barrier + synchronize, CUDA
+events on the launching stream, max over ranks.  The inputs (4.3 GB) are larger
+than L2, so no flush is needed between steps.  --impl reference times the FP64
+CPU oracle on a bounded sample of the same workload on the host cores.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial·Gsamples/s on 1 GB300, FP32 vs tensor-core form at stated error"
+UNIT = "DM-trial·Gsamples/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload(name):
+    import synth
+    if name == "lofar64":
+        return synth.lofar64()
+    if name == "lofar8":
+        return synth.lofar64(nsub=8)
+    if name == "tiny":
+        return synth.tiny()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(w, info=None):
+    d = {"workload": w.name, "nsub": w.nsub, "nsamp": w.nsamp, "f_centre_mhz": w.f_centre, "bw_sub_mhz": w.bw,
+         "ndm": len(w.dms), "dm_range": [w.dms[0], w.dms[-1]], "nchan": w.nchan, "nint": w.nint, "nbin": w.nbin,
+         "pulses": len(w.pulses)}
+    if info:
+        d.update({"nd": info["nd"], "nseg": info["nseg"], "nout": info["nout"], "dm_tile": info["dm_tile"]})
+    return d
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 10:
+                    continue
+                if self.bus_id and self.bus_id.lower() not in p[1].lower():
+                    continue
+                rows.append(p)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        busy = [v for v in sm if v > 0.5 * max(sm)] if sm else []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(busy)) if busy else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------- oracle leg
+
+
+def oracle_sample(w, x, nd, n_sub, n_seg, nthreads=0):
+    """Time the FP64 oracle on the first n_sub subbands x n_seg segments x all DMs."""
+    import oracle
+    oracle.build()
+    S = w.nbin - nd * w.nchan
+    span = (n_seg - 1) * S + w.nbin
+    xs = np.ascontiguousarray(x[:n_sub, :span])
+    fc = w.f_centre - 0.5 * (w.nsub - n_sub) * w.bw
+    t0 = time.perf_counter()
+    oracle.filterbank(xs, fc, w.bw, w.dms, w.nchan, w.nint, w.nbin, nd, nthreads)
+    dt = time.perf_counter() - t0
+    units = len(w.dms) * n_sub * n_seg * S
+    return units, dt, oracle.max_threads() if nthreads <= 0 else nthreads
+
+
+def reference_arm(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nd = oracle.overlap(w.nsub, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin)
+    n_sub, n_seg = [int(v) for v in args.cpu_sample.split("x")]
+    log(f"reference arm: FP64 oracle, {n_sub} subbands x {n_seg} segments x {len(w.dms)} DMs per step")
+    x = w.voltages(threads=16)
+    for _ in range(args.warmup):
+        oracle_sample(w, x, nd, n_sub, n_seg)
+    tot_u, tot_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        u, dt, cores = oracle_sample(w, x, nd, n_sub, n_seg)
+        tot_u += u
+        tot_t += dt
+    v = tot_u / tot_t / 1e9
+    sample = f"{n_sub} of {w.nsub} subbands x {n_seg} of the segments x all {len(w.dms)} DMs per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_fp32.cu", "fft_core.cuh"):
+        with open(os.path.join(ROOT, "paper_1607_00909_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per DM-trial x sample of k_dedisperse from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch / units per launch), valid for the kernel
+# source whose hash is recorded; null otherwise.
+NCU_TRAFFIC = {}
+
+
+def gpu_arm(args, w):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1607_00909_gb300 as cdmt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    log(f"rank {rank}: generating {w.name} ...")
+    t0 = time.perf_counter()
+    x = w.voltages(threads=16, beam=rank)
+    log(f"rank {rank}: inputs ready in {time.perf_counter() - t0:.1f}s ({x.nbytes / 1e9:.2f} GB)")
+    plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    info = plan.info
+    xin = torch.from_numpy(x).to(dev)
+    out = torch.empty(plan.out_shape(), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+
+    for _ in range(args.warmup):
+        plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
+    torch.cuda.synchronize(dev)
+    cdmt.cdmt_set_timing(plan.handle, True)
+    cdmt.cdmt_stage_times(plan.handle)
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except AttributeError:
+        pass
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(bus) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    clocks = clk.summary()
+    ms = ev0.elapsed_time(ev1)
+    (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
+    cdmt.cdmt_set_timing(plan.handle, False)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = info["units"]
+    value = world * units * args.steps / (ms_max / 1e3) / 1e9
+    launches_per_step = (fwd_n + dd_n) // max(1, args.steps)
+
+    # ---- roofline of the dominant kernel (dedispersion: chirp, backward FFTs, detect, integrate)
+    nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
+    flops_per_unit = 10.0 * nbin * np.log2(mbin) / info["nvalid"]       # 2 pols x n_c x 5 M log2 M per segment
+    flops_per_launch = flops_per_unit * units
+    dd_avg_s = dd_ms / max(1, dd_n) / 1e3
+    achieved = flops_per_launch / dd_avg_s / 1e12
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    traffic = None
+    tr = NCU_TRAFFIC.get(kernel_source_hash())
+    if tr:
+        traffic = tr * units
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_dedisperse", "kernel_ms_per_launch": dd_avg_s * 1e3,
+                "share_of_step": dd_ms / max(1e-9, dd_ms + fwd_ms),
+                "flops_per_unit": flops_per_unit,
+                "peak_basis": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+
+    # ---- end to end through the host-memory entry point
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(x).pin_memory()
+        hout = torch.empty(plan.out_shape(), dtype=torch.float32, pin_memory=True)
+        plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)   # warm-up (allocates staging)
+        ne = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = time.perf_counter()
+        for _ in range(ne):
+            plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)
+        torch.cuda.synchronize(dev)
+        e_s = time.perf_counter() - e0
+        te = torch.tensor([e_s], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * units * ne / float(te.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
+               "steps": ne, "ms_per_step": float(te.item()) / ne * 1e3}
+        del hin, hout
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_sub, n_seg = [int(v) for v in args.cpu_sample.split("x")]
+        u, dt, cores = oracle_sample(w, x, info["nd"], n_sub, n_seg)
+        cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_sub} of {w.nsub} subbands x {n_seg} of {nseg} segments x all {len(w.dms)} DMs "
+                         f"({u:.3g} units in {dt:.1f} s)"}
+
+    if rank == 0:
+        cfg = describe(w, info)
+        cfg.update({"l2": f"inputs ({x.nbytes / 1e9:.2f} GB) larger than L2; no flush", "precision": "fp32",
+                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches_per_step * args.steps),
+                "stage_ms_per_step": {"forward": fwd_ms / args.steps, "dedisperse": dd_ms / args.steps}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cdmt", choices=["cdmt", "reference"])
+    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("note: fewer than 3 warm-up steps")
+    w = workload(args.workload)
+    if args.impl == "reference":
+        return reference_arm(args, w)
+    return gpu_arm(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * cdmt.h - C ABI of the GB300 coherent-dedispersion library.
+ *
+ * The library computes, on one GPU, the hot path of the convolving synthetic
+ * filterbank with coherent dedispersion to many DM trials described by Bassa,
+ * Pleunis & Hessels (2016, "cdmt"):
+ *   Sec. 2 (Eq. 1, Eq. 2, Fig. 2): overlap-save segments of N_bin input samples,
+ *     a forward FFT of N_bin, per-channel multiplication by the inverse of the
+ *     ISM transfer function of Eq. 1, and n_c backward FFTs of M_bin = N_bin/n_c;
+ *   Sec. 3 (Algorithm 1): swap halves, chirp multiply, backward FFT, transpose,
+ *     unpad (n_d/2 samples per edge) and detect (Stokes I = |X|^2 + |Y|^2);
+ * and it integrates nint consecutive samples into a DM x channel x time
+ * filterbank.
+ *
+ * Conventions shared by every entry point:
+ *  - Frequencies in MHz, DM in pc cm^-3, dispersion constant
+ *    D = 4.148808e3 MHz^2 pc^-1 cm^3 s.  Subband s (0-based) is centred on
+ *    f_centre + (s - (nsub-1)/2) * bw_sub: the band is contiguous and f_centre
+ *    is the centre of the whole band.  Sample rate r = bw_sub * 1e6 complex
+ *    samples per second (Nyquist-sampled complex subbands, Sec. 3).
+ *  - Input layout: [nsub][nsamp] samples, each sample 16 bytes =
+ *    float32 (X re, X im, Y re, Y im) (CDMT_IN_C64), or 4 bytes = int8
+ *    (X re, X im, Y re, Y im) scaled by a per-subband float (CDMT_IN_I8).
+ *  - Output layout: float32 [ndm][nsub * nchan][nout]; channel index
+ *    s * nchan + c increases with frequency; output sample t covers input
+ *    samples starting at (t * nint + nd/2) * nchan.
+ *  - Transforms are unitary (1/sqrt(N) forward, 1/sqrt(M) backward), so complex
+ *    white noise with E|x|^2 = sigma^2 per polarisation gives a mean output of
+ *    2 sigma^2 nint.
+ *  - Every function returns CDMT_OK (0) or a negative status; none aborts.
+ *    The message of the last failure is kept per plan (cdmt_last_error) and,
+ *    for failures before a plan exists, per thread (cdmt_last_error(NULL)).
+ *  - A plan is bound to the CUDA device that was current when it was made and
+ *    must be used from host threads one at a time.
+ */
+#ifndef CDMT_H
+#define CDMT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdmt_plan_s *cdmt_plan_t;
+
+enum cdmt_status {
+    CDMT_OK = 0,
+    CDMT_EINVAL = -1,   /* an argument is out of range or inconsistent */
+    CDMT_ENOMEM = -2,   /* a device or pinned-host allocation failed */
+    CDMT_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    CDMT_ETIMEOUT = -4, /* a bounded device wait expired */
+    CDMT_EBUDGET = -5,  /* the plan would exceed the memory budget it was given */
+    CDMT_ENOTSUP = -6   /* the combination of sizes has no kernel */
+};
+
+enum cdmt_precision {
+    CDMT_PREC_FP32 = 0 /* FFT stages on the FP32 pipes */
+};
+
+enum cdmt_in_dtype {
+    CDMT_IN_C64 = 0, /* 16 bytes per dual-pol sample */
+    CDMT_IN_I8 = 1   /* 4 bytes per dual-pol sample plus a per-subband scale */
+};
+
+/* Optional plan overrides (cdmt_plan_ex).  Zero-initialise, then set fields;
+ * a zero / negative field means "let the planner choose". */
+typedef struct cdmt_opts {
+    int64_t nbin;        /* forward FFT length N_bin (power of two); 0 = choose */
+    int64_t nd;          /* overlap n_d in channel samples; < 0 = rule of Sec. 2 */
+    int32_t dm_tile;     /* DM trials per work item (forward spectrum reuse); 0 = choose */
+    int32_t precision;   /* enum cdmt_precision */
+    int32_t in_dtype;    /* enum cdmt_in_dtype */
+    int32_t reserved0;
+    int64_t seg_chunk;   /* segments per internal chunk (workspace size); 0 = choose */
+    int64_t mem_budget;  /* bytes of device memory the plan may hold; 0 = no limit */
+    int64_t reserved[6];
+} cdmt_opts;
+
+/* Derived sizes of a plan (cdmt_plan_info). */
+typedef struct cdmt_info {
+    int64_t nsamp;        /* input samples per subband */
+    int64_t nbin;         /* N_bin */
+    int64_t mbin;         /* M_bin = N_bin / nchan */
+    int64_t nd;           /* overlap n_d (channel samples) */
+    int64_t nvalid;       /* S = N_bin - nd * nchan valid input samples per segment */
+    int64_t nseg;         /* segments per subband = floor((nsamp - N_bin) / S) + 1 */
+    int64_t nout;         /* output samples per channel = nseg * (M_bin - nd) / nint */
+    int64_t seg_chunk;    /* segments per internal chunk */
+    int64_t workspace_bytes; /* device memory the plan holds */
+    int64_t in_bytes;     /* bytes of one input block */
+    int64_t out_bytes;    /* bytes of one output filterbank */
+    double units;         /* DM-trial x input samples consumed per execute = ndm * nsub * nseg * S */
+    int32_t nsub, nchan, nint, ndm;
+    int32_t dm_tile;      /* DM trials per work item */
+    int32_t uniform_dm;   /* 1 if the DM list is evenly spaced (integer phase accumulator) */
+    int32_t precision, in_dtype;
+    int32_t device;
+    int32_t reserved[7];
+} cdmt_info;
+
+/*
+ * cdmt_plan - validate a problem and prepare everything an execute needs.
+ *
+ * Follows the initialisation of Sec. 3 / Algorithm 1 ("compute transfer
+ * function for DM[idm]"): N_bin and n_d are fixed for all subbands and channels
+ * (Sec. 3), n_d follows Sec. 2 (n_d = r t_d / n_c, t_d of Eq. 2 for the lowest
+ * channel at the largest |DM|; rounded up to an even number with (M - n_d)
+ * divisible by nint), and the per-channel chirp phases of Eq. 1 are computed on
+ * the GPU in FP64 and stored as 32-bit fixed-point phase and phase step per
+ * frequency bin and DM tile.
+ *
+ *   plan          out: the new plan (NULL on failure)
+ *   nsub          number of subbands, >= 1
+ *   nsamp         input samples per subband, >= N_bin
+ *   f_centre_mhz  centre of the whole band (MHz); the lowest channel must be > 0
+ *   bw_sub_mhz    subband width = complex sample rate / 1e6, > 0
+ *   dm_list       host array of ndm trial DMs (copied; any order; any sign)
+ *   ndm           >= 1
+ *   nchan         channels per subband n_c, a power of two 2..32
+ *   nint          output integration factor, >= 1
+ * Errors: CDMT_EINVAL (bad argument, N_bin <= n_d n_c, nsamp < N_bin),
+ *         CDMT_ENOTSUP (M_bin outside 512..4096), CDMT_ENOMEM, CDMT_ECUDA.
+ * Allocates device memory (tables and workspace); the plan owns all of it.
+ */
+int cdmt_plan(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz,
+              double bw_sub_mhz, const double *dm_list, int ndm, int nchan, int nint);
+
+/* cdmt_plan with overrides (opts may be NULL = cdmt_plan).  Parity tests use
+ * opts->nbin and opts->nd to fix the segment grid, since the filterbank of the
+ * brick-wall channeliser depends on N_bin. */
+int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz,
+                 double bw_sub_mhz, const double *dm_list, int ndm, int nchan, int nint,
+                 const cdmt_opts *opts);
+
+/* cdmt_plan_info - copy the derived sizes of a plan into *info (host memory).
+ * Errors: CDMT_EINVAL if plan or info is NULL. */
+int cdmt_plan_info(cdmt_plan_t plan, cdmt_info *info);
+
+/*
+ * cdmt_execute - compute the whole filterbank of one input block.
+ *
+ * Algorithm 1's block loop without disk I/O: forward FFT of every segment of
+ * every subband (Sec. 3 "unpack, segment and pad", "forward FFT", "swap halves
+ * per subband"), then for each DM trial the chirp multiply, backward FFTs,
+ * unpad, detection (Sec. 3) and nint-sample integration.
+ *
+ *   d_in         DEVICE pointer to the input block (layout above), caller-owned,
+ *                16-byte aligned; read only
+ *   d_out        DEVICE pointer to float32 [ndm][nsub*nchan][nout], caller-owned,
+ *                4-byte aligned; fully overwritten
+ *   d_scale      DEVICE pointer to nsub float scales for CDMT_IN_I8 input
+ *                (ignored, may be NULL, for CDMT_IN_C64)
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Asynchronous with respect to the host: returns after enqueueing.  The plan's
+ * workspace is reused by every execute, so executes of ONE plan must not
+ * overlap on different streams.
+ * Errors: CDMT_EINVAL (NULL pointers, misaligned input), CDMT_ECUDA.
+ */
+int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *d_scale,
+                 void *cuda_stream);
+
+/*
+ * cdmt_execute_host - the same computation from and to HOST memory.
+ *
+ * Copies the input block host->device, computes, and copies the filterbank
+ * device->host, pipelining the copies of segment chunks with the compute of
+ * others (Algorithm 1: "copy to device" ... "copy to host").  h_in and h_out
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for full speed;
+ * pageable memory works but the copies are then synchronous.  Blocks until
+ * h_out holds the result.  h_scale is a host array of nsub floats for
+ * CDMT_IN_I8 input.
+ * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_ECUDA.
+ */
+int cdmt_execute_host(cdmt_plan_t plan, const void *h_in, float *h_out, const float *h_scale,
+                      void *cuda_stream);
+
+/* cdmt_set_timing - when on != 0, later executes record CUDA events on their
+ * stream around the forward stage (Sec. 3 "forward FFT" and "swap halves per
+ * subband": two kernels per chunk) and around the dedispersion kernel (chirp
+ * multiply through integration: one kernel per chunk), for cdmt_stage_times.
+ * Off by default; recording costs one event per stage boundary.
+ * Errors: CDMT_EINVAL for a NULL plan. */
+int cdmt_set_timing(cdmt_plan_t plan, int on);
+
+/* cdmt_stage_times - wait for the events recorded since the previous call and
+ * return the summed device time in milliseconds of the forward stage (ms[0])
+ * and of the dedispersion kernel (ms[1]), and the number of kernel launches of
+ * each (launches[0], launches[1]).  ms and launches are host arrays of two
+ * elements (launches may be NULL).  Clears the record.
+ * Errors: CDMT_EINVAL (NULL plan or ms), CDMT_ECUDA. */
+int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
+
+/* cdmt_destroy - free every resource of a plan (NULL is accepted).  Waits for
+ * the plan's device work to finish first. */
+int cdmt_destroy(cdmt_plan_t plan);
+
+/* cdmt_strerror - static text for a status code. */
+const char *cdmt_strerror(int status);
+
+/* cdmt_last_error - message of the last failure on this plan, or, for
+ * plan == NULL, of the last failure on this host thread before a plan existed.
+ * The pointer stays valid until the next call on the same plan / thread. */
+const char *cdmt_last_error(cdmt_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDMT_H */

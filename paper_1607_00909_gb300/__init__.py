@@ -1,0 +1,200 @@
+"""Python binding of libcdmt.so (the C ABI declared in include/cdmt.h).
+
+Argument marshalling only: every step of the coherent-dedispersion path runs in
+the library's CUDA kernels.  Function names mirror the C entry points
+(cdmt_plan, cdmt_plan_ex, cdmt_plan_info, cdmt_execute, cdmt_execute_host,
+cdmt_destroy, cdmt_strerror, cdmt_last_error); :class:`Plan` wraps them.
+Device buffers are passed as raw pointers (for example ``tensor.data_ptr()``
+of a CUDA tensor) and streams as ``cudaStream_t`` integers
+(``torch.cuda.current_stream().cuda_stream``).
+
+Importing this module loads the compiled library and raises if it is missing:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdmt.so")
+
+CDMT_OK, CDMT_EINVAL, CDMT_ENOMEM, CDMT_ECUDA, CDMT_ETIMEOUT, CDMT_EBUDGET, CDMT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+CDMT_PREC_FP32 = 0
+CDMT_IN_C64, CDMT_IN_I8 = 0, 1
+
+
+class cdmt_opts(ctypes.Structure):
+    _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+
+
+class cdmt_info(ctypes.Structure):
+    _fields_ = [("nsamp", ctypes.c_int64), ("nbin", ctypes.c_int64), ("mbin", ctypes.c_int64),
+                ("nd", ctypes.c_int64), ("nvalid", ctypes.c_int64), ("nseg", ctypes.c_int64),
+                ("nout", ctypes.c_int64), ("seg_chunk", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("units", ctypes.c_double),
+                ("nsub", ctypes.c_int32), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
+                ("ndm", ctypes.c_int32), ("dm_tile", ctypes.c_int32), ("uniform_dm", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class CdmtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} [status {status}]")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1607_00909_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.cdmt_plan.argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, dp,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.cdmt_plan_ex.argtypes = lib.cdmt_plan.argtypes + [ctypes.POINTER(cdmt_opts)]
+    lib.cdmt_plan_info.argtypes = [P, ctypes.POINTER(cdmt_info)]
+    lib.cdmt_execute.argtypes = [P, P, P, P, P]
+    lib.cdmt_execute_host.argtypes = [P, P, P, P, P]
+    lib.cdmt_destroy.argtypes = [P]
+    lib.cdmt_set_timing.argtypes = [P, ctypes.c_int]
+    lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.cdmt_strerror.argtypes = [ctypes.c_int]
+    lib.cdmt_strerror.restype = ctypes.c_char_p
+    lib.cdmt_last_error.argtypes = [P]
+    lib.cdmt_last_error.restype = ctypes.c_char_p
+    for f in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
+              "cdmt_set_timing", "cdmt_stage_times"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
+            "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times")
+
+
+def lib():
+    return _lib
+
+
+def cdmt_strerror(status: int) -> str:
+    return _lib.cdmt_strerror(status).decode()
+
+
+def cdmt_last_error(plan=None) -> str:
+    return _lib.cdmt_last_error(plan).decode()
+
+
+def _check(rc: int, plan=None):
+    if rc != CDMT_OK:
+        raise CdmtError(rc, f"{cdmt_strerror(rc)}: {cdmt_last_error(plan)}")
+
+
+def cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, opts: cdmt_opts | None = None):
+    """Create a plan; returns the opaque handle (int)."""
+    dms = (ctypes.c_double * len(dm_list))(*[float(d) for d in dm_list])
+    h = ctypes.c_void_p()
+    rc = _lib.cdmt_plan_ex(ctypes.byref(h), int(nsub), int(nsamp), float(f_centre), float(bw_sub), dms,
+                           len(dm_list), int(nchan), int(nint), ctypes.byref(opts) if opts is not None else None)
+    _check(rc)
+    return h.value
+
+
+def cdmt_plan(nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint):
+    return cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, None)
+
+
+def cdmt_plan_info(plan) -> dict:
+    info = cdmt_info()
+    _check(_lib.cdmt_plan_info(plan, ctypes.byref(info)), plan)
+    return {name: (list(getattr(info, name)) if name == "reserved" else getattr(info, name))
+            for name, _ in cdmt_info._fields_ if name != "reserved"}
+
+
+def cdmt_execute(plan, d_in: int, d_out: int, d_scale: int = 0, stream: int = 0):
+    _check(_lib.cdmt_execute(plan, d_in, d_out, d_scale or None, stream or None), plan)
+
+
+def cdmt_execute_host(plan, h_in: int, h_out: int, h_scale: int = 0, stream: int = 0):
+    _check(_lib.cdmt_execute_host(plan, h_in, h_out, h_scale or None, stream or None), plan)
+
+
+def cdmt_destroy(plan):
+    _check(_lib.cdmt_destroy(plan))
+
+
+def cdmt_set_timing(plan, on: bool):
+    _check(_lib.cdmt_set_timing(plan, 1 if on else 0), plan)
+
+
+def cdmt_stage_times(plan):
+    """((forward_ms, dedisperse_ms), (forward_launches, dedisperse_launches))
+    summed since the previous call."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_int64 * 2)()
+    _check(_lib.cdmt_stage_times(plan, ms, n), plan)
+    return (ms[0], ms[1]), (n[0], n[1])
+
+
+class Plan:
+    """Owning wrapper of a cdmt plan."""
+
+    def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
+                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64):
+        o = cdmt_opts()
+        o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
+        o.precision, o.in_dtype = precision, in_dtype
+        self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
+        self.info = cdmt_plan_info(self.handle)
+
+    def execute(self, d_in: int, d_out: int, d_scale: int = 0, stream: int = 0):
+        cdmt_execute(self.handle, d_in, d_out, d_scale, stream)
+
+    def execute_host(self, h_in: int, h_out: int, h_scale: int = 0, stream: int = 0):
+        cdmt_execute_host(self.handle, h_in, h_out, h_scale, stream)
+
+    def out_shape(self):
+        i = self.info
+        return (i["ndm"], i["nsub"] * i["nchan"], i["nout"])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cdmt_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run(plan: Plan, x, out=None, stream=None):
+    """Convenience for torch CUDA tensors: x float32 [nsub][nsamp][4] on the
+    plan's device, out float32 [ndm][nsub*nchan][nout] (allocated if None).
+    Enqueues on `stream` (default: torch's current stream) and returns out."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous float32 CUDA tensor [nsub][nsamp][4]")
+    i = plan.info
+    if tuple(x.shape) != (i["nsub"], i["nsamp"], 4):
+        raise ValueError(f"x has shape {tuple(x.shape)}, plan wants {(i['nsub'], i['nsamp'], 4)}")
+    if out is None:
+        out = torch.empty(plan.out_shape(), dtype=torch.float32, device=x.device)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape) == plan.out_shape()):
+        raise ValueError("out must be a contiguous float32 CUDA tensor of the plan's output shape")
+    st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+    plan.execute(x.data_ptr(), out.data_ptr(), 0, st)
+    return out

@@ -1,0 +1,617 @@
+// Host side of the C ABI declared in include/cdmt.h: validation, planning
+// (Sec. 2 overlap rule, Sec. 3 fixed N_bin / n_d), FP64 table construction on
+// the device (Algorithm 1: "compute transfer function for DM[idm]"), and the
+// execute paths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cdmt.h"
+#include "cdmt_internal.h"
+
+using namespace cdmt;
+
+namespace {
+
+constexpr double kD = 4.148808e3;  // MHz^2 pc^-1 cm^3 s
+
+thread_local std::string g_thread_error;
+
+struct Staging {
+    float4 *in = nullptr;   // [nsub][span_max] samples
+    float *out = nullptr;   // [ndm][nsub*nchan][kc_max*seglen]
+    cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free = nullptr;
+};
+
+}  // namespace
+
+struct cdmt_plan_s {
+    int device = 0;
+    int nsub = 0, nchan = 0, nint = 0, ndm = 0;
+    int64_t nsamp = 0;
+    double f_centre = 0, bw = 0;
+    std::vector<double> dms;
+    int64_t nbin = 0, mbin = 0, nd = 0, nvalid = 0, nseg = 0, nout = 0, seglen = 0;
+    int r = 0;
+    bool uniform = true;
+    double ddm = 0;
+    int dm_tile = 0, ntile = 0;
+    int64_t seg_chunk = 0;
+    int precision = 0, in_dtype = 0;
+    int64_t mem_budget = 0;
+    // device tables
+    float2 *tw_n = nullptr, *tw_af = nullptr, *tw_bf = nullptr, *tw_ai = nullptr, *tw_bi = nullptr;
+    uint2 *nco = nullptr;
+    double *ktab = nullptr, *d_dm = nullptr;
+    float4 *spec = nullptr;
+    int64_t bytes = 0;
+    // host-execute pipeline
+    int64_t host_chunk = 0, span_max = 0;
+    Staging stage[2];
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    // stage timing (cdmt_set_timing / cdmt_stage_times)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_marks;  // triples: before forward, before dedisperse, after dedisperse
+    std::string last_error;
+};
+
+namespace {
+
+int fail(cdmt_plan_s *p, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (p) p->last_error = buf;
+    else g_thread_error = buf;
+    return code;
+}
+
+#define CK(p, call)                                                                                       \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(p, e_ == cudaErrorMemoryAllocation ? CDMT_ENOMEM : CDMT_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+    } while (0)
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Eq. 2
+double sweep(double lo, double hi, double dm) { return kD * dm * (1.0 / (lo * lo) - 1.0 / (hi * hi)); }
+
+// Overlap n_d of Sec. 2 for the lowest channel of the band at the largest |DM|,
+// rounded up to an even number with (M - n_d) % nint == 0.  -1 if none < M.
+int64_t overlap_rule(const cdmt_plan_s &p, int64_t nbin)
+{
+    double dmax = 0;
+    for (double d : p.dms) dmax = std::max(dmax, std::fabs(d));
+    const double band_lo = p.f_centre - 0.5 * p.nsub * p.bw;
+    const double chan_bw = p.bw / p.nchan;
+    const double td = sweep(band_lo, band_lo + chan_bw, dmax);
+    const double want = p.bw * 1e6 * td / p.nchan;
+    int64_t nd = (int64_t)std::ceil(want);
+    nd += nd & 1;
+    const int64_t m = nbin / p.nchan;
+    while (nd < m && (m - nd) % p.nint) nd += 2;
+    return nd < m ? nd : -1;
+}
+
+// ---- FP64 table kernels (run once per plan) ---------------------------------
+
+// tw[k] = exp(sign 2 pi i k / n), k < n
+__global__ void k_twiddle_line(float2 *tw, int64_t n, int sign)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = make_float2((float)c, (float)(sign * s));
+}
+
+// pass-A twiddles W_M^{t m0} at [m0-1][t] and pass-B twiddles W_M^{16 j0 m1} at [m1-1][j0]
+__global__ void k_twiddle_passes(float2 *ta, float2 *tb, int r, int sign)
+{
+    const int m = 256 * r, t_n = 16 * r;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 15 * t_n + 15 * r; i += gridDim.x * blockDim.x) {
+        int64_t p;
+        float2 *dst;
+        if (i < 15 * t_n) {
+            const int m0 = i / t_n + 1, t = i % t_n;
+            p = (int64_t)t * m0;
+            dst = ta + i;
+        } else {
+            const int q = i - 15 * t_n, m1 = q / r + 1, j0 = q % r;
+            p = 16LL * j0 * m1;
+            dst = tb + q;
+        }
+        double s, c;
+        sincospi(2.0 * (double)(p % m) / (double)m, &s, &c);
+        *dst = make_float2((float)c, (float)(sign * s));
+    }
+}
+
+// K = 1e6 D nu^2 / (nu_c^2 (nu_c + nu)) in cycles per unit DM for shifted bin
+// i = c M + j of subband s (Eq. 1 per channel; nu = (j - M/2) bw / N).
+__device__ __forceinline__ double chirp_k(double f_centre, double bw, int nsub, int nchan, int64_t nbin, int s, int64_t i)
+{
+    const int64_t m = nbin / nchan;
+    const int c = (int)(i / m);
+    const int64_t j = i % m;
+    const double nu_s = f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
+    const double nu_c = nu_s - 0.5 * bw + ((double)c + 0.5) * bw / (double)nchan;
+    const double nu = ((double)j - 0.5 * (double)m) * bw / (double)nbin;
+    return 1e6 * 4.148808e3 * nu * nu / (nu_c * nu_c * (nu_c + nu));
+}
+
+// 32-bit fixed-point fraction of x cycles (x * 2^32 rounded, modulo 2^32)
+__device__ __forceinline__ uint32_t fix32(double x) { return (uint32_t)(unsigned long long)llrint(x * 4294967296.0); }
+
+__global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, double f_centre, double bw, int nsub,
+                            int nchan, int64_t nbin, int ntile)
+{
+    const int64_t total = (int64_t)ntile * nsub * nbin;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % nbin;
+        const int s = (int)((q / nbin) % nsub);
+        const int tile = (int)(q / ((int64_t)nbin * nsub));
+        const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i);
+        nco[q] = make_uint2(fix32(-dm_tile0[tile] * k), fix32(-ddm * k));
+    }
+}
+
+__global__ void k_k_table(double *kt, double f_centre, double bw, int nsub, int nchan, int64_t nbin)
+{
+    const int64_t total = (int64_t)nsub * nbin;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+        kt[q] = chirp_k(f_centre, bw, nsub, nchan, nbin, (int)(q / nbin), q % nbin);
+}
+
+template <class T> int dalloc(cdmt_plan_s *p, T **ptr, size_t count)
+{
+    size_t b = sizeof(T) * count;
+    if (p->mem_budget > 0 && p->bytes + (int64_t)b > p->mem_budget)
+        return fail(p, CDMT_EBUDGET, "device memory budget of %lld bytes exceeded (need %lld more)",
+                    (long long)p->mem_budget, (long long)b);
+    cudaError_t e = cudaMalloc((void **)ptr, b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(p, CDMT_ENOMEM, "cudaMalloc(%zu): %s", b, cudaGetErrorString(e));
+    }
+    p->bytes += (int64_t)b;
+    return CDMT_OK;
+}
+
+void release(cdmt_plan_s *p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    void *ptrs[] = {p->tw_n, p->tw_af, p->tw_bf, p->tw_ai, p->tw_bi, p->nco, p->ktab, p->d_dm, p->spec};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (auto &st : p->stage) {
+        if (st.in) cudaFree(st.in);
+        if (st.out) cudaFree(st.out);
+        cudaEvent_t evs[] = {st.in_free, st.in_ready, st.out_ready, st.out_free};
+        for (auto ev : evs)
+            if (ev) cudaEventDestroy(ev);
+    }
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+    for (auto ev : p->ev_pool) cudaEventDestroy(ev);
+    for (auto ev : p->ev_marks) cudaEventDestroy(ev);
+    cudaSetDevice(cur);
+}
+
+int mark(cdmt_plan_s *p, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    if (p->ev_pool.empty()) {
+        CK(p, cudaEventCreate(&ev));
+    } else {
+        ev = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    }
+    p->ev_marks.push_back(ev);
+    CK(p, cudaEventRecord(ev, st));
+    return CDMT_OK;
+}
+
+int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
+                  int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st)
+{
+    ForwardArgs fa{};
+    fa.in = in;
+    fa.spec = p->spec;
+    fa.tw_a = p->tw_af;
+    fa.tw_b = p->tw_bf;
+    fa.tw_n = p->tw_n;
+    fa.nsamp = in_stride;
+    fa.nvalid = p->nvalid;
+    fa.nbin = p->nbin;
+    fa.k0 = in_k0;
+    fa.nchan = p->nchan;
+    fa.kc = kc;
+    fa.nsub = p->nsub;
+    fa.r = p->r;
+    int rc;
+    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    CK(p, fp32_forward(fa, st));
+    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    DedispArgs da{};
+    da.spec = p->spec;
+    da.nco = p->nco;
+    da.ktab = p->ktab;
+    da.dm_list = p->d_dm;
+    da.tw_a = p->tw_ai;
+    da.tw_b = p->tw_bi;
+    da.out = out;
+    da.k0 = out_k0;
+    da.nout = out_stride;
+    da.nsub = p->nsub;
+    da.kc = kc;
+    da.nchan = p->nchan;
+    da.ndm = p->ndm;
+    da.dm_tile = p->dm_tile;
+    da.nd = (int)p->nd;
+    da.nint = p->nint;
+    da.r = p->r;
+    da.uniform = p->uniform;
+    da.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
+    CK(p, fp32_dedisperse(da, st));
+    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    return CDMT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cdmt_strerror(int status)
+{
+    switch (status) {
+    case CDMT_OK: return "success";
+    case CDMT_EINVAL: return "invalid argument";
+    case CDMT_ENOMEM: return "out of memory";
+    case CDMT_ECUDA: return "CUDA error";
+    case CDMT_ETIMEOUT: return "device wait timed out";
+    case CDMT_EBUDGET: return "memory budget exceeded";
+    case CDMT_ENOTSUP: return "unsupported size combination";
+    default: return "unknown status";
+    }
+}
+
+const char *cdmt_last_error(cdmt_plan_t plan)
+{
+    return plan ? plan->last_error.c_str() : g_thread_error.c_str();
+}
+
+int cdmt_plan(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz, double bw_sub_mhz,
+              const double *dm_list, int ndm, int nchan, int nint)
+{
+    return cdmt_plan_ex(plan, nsub, nsamp, f_centre_mhz, bw_sub_mhz, dm_list, ndm, nchan, nint, nullptr);
+}
+
+int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz, double bw_sub_mhz,
+                 const double *dm_list, int ndm, int nchan, int nint, const cdmt_opts *opts)
+{
+    if (!plan) return fail(nullptr, CDMT_EINVAL, "plan pointer is NULL");
+    *plan = nullptr;
+    cdmt_opts o{};
+    if (opts) o = *opts;
+    if (nsub < 1) return fail(nullptr, CDMT_EINVAL, "nsub must be >= 1 (got %d)", nsub);
+    if (ndm < 1 || !dm_list) return fail(nullptr, CDMT_EINVAL, "need ndm >= 1 and a DM list");
+    if (!(bw_sub_mhz > 0) || !std::isfinite(bw_sub_mhz)) return fail(nullptr, CDMT_EINVAL, "bw_sub must be > 0");
+    if (!is_pow2(nchan) || nchan < 2 || nchan > 32)
+        return fail(nullptr, CDMT_EINVAL, "nchan must be a power of two in 2..32 (got %d)", nchan);
+    if (nint < 1) return fail(nullptr, CDMT_EINVAL, "nint must be >= 1 (got %d)", nint);
+    for (int i = 0; i < ndm; i++)
+        if (!std::isfinite(dm_list[i])) return fail(nullptr, CDMT_EINVAL, "DM %d is not finite", i);
+    const double band_lo = f_centre_mhz - 0.5 * nsub * bw_sub_mhz;
+    if (!(band_lo > 0)) return fail(nullptr, CDMT_EINVAL, "lowest frequency %.6g MHz must be > 0", band_lo);
+    if (o.precision != CDMT_PREC_FP32) return fail(nullptr, CDMT_ENOTSUP, "precision %d not available", o.precision);
+    if (o.in_dtype != CDMT_IN_C64) return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
+
+    auto *p = new cdmt_plan_s();
+    cudaGetDevice(&p->device);
+    p->nsub = nsub;
+    p->nsamp = nsamp;
+    p->f_centre = f_centre_mhz;
+    p->bw = bw_sub_mhz;
+    p->dms.assign(dm_list, dm_list + ndm);
+    p->ndm = ndm;
+    p->nchan = nchan;
+    p->nint = nint;
+    p->precision = o.precision;
+    p->in_dtype = o.in_dtype;
+    p->mem_budget = o.mem_budget;
+
+    // N_bin: explicit, or the largest M in 512..4096 whose overlap wastes <= 1/4
+    int64_t nbin = o.nbin;
+    if (nbin > 0) {
+        if (!is_pow2(nbin) || nbin % nchan) {
+            delete p;
+            return fail(nullptr, CDMT_EINVAL, "nbin must be a power of two divisible by nchan");
+        }
+    } else {
+        nbin = 0;
+        for (int64_t m = 4096; m >= 512; m /= 2) {
+            int64_t n = m * nchan;
+            if (n > nsamp) continue;
+            int64_t nd = o.nd >= 0 ? o.nd : overlap_rule(*p, n);
+            if (nd < 0) continue;
+            if (!nbin) nbin = n;  // largest that fits at all
+            if (nd * 4 <= m) { nbin = n; break; }
+        }
+        if (!nbin) {
+            delete p;
+            return fail(nullptr, CDMT_EINVAL, "no FFT length in 512*nchan..4096*nchan fits nsamp=%lld with its overlap",
+                        (long long)nsamp);
+        }
+    }
+    p->nbin = nbin;
+    p->mbin = nbin / nchan;
+    if (p->mbin < 512 || p->mbin > 4096) {
+        delete p;
+        return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)p->mbin);
+    }
+    p->r = (int)(p->mbin / 256);
+    if (nsamp < nbin) {
+        delete p;
+        return fail(nullptr, CDMT_EINVAL, "nsamp (%lld) < N_bin (%lld)", (long long)nsamp, (long long)nbin);
+    }
+    p->nd = o.nd >= 0 ? o.nd : overlap_rule(*p, nbin);
+    if (p->nd < 0 || p->nd % 2 || p->nd >= p->mbin || (p->mbin - p->nd) % nint) {
+        delete p;
+        return fail(nullptr, CDMT_EINVAL, "overlap nd=%lld invalid for M=%lld, nint=%d (need even, < M, (M-nd) %% nint == 0)",
+                    (long long)p->nd, (long long)p->mbin, nint);
+    }
+    p->nvalid = nbin - p->nd * nchan;
+    p->nseg = (nsamp - nbin) / p->nvalid + 1;
+    p->seglen = (p->mbin - p->nd) / nint;
+    p->nout = p->nseg * p->seglen;
+
+    // DM list spacing
+    p->ddm = ndm > 1 ? (dm_list[ndm - 1] - dm_list[0]) / (ndm - 1) : 0.0;
+    p->uniform = true;
+    for (int i = 0; i < ndm; i++) {
+        double want = dm_list[0] + i * p->ddm;
+        if (std::fabs(dm_list[i] - want) > 1e-9 * std::max(1.0, std::fabs(dm_list[i]))) p->uniform = false;
+    }
+
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    // DM tile: all DMs, unless that leaves too few work items to fill the GPU
+    const int64_t items = (int64_t)nsub * p->nseg * nchan;
+    const int64_t want_items = 4LL * nsm;
+    int tiles = 1;
+    if (o.dm_tile > 0) tiles = (ndm + o.dm_tile - 1) / o.dm_tile;
+    else if (items < want_items) tiles = (int)std::min<int64_t>(ndm, (want_items + items - 1) / items);
+    p->dm_tile = (ndm + tiles - 1) / tiles;
+    p->ntile = (ndm + p->dm_tile - 1) / p->dm_tile;
+
+    // workspace chunk: all segments unless the budget / a request says otherwise
+    p->seg_chunk = o.seg_chunk > 0 ? std::min<int64_t>(o.seg_chunk, p->nseg) : p->nseg;
+    const int64_t spec_bytes_per_seg = (int64_t)nsub * nbin * 16;
+    if (o.seg_chunk <= 0 && p->mem_budget > 0) {
+        int64_t room = p->mem_budget / 2 / spec_bytes_per_seg;
+        p->seg_chunk = std::max<int64_t>(1, std::min<int64_t>(room, p->nseg));
+    }
+
+    int rc;
+    cudaError_t e = fp32_prepare(p->r);
+    if (e != cudaSuccess) {
+        release(p);
+        delete p;
+        return fail(nullptr, CDMT_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    }
+#define TRY(x)                          \
+    do {                                \
+        if ((rc = (x)) != CDMT_OK) {    \
+            g_thread_error = p->last_error; \
+            release(p);                 \
+            delete p;                   \
+            return rc;                  \
+        }                               \
+    } while (0)
+    const int tn = 16 * p->r;
+    TRY(dalloc(p, &p->tw_n, (size_t)nbin));
+    TRY(dalloc(p, &p->tw_af, (size_t)15 * (tn + p->r)));
+    TRY(dalloc(p, &p->tw_ai, (size_t)15 * (tn + p->r)));
+    p->tw_bf = p->tw_af + 15 * tn;
+    p->tw_bi = p->tw_ai + 15 * tn;
+    TRY(dalloc(p, &p->d_dm, (size_t)ndm));
+    if (p->uniform) TRY(dalloc(p, &p->nco, (size_t)p->ntile * nsub * nbin));
+    else TRY(dalloc(p, &p->ktab, (size_t)nsub * nbin));
+    TRY(dalloc(p, &p->spec, (size_t)p->seg_chunk * nsub * nbin));
+
+    std::vector<double> tile0(p->ntile);
+    for (int t = 0; t < p->ntile; t++) tile0[t] = dm_list[t * p->dm_tile];
+    double *d_tile0 = nullptr;
+#define TRYC(x)                                                                            \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) {                                                           \
+            fail(nullptr, CDMT_ECUDA, "%s: %s", #x, cudaGetErrorString(e_));               \
+            if (d_tile0) cudaFree(d_tile0);                                                \
+            release(p);                                                                    \
+            delete p;                                                                      \
+            return CDMT_ECUDA;                                                             \
+        }                                                                                  \
+    } while (0)
+    TRYC(cudaMemcpy(p->d_dm, dm_list, sizeof(double) * ndm, cudaMemcpyHostToDevice));
+    k_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256>>>(p->tw_n, nbin, -1);
+    k_twiddle_passes<<<64, 256>>>(p->tw_af, p->tw_bf, p->r, -1);
+    k_twiddle_passes<<<64, 256>>>(p->tw_ai, p->tw_bi, p->r, +1);
+    if (p->uniform) {
+        TRYC(cudaMalloc(&d_tile0, sizeof(double) * p->ntile));
+        TRYC(cudaMemcpy(d_tile0, tile0.data(), sizeof(double) * p->ntile, cudaMemcpyHostToDevice));
+        k_nco_table<<<1024, 256>>>(p->nco, d_tile0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile);
+    } else {
+        k_k_table<<<1024, 256>>>(p->ktab, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin);
+    }
+    TRYC(cudaGetLastError());
+    TRYC(cudaDeviceSynchronize());
+    if (d_tile0) cudaFree(d_tile0);
+#undef TRY
+#undef TRYC
+    *plan = p;
+    return CDMT_OK;
+}
+
+int cdmt_plan_info(cdmt_plan_t p, cdmt_info *info)
+{
+    if (!p || !info) return fail(p, CDMT_EINVAL, "NULL plan or info");
+    std::memset(info, 0, sizeof *info);
+    info->nsamp = p->nsamp;
+    info->nbin = p->nbin;
+    info->mbin = p->mbin;
+    info->nd = p->nd;
+    info->nvalid = p->nvalid;
+    info->nseg = p->nseg;
+    info->nout = p->nout;
+    info->seg_chunk = p->seg_chunk;
+    info->workspace_bytes = p->bytes;
+    info->in_bytes = (int64_t)p->nsub * p->nsamp * 16;
+    info->out_bytes = (int64_t)p->ndm * p->nsub * p->nchan * p->nout * 4;
+    info->units = (double)p->ndm * p->nsub * p->nseg * p->nvalid;
+    info->nsub = p->nsub;
+    info->nchan = p->nchan;
+    info->nint = p->nint;
+    info->ndm = p->ndm;
+    info->dm_tile = p->dm_tile;
+    info->uniform_dm = p->uniform ? 1 : 0;
+    info->precision = p->precision;
+    info->in_dtype = p->in_dtype;
+    info->device = p->device;
+    return CDMT_OK;
+}
+
+int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_scale, void *cuda_stream)
+{
+    (void)d_scale;
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    if (!d_in || !d_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
+    if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(p, CDMT_EINVAL, "input must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d_out) % 4) return fail(p, CDMT_EINVAL, "output must be 4-byte aligned");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int rc = CDMT_OK;
+    for (int64_t k0 = 0; k0 < p->nseg && rc == CDMT_OK; k0 += p->seg_chunk) {
+        const int kc = (int)std::min<int64_t>(p->seg_chunk, p->nseg - k0);
+        rc = enqueue_chunk(p, static_cast<const float4 *>(d_in), p->nsamp, k0, d_out, p->nout, k0, kc, st);
+    }
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
+}
+
+int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float *h_scale, void *cuda_stream)
+{
+    (void)h_scale;
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    if (!h_in || !h_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
+    if (!p->host_chunk) {
+        // chunks small enough to pipeline, large enough to fill the GPU
+        int64_t kc = std::max<int64_t>(1, std::min<int64_t>(p->seg_chunk, (p->nseg + 7) / 8));
+        p->host_chunk = kc;
+        p->span_max = (kc - 1) * p->nvalid + p->nbin;
+        for (auto &sg : p->stage) {
+            int rc;
+            if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
+            if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
+            CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.in_ready, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.out_ready, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.out_free, cudaEventDisableTiming));
+            CK(p, cudaEventRecord(sg.in_free, st));
+            CK(p, cudaEventRecord(sg.out_free, st));
+        }
+        CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+        CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+    }
+    const int64_t kcm = p->host_chunk;
+    const auto *src = static_cast<const float4 *>(h_in);
+    int b = 0;
+    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, b ^= 1) {
+        Staging &sg = p->stage[b];
+        const int kc = (int)std::min<int64_t>(kcm, p->nseg - k0);
+        const int64_t span = (kc - 1) * p->nvalid + p->nbin;
+        CK(p, cudaStreamWaitEvent(p->s_h2d, sg.in_free, 0));
+        CK(p, cudaMemcpy2DAsync(sg.in, p->span_max * 16, src + k0 * p->nvalid, p->nsamp * 16, span * 16, p->nsub,
+                                cudaMemcpyHostToDevice, p->s_h2d));
+        CK(p, cudaEventRecord(sg.in_ready, p->s_h2d));
+        CK(p, cudaStreamWaitEvent(st, sg.in_ready, 0));
+        CK(p, cudaStreamWaitEvent(st, sg.out_free, 0));
+        int rc = enqueue_chunk(p, sg.in, p->span_max, 0, sg.out, kcm * p->seglen, 0, kc, st);
+        if (rc != CDMT_OK) return rc;
+        CK(p, cudaEventRecord(sg.in_free, st));
+        CK(p, cudaEventRecord(sg.out_ready, st));
+        CK(p, cudaStreamWaitEvent(p->s_d2h, sg.out_ready, 0));
+        CK(p, cudaMemcpy2DAsync(h_out + k0 * p->seglen, p->nout * 4, sg.out, kcm * p->seglen * 4, kc * p->seglen * 4,
+                                rows, cudaMemcpyDeviceToHost, p->s_d2h));
+        CK(p, cudaEventRecord(sg.out_free, p->s_d2h));
+    }
+    CK(p, cudaStreamSynchronize(p->s_d2h));
+    CK(p, cudaStreamSynchronize(st));
+    if (cur != p->device) cudaSetDevice(cur);
+    return CDMT_OK;
+}
+
+int cdmt_set_timing(cdmt_plan_t p, int on)
+{
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    p->timing = on != 0;
+    return CDMT_OK;
+}
+
+int cdmt_stage_times(cdmt_plan_t p, double *ms, int64_t *launches)
+{
+    if (!p || !ms) return fail(p, CDMT_EINVAL, "NULL plan or ms");
+    ms[0] = ms[1] = 0.0;
+    int64_t n = 0;
+    for (size_t i = 0; i + 2 < p->ev_marks.size(); i += 3) {
+        float a = 0.f, b = 0.f;
+        CK(p, cudaEventSynchronize(p->ev_marks[i + 2]));
+        CK(p, cudaEventElapsedTime(&a, p->ev_marks[i], p->ev_marks[i + 1]));
+        CK(p, cudaEventElapsedTime(&b, p->ev_marks[i + 1], p->ev_marks[i + 2]));
+        ms[0] += a;
+        ms[1] += b;
+        n++;
+    }
+    if (launches) {
+        launches[0] = 2 * n;  // decimated FFTs + column DFTs per chunk
+        launches[1] = n;
+    }
+    p->ev_pool.insert(p->ev_pool.end(), p->ev_marks.begin(), p->ev_marks.end());
+    p->ev_marks.clear();
+    return CDMT_OK;
+}
+
+int cdmt_destroy(cdmt_plan_t p)
+{
+    if (!p) return CDMT_OK;
+    release(p);
+    delete p;
+    return CDMT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,39 @@
+// Internal interfaces between the host planner and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdmt {
+
+struct ForwardArgs {
+    const float4 *in;  // first sample of the block's subband 0 (segment 0 of the chunk at in + k0 * nvalid)
+    float4 *spec;      // [nsub][kc][nchan][M] float4 workspace
+    const float2 *tw_a, *tw_b, *tw_n;
+    int64_t nsamp;     // samples between consecutive subbands in `in`
+    int64_t nvalid;    // S
+    int64_t nbin;
+    int64_t k0;        // first segment of the chunk, counted from `in`
+    int nchan, kc, nsub, r;
+};
+
+struct DedispArgs {
+    const float4 *spec;
+    const uint2 *nco;     // uniform: [ntile][nsub][nchan*M] (a, b)
+    const double *ktab;   // non-uniform: [nsub][nchan*M] K (cycles per unit DM)
+    const double *dm_list;
+    const float2 *tw_a, *tw_b;
+    float *out;
+    int64_t k0;           // segment index of the chunk's first segment in the output time axis
+    int64_t nout;         // output row stride (floats)
+    int nsub, kc, nchan, ndm, dm_tile, nd, nint, r;
+    bool uniform;
+    float scale;
+};
+
+cudaError_t fp32_prepare(int r);
+size_t fp32_dedisp_smem(int r);
+cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st);
+cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st);
+
+}  // namespace cdmt

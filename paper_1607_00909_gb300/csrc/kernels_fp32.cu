@@ -1,0 +1,311 @@
+// FP32 kernels of the coherent-dedispersion hot path (sm_103a).
+//
+// Forward stage (Sec. 3: "unpack, segment and pad", "forward FFT", "swap halves
+// per subband").  The N-point forward DFT of a segment is split as
+// N = nchan * M with input n = n1 + nchan * n2 and output F = j + M c':
+//   X[j + M c'] = sum_n1 W_nchan^{n1 c'} W_N^{n1 j} sum_n2 x[n1 + nchan n2] W_M^{n2 j}.
+//   k_forward_decimated: one CTA per (subband, segment, n1) gathers the
+//     decimated series x[k S + n1 + nchan n2], runs the M-point FFT and applies
+//     W_N^{n1 j}.
+//   k_forward_columns: the nchan-point DFT over n1 for every bin j, written in
+//     place with the halves of the spectrum swapped: unshifted channel c' lands
+//     in channel slot c = (c' + nchan/2) mod nchan, so that slot c holds bins of
+//     increasing frequency of channel c.
+//
+// DM stage (Sec. 3: "complex multiplication with transfer function", "swap
+// halves per channel", "backward FFT", "transpose, unpad and detect"), fused in
+// k_dedisperse: one CTA per (DM tile, subband, segment, channel) keeps the
+// channel's M spectral bins of both polarisations in shared memory and, for
+// each DM of its tile, multiplies them by the chirp, runs the M-point backward
+// FFT, forms |X|^2 + |Y|^2, drops nd/2 samples at each edge, sums nint samples
+// and stores the filterbank row segment.  The per-channel swap of halves is a
+// factor (-1)^m on the time series, which the detection removes, so it is not
+// performed.  Spectra never leave the chip between chirp and detection.
+//
+// Chirp (Eq. 1, conjugated for dedispersion): bin j of channel c has
+// exp(-2 pi i DM K), K = 1e6 D nu^2 / (nu_c^2 (nu_c + nu)).  The planner stores,
+// per bin and DM tile, the 32-bit fixed-point phase a = -DM_0 K and step
+// b = -dDM K (in cycles, computed in FP64); DM number d of the tile then has
+// phase a + d b exactly modulo 2^32.  Lists that are not evenly spaced use the
+// FP64 product DM K per bin and DM instead.
+#include "cdmt_internal.h"
+#include "fft_core.cuh"
+
+namespace cdmt {
+
+constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;  // 2 pi / 2^32
+
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(16 * R)
+k_forward_decimated(const float4 *__restrict__ in, float4 *__restrict__ spec, const float2 *__restrict__ tw_a,
+                    const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n, int64_t nsamp,
+                    int64_t nvalid, int nchan, int64_t k0, int kc)
+{
+    using F = Fft3<R>;
+    constexpr int M = F::M, T = F::T;
+    extern __shared__ float4 smem[];
+    float4 *ex = smem;
+    float2 *ta = reinterpret_cast<float2 *>(ex + M);
+    float2 *tb = ta + F::NTA;
+
+    const int t = threadIdx.x;
+    const int n1 = blockIdx.x;
+    const int kk = blockIdx.y;
+    const int s = blockIdx.z;
+    for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
+    for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
+
+    const float4 *src = in + (int64_t)s * nsamp + (k0 + kk) * nvalid + n1;
+    float2 x[16], y[16];
+    #pragma unroll
+    for (int j2 = 0; j2 < 16; j2++) {
+        float4 v = __ldg(src + (int64_t)nchan * (j2 * T + t));
+        x[j2] = make_float2(v.x, v.y);
+        y[j2] = make_float2(v.z, v.w);
+    }
+    __syncthreads();  // twiddles in place
+    F::template pass_a<-1>(x, y, ex, ta, t);
+    __syncthreads();
+    F::template pass_b<-1>(x, y, ex, tb, t);
+    __syncthreads();
+    float4 *dst = spec + (((int64_t)s * kc + kk) * nchan + n1) * M;
+    F::template pass_c<-1>(ex, t, [&](int j, float2 a, float2 b) {
+        float2 w = __ldg(tw_n + n1 * j);
+        dst[j] = pack(cmul(a, w), cmul(b, w));
+    });
+}
+
+// nchan-point DFT over n1 (stride M) for every bin j; in place.
+template <int NC>
+__global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ spec, const float2 *__restrict__ tw_n,
+                                                         int m, int64_t nbin)
+{
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    if (j >= m) return;
+    float4 *col = spec + ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * nbin + j;
+    float2 x[NC], y[NC];
+    #pragma unroll
+    for (int n1 = 0; n1 < NC; n1++) {
+        float4 v = col[(int64_t)n1 * m];
+        x[n1] = make_float2(v.x, v.y);
+        y[n1] = make_float2(v.z, v.w);
+    }
+    if constexpr (NC <= 16) {
+        dft_r<NC, -1>(x);
+        dft_r<NC, -1>(y);
+    } else {
+        // NC = 32: two 16-point DFTs (even / odd n1) and one radix-2 step with
+        // twiddles W_32^k = W_N^{k N / 32}
+        float2 ex_[16], ox[16], ey[16], oy[16];
+        #pragma unroll
+        for (int i = 0; i < 16; i++) {
+            ex_[i] = x[2 * i]; ox[i] = x[2 * i + 1];
+            ey[i] = y[2 * i]; oy[i] = y[2 * i + 1];
+        }
+        dft16<-1>(ex_); dft16<-1>(ox); dft16<-1>(ey); dft16<-1>(oy);
+        #pragma unroll
+        for (int k = 0; k < 16; k++) {
+            float2 w = __ldg(tw_n + (int64_t)k * (nbin / 32));
+            float2 a = cmul(ox[k], w), b = cmul(oy[k], w);
+            x[k] = cadd(ex_[k], a); x[k + 16] = csub(ex_[k], a);
+            y[k] = cadd(ey[k], b); y[k + 16] = csub(ey[k], b);
+        }
+    }
+    #pragma unroll
+    for (int cp = 0; cp < NC; cp++) {
+        const int c = (cp + NC / 2) % NC;
+        col[(int64_t)c * m] = pack(x[cp], y[cp]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// UNIFORM: phase table holds (a, b) per bin for the tile; otherwise it holds
+// K per bin as double and the DM values come from dm_list.
+template <int R, bool UNIFORM>
+__global__ void __launch_bounds__(16 * R)
+k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
+             const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
+             float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
+             int nint, int64_t nout, float scale)
+{
+    using F = Fft3<R>;
+    constexpr int M = F::M, T = F::T;
+    extern __shared__ float4 smem[];
+    float4 *xs = smem;                                    // M spectral bins, both pols
+    float4 *ex = xs + M;                                  // exchange buffer
+    uint2 *ph = reinterpret_cast<uint2 *>(ex + M);        // M phase words (a, b) or K as double
+    float2 *ta = reinterpret_cast<float2 *>(ph + M);
+    float2 *tb = ta + F::NTA;
+    float *ib = reinterpret_cast<float *>(tb + F::NTB);   // M detected powers
+
+    const int t = threadIdx.x;
+    int64_t item = blockIdx.x;
+    const int c = (int)(item % nchan); item /= nchan;
+    const int kk = (int)(item % kc); item /= kc;
+    const int s = (int)(item % nsub); item /= nsub;
+    const int tile = (int)item;
+    const int dm0 = tile * dm_tile;
+    const int ndt = min(dm_tile, ndm - dm0);
+
+    const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * M;
+    for (int i = t; i < M; i += T) xs[i] = src[i];
+    if constexpr (UNIFORM) {
+        const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * M + (int64_t)c * M;
+        for (int i = t; i < M; i += T) ph[i] = p[i];
+    } else {
+        const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * M);
+        for (int i = t; i < M; i += T) ph[i] = p[i];
+    }
+    for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
+    for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
+    __syncthreads();
+
+    const int half = nd / 2;
+    const int seglen = (M - nd) / nint;
+    const int64_t rows = (int64_t)nsub * nchan;
+    const int64_t obase = (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+
+    for (int d = 0; d < ndt; d++) {
+        float2 x[16], y[16];
+        double dmv = 0.0;
+        if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            const int j = j2 * T + t;
+            float4 v = xs[j];
+            float sn, cs;
+            if constexpr (UNIFORM) {
+                uint2 ab = ph[j];
+                int32_t p = (int32_t)(ab.x + (uint32_t)d * ab.y);
+                __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
+            } else {
+                double kj = __hiloint2double((int)ph[j].y, (int)ph[j].x);
+                double cyc = dmv * kj;
+                cyc -= rint(cyc);
+                __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
+            }
+            x[j2] = make_float2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+            y[j2] = make_float2(v.z * cs - v.w * sn, v.z * sn + v.w * cs);
+        }
+        F::template pass_a<+1>(x, y, ex, ta, t);
+        __syncthreads();
+        F::template pass_b<+1>(x, y, ex, tb, t);
+        __syncthreads();
+        F::template pass_c<+1>(ex, t, [&](int m, float2 a, float2 b) {
+            ib[m] = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(b.x, b.x, b.y * b.y)));
+        });
+        __syncthreads();
+        float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
+        for (int u = t; u < seglen; u += T) {
+            const float *p = ib + half + u * nint;
+            float acc = 0.f;
+            for (int q = 0; q < nint; q++) acc += p[q];
+            orow[u] = acc * scale;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>::M + sizeof(float2) * (Fft3<R>::NTA + Fft3<R>::NTB); }
+template <int R> static size_t smem_dedisp()
+{
+    using F = Fft3<R>;
+    return sizeof(float4) * 2 * F::M + sizeof(uint2) * F::M + sizeof(float2) * (F::NTA + F::NTB) + sizeof(float) * F::M;
+}
+
+template <int R> static cudaError_t set_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_forward_decimated<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forward<R>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
+}
+
+cudaError_t fp32_prepare(int r)
+{
+    switch (r) {
+    case 2: return set_attrs<2>();
+    case 4: return set_attrs<4>();
+    case 8: return set_attrs<8>();
+    case 16: return set_attrs<16>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t fp32_dedisp_smem(int r)
+{
+    switch (r) {
+    case 2: return smem_dedisp<2>();
+    case 4: return smem_dedisp<4>();
+    case 8: return smem_dedisp<8>();
+    case 16: return smem_dedisp<16>();
+    default: return 0;
+    }
+}
+
+template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t st)
+{
+    dim3 g(a.nchan, a.kc, a.nsub);
+    k_forward_decimated<R><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(a.in, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp,
+                                                                    a.nvalid, a.nchan, a.k0, a.kc);
+}
+
+template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t st)
+{
+    const int m = (int)(a.nbin / NC);
+    dim3 g((m + 255) / 256, a.kc, a.nsub);
+    k_forward_columns<NC><<<g, 256, 0, st>>>(a.spec, a.tw_n, m, a.nbin);
+}
+
+cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st)
+{
+    switch (a.r) {
+    case 2: launch_forward<2>(a, st); break;
+    case 4: launch_forward<4>(a, st); break;
+    case 8: launch_forward<8>(a, st); break;
+    case 16: launch_forward<16>(a, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (a.nchan) {
+    case 2: launch_columns<2>(a, st); break;
+    case 4: launch_columns<4>(a, st); break;
+    case 8: launch_columns<8>(a, st); break;
+    case 16: launch_columns<16>(a, st); break;
+    case 32: launch_columns<32>(a, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStream_t st)
+{
+    const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
+    const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
+    k_dedisperse<R, U><<<(unsigned)nblk, Fft3<R>::T, smem_dedisp<R>(), st>>>(
+        a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
+        a.nd, a.nint, a.nout, a.scale);
+}
+
+cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)
+{
+    switch (a.r * 2 + (a.uniform ? 1 : 0)) {
+    case 4 + 1: launch_dedisp<2, true>(a, st); break;
+    case 4: launch_dedisp<2, false>(a, st); break;
+    case 8 + 1: launch_dedisp<4, true>(a, st); break;
+    case 8: launch_dedisp<4, false>(a, st); break;
+    case 16 + 1: launch_dedisp<8, true>(a, st); break;
+    case 16: launch_dedisp<8, false>(a, st); break;
+    case 32 + 1: launch_dedisp<16, true>(a, st); break;
+    case 32: launch_dedisp<16, false>(a, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cdmt

@@ -1,0 +1,97 @@
+"""The C ABI library loads, exports every function include/cdmt.h declares, and
+rejects bad arguments with a status (no GPU needed: validation happens before
+any CUDA call)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(HEADER_DIR):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(cdmt_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def cdmt():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1607_00909_gb300 as m
+    return m
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host",
+              "cdmt_destroy", "cdmt_strerror", "cdmt_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(cdmt):
+    out = subprocess.run(["nm", "-D", "--defined-only", cdmt.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = _declared() - exported
+    assert not missing, missing
+    for n in _declared():
+        assert hasattr(cdmt.lib(), n)
+
+
+def test_binding_names_match_header(cdmt):
+    for n in _declared():
+        assert callable(getattr(cdmt, n)), n
+
+
+def test_status_strings(cdmt):
+    assert cdmt.cdmt_strerror(0) == "success"
+    assert cdmt.cdmt_strerror(cdmt.CDMT_EINVAL) == "invalid argument"
+    assert cdmt.cdmt_strerror(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(nsub=0), "nsub"),
+    (dict(nchan=12), "nchan"),
+    (dict(nchan=64), "nchan"),
+    (dict(nint=0), "nint"),
+    (dict(dm_list=[]), "ndm"),
+    (dict(bw_sub=-1.0), "bw_sub"),
+    (dict(f_centre=0.01), "lowest frequency"),
+    (dict(dm_list=[0.0, float("nan")]), "finite"),
+])
+def test_plan_rejects_bad_arguments(cdmt, kw, msg):
+    args = dict(nsub=1, nsamp=1 << 17, f_centre=135.0, bw_sub=0.1953125, dm_list=[0.0, 5.0], nchan=8, nint=4)
+    args.update(kw)
+    with pytest.raises(cdmt.CdmtError) as e:
+        cdmt.cdmt_plan(args["nsub"], args["nsamp"], args["f_centre"], args["bw_sub"], args["dm_list"],
+                       args["nchan"], args["nint"])
+    assert e.value.status == cdmt.CDMT_EINVAL
+    assert msg in str(e.value)
+    assert msg in cdmt.cdmt_last_error(None)
+
+
+def test_plan_rejects_unsupported_precision(cdmt):
+    o = cdmt.cdmt_opts()
+    o.precision = 77
+    with pytest.raises(cdmt.CdmtError) as e:
+        cdmt.cdmt_plan_ex(1, 1 << 17, 135.0, 0.1953125, [0.0], 8, 4, o)
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+
+
+def test_null_handles(cdmt):
+    lib = cdmt.lib()
+    assert lib.cdmt_plan_info(None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_execute(None, None, None, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_execute_host(None, None, None, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_destroy(None) == cdmt.CDMT_OK
+    assert lib.cdmt_plan_ex(None, 1, 1, 1.0, 1.0, None, 0, 8, 1, None) == cdmt.CDMT_EINVAL

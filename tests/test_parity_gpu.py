@@ -1,0 +1,190 @@
+"""GPU filterbanks against the FP64 oracle (run through the C ABI).
+
+Tolerance for the plain FP32 path: max |gpu - oracle| / mean(oracle) <= 1e-5
+and ||gpu - oracle|| / ||oracle|| <= 1e-5 (relative errors against the mean
+output; the FP32 FFTs, the 32-bit fixed-point chirp phase and the FP32 sine /
+cosine each contribute ~1e-7 relative to the field).  Integer plan quantities
+(n_d, S, nseg, nout) must equal the oracle's exactly.
+"""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_filterbank, pulse_snr, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL_MAX = 1e-5
+TOL_RMS = 1e-5
+BW = 0.1953125
+
+
+@pytest.fixture(scope="module")
+def cdmt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1607_00909_gb300 as m
+    return m
+
+
+def _plan(cdmt, nsub, nsamp, fc, dms, nchan, nint, **kw):
+    return cdmt.Plan(nsub, nsamp, fc, BW, dms, nchan, nint, **kw)
+
+
+def _compare(orc, plan, x, fc, dms, nchan, nint):
+    i = plan.info
+    g = gpu_filterbank(plan, x)
+    assert np.all(np.isfinite(g)), "output not fully written"
+    o = orc.filterbank(x, fc, BW, dms, nchan, nint, i["nbin"], i["nd"])
+    assert g.shape == o.shape
+    return g, o, rel_errors(g, o)
+
+
+def test_tiny_workload_full_parity(cdmt, orc):
+    w = synth.tiny()
+    x = w.voltages()
+    plan = _plan(cdmt, w.nsub, w.nsamp, w.f_centre, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    i = plan.info
+    # plan quantities, bit-exact against the oracle's own rule and grid
+    assert i["nd"] == orc.overlap(w.nsub, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin) == 32
+    assert (i["nvalid"], i["nseg"], i["nout"]) == orc.grid(w.nsamp, w.nbin, w.nchan, i["nd"], w.nint)
+    g, o, (emax, erms) = _compare(orc, plan, x, w.f_centre, w.dms, w.nchan, w.nint)
+    print(f"tiny: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert emax <= TOL_MAX and erms <= TOL_RMS
+    # the injected pulse keeps its S/N to 1 %
+    p = w.pulses[0]
+    sg = pulse_snr(g, w.dms, p, w.f_centre, w.bw, w.nsub, w.nchan, w.nint, i["nd"])
+    so = pulse_snr(o, w.dms, p, w.f_centre, w.bw, w.nsub, w.nchan, w.nint, i["nd"])
+    assert so > 5
+    assert abs(sg / so - 1) <= 0.01
+
+
+@pytest.mark.parametrize("nchan,mbin,nint", [(2, 512, 1), (4, 1024, 2), (8, 2048, 4), (16, 4096, 8),
+                                             (32, 512, 16), (32, 2048, 3), (16, 1024, 5)])
+def test_channel_and_fft_shapes(cdmt, orc, nchan, mbin, nint):
+    nbin = nchan * mbin
+    nsamp = 3 * nbin + 777          # several segments and a ragged tail
+    dms = [0.0, 2.5, 5.0, 7.5, 10.0]
+    x = synth.noise(3, 2, nsamp)
+    plan = _plan(cdmt, 2, nsamp, 150.0, dms, nchan, nint, nbin=nbin)
+    g, o, (emax, erms) = _compare(orc, plan, x, 150.0, dms, nchan, nint)
+    assert plan.info["nseg"] >= 3
+    assert emax <= TOL_MAX and erms <= TOL_RMS, (emax, erms)
+
+
+def test_uneven_dm_list_uses_fp64_products(cdmt, orc):
+    dms = [0.0, 3.7, -5.0, 12.1, 40.0, 39.99]
+    x = synth.noise(4, 1, 1 << 15)
+    plan = _plan(cdmt, 1, 1 << 15, 120.0, dms, 8, 2, nbin=1 << 13)
+    assert plan.info["uniform_dm"] == 0
+    g, o, (emax, erms) = _compare(orc, plan, x, 120.0, dms, 8, 2)
+    assert emax <= TOL_MAX and erms <= TOL_RMS, (emax, erms)
+
+
+def test_dm_zero_only_needs_no_overlap(cdmt, orc):
+    x = synth.noise(5, 1, 1 << 14)
+    plan = _plan(cdmt, 1, 1 << 14, 135.0, [0.0], 8, 4, nbin=1 << 12)
+    assert plan.info["nd"] == 0 and plan.info["nvalid"] == 1 << 12
+    g, o, (emax, erms) = _compare(orc, plan, x, 135.0, [0.0], 8, 4)
+    assert emax <= TOL_MAX and erms <= TOL_RMS
+
+
+def test_chunked_workspace_and_ragged_dm_tiles(cdmt, orc):
+    dms = [1.0 * i for i in range(7)]
+    nsamp = 6 * (1 << 12) + 100
+    x = synth.noise(6, 3, nsamp)
+    ref = _plan(cdmt, 3, nsamp, 140.0, dms, 4, 2, nbin=1 << 12, dm_tile=3)
+    plan = _plan(cdmt, 3, nsamp, 140.0, dms, 4, 2, nbin=1 << 12, seg_chunk=3, dm_tile=3)
+    assert plan.info["seg_chunk"] == 3 and plan.info["dm_tile"] == 3 and ref.info["seg_chunk"] == ref.info["nseg"]
+    g, o, (emax, erms) = _compare(orc, plan, x, 140.0, dms, 4, 2)
+    assert emax <= TOL_MAX and erms <= TOL_RMS
+    # chunking the workspace changes the schedule, not the arithmetic (a different
+    # DM tiling would: each tile rounds its own fixed-point start phase)
+    assert np.array_equal(g, gpu_filterbank(ref, x))
+
+
+def test_execute_host_matches_execute(cdmt):
+    import torch
+    w = synth.tiny()
+    x = w.voltages()
+    plan = _plan(cdmt, w.nsub, w.nsamp, w.f_centre, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    dev = gpu_filterbank(plan, x)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.full(plan.out_shape(), float("nan"), dtype=torch.float32).pin_memory()
+    plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
+    assert np.array_equal(hout.numpy(), dev)
+    # pageable host memory also works
+    hout2 = np.full(plan.out_shape(), np.nan, dtype=np.float32)
+    plan.execute_host(x.ctypes.data, hout2.ctypes.data, 0, 0)
+    assert np.array_equal(hout2, dev)
+
+
+def test_repeatable_and_stream_ordered(cdmt):
+    import torch
+    w = synth.tiny()
+    x = w.voltages()
+    plan = _plan(cdmt, w.nsub, w.nsamp, w.f_centre, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    s = torch.cuda.Stream()
+    a = gpu_filterbank(plan, x, stream=s)
+    b = gpu_filterbank(plan, x)
+    assert np.array_equal(a, b)
+
+
+def test_noise_mean_on_gpu(cdmt):
+    # unitary transforms: complex white noise, E|x|^2 = 1 per pol -> mean 2 nint
+    x = synth.noise(8, 4, 1 << 18)
+    plan = _plan(cdmt, 4, 1 << 18, 135.0, [0.0, 10.0, 20.0], 16, 8, nbin=1 << 16)
+    g = gpu_filterbank(plan, x)
+    v = g.ravel().astype(np.float64)
+    assert abs(v.mean() - 16.0) < 3 * v.std() / np.sqrt(v.size)
+
+
+def test_plan_errors_on_device(cdmt):
+    with pytest.raises(cdmt.CdmtError) as e:
+        _plan(cdmt, 1, 1 << 14, 135.0, [0.0, 5000.0], 8, 4, nbin=1 << 14)  # overlap does not fit
+    assert e.value.status == cdmt.CDMT_EINVAL
+    with pytest.raises(cdmt.CdmtError) as e:
+        _plan(cdmt, 1, 1 << 14, 135.0, [0.0], 16, 4, nbin=1 << 16)         # nsamp < N
+    assert e.value.status == cdmt.CDMT_EINVAL
+    with pytest.raises(cdmt.CdmtError) as e:
+        _plan(cdmt, 1, 1 << 16, 135.0, [0.0], 8, 4, nbin=1 << 16)          # M = 8192 has no kernel yet
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+    with pytest.raises(cdmt.CdmtError) as e:
+        _plan(cdmt, 64, 1 << 20, 135.0, [0.0], 16, 8, nbin=1 << 16, mem_budget=1 << 20)
+    assert e.value.status == cdmt.CDMT_EBUDGET
+
+
+@pytest.mark.slow
+def test_lofar64_full_size_sampled_tiles(cdmt, orc):
+    """The 64-subband, 2^22-sample, 128-DM workload in the launch configuration
+    the benchmark times; 40 random (subband, segment, DM) tiles recomputed by
+    the oracle, plus whole-output properties."""
+    import torch
+    w = synth.lofar64()
+    x = w.voltages(threads=16)
+    plan = _plan(cdmt, w.nsub, w.nsamp, w.f_centre, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    i = plan.info
+    assert i["nd"] == orc.overlap(w.nsub, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin)
+    xt = torch.from_numpy(x).cuda()
+    del x
+    out = torch.full(plan.out_shape(), float("nan"), dtype=torch.float32, device="cuda")
+    import paper_1607_00909_gb300 as m
+    m.run(plan, xt, out)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out).all())
+    x = xt.cpu().numpy()
+    del xt
+    g = np.random.default_rng(2024)
+    ntile = 40
+    sub = g.integers(0, w.nsub, ntile)
+    seg = g.integers(0, i["nseg"], ntile)
+    seg[:2] = [0, i["nseg"] - 1]
+    dmi = g.integers(0, len(w.dms), ntile)
+    o = orc.tiles(x, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin, i["nd"], sub, seg, dmi)
+    L = (i["mbin"] - i["nd"]) // w.nint
+    gt = np.stack([out[dmi[t], sub[t] * w.nchan:(sub[t] + 1) * w.nchan, seg[t] * L:(seg[t] + 1) * L].cpu().numpy()
+                   for t in range(ntile)])
+    emax, erms = rel_errors(gt, o)
+    print(f"lofar64 tiles: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert emax <= TOL_MAX and erms <= TOL_RMS
