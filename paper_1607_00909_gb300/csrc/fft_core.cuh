@@ -7,11 +7,13 @@
 //   pass A  thread t = j1 R + j0:   a[m0]  = sum_j2 x[j2 T + t] W_16^{j2 m0},  a *= W_M^{t m0}
 //   pass B  thread u = m0 R + j0:   b[m1]  = sum_j1 a[m0; j1, j0] W_16^{j1 m1}, b *= W_M^{16 j0 m1}
 //   pass C  butterfly (m0, m1):     y[m2]  = sum_j0 b[m0, m1; j0] W_R^{j0 m2}
-// W_n = exp(S 2 pi i / n), S = -1 forward, +1 backward.  Each thread keeps its 16
-// points of both polarisations in registers; the two re-orderings between
-// passes go through one shared-memory buffer of M float4 (X re, X im, Y re,
-// Y im).  The buffer indices carry an XOR swizzle on their low four bits that
-// makes every 16-byte access pattern of the passes free of bank conflicts.
+// W_n = exp(S 2 pi i / n), S = -1 forward, +1 backward.  Each thread keeps 16
+// points in registers, of both polarisations (float4 exchange elements:
+// X re, X im, Y re, Y im) or of one (float2 elements); the two re-orderings
+// between passes go through one shared-memory buffer of M elements.  The buffer
+// indices carry an XOR swizzle on their low four bits that makes every access
+// pattern of the passes free of bank conflicts (16-byte elements per
+// quarter-warp, 8-byte elements per half-warp).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -118,10 +120,52 @@ template <int R> struct Fft3 {
     static constexpr int T = 16 * R;
     static constexpr int NTA = 15 * T;  // pass-A twiddles W_M^{t m0}, m0 = 1..15, layout [m0-1][t]
     static constexpr int NTB = 15 * R;  // pass-B twiddles W_M^{16 j0 m1}, m1 = 1..15, layout [m1-1][j0]
-    static constexpr int GB = R >= 8 ? 1 : 8 / R;
+    static constexpr int GB = R >= 8 ? 1 : 8 / R;   // pass-B write swizzle step, 16-byte elements
+    static constexpr int GB1 = 16 / R;              // the same for 8-byte elements
 
     __device__ __forceinline__ static int ex1(int m0, int t) { return m0 * T + (t ^ ((m0 * R) & 15)); }
     __device__ __forceinline__ static int ex2(int j0, int beta) { return j0 * 256 + (beta ^ (j0 * GB)); }
+    __device__ __forceinline__ static int ex2s(int j0, int beta) { return j0 * 256 + (beta ^ (j0 * GB1)); }
+
+    // ---- one polarisation per thread (float2 exchange) ----
+    template <int S>
+    __device__ __forceinline__ static void pass_a1(float2 *x, float2 *ex, const float2 *ta, int t)
+    {
+        dft16<S>(x);
+        #pragma unroll
+        for (int m0 = 1; m0 < 16; m0++) x[m0] = cmul(x[m0], ta[(m0 - 1) * T + t]);
+        #pragma unroll
+        for (int m0 = 0; m0 < 16; m0++) ex[ex1(m0, t)] = x[m0];
+    }
+
+    template <int S>
+    __device__ __forceinline__ static void pass_b1(float2 *x, float2 *ex, const float2 *tb, int t)
+    {
+        const int m0 = t / R, j0 = t % R;
+        #pragma unroll
+        for (int j1 = 0; j1 < 16; j1++) x[j1] = ex[ex1(m0, j1 * R + j0)];
+        __syncthreads();
+        dft16<S>(x);
+        #pragma unroll
+        for (int m1 = 1; m1 < 16; m1++) x[m1] = cmul(x[m1], tb[(m1 - 1) * R + j0]);
+        #pragma unroll
+        for (int m1 = 0; m1 < 16; m1++) ex[ex2s(j0, m0 + 16 * m1)] = x[m1];
+    }
+
+    template <int S, class Emit>
+    __device__ __forceinline__ static void pass_c1(const float2 *ex, int t, Emit &&emit)
+    {
+        #pragma unroll
+        for (int i = 0; i < 16 / R; i++) {
+            const int beta = t + T * i;
+            float2 x[R];
+            #pragma unroll
+            for (int j0 = 0; j0 < R; j0++) x[j0] = ex[ex2s(j0, beta)];
+            dft_r<R, S>(x);
+            #pragma unroll
+            for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2]);
+        }
+    }
 
     // x, y: the 16 points x[j2 T + t] (j2 = 0..15) of each polarisation.  Leaves
     // pass-A results in ex.  Caller synchronises before pass_b.

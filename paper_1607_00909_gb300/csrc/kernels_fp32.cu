@@ -15,10 +15,11 @@
 // DM stage (Sec. 3: "complex multiplication with transfer function", "swap
 // halves per channel", "backward FFT", "transpose, unpad and detect"), fused in
 // k_dedisperse: one CTA per (DM tile, subband, segment, channel) keeps the
-// channel's M spectral bins of both polarisations in shared memory and, for
-// each DM of its tile, multiplies them by the chirp, runs the M-point backward
-// FFT, forms |X|^2 + |Y|^2, drops nd/2 samples at each edge, sums nint samples
-// and stores the filterbank row segment.  The per-channel swap of halves is a
+// channel's M spectral bins of both polarisations in registers (one
+// polarisation per half of the CTA) and, for each DM of its tile, multiplies
+// them by the chirp, runs the M-point backward FFT, forms |X|^2 + |Y|^2, drops
+// nd/2 samples at each edge, sums nint samples and stores the filterbank row
+// segment.  The per-channel swap of halves is a
 // factor (-1)^m on the time series, which the detection removes, so it is not
 // performed.  Spectra never leave the chip between chirp and detection.
 //
@@ -120,26 +121,32 @@ __global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ sp
 }
 
 // ---------------------------------------------------------------------------
-// UNIFORM: phase table holds (a, b) per bin for the tile; otherwise it holds
-// K per bin as double and the DM values come from dm_list.
+// One CTA of 2T threads per (DM tile, subband, segment, channel): threads
+// [0, T) carry polarisation X, [T, 2T) polarisation Y.  Each thread keeps its
+// 16 spectral bins of its polarisation in registers for the whole DM tile.
+// Shared memory holds the phase words of the channel's M bins, the twiddles,
+// one exchange buffer per polarisation and one detected-power row per
+// polarisation.
+// UNIFORM: the phase table holds (a, b) per bin for the tile; otherwise it
+// holds K per bin as double and the DM values come from dm_list.
 template <int R, bool UNIFORM>
-__global__ void __launch_bounds__(16 * R)
+__global__ void __launch_bounds__(32 * R, 16 / R)
 k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
              const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
              float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
              int nint, int64_t nout, float scale)
 {
     using F = Fft3<R>;
-    constexpr int M = F::M, T = F::T;
+    constexpr int M = F::M, T = F::T, NT = 2 * T;
     extern __shared__ float4 smem[];
-    float4 *xs = smem;                                    // M spectral bins, both pols
-    float4 *ex = xs + M;                                  // exchange buffer
-    uint2 *ph = reinterpret_cast<uint2 *>(ex + M);        // M phase words (a, b) or K as double
+    float2 *ex = reinterpret_cast<float2 *>(smem);        // [2][M] exchange buffers
+    uint2 *ph = reinterpret_cast<uint2 *>(ex + 2 * M);   // M phase words (a, b) or K as double
     float2 *ta = reinterpret_cast<float2 *>(ph + M);
     float2 *tb = ta + F::NTA;
-    float *ib = reinterpret_cast<float *>(tb + F::NTB);   // M detected powers
+    float *ib = reinterpret_cast<float *>(tb + F::NTB);  // [2][M] detected powers
 
-    const int t = threadIdx.x;
+    const int tid = threadIdx.x;
+    const int pol = tid / T, t = tid % T;
     int64_t item = blockIdx.x;
     const int c = (int)(item % nchan); item /= nchan;
     const int kk = (int)(item % kc); item /= kc;
@@ -149,31 +156,40 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
     const int ndt = min(dm_tile, ndm - dm0);
 
     const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * M;
-    for (int i = t; i < M; i += T) xs[i] = src[i];
+    float2 xr[16];
+    #pragma unroll
+    for (int j2 = 0; j2 < 16; j2++) {
+        float4 v = __ldg(src + j2 * T + t);
+        xr[j2] = pol ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+    }
     if constexpr (UNIFORM) {
         const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * M + (int64_t)c * M;
-        for (int i = t; i < M; i += T) ph[i] = p[i];
+        for (int i = tid; i < M; i += NT) ph[i] = p[i];
     } else {
         const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * M);
-        for (int i = t; i < M; i += T) ph[i] = p[i];
+        for (int i = tid; i < M; i += NT) ph[i] = p[i];
     }
-    for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
-    for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
+    for (int i = tid; i < F::NTA; i += NT) ta[i] = tw_a[i];
+    for (int i = tid; i < F::NTB; i += NT) tb[i] = tw_b[i];
     __syncthreads();
 
+    float2 *exp_ = ex + pol * M;
+    float *ibp = ib + pol * M;
     const int half = nd / 2;
     const int seglen = (M - nd) / nint;
     const int64_t rows = (int64_t)nsub * nchan;
     const int64_t obase = (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+    // conflict-free integration: lane l starts its nint-sample sum at a rotated offset
+    const bool pow2 = (nint & (nint - 1)) == 0 && nint <= 32;
+    const int rot = pow2 ? (((tid & 31) * nint) >> 5) : 0;
 
     for (int d = 0; d < ndt; d++) {
-        float2 x[16], y[16];
+        float2 x[16];
         double dmv = 0.0;
         if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
         #pragma unroll
         for (int j2 = 0; j2 < 16; j2++) {
             const int j = j2 * T + t;
-            float4 v = xs[j];
             float sn, cs;
             if constexpr (UNIFORM) {
                 uint2 ab = ph[j];
@@ -185,22 +201,27 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
                 cyc -= rint(cyc);
                 __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
             }
-            x[j2] = make_float2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
-            y[j2] = make_float2(v.z * cs - v.w * sn, v.z * sn + v.w * cs);
+            x[j2] = make_float2(xr[j2].x * cs - xr[j2].y * sn, xr[j2].x * sn + xr[j2].y * cs);
         }
-        F::template pass_a<+1>(x, y, ex, ta, t);
+        F::template pass_a1<+1>(x, exp_, ta, t);
         __syncthreads();
-        F::template pass_b<+1>(x, y, ex, tb, t);
+        F::template pass_b1<+1>(x, exp_, tb, t);
         __syncthreads();
-        F::template pass_c<+1>(ex, t, [&](int m, float2 a, float2 b) {
-            ib[m] = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(b.x, b.x, b.y * b.y)));
-        });
+        F::template pass_c1<+1>(exp_, t, [&](int m, float2 a) { ibp[m] = fmaf(a.x, a.x, a.y * a.y); });
         __syncthreads();
         float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
-        for (int u = t; u < seglen; u += T) {
-            const float *p = ib + half + u * nint;
+        for (int u = tid; u < seglen; u += NT) {
+            const float *px = ib + half + u * nint;
+            const float *py = px + M;
             float acc = 0.f;
-            for (int q = 0; q < nint; q++) acc += p[q];
+            if (pow2) {
+                for (int q = 0; q < nint; q++) {
+                    const int qq = (q + rot) & (nint - 1);
+                    acc += px[qq] + py[qq];
+                }
+            } else {
+                for (int q = 0; q < nint; q++) acc += px[q] + py[q];
+            }
             orow[u] = acc * scale;
         }
     }
@@ -213,7 +234,7 @@ template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>:
 template <int R> static size_t smem_dedisp()
 {
     using F = Fft3<R>;
-    return sizeof(float4) * 2 * F::M + sizeof(uint2) * F::M + sizeof(float2) * (F::NTA + F::NTB) + sizeof(float) * F::M;
+    return sizeof(float2) * 2 * F::M + sizeof(uint2) * F::M + sizeof(float2) * (F::NTA + F::NTB) + sizeof(float) * 2 * F::M;
 }
 
 template <int R> static cudaError_t set_attrs()
@@ -287,7 +308,7 @@ template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStre
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
-    k_dedisperse<R, U><<<(unsigned)nblk, Fft3<R>::T, smem_dedisp<R>(), st>>>(
+    k_dedisperse<R, U><<<(unsigned)nblk, 2 * Fft3<R>::T, smem_dedisp<R>(), st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
         a.nd, a.nint, a.nout, a.scale);
 }
