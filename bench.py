@@ -174,7 +174,7 @@ def reference_arm(args, w):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels_fp32.cu", "fft_core.cuh"):
+    for f in ("kernels_fp32.cu", "kernels_tc.cu", "fft_core.cuh", "tc_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_1607_00909_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -185,8 +185,69 @@ def kernel_source_hash():
 # source whose hash is recorded; null otherwise.
 NCU_TRAFFIC = {
     # 8-subband workload, one launch: 547.6 MB read + 2075.5 MB written for 4.253e9 units
-    "d471ae82b8c71f17": 0.6168,
+    "d471ae82b8c71f17:fp32": 0.6168,
 }
+
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        MEASURED = json.load(_f)
+except (OSError, ValueError):
+    MEASURED = {}
+
+
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+DTYPE = {"fp32": "f32", "fp16": "f16 (FP32 accumulate)", "bf16": "bf16 hi/lo (FP32 accumulate)"}
+
+
+def sampled_error(w, x, out, info, ntile=8, seed=5):
+    """max |gpu - oracle| / mean(oracle) and the RMS ratio on ntile random
+    (subband, segment, DM) tiles of this run's output."""
+    import oracle
+    g = np.random.default_rng(seed)
+    sub = g.integers(0, w.nsub, ntile)
+    seg = g.integers(0, info["nseg"], ntile)
+    dmi = g.integers(0, len(w.dms), ntile)
+    o = oracle.tiles(x, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin, info["nd"], sub, seg, dmi)
+    L = (info["mbin"] - info["nd"]) // w.nint
+    gt = np.stack([out[dmi[t], sub[t] * w.nchan:(sub[t] + 1) * w.nchan, seg[t] * L:(seg[t] + 1) * L]
+                   .cpu().numpy().astype(np.float64) for t in range(ntile)])
+    d = gt - o
+    return {"rel_max": float(np.max(np.abs(d)) / np.mean(o)),
+            "rel_rms": float(np.linalg.norm(d) / np.linalg.norm(o)), "tiles": ntile}
+
+
+def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
+    """Plan one precision form, warm up, time args.steps executes; returns a dict."""
+    import torch
+    import torch.distributed as dist
+    plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, precision=PREC[prec])
+    info = plan.info
+    st = stream.cuda_stream
+    for _ in range(args.warmup):
+        plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
+    torch.cuda.synchronize(dev)
+    plan.device_status()
+    cdmt.cdmt_set_timing(plan.handle, True)
+    cdmt.cdmt_stage_times(plan.handle)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    plan.device_status()
+    ms = ev0.elapsed_time(ev1)
+    (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
+    cdmt.cdmt_set_timing(plan.handle, False)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return {"plan": plan, "info": info, "ms_max": ms_max, "fwd_ms": fwd_ms, "dd_ms": dd_ms, "fwd_n": fwd_n,
+            "dd_n": dd_n, "value": world * info["units"] * args.steps / (ms_max / 1e3) / 1e9}
 
 
 def gpu_arm(args, w):
@@ -207,72 +268,79 @@ def gpu_arm(args, w):
         if world > 1:
             dist.barrier()
 
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    head = forms[-1]
     log(f"rank {rank}: generating {w.name} ...")
     t0 = time.perf_counter()
     x = w.voltages(threads=16, beam=rank)
     log(f"rank {rank}: inputs ready in {time.perf_counter() - t0:.1f}s ({x.nbytes / 1e9:.2f} GB)")
-    plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
-    info = plan.info
     xin = torch.from_numpy(x).to(dev)
-    out = torch.empty(plan.out_shape(), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    st = stream.cuda_stream
-
-    for _ in range(args.warmup):
-        plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
-    torch.cuda.synchronize(dev)
-    cdmt.cdmt_set_timing(plan.handle, True)
-    cdmt.cdmt_stage_times(plan.handle)
-
     props = torch.cuda.get_device_properties(dev)
     bus = None
     try:
         bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
     except AttributeError:
         pass
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(bus) as clk:
-        barrier()
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            plan.execute(xin.data_ptr(), out.data_ptr(), 0, st)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-    clocks = clk.summary()
-    ms = ev0.elapsed_time(ev1)
-    (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
-    cdmt.cdmt_set_timing(plan.handle, False)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    units = info["units"]
-    value = world * units * args.steps / (ms_max / 1e3) / 1e9
-    launches_per_step = (fwd_n + dd_n) // max(1, args.steps)
 
-    # ---- roofline of the dominant kernel (dedispersion: chirp, backward FFTs, detect, integrate)
+    results = {}
+    out = None
+    clocks = None
+    for f in forms:
+        if out is None:
+            probe = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
+            out = torch.empty(probe.out_shape(), dtype=torch.float32, device=dev)
+            probe.close()
+        if f == head:
+            with ClockSampler(bus) as clk:
+                r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world)
+            clocks = clk.summary()
+        else:
+            r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world)
+        if rank == 0 and not args.no_error:
+            r["error"] = sampled_error(w, x, out, r["info"])
+        results[f] = r
+        if f != head:
+            r["plan"].close()
+        log(f"rank {rank}: {f}: {r['value']:.2f} {UNIT}, {r['ms_max'] / args.steps:.2f} ms/step, "
+            f"error {r.get('error')}")
+
+    R = results[head]
+    plan, info = R["plan"], R["info"]
+    units = info["units"]
+
+    # ---- roofline of the dominant kernel of the headline form
     nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
-    flops_per_unit = 10.0 * nbin * np.log2(mbin) / info["nvalid"]       # 2 pols x n_c x 5 M log2 M per segment
-    flops_per_launch = flops_per_unit * units
-    dd_avg_s = dd_ms / max(1, dd_n) / 1e3
-    achieved = flops_per_launch / dd_avg_s / 1e12
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    traffic = None
-    tr = NCU_TRAFFIC.get(kernel_source_hash())
-    if tr:
-        traffic = tr * units
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_dedisperse", "kernel_ms_per_launch": dd_avg_s * 1e3,
-                "share_of_step": dd_ms / max(1e-9, dd_ms + fwd_ms),
-                "flops_per_unit": flops_per_unit,
-                "peak_basis": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    dd_avg_s = R["dd_ms"] / max(1, R["dd_n"]) / 1e3
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fft_flops_unit = 10.0 * nbin * np.log2(mbin) / info["nvalid"]   # 2 pols x n_c x 5 M log2 M per segment
+    if head == "fp32":
+        achieved = fft_flops_unit * units / dd_avg_s / 1e12
+        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "kernel": "k_dedisperse", "work": "nominal FFT flops 10 N log2(M) / S per unit",
+                    "flops_per_unit": fft_flops_unit,
+                    "peak_basis": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    else:
+        # the tensor-core GEMM work actually issued: 2 passes x 128 rows x 128 x 128 x 2 flops per (channel, DM)
+        # (x3 for the BF16 hi/lo products), per unit = that x n_c / S
+        mult = 3 if head == "bf16" else 1
+        tc_flops_unit = mult * 2 * 128 * 128 * 128 * 2 * info["nchan"] / info["nvalid"]
+        achieved = tc_flops_unit * units / dd_avg_s / 1e12
+        peak = MEASURED.get("bf16_tflops_sustained") or 1703.7
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "kernel": "k_dedisperse_tc", "work": "tensor-core GEMM flops issued (DFT-64 as real 128x128 GEMMs)",
+                    "flops_per_unit": tc_flops_unit,
+                    "nominal_fft_tflops": fft_flops_unit * units / dd_avg_s / 1e12,
+                    "peak_basis": "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); FP16 dense rate equals BF16"}
+    tr = NCU_TRAFFIC.get(kernel_source_hash() + ":" + head)
+    roofline.update({"traffic": tr * units if tr else None, "kernel_ms_per_launch": dd_avg_s * 1e3,
+                     "share_of_step": R["dd_ms"] / max(1e-9, R["dd_ms"] + R["fwd_ms"])})
 
     # ---- end to end through the host-memory entry point
     e2e = None
     if not args.no_e2e:
+        st = stream.cuda_stream
         hin = torch.from_numpy(x).pin_memory()
         hout = torch.empty(plan.out_shape(), dtype=torch.float32, pin_memory=True)
         plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)   # warm-up (allocates staging)
@@ -284,6 +352,7 @@ def gpu_arm(args, w):
             plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)
         torch.cuda.synchronize(dev)
         e_s = time.perf_counter() - e0
+        plan.device_status()
         te = torch.tensor([e_s], device=dev, dtype=torch.float64)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -302,14 +371,19 @@ def gpu_arm(args, w):
 
     if rank == 0:
         cfg = describe(w, info)
-        cfg.update({"l2": f"inputs ({x.nbytes / 1e9:.2f} GB) larger than L2; no flush", "precision": "fp32",
+        cfg.update({"l2": f"inputs ({x.nbytes / 1e9:.2f} GB) larger than L2; no flush", "precision": head,
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU"})
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        launches = (R["fwd_n"] + R["dd_n"])
+        line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": R["ms_max"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": int(launches_per_step * args.steps),
-                "stage_ms_per_step": {"forward": fwd_ms / args.steps, "dedisperse": dd_ms / args.steps}}
+                "gpu_launches": int(launches),
+                "error_vs_oracle": R.get("error"),
+                "forms": {f: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
+                              "dedisperse_ms_per_step": r["dd_ms"] / args.steps,
+                              "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error")}
+                          for f, r in results.items()}}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -327,6 +401,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
+    ap.add_argument("--forms", default="fp32,fp16",
+                    help="precision forms to time, comma-separated (fp32, fp16, bf16); the last is the headline")
+    ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

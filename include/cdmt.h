@@ -55,7 +55,9 @@ enum cdmt_status {
 };
 
 enum cdmt_precision {
-    CDMT_PREC_FP32 = 0 /* FFT stages on the FP32 pipes */
+    CDMT_PREC_FP32 = 0, /* every FFT stage on the FP32 pipes */
+    CDMT_PREC_FP16 = 1, /* per-DM backward FFT as FP16 DFT-64 GEMMs on the tensor cores, FP32 accumulate */
+    CDMT_PREC_BF16 = 2  /* the same with BF16 operands split into hi + lo parts (3 MMAs per step) */
 };
 
 enum cdmt_in_dtype {
@@ -120,7 +122,8 @@ typedef struct cdmt_info {
  *   nchan         channels per subband n_c, a power of two 2..32
  *   nint          output integration factor, >= 1
  * Errors: CDMT_EINVAL (bad argument, N_bin <= n_d n_c, nsamp < N_bin),
- *         CDMT_ENOTSUP (M_bin outside 512..4096), CDMT_ENOMEM, CDMT_ECUDA.
+ *         CDMT_ENOTSUP (M_bin outside 512..4096; tensor-core precisions need
+ *         M_bin = 4096), CDMT_ENOMEM, CDMT_ECUDA.
  * Allocates device memory (tables and workspace); the plan owns all of it.
  */
 int cdmt_plan(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz,
@@ -174,6 +177,12 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  */
 int cdmt_execute_host(cdmt_plan_t plan, const void *h_in, float *h_out, const float *h_scale,
                       void *cuda_stream);
+
+/* cdmt_device_status - wait for the plan's device work and report whether
+ * any tensor-core wait in it gave up (CDMT_ETIMEOUT; its outputs are then
+ * incomplete).  The flag is cleared.  Returns CDMT_OK otherwise, CDMT_ECUDA on
+ * a CUDA error, CDMT_EINVAL for a NULL plan. */
+int cdmt_device_status(cdmt_plan_t plan);
 
 /* cdmt_set_timing - when on != 0, later executes record CUDA events on their
  * stream around the forward stage (Sec. 3 "forward FFT" and "swap halves per

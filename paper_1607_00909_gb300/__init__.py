@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcdmt.so")
 
 CDMT_OK, CDMT_EINVAL, CDMT_ENOMEM, CDMT_ECUDA, CDMT_ETIMEOUT, CDMT_EBUDGET, CDMT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-CDMT_PREC_FP32 = 0
+CDMT_PREC_FP32, CDMT_PREC_FP16, CDMT_PREC_BF16 = 0, 1, 2
 CDMT_IN_C64, CDMT_IN_I8 = 0, 1
 
 
@@ -62,13 +62,14 @@ def _load():
     lib.cdmt_execute_host.argtypes = [P, P, P, P, P]
     lib.cdmt_destroy.argtypes = [P]
     lib.cdmt_set_timing.argtypes = [P, ctypes.c_int]
+    lib.cdmt_device_status.argtypes = [P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_strerror.argtypes = [ctypes.c_int]
     lib.cdmt_strerror.restype = ctypes.c_char_p
     lib.cdmt_last_error.argtypes = [P]
     lib.cdmt_last_error.restype = ctypes.c_char_p
     for f in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
-              "cdmt_set_timing", "cdmt_stage_times"):
+              "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -76,7 +77,7 @@ def _load():
 _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
-            "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times")
+            "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status")
 
 
 def lib():
@@ -129,6 +130,11 @@ def cdmt_destroy(plan):
     _check(_lib.cdmt_destroy(plan))
 
 
+def cdmt_device_status(plan):
+    """Raise CdmtError(CDMT_ETIMEOUT) if a tensor-core wait of the plan gave up."""
+    _check(_lib.cdmt_device_status(plan), plan)
+
+
 def cdmt_set_timing(plan, on: bool):
     _check(_lib.cdmt_set_timing(plan, 1 if on else 0), plan)
 
@@ -158,6 +164,9 @@ class Plan:
 
     def execute_host(self, h_in: int, h_out: int, h_scale: int = 0, stream: int = 0):
         cdmt_execute_host(self.handle, h_in, h_out, h_scale, stream)
+
+    def device_status(self):
+        cdmt_device_status(self.handle)
 
     def out_shape(self):
         i = self.info

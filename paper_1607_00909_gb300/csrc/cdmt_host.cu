@@ -12,6 +12,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/cdmt.h"
 #include "cdmt_internal.h"
 
@@ -50,6 +53,10 @@ struct cdmt_plan_s {
     uint2 *nco = nullptr;
     double *ktab = nullptr, *d_dm = nullptr;
     float4 *spec = nullptr;
+    // tensor-core form
+    uint4 *tc_bmat = nullptr;
+    float2 *tc_twq = nullptr;
+    int *d_status = nullptr;
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0;
@@ -176,6 +183,41 @@ __global__ void k_k_table(double *kt, double f_centre, double bw, int nsub, int 
         kt[q] = chirp_k(f_centre, bw, nsub, nchan, nbin, (int)(q / nbin), q % nbin);
 }
 
+// 128 x 128 real form of the backward 64-point DFT (W = exp(+2 pi i / 64)) in
+// the K-major canonical layout (SBO 2048 B, LBO 128 B): output n = 2 m + (re, im),
+// input k = 2 j + (re, im).  ab = 0: FP16; ab = 1: BF16 hi at [0, 16384) and
+// the BF16 rounding residue (lo) at [16384, 32768) (16-bit elements).
+__global__ void k_tc_bmat(uint16_t *out, int ab)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * 128; idx += gridDim.x * blockDim.x) {
+        const int n = idx / 128, k = idx % 128;
+        const int m = n >> 1, ro = n & 1, j = k >> 1, ri = k & 1;
+        double sn, cs;
+        sincospi(2.0 * (double)((j * m) % 64) / 64.0, &sn, &cs);
+        const double v = ro == 0 ? (ri == 0 ? cs : -sn) : (ri == 0 ? sn : cs);
+        const int off = (n / 8) * 1024 + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+        if (ab == 0) {
+            out[off] = __half_as_ushort(__double2half(v));
+        } else {
+            const __nv_bfloat16 hi = __double2bfloat16(v);
+            const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+            out[off] = __bfloat16_as_ushort(hi);
+            out[16384 + off] = __bfloat16_as_ushort(lo);
+        }
+    }
+}
+
+// W_4096^{j_lo m0} = exp(+2 pi i j_lo m0 / 4096) at [m0][j_lo]
+__global__ void k_tc_twq(float2 *tw)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4096) return;
+    const int m0 = idx / 64, jlo = idx % 64;
+    double sn, cs;
+    sincospi(2.0 * (double)(jlo * m0) / 4096.0, &sn, &cs);
+    tw[idx] = make_float2((float)cs, (float)sn);
+}
+
 template <class T> int dalloc(cdmt_plan_s *p, T **ptr, size_t count)
 {
     size_t b = sizeof(T) * count;
@@ -198,7 +240,8 @@ void release(cdmt_plan_s *p)
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {p->tw_n, p->tw_af, p->tw_bf, p->tw_ai, p->tw_bi, p->nco, p->ktab, p->d_dm, p->spec};
+    void *ptrs[] = {p->tw_n, p->tw_af, p->tw_bf, p->tw_ai, p->tw_bi, p->nco, p->ktab, p->d_dm, p->spec,
+                    p->tc_bmat, p->tc_twq, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {
@@ -250,6 +293,32 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
     if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
     CK(p, fp32_forward(fa, st));
     if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    if (p->precision != CDMT_PREC_FP32) {
+        TcArgs ta{};
+        ta.spec = p->spec;
+        ta.nco = p->nco;
+        ta.ktab = p->ktab;
+        ta.dm_list = p->d_dm;
+        ta.bmat = p->tc_bmat;
+        ta.twq = p->tc_twq;
+        ta.out = out;
+        ta.status = p->d_status;
+        ta.k0 = out_k0;
+        ta.nout = out_stride;
+        ta.nsub = p->nsub;
+        ta.kc = kc;
+        ta.nchan = p->nchan;
+        ta.ndm = p->ndm;
+        ta.dm_tile = p->dm_tile;
+        ta.nd = (int)p->nd;
+        ta.nint = p->nint;
+        ta.ab = p->precision == CDMT_PREC_BF16 ? 1 : 0;
+        ta.uniform = p->uniform;
+        ta.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
+        CK(p, tc_dedisperse(ta, st));
+        if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+        return CDMT_OK;
+    }
     DedispArgs da{};
     da.spec = p->spec;
     da.nco = p->nco;
@@ -321,7 +390,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         if (!std::isfinite(dm_list[i])) return fail(nullptr, CDMT_EINVAL, "DM %d is not finite", i);
     const double band_lo = f_centre_mhz - 0.5 * nsub * bw_sub_mhz;
     if (!(band_lo > 0)) return fail(nullptr, CDMT_EINVAL, "lowest frequency %.6g MHz must be > 0", band_lo);
-    if (o.precision != CDMT_PREC_FP32) return fail(nullptr, CDMT_ENOTSUP, "precision %d not available", o.precision);
+    if (o.precision != CDMT_PREC_FP32 && o.precision != CDMT_PREC_FP16 && o.precision != CDMT_PREC_BF16)
+        return fail(nullptr, CDMT_ENOTSUP, "precision %d not available", o.precision);
     if (o.in_dtype != CDMT_IN_C64) return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
 
     auto *p = new cdmt_plan_s();
@@ -368,6 +438,10 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)p->mbin);
     }
     p->r = (int)(p->mbin / 256);
+    if (p->precision != CDMT_PREC_FP32 && p->mbin != 4096) {
+        delete p;
+        return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need M_bin = 4096 (got %lld)", (long long)p->mbin);
+    }
     if (nsamp < nbin) {
         delete p;
         return fail(nullptr, CDMT_EINVAL, "nsamp (%lld) < N_bin (%lld)", (long long)nsamp, (long long)nbin);
@@ -412,6 +486,7 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
 
     int rc;
     cudaError_t e = fp32_prepare(p->r);
+    if (e == cudaSuccess && p->precision != CDMT_PREC_FP32) e = tc_prepare(p->precision == CDMT_PREC_BF16 ? 1 : 0);
     if (e != cudaSuccess) {
         release(p);
         delete p;
@@ -436,6 +511,11 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     if (p->uniform) TRY(dalloc(p, &p->nco, (size_t)p->ntile * nsub * nbin));
     else TRY(dalloc(p, &p->ktab, (size_t)nsub * nbin));
     TRY(dalloc(p, &p->spec, (size_t)p->seg_chunk * nsub * nbin));
+    TRY(dalloc(p, &p->d_status, 1));
+    if (p->precision != CDMT_PREC_FP32) {
+        TRY(dalloc(p, &p->tc_bmat, (size_t)(p->precision == CDMT_PREC_BF16 ? 4096 : 2048)));
+        TRY(dalloc(p, &p->tc_twq, (size_t)4096));
+    }
 
     std::vector<double> tile0(p->ntile);
     for (int t = 0; t < p->ntile; t++) tile0[t] = dm_list[t * p->dm_tile];
@@ -452,6 +532,11 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         }                                                                                  \
     } while (0)
     TRYC(cudaMemcpy(p->d_dm, dm_list, sizeof(double) * ndm, cudaMemcpyHostToDevice));
+    TRYC(cudaMemset(p->d_status, 0, sizeof(int)));
+    if (p->precision != CDMT_PREC_FP32) {
+        k_tc_bmat<<<64, 256>>>(reinterpret_cast<uint16_t *>(p->tc_bmat), p->precision == CDMT_PREC_BF16 ? 1 : 0);
+        k_tc_twq<<<16, 256>>>(p->tc_twq);
+    }
     k_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256>>>(p->tw_n, nbin, -1);
     k_twiddle_passes<<<64, 256>>>(p->tw_af, p->tw_bf, p->r, -1);
     k_twiddle_passes<<<64, 256>>>(p->tw_ai, p->tw_bi, p->r, +1);
@@ -573,6 +658,20 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     CK(p, cudaStreamSynchronize(p->s_d2h));
     CK(p, cudaStreamSynchronize(st));
     if (cur != p->device) cudaSetDevice(cur);
+    return CDMT_OK;
+}
+
+int cdmt_device_status(cdmt_plan_t p)
+{
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    int flag = 0;
+    CK(p, cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) CK(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    if (cur != p->device) cudaSetDevice(cur);
+    if (flag) return fail(p, CDMT_ETIMEOUT, "a tensor-core wait gave up; outputs of that execute are incomplete");
     return CDMT_OK;
 }
 

@@ -31,6 +31,26 @@ struct DedispArgs {
     float scale;
 };
 
+struct TcArgs {
+    const float4 *spec;
+    const uint2 *nco;
+    const double *ktab;
+    const double *dm_list;
+    const uint4 *bmat;    // 64-point DFT matrix in the K-major canonical layout (hi [, lo])
+    const float2 *twq;    // W_4096^{j_lo m0} at [m0][j_lo]
+    float *out;
+    int *status;          // set to 1 by a CTA whose tensor-core wait timed out
+    int64_t k0, nout;
+    int nsub, kc, nchan, ndm, dm_tile, nd, nint;
+    int ab;               // 0 FP16, 1 BF16 hi/lo
+    bool uniform;
+    float scale;
+};
+
+cudaError_t tc_prepare(int ab);
+size_t tc_smem(int ab);
+cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st);
+
 cudaError_t fp32_prepare(int r);
 size_t fp32_dedisp_smem(int r);
 cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st);

@@ -1,0 +1,381 @@
+// Tensor-core form of the DM stage (sm_103a tcgen05), for channels of M = 4096 bins.
+//
+// The backward M-point DFT of each channel is split as M = 64 x 64 (input
+// j = 64 j_hi + j_lo, output m = m0 + 64 m1):
+//   pass A  for every j_lo:  y[m0] = sum_j_hi x[64 j_hi + j_lo] W_64^{j_hi m0},  y *= W_4096^{j_lo m0}
+//   pass B  for every m0:    z[m1] = sum_j_lo y_j_lo[m0] W_64^{j_lo m1}
+// Each pass is one real GEMM on the tensor cores: 128 rows (64 groups x 2
+// polarisations) by K = 128 (64 complex inputs, real and imaginary parts
+// interleaved) by N = 128 (64 complex outputs), with the 128 x 128 real form of
+// the 64-point DFT matrix as operand B, half-precision operands and an FP32
+// accumulator in tensor memory.  Between the passes each thread reads its own
+// GEMM row from tensor memory, applies the W_4096 twiddles in FP32 and writes
+// the row as a K-column of the next operand (MN-major layout), so the
+// transposition costs only 16-byte shared-memory stores.
+//
+// The chirp (Eq. 1, conjugated) and the data scaling run in FP32 before the
+// rounding to half precision; the chirp phase comes from the same FP64-derived
+// fixed-point (phase, step) words as in the FP32 form.  Each CTA scales its
+// spectrum by a power of two so that every half-precision operand stays below
+// 2^15 whatever the signal; the scale is undone exactly on the output.
+//
+// Work split: one CTA per (DM tile, subband, segment, channel), 256 threads =
+// two warpgroups that take alternate DMs of the tile, each with its own operand
+// buffer, tensor-memory columns and mbarrier, so the tensor core works on one
+// warpgroup's GEMM while the other does its FP32 work.
+//
+// BF16 operands carry 8 mantissa bits, too few for the 2e-3 error target, so in
+// BF16 mode both the data and the DFT matrix are split into hi + lo parts and
+// each K-step issues three MMAs (hi*hi + lo*hi + hi*lo); the two warpgroups then
+// share the CTA's shared memory by running one DM at a time.
+#include "cdmt_internal.h"
+#include "fft_core.cuh"
+#include "tc_ptx.cuh"
+
+namespace cdmt {
+
+namespace {
+
+constexpr int kM = 4096;
+constexpr uint32_t kLboA = 128, kSboA = 2048;    // pass-A operand, K-major
+constexpr uint32_t kLboB = 2064, kSboB = 128;    // pass-B operand, MN-major; K-core stride padded by 16 B
+constexpr uint32_t kAbuf = 33024;                // >= 15 * 2064 + 2048 and >= 2 * 4096 floats
+constexpr uint32_t kBmat = 32768;                // one 128 x 128 half-precision DFT matrix
+constexpr uint32_t kWaitPolls = 1u << 26;          // backstop on polls
+constexpr uint64_t kWaitNs = 50ull * 1000 * 1000;  // a GEMM batch takes microseconds; give up after 50 ms
+constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;
+
+// shared-memory map
+template <int AB> struct TcLayout {
+    static constexpr uint32_t nb = AB ? 2 : 1;         // B matrices (hi, lo)
+    static constexpr uint32_t na = AB ? 2 : 1;         // operand planes per warpgroup (hi, lo)
+    static constexpr uint32_t nwgbuf = AB ? 1 : 2;     // BF16: one operand set shared by both warpgroups
+    static constexpr uint32_t off_b = 0;
+    static constexpr uint32_t off_x = off_b + nb * kBmat;
+    static constexpr uint32_t off_ph = off_x + 16 * kM;
+    static constexpr uint32_t off_a = off_ph + 8 * kM;
+    static constexpr uint32_t abytes = na * kAbuf;
+    static constexpr uint32_t off_misc = off_a + nwgbuf * abytes;
+    static constexpr uint32_t total = off_misc + 128;
+};
+
+__device__ __forceinline__ bool bar_and(int id, int count, bool v)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id), "r"(count)
+                 : "memory");
+    return r != 0;
+}
+
+template <int AB> __device__ __forceinline__ uint32_t pk(float lo, float hi)
+{
+    return AB ? tc::pack_bf16(lo, hi) : tc::pack_f16(lo, hi);
+}
+
+// hi part of a bf16 split: round to bf16 and back
+__device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__float_as_uint(__uint_as_float(tc::pack_bf16(x, 0.f) << 16))); }
+
+}  // namespace
+
+// AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
+template <bool UNIFORM, int AB>
+__global__ void __launch_bounds__(256, 1)
+k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
+                const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
+                float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
+                int dm_tile, int nd, int nint, int64_t nout, float scale_out)
+{
+    using L = TcLayout<AB>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *bm = smem + L::off_b;
+    float4 *xs = reinterpret_cast<float4 *>(smem + L::off_x);
+    uint2 *ph = reinterpret_cast<uint2 *>(smem + L::off_ph);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 16);
+    float *red = reinterpret_cast<float *>(smem + L::off_misc + 32);
+
+    const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2, t = tid & 127;
+    // once any CTA has given up on a tensor-core wait, the rest of the launch
+    // returns at once (one read, block-uniform decision)
+    if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
+    int64_t item = blockIdx.x;
+    const int c = (int)(item % nchan); item /= nchan;
+    const int kk = (int)(item % kc); item /= kc;
+    const int s = (int)(item % nsub); item /= nsub;
+    const int tile = (int)item;
+    const int dm0 = tile * dm_tile;
+    const int ndt = min(dm_tile, ndm - dm0);
+
+    // ---- stage the DFT matrix, the channel's spectrum and its phase words
+    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += 256) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
+    const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
+    float vmax = 0.f;
+    for (int i = tid; i < kM; i += 256) {
+        float4 v = __ldg(src + i);
+        xs[i] = v;
+        vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    if constexpr (UNIFORM) {
+        const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
+        for (int i = tid; i < kM; i += 256) ph[i] = p[i];
+    } else {
+        const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
+        for (int i = tid; i < kM; i += 256) ph[i] = p[i];
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((tid & 31) == 0) red[warp] = vmax;
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    float bmax = 0.f;
+    #pragma unroll
+    for (int w = 0; w < 8; w++) bmax = fmaxf(bmax, red[w]);
+    // power-of-two scale: |x| 2^e <= 512, so a 64-point pass stays below 2^15
+    int e = bmax > 0.f ? (int)floorf(log2f(512.f / bmax)) : 0;
+    e = max(-100, min(100, e));
+    const float xscale = ldexpf(1.f, e);
+    const float oscale = scale_out * ldexpf(1.f, -2 * e);
+    const uint32_t tmem = *tslot;
+
+    // BF16 mode runs one DM at a time through one operand set; FP16 overlaps two
+    constexpr int NPIPE = AB ? 1 : 2;
+    const int lane_sel = warp & 3;
+    const uint32_t lane_off = (uint32_t)(32 * lane_sel) << 16;
+    const int pipe = AB ? 0 : wg;
+    const uint32_t dcol = tmem + 128 * pipe;
+    uint8_t *ab = smem + L::off_a + (AB ? 0 : wg * L::abytes);
+    uint64_t *mb = &mbar[pipe];
+    const int bar_id = 1 + pipe;
+    const int nthr = AB ? 256 : 128;
+    const int q = AB ? tid : t;       // index within the group working on one DM
+
+    const int half = nd / 2;
+    const int seglen = (kM - nd) / nint;
+    const int64_t rows = (int64_t)nsub * nchan;
+    const int64_t obase = (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+    const bool pow2 = (nint & (nint - 1)) == 0 && nint <= 32;
+    const int rot = pow2 ? (((tid & 31) * nint) >> 5) : 0;
+    const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);
+    const uint32_t id_b = tc::idesc(128, 128, AB, 1, 0);
+    const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
+    uint32_t ok = 1;
+
+    for (int d = AB ? 0 : wg; d < ndt; d += NPIPE) {
+        // ---- chirp, scale, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
+        {
+            double dmv = 0.0;
+            if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
+            const int jlo = q & 63;
+            const int nq = AB ? 4 : 2;              // quarters / halves of j_hi per thread
+            const int part = q >> 6;
+            #pragma unroll 1
+            for (int c4 = 0; c4 < 16 / nq; c4++) {
+                uint32_t hx[4], hy[4], lx[4], ly[4];
+                #pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int jhi = (64 / nq) * part + 4 * c4 + i;
+                    const int j = jhi * 64 + jlo;
+                    float sn, cs;
+                    if constexpr (UNIFORM) {
+                        const uint2 w = ph[j];
+                        const int32_t p = (int32_t)(w.x + (uint32_t)d * w.y);
+                        __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
+                    } else {
+                        const double kj = __hiloint2double((int)ph[j].y, (int)ph[j].x);
+                        double cyc = dmv * kj;
+                        cyc -= rint(cyc);
+                        __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
+                    }
+                    cs *= xscale;
+                    sn *= xscale;
+                    const float4 v = xs[j];
+                    const float xr = v.x * cs - v.y * sn, xi = v.x * sn + v.y * cs;
+                    const float yr = v.z * cs - v.w * sn, yi = v.z * sn + v.w * cs;
+                    hx[i] = pk<AB>(xr, xi);
+                    hy[i] = pk<AB>(yr, yi);
+                    if constexpr (AB) {
+                        lx[i] = tc::pack_bf16(xr - bf16_round(xr), xi - bf16_round(xi));
+                        ly[i] = tc::pack_bf16(yr - bf16_round(yr), yi - bf16_round(yi));
+                    }
+                }
+                const int kcore = ((64 / nq) * part + 4 * c4) / 4;
+                const uint32_t ox = (uint32_t)(jlo / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
+                const uint32_t oy = (uint32_t)((64 + jlo) / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
+                *reinterpret_cast<uint4 *>(ab + ox) = make_uint4(hx[0], hx[1], hx[2], hx[3]);
+                *reinterpret_cast<uint4 *>(ab + oy) = make_uint4(hy[0], hy[1], hy[2], hy[3]);
+                if constexpr (AB) {
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + ox) = make_uint4(lx[0], lx[1], lx[2], lx[3]);
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + oy) = make_uint4(ly[0], ly[1], ly[2], ly[3]);
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        tc::bar(bar_id, nthr);
+        tc::fence_after();
+        if (q == 0) {
+            #pragma unroll 1
+            for (int ks = 0; ks < 8; ks++) {
+                const uint64_t bh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
+                tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboA), bh, id_a, ks > 0);
+                if constexpr (AB) {
+                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 256, kLboA, kSboA), bh, id_a, 1);
+                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboA),
+                            tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), id_a, 1);
+                }
+            }
+            tc::commit(mb);
+        }
+        ok = bar_and(bar_id, nthr, tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
+        if (!ok) break;
+        tc::fence_after();
+
+        // ---- pass-A rows -> twiddle -> pass-B operand (MN-major): row = pol * 64 + m0, k = 2 j_lo + (re, im)
+        if (!AB || tid < 128) {
+            const int pol = t >> 6, jlo = t & 63;
+            #pragma unroll 1
+            for (int cc = 0; cc < 4; cc++) {
+                float v[32];
+                tc::tmem_ld32(dcol + lane_off + 32 * cc, v);
+                float re[16], im[16];
+                #pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const float2 w = __ldg(twq + (16 * cc + i) * 64 + jlo);
+                    const float2 z = cmul(make_float2(v[2 * i], v[2 * i + 1]), w);
+                    re[i] = z.x;
+                    im[i] = z.y;
+                }
+                #pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    const uint32_t mcore = (uint32_t)(pol * 64 + 16 * cc + 8 * g) / 8;
+                    const uint32_t o = mcore * kSboB + (uint32_t)(2 * jlo / 8) * kLboB + (uint32_t)((2 * jlo) % 8) * 16;
+                    const float *r8 = re + 8 * g, *i8 = im + 8 * g;
+                    *reinterpret_cast<uint4 *>(ab + o) =
+                        make_uint4(pk<AB>(r8[0], r8[1]), pk<AB>(r8[2], r8[3]), pk<AB>(r8[4], r8[5]), pk<AB>(r8[6], r8[7]));
+                    *reinterpret_cast<uint4 *>(ab + o + 16) =
+                        make_uint4(pk<AB>(i8[0], i8[1]), pk<AB>(i8[2], i8[3]), pk<AB>(i8[4], i8[5]), pk<AB>(i8[6], i8[7]));
+                    if constexpr (AB) {
+                        float lr[8], li[8];
+                        #pragma unroll
+                        for (int z = 0; z < 8; z++) {
+                            lr[z] = r8[z] - bf16_round(r8[z]);
+                            li[z] = i8[z] - bf16_round(i8[z]);
+                        }
+                        *reinterpret_cast<uint4 *>(ab + kAbuf + o) = make_uint4(
+                            pk<1>(lr[0], lr[1]), pk<1>(lr[2], lr[3]), pk<1>(lr[4], lr[5]), pk<1>(lr[6], lr[7]));
+                        *reinterpret_cast<uint4 *>(ab + kAbuf + o + 16) = make_uint4(
+                            pk<1>(li[0], li[1]), pk<1>(li[2], li[3]), pk<1>(li[4], li[5]), pk<1>(li[6], li[7]));
+                    }
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        tc::bar(bar_id, nthr);
+        tc::fence_after();
+        if (q == 0) {
+            #pragma unroll 1
+            for (int ks = 0; ks < 8; ks++) {
+                const uint64_t bh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
+                tc::mma(dcol, tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB), bh, id_b, ks > 0);
+                if constexpr (AB) {
+                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), bh, id_b, 1);
+                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB),
+                            tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), id_b, 1);
+                }
+            }
+            tc::commit(mb);
+        }
+        ok = bar_and(bar_id, nthr, tc::mbar_wait(mb, 1, kWaitNs, kWaitPolls));
+        if (!ok) break;
+        tc::fence_after();
+
+        // ---- detect: row = pol * 64 + m0 holds z[m1], time sample m = m0 + 64 m1
+        float *ib = reinterpret_cast<float *>(ab);   // [2][4096], the operand is consumed
+        if (!AB || tid < 128) {
+            const int pol = t >> 6, m0 = t & 63;
+            #pragma unroll 1
+            for (int cc = 0; cc < 4; cc++) {
+                float v[32];
+                tc::tmem_ld32(dcol + lane_off + 32 * cc, v);
+                #pragma unroll
+                for (int i = 0; i < 16; i++)
+                    ib[pol * kM + m0 + 64 * (16 * cc + i)] = fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]);
+            }
+        }
+        tc::fence_before();
+        tc::bar(bar_id, nthr);
+        tc::fence_after();
+        float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
+        for (int u = q; u < seglen; u += nthr) {
+            const float *px = ib + half + u * nint;
+            const float *py = px + kM;
+            float acc = 0.f;
+            if (pow2) {
+                for (int qq = 0; qq < nint; qq++) {
+                    const int r = (qq + rot) & (nint - 1);
+                    acc += px[r] + py[r];
+                }
+            } else {
+                for (int qq = 0; qq < nint; qq++) acc += px[qq] + py[qq];
+            }
+            orow[u] = acc * oscale;
+        }
+        tc::bar(bar_id, nthr);
+    }
+    if (!ok && q == 0) atomicExch(status, 1);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+
+size_t tc_smem(int ab) { return ab ? TcLayout<1>::total : TcLayout<0>::total; }
+
+template <bool U, int AB> static cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(k_dedisperse_tc<U, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TcLayout<AB>::total);
+}
+
+cudaError_t tc_prepare(int ab)
+{
+    cudaError_t e = ab ? set_attr<true, 1>() : set_attr<true, 0>();
+    if (e != cudaSuccess) return e;
+    return ab ? set_attr<false, 1>() : set_attr<false, 0>();
+}
+
+template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
+{
+    const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
+    const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
+    k_dedisperse_tc<U, AB><<<(unsigned)nblk, 256, TcLayout<AB>::total, st>>>(
+        a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan, a.ndm,
+        a.dm_tile, a.nd, a.nint, a.nout, a.scale);
+}
+
+cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st)
+{
+    if (a.uniform) {
+        if (a.ab) launch<true, 1>(a, st);
+        else launch<true, 0>(a, st);
+    } else {
+        if (a.ab) launch<false, 1>(a, st);
+        else launch<false, 0>(a, st);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cdmt
