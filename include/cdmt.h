@@ -200,6 +200,42 @@ int cdmt_set_timing(cdmt_plan_t plan, int on);
  * Errors: CDMT_EINVAL (NULL plan or ms), CDMT_ECUDA. */
 int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
 
+/* Bytes of the device array that backs cdmt_execute_static (64 MiB). */
+#define CDMT_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/*
+ * cdmt_execute_static - cdmt_plan + cdmt_execute in one call that allocates no
+ * memory at all.  The paper has no counterpart: it serves callers that must not
+ * call cudaMalloc / cudaFree, for example because their device memory belongs
+ * to another framework's pool, or because a real-time loop cannot pay the
+ * device-wide synchronisation those calls imply.
+ *
+ * Computes the FP32-form filterbank of one input block (same kernels and
+ * results as a plan with precision CDMT_PREC_FP32, nbin and nd given) for the
+ * evenly spaced DM list dm_first + i * dm_step, i < ndm.  nd < 0 applies the
+ * overlap rule of Sec. 2.  d_in / d_out are the caller's DEVICE buffers in the
+ * layouts above (d_out: float32 [ndm][nsub*nchan][nout] with nout =
+ * nseg * (M - nd) / nint); enqueued on cuda_stream, asynchronous.
+ *
+ * All other memory it uses (twiddles, chirp-phase words, the forward spectrum
+ * of a chunk of segments) is one file-scope __device__ array of
+ * CDMT_STATIC_SCRATCH_BYTES, which every GPU that loads this part of the
+ * library keeps until the process exits.  Limit: about 24 * nsub * nbin bytes
+ * must fit in it (e.g. nsub <= 42 at nbin = 65536); larger problems return
+ * CDMT_EBUDGET with the sizes in cdmt_last_error(NULL), and need cdmt_plan.
+ * The first call on a device looks up the array's device address (and sets the
+ * kernels' shared-memory attributes) with that device current; make that first
+ * call before any stream capture.  Every call writes every scratch byte it
+ * later reads, so nothing carries over from a previous call, but all calls on a
+ * device share the one array: calls whose work overlaps on the GPU (different
+ * streams, or host threads racing) corrupt each other's results.
+ * Errors: CDMT_EINVAL, CDMT_ENOTSUP (M_bin outside 512..4096), CDMT_EBUDGET,
+ * CDMT_ECUDA; messages via cdmt_last_error(NULL).
+ */
+int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz, double bw_sub_mhz, double dm_first,
+                        double dm_step, int ndm, int nchan, int nint, int64_t nbin, int64_t nd, const void *d_in,
+                        float *d_out, void *cuda_stream);
+
 /* cdmt_destroy - free every resource of a plan (NULL is accepted).  Waits for
  * the plan's device work to finish first. */
 int cdmt_destroy(cdmt_plan_t plan);

@@ -63,13 +63,15 @@ def _load():
     lib.cdmt_destroy.argtypes = [P]
     lib.cdmt_set_timing.argtypes = [P, ctypes.c_int]
     lib.cdmt_device_status.argtypes = [P]
+    lib.cdmt_execute_static.argtypes = [ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_strerror.argtypes = [ctypes.c_int]
     lib.cdmt_strerror.restype = ctypes.c_char_p
     lib.cdmt_last_error.argtypes = [P]
     lib.cdmt_last_error.restype = ctypes.c_char_p
     for f in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
-              "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status"):
+              "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status", "cdmt_execute_static"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -77,7 +79,8 @@ def _load():
 _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
-            "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status")
+            "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
+            "cdmt_execute_static")
 
 
 def lib():
@@ -128,6 +131,15 @@ def cdmt_execute_host(plan, h_in: int, h_out: int, h_scale: int = 0, stream: int
 
 def cdmt_destroy(plan):
     _check(_lib.cdmt_destroy(plan))
+
+
+def cdmt_execute_static(nsub, nsamp, f_centre, bw_sub, dm_first, dm_step, ndm, nchan, nint, nbin, nd,
+                        d_in: int, d_out: int, stream: int = 0):
+    """The allocation-free entry point: filterbank of one block for the DMs
+    dm_first + i dm_step, using the library's fixed device scratch array."""
+    _check(_lib.cdmt_execute_static(int(nsub), int(nsamp), float(f_centre), float(bw_sub), float(dm_first),
+                                    float(dm_step), int(ndm), int(nchan), int(nint), int(nbin), int(nd),
+                                    d_in, d_out, stream or None))
 
 
 def cdmt_device_status(plan):

@@ -346,6 +346,11 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
 
 }  // namespace
 
+namespace cdmt {
+// lets other translation units of the library report an error before a plan exists
+void set_thread_error(const char *msg) { g_thread_error = msg; }
+}  // namespace cdmt
+
 extern "C" {
 
 const char *cdmt_strerror(int status)

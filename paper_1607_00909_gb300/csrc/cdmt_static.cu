@@ -1,0 +1,233 @@
+// cdmt_execute_static: the whole filterbank of one input block without any
+// device-memory allocation, for callers that must not call cudaMalloc.
+//
+// Who needs it: a caller whose device memory belongs to another framework's
+// pool (so a cudaMalloc here would compete with, or fail under, that pool), or
+// a real-time loop that cannot afford the device-wide synchronisation and
+// latency of cudaMalloc / cudaFree between blocks.  Such a caller still owns
+// and passes the input and the output; every other byte this call touches
+// (twiddle tables, chirp-phase words, the forward spectrum of a chunk of
+// segments) lives in one file-scope __device__ array of
+// CDMT_STATIC_SCRATCH_BYTES, which the CUDA runtime reserves on each GPU that
+// loads this part of the library and keeps until the process exits.
+//
+// The computation is the same as cdmt_plan + cdmt_execute in the FP32 form with
+// an evenly spaced DM list (the same kernels; only the location of the scratch
+// differs).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/cdmt.h"
+#include "cdmt_internal.h"
+
+namespace cdmt {
+
+void set_thread_error(const char *msg);
+
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[CDMT_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 128;
+void *g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device
+std::mutex g_scratch_mu;
+
+constexpr double kD = 4.148808e3;  // MHz^2 pc^-1 cm^3 s
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_thread_error(buf);
+    return code;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// tw[k] = exp(sign 2 pi i k / n)
+__global__ void k_static_twiddle_line(float2 *tw, int64_t n, int sign)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = make_float2((float)c, (float)(sign * s));
+}
+
+// the three-pass FFT's twiddles: W_M^{t m0} at [m0-1][t], then W_M^{16 j0 m1} at [m1-1][j0]
+__global__ void k_static_twiddle_passes(float2 *tw, int r, int sign)
+{
+    const int m = 256 * r, tn = 16 * r;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 15 * (tn + r); i += gridDim.x * blockDim.x) {
+        int64_t p;
+        if (i < 15 * tn) p = (int64_t)(i % tn) * (i / tn + 1);
+        else p = 16LL * ((i - 15 * tn) % r) * ((i - 15 * tn) / r + 1);
+        double s, c;
+        sincospi(2.0 * (double)(p % m) / (double)m, &s, &c);
+        tw[i] = make_float2((float)c, (float)(sign * s));
+    }
+}
+
+// fixed-point chirp phase and step per bin for the single DM tile: Eq. 1 per
+// channel, phase -dm_first K and step -dm_step K in 2^-32 cycles
+__global__ void k_static_nco(uint2 *nco, double dm_first, double dm_step, double f_centre, double bw, int nsub,
+                             int nchan, int64_t nbin)
+{
+    const int64_t total = (int64_t)nsub * nbin;
+    const int64_t m = nbin / nchan;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % nbin;
+        const int s = (int)(q / nbin);
+        const int c = (int)(i / m);
+        const int64_t j = i % m;
+        const double nu_s = f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
+        const double nu_c = nu_s - 0.5 * bw + ((double)c + 0.5) * bw / (double)nchan;
+        const double nu = ((double)j - 0.5 * (double)m) * bw / (double)nbin;
+        const double k = 1e6 * kD * nu * nu / (nu_c * nu_c * (nu_c + nu));
+        nco[q] = make_uint2((uint32_t)(unsigned long long)llrint(-dm_first * k * 4294967296.0),
+                            (uint32_t)(unsigned long long)llrint(-dm_step * k * 4294967296.0));
+    }
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+}  // namespace cdmt
+
+using namespace cdmt;
+
+extern "C" int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz, double bw_sub_mhz,
+                                   double dm_first, double dm_step, int ndm, int nchan, int nint, int64_t nbin,
+                                   int64_t nd, const void *d_in, float *d_out, void *cuda_stream)
+{
+    // ---- arguments (same rules as cdmt_plan_ex)
+    if (nsub < 1 || ndm < 1 || nint < 1) return fail(CDMT_EINVAL, "need nsub, ndm, nint >= 1");
+    if (!(bw_sub_mhz > 0) || !std::isfinite(bw_sub_mhz)) return fail(CDMT_EINVAL, "bw_sub must be > 0");
+    if (!std::isfinite(dm_first) || !std::isfinite(dm_step)) return fail(CDMT_EINVAL, "DMs must be finite");
+    if (!is_pow2(nchan) || nchan < 2 || nchan > 32) return fail(CDMT_EINVAL, "nchan must be a power of two in 2..32");
+    const double band_lo = f_centre_mhz - 0.5 * nsub * bw_sub_mhz;
+    if (!(band_lo > 0)) return fail(CDMT_EINVAL, "lowest frequency %.6g MHz must be > 0", band_lo);
+    if (!is_pow2(nbin) || nbin % nchan) return fail(CDMT_EINVAL, "nbin must be a power of two divisible by nchan");
+    const int64_t m = nbin / nchan;
+    if (m < 512 || m > 4096) return fail(CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)m);
+    if (nsamp < nbin) return fail(CDMT_EINVAL, "nsamp (%lld) < nbin (%lld)", (long long)nsamp, (long long)nbin);
+    if (!d_in || !d_out) return fail(CDMT_EINVAL, "NULL input or output pointer");
+    if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(CDMT_EINVAL, "input must be 16-byte aligned");
+    if (nd < 0) {
+        // Sec. 2: n_d = r t_d / n_c with t_d of Eq. 2 for the lowest channel at the largest |DM|
+        const double dmax = std::fmax(std::fabs(dm_first), std::fabs(dm_first + (ndm - 1) * dm_step));
+        const double lo = band_lo, hi = band_lo + bw_sub_mhz / nchan;
+        const double td = kD * dmax * (1.0 / (lo * lo) - 1.0 / (hi * hi));
+        nd = (int64_t)std::ceil(bw_sub_mhz * 1e6 * td / nchan);
+        nd += nd & 1;
+        while (nd < m && (m - nd) % nint) nd += 2;
+    }
+    if (nd % 2 || nd >= m || (m - nd) % nint)
+        return fail(CDMT_EINVAL, "overlap nd=%lld invalid for M=%lld, nint=%d", (long long)nd, (long long)m, nint);
+    const int r = (int)(m / 256);
+    const int64_t nvalid = nbin - nd * nchan;
+    const int64_t nseg = (nsamp - nbin) / nvalid + 1;
+    const int64_t seglen = (m - nd) / nint;
+    const int64_t nout = nseg * seglen;
+
+    // ---- scratch map inside the static array; refuse what does not fit
+    const size_t ntw = (size_t)15 * (16 * r + r);
+    const size_t off_twn = 0;
+    const size_t off_twf = align256(off_twn + sizeof(float2) * (size_t)nbin);
+    const size_t off_twi = align256(off_twf + sizeof(float2) * ntw);
+    const size_t off_nco = align256(off_twi + sizeof(float2) * ntw);
+    const size_t off_spec = align256(off_nco + sizeof(uint2) * (size_t)nsub * (size_t)nbin);
+    const size_t per_seg = sizeof(float4) * (size_t)nsub * (size_t)nbin;
+    if (off_spec + per_seg > (size_t)CDMT_STATIC_SCRATCH_BYTES)
+        return fail(CDMT_EBUDGET,
+                    "nsub=%d, nbin=%lld need %zu bytes of scratch for one segment; the static scratch holds %zu "
+                    "(about 24 * nsub * nbin bytes are needed)",
+                    nsub, (long long)nbin, off_spec + per_seg, (size_t)CDMT_STATIC_SCRATCH_BYTES);
+    const int64_t kc_max = std::min<int64_t>(nseg, (int64_t)(((size_t)CDMT_STATIC_SCRATCH_BYTES - off_spec) / per_seg));
+
+    // ---- once per device: the device address of the static array
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(CDMT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(CDMT_EINVAL, "device %d out of range", dev);
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p) return fail(CDMT_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_scratch_addr[dev] = p;
+        }
+        base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    }
+    e = fp32_prepare(r);
+    if (e != cudaSuccess) return fail(CDMT_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+
+    // ---- tables (every byte read later is written here first: nothing needs clearing)
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    float2 *twn = reinterpret_cast<float2 *>(base + off_twn);
+    float2 *twf = reinterpret_cast<float2 *>(base + off_twf);
+    float2 *twi = reinterpret_cast<float2 *>(base + off_twi);
+    uint2 *nco = reinterpret_cast<uint2 *>(base + off_nco);
+    float4 *spec = reinterpret_cast<float4 *>(base + off_spec);
+    k_static_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256, 0, st>>>(twn, nbin, -1);
+    k_static_twiddle_passes<<<64, 256, 0, st>>>(twf, r, -1);
+    k_static_twiddle_passes<<<64, 256, 0, st>>>(twi, r, +1);
+    k_static_nco<<<1024, 256, 0, st>>>(nco, dm_first, dm_step, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(CDMT_ECUDA, "table kernels: %s", cudaGetErrorString(e));
+
+    // ---- segment chunks: forward stage into the scratch spectrum, then the DM stage
+    for (int64_t k0 = 0; k0 < nseg; k0 += kc_max) {
+        const int kc = (int)std::min<int64_t>(kc_max, nseg - k0);
+        ForwardArgs fa{};
+        fa.in = static_cast<const float4 *>(d_in);
+        fa.spec = spec;
+        fa.tw_a = twf;
+        fa.tw_b = twf + 15 * 16 * r;
+        fa.tw_n = twn;
+        fa.nsamp = nsamp;
+        fa.nvalid = nvalid;
+        fa.nbin = nbin;
+        fa.k0 = k0;
+        fa.nchan = nchan;
+        fa.kc = kc;
+        fa.nsub = nsub;
+        fa.r = r;
+        e = fp32_forward(fa, st);
+        if (e != cudaSuccess) return fail(CDMT_ECUDA, "forward stage: %s", cudaGetErrorString(e));
+        DedispArgs da{};
+        da.spec = spec;
+        da.nco = nco;
+        da.ktab = nullptr;
+        da.dm_list = nullptr;
+        da.tw_a = twi;
+        da.tw_b = twi + 15 * 16 * r;
+        da.out = d_out;
+        da.k0 = k0;
+        da.nout = nout;
+        da.nsub = nsub;
+        da.kc = kc;
+        da.nchan = nchan;
+        da.ndm = ndm;
+        da.dm_tile = ndm;
+        da.nd = (int)nd;
+        da.nint = nint;
+        da.r = r;
+        da.uniform = true;
+        da.scale = (float)(1.0 / ((double)nbin * (double)m));
+        e = fp32_dedisperse(da, st);
+        if (e != cudaSuccess) return fail(CDMT_ECUDA, "DM stage: %s", cudaGetErrorString(e));
+    }
+    return CDMT_OK;
+}
