@@ -19,15 +19,15 @@
 // spectrum by a power of two so that every half-precision operand stays below
 // 2^15 whatever the signal; the scale is undone exactly on the output.
 //
-// Work split: one CTA per (DM tile, subband, segment, channel), 256 threads =
-// two warpgroups that take alternate DMs of the tile, each with its own operand
-// buffer, tensor-memory columns and mbarrier, so the tensor core works on one
-// warpgroup's GEMM while the other does its FP32 work.
+// Work split: one CTA of 512 threads per (DM tile, subband, segment, channel).
+// FP16: two pipes of 256 threads take alternate DMs of the tile, each with its
+// own operand buffer, tensor-memory columns and mbarrier, so the tensor core
+// works on one pipe's GEMM while the other does its FP32 work.
 //
 // BF16 operands carry 8 mantissa bits, too few for the 2e-3 error target, so in
 // BF16 mode both the data and the DFT matrix are split into hi + lo parts and
-// each K-step issues three MMAs (hi*hi + lo*hi + hi*lo); the two warpgroups then
-// share the CTA's shared memory by running one DM at a time.
+// each K-step issues three MMAs (hi*hi + lo*hi + hi*lo); the CTA then runs one
+// DM at a time with all 512 threads (two operand sets do not fit).
 #include "cdmt_internal.h"
 #include "fft_core.cuh"
 #include "tc_ptx.cuh"
@@ -55,7 +55,8 @@ template <int AB> struct TcLayout {
     static constexpr uint32_t off_ph = off_x + 16 * kM;
     static constexpr uint32_t off_a = off_ph + 8 * kM;
     static constexpr uint32_t abytes = na * kAbuf;
-    static constexpr uint32_t off_misc = off_a + nwgbuf * abytes;
+    static constexpr uint32_t off_tw = off_a + nwgbuf * abytes;       // FP16: W_4096 twiddles [m0][j_lo]
+    static constexpr uint32_t off_misc = off_tw + (AB ? 0 : 8 * kM);
     static constexpr uint32_t total = off_misc + 128;
 };
 
@@ -80,23 +81,34 @@ __device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__
 }  // namespace
 
 // AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
+// 512 threads.  FP16: two pipes of 256 threads, each carrying one DM at a time
+// through its own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of
+// 512 threads (one operand set fits).  Within a pipe the chirp stage is split
+// over all its threads, and each tensor-memory read-out is split by column
+// groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
 template <bool UNIFORM, int AB>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(512, 1)
 k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
                 float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
                 int dm_tile, int nd, int nint, int64_t nout, float scale_out)
 {
     using L = TcLayout<AB>;
+    constexpr int NT = 512;
+    constexpr int NPIPE = AB ? 1 : 2;
+    constexpr int PT = NT / NPIPE;          // threads per pipe
+    constexpr int NCG = PT / 128;           // TMEM column groups per pipe
+    constexpr int COLS = 128 / NCG;         // columns read per thread per read-out
+    constexpr int JH = 4096 / PT;           // j_hi values per thread in the chirp stage
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *bm = smem + L::off_b;
     float4 *xs = reinterpret_cast<float4 *>(smem + L::off_x);
     uint2 *ph = reinterpret_cast<uint2 *>(smem + L::off_ph);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 16);
-    float *red = reinterpret_cast<float *>(smem + L::off_misc + 32);
+    float *red = reinterpret_cast<float *>(smem + L::off_misc + 32);   // 16 floats
 
-    const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2, t = tid & 127;
+    const int tid = threadIdx.x, warp = tid >> 5;
     // once any CTA has given up on a tensor-core wait, the rest of the launch
     // returns at once (one read, block-uniform decision)
     if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
@@ -108,21 +120,24 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     const int dm0 = tile * dm_tile;
     const int ndt = min(dm_tile, ndm - dm0);
 
-    // ---- stage the DFT matrix, the channel's spectrum and its phase words
-    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += 256) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
+    // ---- stage the DFT matrix, the twiddles, the channel's spectrum and its phase words
+    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
+    float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
+    if constexpr (!AB)
+        for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
     const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
     float vmax = 0.f;
-    for (int i = tid; i < kM; i += 256) {
+    for (int i = tid; i < kM; i += NT) {
         float4 v = __ldg(src + i);
         xs[i] = v;
         vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
     if constexpr (UNIFORM) {
         const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
-        for (int i = tid; i < kM; i += 256) ph[i] = p[i];
+        for (int i = tid; i < kM; i += NT) ph[i] = p[i];
     } else {
         const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
-        for (int i = tid; i < kM; i += 256) ph[i] = p[i];
+        for (int i = tid; i < kM; i += NT) ph[i] = p[i];
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -139,25 +154,29 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     tc::fence_after();
     float bmax = 0.f;
     #pragma unroll
-    for (int w = 0; w < 8; w++) bmax = fmaxf(bmax, red[w]);
-    // power-of-two scale: |x| 2^e <= 512, so a 64-point pass stays below 2^15
+    for (int w = 0; w < NT / 32; w++) bmax = fmaxf(bmax, red[w]);
+    // power-of-two scale: |x| 2^e <= 512, so a 64-point pass stays below 2^15;
+    // applied once to the staged spectrum (each thread rescales what it loaded)
     int e = bmax > 0.f ? (int)floorf(log2f(512.f / bmax)) : 0;
     e = max(-100, min(100, e));
     const float xscale = ldexpf(1.f, e);
     const float oscale = scale_out * ldexpf(1.f, -2 * e);
     const uint32_t tmem = *tslot;
+    for (int i = tid; i < kM; i += NT) {
+        float4 v = xs[i];
+        xs[i] = make_float4(v.x * xscale, v.y * xscale, v.z * xscale, v.w * xscale);
+    }
+    __syncthreads();
 
-    // BF16 mode runs one DM at a time through one operand set; FP16 overlaps two
-    constexpr int NPIPE = AB ? 1 : 2;
-    const int lane_sel = warp & 3;
-    const uint32_t lane_off = (uint32_t)(32 * lane_sel) << 16;
-    const int pipe = AB ? 0 : wg;
+    const int pipe = tid / PT;
+    const int q = tid % PT;                  // index within the pipe
+    const int t = q & 127;                   // TMEM lane = GEMM row = 32 (warp % 4) + lane
+    const int cg = q >> 7;                   // column group of this thread's read-outs
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t dcol = tmem + 128 * pipe;
-    uint8_t *ab = smem + L::off_a + (AB ? 0 : wg * L::abytes);
+    uint8_t *ab = smem + L::off_a + pipe * L::abytes;
     uint64_t *mb = &mbar[pipe];
     const int bar_id = 1 + pipe;
-    const int nthr = AB ? 256 : 128;
-    const int q = AB ? tid : t;       // index within the group working on one DM
 
     const int half = nd / 2;
     const int seglen = (kM - nd) / nint;
@@ -170,21 +189,19 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
     uint32_t ok = 1;
 
-    for (int d = AB ? 0 : wg; d < ndt; d += NPIPE) {
+    for (int d = pipe; d < ndt; d += NPIPE) {
         // ---- chirp, scale, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
         {
             double dmv = 0.0;
             if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
             const int jlo = q & 63;
-            const int nq = AB ? 4 : 2;              // quarters / halves of j_hi per thread
-            const int part = q >> 6;
-            #pragma unroll 1
-            for (int c4 = 0; c4 < 16 / nq; c4++) {
+            const int jbase = JH * (q >> 6);
+            #pragma unroll
+            for (int c4 = 0; c4 < JH / 4; c4++) {
                 uint32_t hx[4], hy[4], lx[4], ly[4];
                 #pragma unroll
                 for (int i = 0; i < 4; i++) {
-                    const int jhi = (64 / nq) * part + 4 * c4 + i;
-                    const int j = jhi * 64 + jlo;
+                    const int j = (jbase + 4 * c4 + i) * 64 + jlo;
                     float sn, cs;
                     if constexpr (UNIFORM) {
                         const uint2 w = ph[j];
@@ -196,8 +213,6 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
                         cyc -= rint(cyc);
                         __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
                     }
-                    cs *= xscale;
-                    sn *= xscale;
                     const float4 v = xs[j];
                     const float xr = v.x * cs - v.y * sn, xi = v.x * sn + v.y * cs;
                     const float yr = v.z * cs - v.w * sn, yi = v.z * sn + v.w * cs;
@@ -208,7 +223,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
                         ly[i] = tc::pack_bf16(yr - bf16_round(yr), yi - bf16_round(yi));
                     }
                 }
-                const int kcore = ((64 / nq) * part + 4 * c4) / 4;
+                const int kcore = (jbase + 4 * c4) / 4;
                 const uint32_t ox = (uint32_t)(jlo / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
                 const uint32_t oy = (uint32_t)((64 + jlo) / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
                 *reinterpret_cast<uint4 *>(ab + ox) = make_uint4(hx[0], hx[1], hx[2], hx[3]);
@@ -221,7 +236,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         }
         tc::fence_async_smem();
         tc::fence_before();
-        tc::bar(bar_id, nthr);
+        tc::bar(bar_id, PT);
         tc::fence_after();
         if (q == 0) {
             #pragma unroll 1
@@ -236,52 +251,57 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
             }
             tc::commit(mb);
         }
-        ok = bar_and(bar_id, nthr, tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
+        ok = bar_and(bar_id, PT, tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
         if (!ok) break;
         tc::fence_after();
 
-        // ---- pass-A rows -> twiddle -> pass-B operand (MN-major): row = pol * 64 + m0, k = 2 j_lo + (re, im)
-        if (!AB || tid < 128) {
+        // ---- pass-A rows -> twiddle -> pass-B operand (MN-major): row = pol * 64 + m0, k = 2 j_lo + (re, im).
+        // Two 16-column TMEM loads (8 complex m0 each) are issued together and
+        // waited for once; no loaded register is touched before the wait.
+        {
             const int pol = t >> 6, jlo = t & 63;
-            #pragma unroll 1
-            for (int cc = 0; cc < 4; cc++) {
-                float v[32];
-                tc::tmem_ld32(dcol + lane_off + 32 * cc, v);
-                float re[16], im[16];
+            constexpr int NST = COLS / 16;
+            uint32_t buf[2][16];
+            #pragma unroll
+            for (int st = 0; st < NST; st++) {
+                if ((st & 1) == 0) {
+                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * st, buf[0]);
+                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * (st + 1), buf[1]);
+                    tc::tmem_wait();
+                }
+                const uint32_t *v = buf[st & 1];
+                const int m0b = (cg * COLS + 16 * st) / 2;   // first of 8 consecutive m0
+                float re[8], im[8];
                 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float2 w = __ldg(twq + (16 * cc + i) * 64 + jlo);
-                    const float2 z = cmul(make_float2(v[2 * i], v[2 * i + 1]), w);
+                for (int i = 0; i < 8; i++) {
+                    const float2 w = AB ? __ldg(twq + (m0b + i) * 64 + jlo) : tws[(m0b + i) * 64 + jlo];
+                    const float2 z = cmul(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), w);
                     re[i] = z.x;
                     im[i] = z.y;
                 }
-                #pragma unroll
-                for (int g = 0; g < 2; g++) {
-                    const uint32_t mcore = (uint32_t)(pol * 64 + 16 * cc + 8 * g) / 8;
-                    const uint32_t o = mcore * kSboB + (uint32_t)(2 * jlo / 8) * kLboB + (uint32_t)((2 * jlo) % 8) * 16;
-                    const float *r8 = re + 8 * g, *i8 = im + 8 * g;
-                    *reinterpret_cast<uint4 *>(ab + o) =
-                        make_uint4(pk<AB>(r8[0], r8[1]), pk<AB>(r8[2], r8[3]), pk<AB>(r8[4], r8[5]), pk<AB>(r8[6], r8[7]));
-                    *reinterpret_cast<uint4 *>(ab + o + 16) =
-                        make_uint4(pk<AB>(i8[0], i8[1]), pk<AB>(i8[2], i8[3]), pk<AB>(i8[4], i8[5]), pk<AB>(i8[6], i8[7]));
-                    if constexpr (AB) {
-                        float lr[8], li[8];
-                        #pragma unroll
-                        for (int z = 0; z < 8; z++) {
-                            lr[z] = r8[z] - bf16_round(r8[z]);
-                            li[z] = i8[z] - bf16_round(i8[z]);
-                        }
-                        *reinterpret_cast<uint4 *>(ab + kAbuf + o) = make_uint4(
-                            pk<1>(lr[0], lr[1]), pk<1>(lr[2], lr[3]), pk<1>(lr[4], lr[5]), pk<1>(lr[6], lr[7]));
-                        *reinterpret_cast<uint4 *>(ab + kAbuf + o + 16) = make_uint4(
-                            pk<1>(li[0], li[1]), pk<1>(li[2], li[3]), pk<1>(li[4], li[5]), pk<1>(li[6], li[7]));
+                const uint32_t o = (uint32_t)((pol * 64 + m0b) / 8) * kSboB + (uint32_t)(2 * jlo / 8) * kLboB +
+                                   (uint32_t)((2 * jlo) % 8) * 16;
+                *reinterpret_cast<uint4 *>(ab + o) =
+                    make_uint4(pk<AB>(re[0], re[1]), pk<AB>(re[2], re[3]), pk<AB>(re[4], re[5]), pk<AB>(re[6], re[7]));
+                *reinterpret_cast<uint4 *>(ab + o + 16) =
+                    make_uint4(pk<AB>(im[0], im[1]), pk<AB>(im[2], im[3]), pk<AB>(im[4], im[5]), pk<AB>(im[6], im[7]));
+                if constexpr (AB) {
+                    float lr[8], li[8];
+                    #pragma unroll
+                    for (int z = 0; z < 8; z++) {
+                        lr[z] = re[z] - bf16_round(re[z]);
+                        li[z] = im[z] - bf16_round(im[z]);
                     }
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + o) = make_uint4(
+                        pk<1>(lr[0], lr[1]), pk<1>(lr[2], lr[3]), pk<1>(lr[4], lr[5]), pk<1>(lr[6], lr[7]));
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + o + 16) = make_uint4(
+                        pk<1>(li[0], li[1]), pk<1>(li[2], li[3]), pk<1>(li[4], li[5]), pk<1>(li[6], li[7]));
                 }
             }
         }
         tc::fence_async_smem();
         tc::fence_before();
-        tc::bar(bar_id, nthr);
+        tc::bar(bar_id, PT);
         tc::fence_after();
         if (q == 0) {
             #pragma unroll 1
@@ -296,28 +316,37 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
             }
             tc::commit(mb);
         }
-        ok = bar_and(bar_id, nthr, tc::mbar_wait(mb, 1, kWaitNs, kWaitPolls));
+        ok = bar_and(bar_id, PT, tc::mbar_wait(mb, 1, kWaitNs, kWaitPolls));
         if (!ok) break;
         tc::fence_after();
 
         // ---- detect: row = pol * 64 + m0 holds z[m1], time sample m = m0 + 64 m1
         float *ib = reinterpret_cast<float *>(ab);   // [2][4096], the operand is consumed
-        if (!AB || tid < 128) {
+        {
             const int pol = t >> 6, m0 = t & 63;
-            #pragma unroll 1
-            for (int cc = 0; cc < 4; cc++) {
-                float v[32];
-                tc::tmem_ld32(dcol + lane_off + 32 * cc, v);
+            constexpr int NST = COLS / 16;
+            uint32_t buf[2][16];
+            #pragma unroll
+            for (int st = 0; st < NST; st++) {
+                if ((st & 1) == 0) {
+                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * st, buf[0]);
+                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * (st + 1), buf[1]);
+                    tc::tmem_wait();
+                }
+                const uint32_t *v = buf[st & 1];
+                const int m1b = (cg * COLS + 16 * st) / 2;
                 #pragma unroll
-                for (int i = 0; i < 16; i++)
-                    ib[pol * kM + m0 + 64 * (16 * cc + i)] = fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]);
+                for (int i = 0; i < 8; i++) {
+                    const float a = __uint_as_float(v[2 * i]), b = __uint_as_float(v[2 * i + 1]);
+                    ib[pol * kM + m0 + 64 * (m1b + i)] = fmaf(a, a, b * b);
+                }
             }
         }
         tc::fence_before();
-        tc::bar(bar_id, nthr);
+        tc::bar(bar_id, PT);
         tc::fence_after();
         float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
-        for (int u = q; u < seglen; u += nthr) {
+        for (int u = q; u < seglen; u += PT) {
             const float *px = ib + half + u * nint;
             const float *py = px + kM;
             float acc = 0.f;
@@ -331,7 +360,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
             }
             orow[u] = acc * oscale;
         }
-        tc::bar(bar_id, nthr);
+        tc::bar(bar_id, PT);
     }
     if (!ok && q == 0) atomicExch(status, 1);
     tc::fence_before();
@@ -361,7 +390,7 @@ template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
-    k_dedisperse_tc<U, AB><<<(unsigned)nblk, 256, TcLayout<AB>::total, st>>>(
+    k_dedisperse_tc<U, AB><<<(unsigned)nblk, 512, TcLayout<AB>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan, a.ndm,
         a.dm_tile, a.nd, a.nint, a.nout, a.scale);
 }
