@@ -19,10 +19,10 @@
 // spectrum by a power of two so that every half-precision operand stays below
 // 2^15 whatever the signal; the scale is undone exactly on the output.
 //
-// Work split: one CTA of 512 threads per (DM tile, subband, segment, channel).
-// FP16: two pipes of 256 threads take alternate DMs of the tile, each with its
-// own operand buffer, tensor-memory columns and mbarrier, so the tensor core
-// works on one pipe's GEMM while the other does its FP32 work.
+// Work split: one CTA per (DM tile, subband, segment, channel).  FP16: three
+// pipes of 256 threads take every third DM of the tile, each with its own
+// operand buffer, tensor-memory columns and mbarrier, so the tensor core works
+// on one pipe's GEMM while the others do their FP32 work.
 //
 // BF16 operands carry 8 mantissa bits, too few for the 2e-3 error target, so in
 // BF16 mode both the data and the DFT matrix are split into hi + lo parts and
@@ -45,19 +45,25 @@ constexpr uint32_t kWaitPolls = 1u << 26;          // backstop on polls
 constexpr uint64_t kWaitNs = 50ull * 1000 * 1000;  // a GEMM batch takes microseconds; give up after 50 ms
 constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;
 
-// shared-memory map
+// Shared-memory map and thread organisation.  The per-bin chirp-phase words
+// live in tensor memory (64 columns after the accumulators): the chirp-stage
+// thread q of every pipe reads TMEM lane q mod 128, and the bins a lane's
+// threads handle are the same in every pipe, so one copy serves all pipes.
 template <int AB> struct TcLayout {
+    static constexpr int npipe = AB ? 1 : 3;           // DMs in flight per CTA
+    static constexpr int pt = AB ? 512 : 256;          // threads per pipe
+    static constexpr int nt = npipe * pt;
     static constexpr uint32_t nb = AB ? 2 : 1;         // B matrices (hi, lo)
-    static constexpr uint32_t na = AB ? 2 : 1;         // operand planes per warpgroup (hi, lo)
-    static constexpr uint32_t nwgbuf = AB ? 1 : 2;     // BF16: one operand set shared by both warpgroups
+    static constexpr uint32_t na = AB ? 2 : 1;         // operand planes per pipe (hi, lo)
     static constexpr uint32_t off_b = 0;
     static constexpr uint32_t off_x = off_b + nb * kBmat;
-    static constexpr uint32_t off_ph = off_x + 16 * kM;
-    static constexpr uint32_t off_a = off_ph + 8 * kM;
+    static constexpr uint32_t off_tw = off_x + 16 * kM;               // W_4096 twiddles [m0][j_lo]
+    static constexpr uint32_t off_a = off_tw + 8 * kM;
     static constexpr uint32_t abytes = na * kAbuf;
-    static constexpr uint32_t off_tw = off_a + nwgbuf * abytes;       // FP16: W_4096 twiddles [m0][j_lo]
-    static constexpr uint32_t off_misc = off_tw + (AB ? 0 : 8 * kM);
-    static constexpr uint32_t total = off_misc + 128;
+    static constexpr uint32_t off_misc = off_a + npipe * abytes;
+    static constexpr uint32_t total = off_misc + 256;
+    static constexpr uint32_t tmem_cols = AB ? 256 : 512;            // power of two >= npipe * 128 + 64
+    static constexpr uint32_t ph_col = npipe * 128;                   // first phase-word column
 };
 
 __device__ __forceinline__ bool bar_and(int id, int count, bool v)
@@ -81,32 +87,32 @@ __device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__
 }  // namespace
 
 // AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
-// 512 threads.  FP16: two pipes of 256 threads, each carrying one DM at a time
-// through its own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of
-// 512 threads (one operand set fits).  Within a pipe the chirp stage is split
+// FP16: three pipes of 256 threads, each carrying one DM at a time through its
+// own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of 512
+// threads (one hi/lo operand set fits).  Within a pipe the chirp stage is split
 // over all its threads, and each tensor-memory read-out is split by column
 // groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
 template <bool UNIFORM, int AB>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
 k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
                 float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
                 int dm_tile, int nd, int nint, int64_t nout, float scale_out)
 {
     using L = TcLayout<AB>;
-    constexpr int NT = 512;
-    constexpr int NPIPE = AB ? 1 : 2;
-    constexpr int PT = NT / NPIPE;          // threads per pipe
+    constexpr int NT = L::nt;
+    constexpr int NPIPE = L::npipe;
+    constexpr int PT = L::pt;                // threads per pipe
     constexpr int NCG = PT / 128;           // TMEM column groups per pipe
-    constexpr int COLS = 128 / NCG;         // columns read per thread per read-out
+    constexpr int COLS = 128 / NCG;         // accumulator columns read per thread per read-out
     constexpr int JH = 4096 / PT;           // j_hi values per thread in the chirp stage
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *bm = smem + L::off_b;
     float4 *xs = reinterpret_cast<float4 *>(smem + L::off_x);
-    uint2 *ph = reinterpret_cast<uint2 *>(smem + L::off_ph);
+    float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 16);
-    float *red = reinterpret_cast<float *>(smem + L::off_misc + 32);   // 16 floats
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 32);
+    float *red = reinterpret_cast<float *>(smem + L::off_misc + 64);   // one float per warp
 
     const int tid = threadIdx.x, warp = tid >> 5;
     // once any CTA has given up on a tensor-core wait, the rest of the launch
@@ -120,11 +126,17 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     const int dm0 = tile * dm_tile;
     const int ndt = min(dm_tile, ndm - dm0);
 
-    // ---- stage the DFT matrix, the twiddles, the channel's spectrum and its phase words
+    const int pipe = tid / PT;
+    const int q = tid % PT;                  // index within the pipe
+    const int t = q & 127;                   // TMEM lane = GEMM row = 32 (warp % 4) + lane
+    const int cg = q >> 7;                   // column group of this thread's read-outs / phase words
+    const int jlo = q & 63;                  // chirp stage: bins j_hi * 64 + jlo, j_hi in [jbase, jbase + JH)
+    const int jbase = JH * (q >> 6);
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+
+    // ---- stage the DFT matrix, the twiddles and the channel's spectrum
     for (int i = tid; i < (int)(L::nb * kBmat / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
-    float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
-    if constexpr (!AB)
-        for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
+    for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
     const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
     float vmax = 0.f;
     for (int i = tid; i < kM; i += NT) {
@@ -132,20 +144,12 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         xs[i] = v;
         vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
-    if constexpr (UNIFORM) {
-        const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
-        for (int i = tid; i < kM; i += NT) ph[i] = p[i];
-    } else {
-        const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
-        for (int i = tid; i < kM; i += NT) ph[i] = p[i];
-    }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if ((tid & 31) == 0) red[warp] = vmax;
-    if (warp == 0) tc::tmem_alloc(tslot, 256);
-    if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+    if (warp == 0) tc::tmem_alloc(tslot, L::tmem_cols);
+    if (tid < NPIPE) {
+        tc::mbar_init(&mbar[tid], 1);
         tc::fence_mbar_init();
     }
     tc::fence_async_smem();
@@ -153,7 +157,6 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     __syncthreads();
     tc::fence_after();
     float bmax = 0.f;
-    #pragma unroll
     for (int w = 0; w < NT / 32; w++) bmax = fmaxf(bmax, red[w]);
     // power-of-two scale: |x| 2^e <= 512, so a 64-point pass stays below 2^15;
     // applied once to the staged spectrum (each thread rescales what it loaded)
@@ -166,13 +169,34 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         float4 v = xs[i];
         xs[i] = make_float4(v.x * xscale, v.y * xscale, v.z * xscale, v.w * xscale);
     }
+    // phase words of this thread's chirp bins -> TMEM (pipe 0 writes; every pipe reads the same lanes)
+    const uint32_t ph_taddr = tmem + lane_off + L::ph_col + 2 * JH * cg;
+    if (pipe == 0) {
+        uint32_t w[2 * JH];
+        if constexpr (UNIFORM) {
+            const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
+            #pragma unroll
+            for (int i = 0; i < JH; i++) {
+                const uint2 v = __ldg(p + (jbase + i) * 64 + jlo);
+                w[2 * i] = v.x;
+                w[2 * i + 1] = v.y;
+            }
+        } else {
+            const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
+            #pragma unroll
+            for (int i = 0; i < JH; i++) {
+                const uint2 v = __ldg(p + (jbase + i) * 64 + jlo);
+                w[2 * i] = v.x;
+                w[2 * i + 1] = v.y;
+            }
+        }
+        if constexpr (JH == 16) tc::tmem_st32(ph_taddr, w);
+        else tc::tmem_st16(ph_taddr, w);
+    }
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
 
-    const int pipe = tid / PT;
-    const int q = tid % PT;                  // index within the pipe
-    const int t = q & 127;                   // TMEM lane = GEMM row = 32 (warp % 4) + lane
-    const int cg = q >> 7;                   // column group of this thread's read-outs
-    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t dcol = tmem + 128 * pipe;
     uint8_t *ab = smem + L::off_a + pipe * L::abytes;
     uint64_t *mb = &mbar[pipe];
@@ -190,25 +214,27 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     uint32_t ok = 1;
 
     for (int d = pipe; d < ndt; d += NPIPE) {
-        // ---- chirp, scale, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
+        // ---- chirp, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
         {
             double dmv = 0.0;
             if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
-            const int jlo = q & 63;
-            const int jbase = JH * (q >> 6);
+            uint32_t w[2 * JH];
+            if constexpr (JH == 16) tc::tmem_ld32_async(ph_taddr, w);
+            else tc::tmem_ld16_async(ph_taddr, w);
+            tc::tmem_wait();
             #pragma unroll
             for (int c4 = 0; c4 < JH / 4; c4++) {
                 uint32_t hx[4], hy[4], lx[4], ly[4];
                 #pragma unroll
                 for (int i = 0; i < 4; i++) {
-                    const int j = (jbase + 4 * c4 + i) * 64 + jlo;
+                    const int b = 4 * c4 + i;
+                    const int j = (jbase + b) * 64 + jlo;
                     float sn, cs;
                     if constexpr (UNIFORM) {
-                        const uint2 w = ph[j];
-                        const int32_t p = (int32_t)(w.x + (uint32_t)d * w.y);
+                        const int32_t p = (int32_t)(w[2 * b] + (uint32_t)d * w[2 * b + 1]);
                         __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
                     } else {
-                        const double kj = __hiloint2double((int)ph[j].y, (int)ph[j].x);
+                        const double kj = __hiloint2double((int)w[2 * b + 1], (int)w[2 * b]);
                         double cyc = dmv * kj;
                         cyc -= rint(cyc);
                         __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
@@ -259,7 +285,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         // Two 16-column TMEM loads (8 complex m0 each) are issued together and
         // waited for once; no loaded register is touched before the wait.
         {
-            const int pol = t >> 6, jlo = t & 63;
+            const int pol = t >> 6, rjlo = t & 63;     // pass-A row: (pol, j_lo)
             constexpr int NST = COLS / 16;
             uint32_t buf[2][16];
             #pragma unroll
@@ -274,13 +300,13 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
                 float re[8], im[8];
                 #pragma unroll
                 for (int i = 0; i < 8; i++) {
-                    const float2 w = AB ? __ldg(twq + (m0b + i) * 64 + jlo) : tws[(m0b + i) * 64 + jlo];
+                    const float2 w = tws[(m0b + i) * 64 + rjlo];
                     const float2 z = cmul(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), w);
                     re[i] = z.x;
                     im[i] = z.y;
                 }
-                const uint32_t o = (uint32_t)((pol * 64 + m0b) / 8) * kSboB + (uint32_t)(2 * jlo / 8) * kLboB +
-                                   (uint32_t)((2 * jlo) % 8) * 16;
+                const uint32_t o = (uint32_t)((pol * 64 + m0b) / 8) * kSboB + (uint32_t)(2 * rjlo / 8) * kLboB +
+                                   (uint32_t)((2 * rjlo) % 8) * 16;
                 *reinterpret_cast<uint4 *>(ab + o) =
                     make_uint4(pk<AB>(re[0], re[1]), pk<AB>(re[2], re[3]), pk<AB>(re[4], re[5]), pk<AB>(re[6], re[7]));
                 *reinterpret_cast<uint4 *>(ab + o + 16) =
@@ -366,7 +392,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_free(tmem, 256);
+    if (warp == 0) tc::tmem_free(tmem, L::tmem_cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +416,7 @@ template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
-    k_dedisperse_tc<U, AB><<<(unsigned)nblk, 512, TcLayout<AB>::total, st>>>(
+    k_dedisperse_tc<U, AB><<<(unsigned)nblk, TcLayout<AB>::nt, TcLayout<AB>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan, a.ndm,
         a.dm_tile, a.nd, a.nint, a.nout, a.scale);
 }
