@@ -248,6 +248,103 @@ const char *cdmt_strerror(int status);
  * The pointer stays valid until the next call on the same plan / thread. */
 const char *cdmt_last_error(cdmt_plan_t plan);
 
+/* ------------------------------------------------------------------------
+ * Batches of beams of uneven shapes.
+ *
+ * A batch runs several beams, each with its own subbands, samples, channel
+ * count, integration and evenly spaced DM list, through ONE CUDA graph per
+ * "round".  A round is a chunk of consecutive overlap-save segments of every
+ * beam (the block loop of Algorithm 1, Sec. 3, with N_FFT chosen so that the
+ * round outputs of all beams fit the output budget).  Each graph launch runs
+ * the forward stage of every beam and then one persistent tensor-core launch
+ * that takes (beam, subband, segment, channel, DM tile) items from a device
+ * queue; beams the autotuner assigns to the FP32 form get their own DM-stage
+ * kernel in the same graph.  The round number lives in device memory and the
+ * graph advances it, so one graph serves every round.
+ */
+typedef struct cdmt_batch_s *cdmt_batch_t;
+
+typedef struct cdmt_beam {
+    int32_t nsub;          /* subbands */
+    int32_t ndm;           /* DM trials: dm_first + i * dm_step, i < ndm */
+    int64_t nsamp;         /* samples per subband */
+    double f_centre_mhz;   /* centre of the beam's band */
+    double bw_sub_mhz;     /* subband width */
+    double dm_first, dm_step;
+    int32_t nchan, nint;
+    const void *d_in;      /* DEVICE input [nsub][nsamp] 16-byte samples, caller-owned, valid for the
+                              batch's lifetime (its address is captured in the graph) */
+} cdmt_beam;
+
+typedef struct cdmt_batch_opts {
+    int64_t out_budget;    /* bytes for the round outputs of all beams (0: 16 GiB) */
+    int32_t autotune;      /* 0: FP16 tensor-core form with one DM tile; 1: time candidates */
+    int32_t reserved0;
+    const char *tune_cache;/* text file of tuned choices (read, and appended to), or NULL */
+    int64_t reserved[6];
+} cdmt_batch_opts;
+
+/* per-beam choice of the autotuner */
+typedef struct cdmt_batch_tune {
+    int32_t precision;     /* enum cdmt_precision */
+    int32_t dm_tile;
+    int64_t nbin;
+    double units_per_s;    /* measured DM-trial samples/s on the sample (0 if not measured) */
+    int32_t from_cache;
+    int32_t reserved;
+} cdmt_batch_tune;
+
+typedef struct cdmt_batch_beam_info {
+    cdmt_info plan;        /* the beam's plan (nbin, nd, nseg, nout, ...) */
+    cdmt_batch_tune tune;
+    int32_t nround;        /* rounds to cover every beam's input */
+    int32_t reserved0;
+    int64_t seg_per_round; /* segments of this beam per round; round r covers segments
+                              [r * seg_per_round, ...) (fewer or none near the end) */
+    float *d_out;          /* DEVICE round output, owned by the batch: float32
+                              [ndm][nsub*nchan][out_row_stride]; segment kk of the round at
+                              columns [kk * seglen, (kk + 1) * seglen), seglen = (M - nd) / nint;
+                              overwritten by every round */
+    int64_t out_row_stride;
+    int64_t out_bytes_total; /* round output bytes of all beams */
+} cdmt_batch_beam_info;
+
+/* cdmt_batch_create - tune, plan and capture a batch.  beams: host array of
+ * nbeam descriptors (copied).  stream: used for autotuning runs.  Allocates
+ * device memory (plans, round outputs).
+ * Errors: CDMT_EINVAL, CDMT_EBUDGET (one segment of every beam does not fit the
+ * output budget), CDMT_ENOMEM, CDMT_ECUDA, and the plan errors of a beam. */
+int cdmt_batch_create(cdmt_batch_t *batch, int nbeam, const cdmt_beam *beams, const cdmt_batch_opts *opts,
+                      void *stream);
+
+/* cdmt_batch_info - sizes, tuned choices and the round output buffer of one beam. */
+int cdmt_batch_info(cdmt_batch_t batch, int beam, cdmt_batch_beam_info *info);
+
+/* cdmt_batch_run_round - enqueue round r (0 <= r < nround) on stream: one graph
+ * launch.  The round outputs are valid once the stream reaches that point and
+ * until the next round is enqueued. */
+int cdmt_batch_run_round(cdmt_batch_t batch, int round, void *stream);
+
+/* cdmt_batch_run - enqueue every round in order (each overwrites the round
+ * outputs): throughput runs, or a consumer that drains by stream order. */
+int cdmt_batch_run(cdmt_batch_t batch, void *stream);
+
+/* cdmt_batch_copy_out - copy beam's whole round output buffer
+ * (ndm * nsub*nchan * out_row_stride floats) to dst (host or device memory,
+ * cudaMemcpyDefault), ordered on stream after the rounds enqueued there. */
+int cdmt_batch_copy_out(cdmt_batch_t batch, int beam, void *dst, void *stream);
+
+/* cdmt_batch_status - wait for the batch's device work; CDMT_ETIMEOUT if a
+ * tensor-core wait gave up (flag cleared), else CDMT_OK. */
+int cdmt_batch_status(cdmt_batch_t batch);
+
+/* cdmt_batch_last_error - message of the last failure on the batch (NULL:
+ * this thread's last failure before a batch existed). */
+const char *cdmt_batch_last_error(cdmt_batch_t batch);
+
+/* cdmt_batch_destroy - free the batch (waits for the device first). */
+int cdmt_batch_destroy(cdmt_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

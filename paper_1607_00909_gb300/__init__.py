@@ -41,6 +41,29 @@ class cdmt_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 7)]
 
 
+class cdmt_beam(ctypes.Structure):
+    _fields_ = [("nsub", ctypes.c_int32), ("ndm", ctypes.c_int32), ("nsamp", ctypes.c_int64),
+                ("f_centre_mhz", ctypes.c_double), ("bw_sub_mhz", ctypes.c_double), ("dm_first", ctypes.c_double),
+                ("dm_step", ctypes.c_double), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
+                ("d_in", ctypes.c_void_p)]
+
+
+class cdmt_batch_opts(ctypes.Structure):
+    _fields_ = [("out_budget", ctypes.c_int64), ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p), ("reserved", ctypes.c_int64 * 6)]
+
+
+class cdmt_batch_tune(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("dm_tile", ctypes.c_int32), ("nbin", ctypes.c_int64),
+                ("units_per_s", ctypes.c_double), ("from_cache", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class cdmt_batch_beam_info(ctypes.Structure):
+    _fields_ = [("plan", cdmt_info), ("tune", cdmt_batch_tune), ("nround", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("seg_per_round", ctypes.c_int64), ("d_out", ctypes.c_void_p),
+                ("out_row_stride", ctypes.c_int64), ("out_bytes_total", ctypes.c_int64)]
+
+
 class CdmtError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} [status {status}]")
@@ -63,6 +86,16 @@ def _load():
     lib.cdmt_destroy.argtypes = [P]
     lib.cdmt_set_timing.argtypes = [P, ctypes.c_int]
     lib.cdmt_device_status.argtypes = [P]
+    lib.cdmt_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(cdmt_beam),
+                                      ctypes.POINTER(cdmt_batch_opts), P]
+    lib.cdmt_batch_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(cdmt_batch_beam_info)]
+    lib.cdmt_batch_run_round.argtypes = [P, ctypes.c_int, P]
+    lib.cdmt_batch_run.argtypes = [P, P]
+    lib.cdmt_batch_status.argtypes = [P]
+    lib.cdmt_batch_copy_out.argtypes = [P, ctypes.c_int, P, P]
+    lib.cdmt_batch_destroy.argtypes = [P]
+    lib.cdmt_batch_last_error.argtypes = [P]
+    lib.cdmt_batch_last_error.restype = ctypes.c_char_p
     lib.cdmt_execute_static.argtypes = [ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -71,7 +104,9 @@ def _load():
     lib.cdmt_last_error.argtypes = [P]
     lib.cdmt_last_error.restype = ctypes.c_char_p
     for f in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
-              "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status", "cdmt_execute_static"):
+              "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status", "cdmt_execute_static",
+              "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run", "cdmt_batch_status",
+              "cdmt_batch_destroy", "cdmt_batch_copy_out"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -80,7 +115,8 @@ _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
-            "cdmt_execute_static")
+            "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
+            "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out")
 
 
 def lib():
@@ -140,6 +176,99 @@ def cdmt_execute_static(nsub, nsamp, f_centre, bw_sub, dm_first, dm_step, ndm, n
     _check(_lib.cdmt_execute_static(int(nsub), int(nsamp), float(f_centre), float(bw_sub), float(dm_first),
                                     float(dm_step), int(ndm), int(nchan), int(nint), int(nbin), int(nd),
                                     d_in, d_out, stream or None))
+
+
+def cdmt_batch_last_error(batch=None) -> str:
+    return _lib.cdmt_batch_last_error(batch).decode()
+
+
+def _bcheck(rc: int, batch=None):
+    if rc != CDMT_OK:
+        raise CdmtError(rc, f"{cdmt_strerror(rc)}: {cdmt_batch_last_error(batch)}")
+
+
+def cdmt_batch_create(beams, opts: cdmt_batch_opts | None = None, stream: int = 0):
+    arr = (cdmt_beam * len(beams))(*beams)
+    h = ctypes.c_void_p()
+    _bcheck(_lib.cdmt_batch_create(ctypes.byref(h), len(beams), arr, ctypes.byref(opts) if opts else None,
+                                   stream or None))
+    return h.value
+
+
+def cdmt_batch_info(batch, beam: int) -> cdmt_batch_beam_info:
+    info = cdmt_batch_beam_info()
+    _bcheck(_lib.cdmt_batch_info(batch, beam, ctypes.byref(info)), batch)
+    return info
+
+
+def cdmt_batch_run_round(batch, r: int, stream: int = 0):
+    _bcheck(_lib.cdmt_batch_run_round(batch, r, stream or None), batch)
+
+
+def cdmt_batch_run(batch, stream: int = 0):
+    _bcheck(_lib.cdmt_batch_run(batch, stream or None), batch)
+
+
+def cdmt_batch_copy_out(batch, beam: int, dst: int, stream: int = 0):
+    _bcheck(_lib.cdmt_batch_copy_out(batch, beam, dst, stream or None), batch)
+
+
+def cdmt_batch_status(batch):
+    _bcheck(_lib.cdmt_batch_status(batch), batch)
+
+
+def cdmt_batch_destroy(batch):
+    _bcheck(_lib.cdmt_batch_destroy(batch))
+
+
+class Batch:
+    """Owning wrapper of a batch of beams.  beams: list of dicts with nsub, nsamp,
+    f_centre, bw_sub, dm_first, dm_step, ndm, nchan, nint and d_in (device
+    pointer, kept valid by the caller)."""
+
+    def __init__(self, beams, *, out_budget=0, autotune=False, tune_cache=None, stream=0):
+        bs = [cdmt_beam(int(b["nsub"]), int(b["ndm"]), int(b["nsamp"]), float(b["f_centre"]), float(b["bw_sub"]),
+                        float(b["dm_first"]), float(b["dm_step"]), int(b["nchan"]), int(b["nint"]), int(b["d_in"]))
+              for b in beams]
+        o = cdmt_batch_opts()
+        o.out_budget = int(out_budget)
+        o.autotune = 1 if autotune else 0
+        self._cache = tune_cache.encode() if tune_cache else None
+        o.tune_cache = self._cache
+        self.handle = cdmt_batch_create(bs, o, stream)
+        self.nbeam = len(bs)
+        self.infos = [cdmt_batch_info(self.handle, i) for i in range(self.nbeam)]
+        self.nround = self.infos[0].nround
+
+    def run_round(self, r, stream=0):
+        cdmt_batch_run_round(self.handle, r, stream)
+
+    def run(self, stream=0):
+        cdmt_batch_run(self.handle, stream)
+
+    def status(self):
+        cdmt_batch_status(self.handle)
+
+    def round_output(self, beam, stream=None):
+        """The beam's round output as a new CUDA tensor [ndm][nsub*nchan][out_row_stride]."""
+        import torch
+        inf = self.infos[beam]
+        shape = (inf.plan.ndm, inf.plan.nsub * inf.plan.nchan, inf.out_row_stride)
+        t = torch.empty(shape, dtype=torch.float32, device="cuda")
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        cdmt_batch_copy_out(self.handle, beam, t.data_ptr(), st)
+        return t
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cdmt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cdmt_device_status(plan):

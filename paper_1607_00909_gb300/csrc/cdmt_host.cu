@@ -17,6 +17,7 @@
 
 #include "../../include/cdmt.h"
 #include "cdmt_internal.h"
+#include "cdmt_plan_impl.h"
 
 using namespace cdmt;
 
@@ -26,48 +27,7 @@ constexpr double kD = 4.148808e3;  // MHz^2 pc^-1 cm^3 s
 
 thread_local std::string g_thread_error;
 
-struct Staging {
-    float4 *in = nullptr;   // [nsub][span_max] samples
-    float *out = nullptr;   // [ndm][nsub*nchan][kc_max*seglen]
-    cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free = nullptr;
-};
-
 }  // namespace
-
-struct cdmt_plan_s {
-    int device = 0;
-    int nsub = 0, nchan = 0, nint = 0, ndm = 0;
-    int64_t nsamp = 0;
-    double f_centre = 0, bw = 0;
-    std::vector<double> dms;
-    int64_t nbin = 0, mbin = 0, nd = 0, nvalid = 0, nseg = 0, nout = 0, seglen = 0;
-    int r = 0;
-    bool uniform = true;
-    double ddm = 0;
-    int dm_tile = 0, ntile = 0;
-    int64_t seg_chunk = 0;
-    int precision = 0, in_dtype = 0;
-    int64_t mem_budget = 0;
-    // device tables
-    float2 *tw_n = nullptr, *tw_af = nullptr, *tw_bf = nullptr, *tw_ai = nullptr, *tw_bi = nullptr;
-    uint2 *nco = nullptr;
-    double *ktab = nullptr, *d_dm = nullptr;
-    float4 *spec = nullptr;
-    // tensor-core form
-    uint4 *tc_bmat = nullptr;
-    float2 *tc_twq = nullptr;
-    int *d_status = nullptr;
-    int64_t bytes = 0;
-    // host-execute pipeline
-    int64_t host_chunk = 0, span_max = 0;
-    Staging stage[2];
-    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-    // stage timing (cdmt_set_timing / cdmt_stage_times)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<cudaEvent_t> ev_marks;  // triples: before forward, before dedisperse, after dedisperse
-    std::string last_error;
-};
 
 namespace {
 
@@ -240,8 +200,9 @@ void release(cdmt_plan_s *p)
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {p->tw_n, p->tw_af, p->tw_bf, p->tw_ai, p->tw_bi, p->nco, p->ktab, p->d_dm, p->spec,
-                    p->tc_bmat, p->tc_twq, p->d_status};
+    // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
+    void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
+                    p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {
@@ -255,6 +216,7 @@ void release(cdmt_plan_s *p)
     if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     for (auto ev : p->ev_pool) cudaEventDestroy(ev);
     for (auto ev : p->ev_marks) cudaEventDestroy(ev);
+    cudaGetLastError();  // leave no error of the teardown behind for a later call to pick up
     cudaSetDevice(cur);
 }
 
@@ -349,6 +311,18 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
 namespace cdmt {
 // lets other translation units of the library report an error before a plan exists
 void set_thread_error(const char *msg) { g_thread_error = msg; }
+
+int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin)
+{
+    cdmt_plan_s p;
+    p.nsub = nsub;
+    p.f_centre = f_centre;
+    p.bw = bw;
+    p.nchan = nchan;
+    p.nint = nint;
+    p.dms.assign(1, dm_abs_max);
+    return overlap_rule(p, nbin);
+}
 }  // namespace cdmt
 
 extern "C" {

@@ -15,6 +15,8 @@ struct ForwardArgs {
     int64_t nbin;
     int64_t k0;        // first segment of the chunk, counted from `in`
     int nchan, kc, nsub, r;
+    const int *round_dev = nullptr;  // batches: first segment = *round_dev * kc (k0 ignored)
+    int64_t nseg = 0;                // batches: segments of the whole input
 };
 
 struct DedispArgs {
@@ -29,6 +31,8 @@ struct DedispArgs {
     int nsub, kc, nchan, ndm, dm_tile, nd, nint, r;
     bool uniform;
     float scale;
+    const int *round_dev = nullptr;  // batches: skip segments round * kc + kk >= nseg
+    int64_t nseg = 0;
 };
 
 struct TcArgs {
@@ -47,7 +51,20 @@ struct TcArgs {
     float scale;
 };
 
+// one beam of a batch, as the persistent tensor-core kernel sees it
+struct TcBeam {
+    const float4 *spec;   // [nsub][kc][nchan][4096] forward spectra of the round's segments
+    const uint2 *nco;     // [ntile][nsub][nchan*4096] (phase, step) words
+    float *out;           // round output: [ndm][nsub*nchan][out_stride], segment kk at kk * seglen
+    int64_t out_stride;   // floats per output row in the round buffer (kc * seglen)
+    int64_t nseg;         // segments of the whole input
+    int nsub, kc, nchan, ndm, dm_tile, ntile, nd, nint;
+    float scale;
+};
+
 cudaError_t tc_prepare(int ab);
+cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev, int *queue, const uint4 *bmat,
+                            const float2 *twq, int *status, int ab, int nctas, cudaStream_t st);
 size_t tc_smem(int ab);
 cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st);
 

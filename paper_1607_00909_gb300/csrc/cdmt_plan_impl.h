@@ -1,0 +1,62 @@
+// Internal definition of a plan (shared by the host translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "cdmt_internal.h"
+
+namespace cdmt {
+
+struct Staging {
+    float4 *in = nullptr;   // [nsub][span_max] samples
+    float *out = nullptr;   // [ndm][nsub*nchan][kc_max*seglen]
+    cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free = nullptr;
+};
+
+
+}  // namespace cdmt
+
+struct cdmt_plan_s {
+    int device = 0;
+    int nsub = 0, nchan = 0, nint = 0, ndm = 0;
+    int64_t nsamp = 0;
+    double f_centre = 0, bw = 0;
+    std::vector<double> dms;
+    int64_t nbin = 0, mbin = 0, nd = 0, nvalid = 0, nseg = 0, nout = 0, seglen = 0;
+    int r = 0;
+    bool uniform = true;
+    double ddm = 0;
+    int dm_tile = 0, ntile = 0;
+    int64_t seg_chunk = 0;
+    int precision = 0, in_dtype = 0;
+    int64_t mem_budget = 0;
+    // device tables
+    float2 *tw_n = nullptr, *tw_af = nullptr, *tw_bf = nullptr, *tw_ai = nullptr, *tw_bi = nullptr;
+    uint2 *nco = nullptr;
+    double *ktab = nullptr, *d_dm = nullptr;
+    float4 *spec = nullptr;
+    // tensor-core form
+    uint4 *tc_bmat = nullptr;
+    float2 *tc_twq = nullptr;
+    int *d_status = nullptr;
+    int64_t bytes = 0;
+    // host-execute pipeline
+    int64_t host_chunk = 0, span_max = 0;
+    cdmt::Staging stage[2];
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    // stage timing (cdmt_set_timing / cdmt_stage_times)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_marks;  // triples: before forward, before dedisperse, after dedisperse
+    std::string last_error;
+};
+
+
+namespace cdmt {
+// overlap n_d of Sec. 2 for a band (defined in cdmt_host.cu); -1 if none < M
+int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin);
+}  // namespace cdmt

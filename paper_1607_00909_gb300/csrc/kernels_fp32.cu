@@ -41,8 +41,12 @@ template <int R>
 __global__ void __launch_bounds__(16 * R)
 k_forward_decimated(const float4 *__restrict__ in, float4 *__restrict__ spec, const float2 *__restrict__ tw_a,
                     const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n, int64_t nsamp,
-                    int64_t nvalid, int nchan, int64_t k0, int kc)
+                    int64_t nvalid, int nchan, int64_t k0, int kc, const int *__restrict__ round_dev, int64_t nseg)
 {
+    // batches: the chunk's first segment is round * kc, read from device memory;
+    // segments past the end of the input are skipped
+    if (round_dev) k0 = (int64_t)(*round_dev) * kc;
+    if (k0 + (int64_t)blockIdx.y >= nseg) return;
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T;
     extern __shared__ float4 smem[];
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
 k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
              const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
              float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
-             int nint, int64_t nout, float scale)
+             int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg)
 {
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T, NT = 2 * T;
@@ -154,6 +158,8 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
     const int tile = (int)item;
     const int dm0 = tile * dm_tile;
     const int ndt = min(dm_tile, ndm - dm0);
+    // batches: this chunk's segments start at round * kc; none past the end of the input
+    if (round_dev && (int64_t)(*round_dev) * kc + kk >= nseg) return;
 
     const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * M;
     float2 xr[16];
@@ -272,7 +278,8 @@ template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t s
 {
     dim3 g(a.nchan, a.kc, a.nsub);
     k_forward_decimated<R><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(a.in, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp,
-                                                                    a.nvalid, a.nchan, a.k0, a.kc);
+                                                                    a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
+                                                                    a.round_dev ? a.nseg : INT64_MAX);
 }
 
 template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t st)
@@ -310,7 +317,7 @@ template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStre
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
     k_dedisperse<R, U><<<(unsigned)nblk, 2 * Fft3<R>::T, smem_dedisp<R>(), st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
-        a.nd, a.nint, a.nout, a.scale);
+        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg);
 }
 
 cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)

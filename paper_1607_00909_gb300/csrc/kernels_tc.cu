@@ -86,18 +86,58 @@ __device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__
 
 }  // namespace
 
-// AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
-// FP16: three pipes of 256 threads, each carrying one DM at a time through its
-// own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of 512
-// threads (one hi/lo operand set fits).  Within a pipe the chirp stage is split
-// over all its threads, and each tensor-memory read-out is split by column
-// groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
+// One work item: the M spectral bins of one channel of one overlap-save
+// segment of one subband, and a tile of consecutive DM trials.
+struct TcItem {
+    const float4 *src;     // M bins, (X re, X im, Y re, Y im)
+    const uint2 *ph;       // per-bin words: uniform DM list (a, b) of this tile, otherwise K as double
+    const double *dms;     // DM values from the tile's first DM (uneven lists)
+    int ndt;               // DMs in the tile
+    float *out;            // output of the tile's first DM at this channel row and segment offset
+    int64_t dm_stride;     // floats between the rows of consecutive DMs
+    int nd, nint;
+    float scale_out;
+};
+
+// Per-CTA set-up: DFT matrix and twiddles to shared memory, tensor memory,
+// mbarriers.  Returns the TMEM base address.
+template <int AB>
+__device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__restrict__ bmat,
+                                                 const float2 *__restrict__ twq)
+{
+    using L = TcLayout<AB>;
+    constexpr int NT = L::nt;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t *bm = smem + L::off_b;
+    float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 32);
+    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
+    for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
+    if (warp == 0) tc::tmem_alloc(tslot, L::tmem_cols);
+    if (tid < L::npipe) {
+        tc::mbar_init(&mbar[tid], 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return *tslot;
+}
+
+template <int AB> __device__ __forceinline__ void tc_cta_teardown(uint32_t tmem)
+{
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_free(tmem, TcLayout<AB>::tmem_cols);
+}
+
+// The DM stage of one item.  Must be called by every thread of the CTA;
+// returns false (for every thread) if a tensor-core wait gave up.
 template <bool UNIFORM, int AB>
-__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
-k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
-                const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
-                float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
-                int dm_tile, int nd, int nint, int64_t nout, float scale_out)
+__device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uint32_t tmem)
 {
     using L = TcLayout<AB>;
     constexpr int NT = L::nt;
@@ -106,26 +146,13 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     constexpr int NCG = PT / 128;           // TMEM column groups per pipe
     constexpr int COLS = 128 / NCG;         // accumulator columns read per thread per read-out
     constexpr int JH = 4096 / PT;           // j_hi values per thread in the chirp stage
-    extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *bm = smem + L::off_b;
     float4 *xs = reinterpret_cast<float4 *>(smem + L::off_x);
     float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 32);
     float *red = reinterpret_cast<float *>(smem + L::off_misc + 64);   // one float per warp
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    // once any CTA has given up on a tensor-core wait, the rest of the launch
-    // returns at once (one read, block-uniform decision)
-    if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
-    int64_t item = blockIdx.x;
-    const int c = (int)(item % nchan); item /= nchan;
-    const int kk = (int)(item % kc); item /= kc;
-    const int s = (int)(item % nsub); item /= nsub;
-    const int tile = (int)item;
-    const int dm0 = tile * dm_tile;
-    const int ndt = min(dm_tile, ndm - dm0);
-
     const int pipe = tid / PT;
     const int q = tid % PT;                  // index within the pipe
     const int t = q & 127;                   // TMEM lane = GEMM row = 32 (warp % 4) + lane
@@ -133,38 +160,26 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     const int jlo = q & 63;                  // chirp stage: bins j_hi * 64 + jlo, j_hi in [jbase, jbase + JH)
     const int jbase = JH * (q >> 6);
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    tc::fence_after();   // order this item's tensor-memory writes after the previous item's reads
 
-    // ---- stage the DFT matrix, the twiddles and the channel's spectrum
-    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
-    for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
-    const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
+    // ---- the channel's spectrum, scaled by a power of two so that |x| 2^e <= 512
+    //      (a 64-point pass then stays below 2^15); the scale is undone on the output
     float vmax = 0.f;
     for (int i = tid; i < kM; i += NT) {
-        float4 v = __ldg(src + i);
+        float4 v = __ldg(it.src + i);
         xs[i] = v;
         vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if ((tid & 31) == 0) red[warp] = vmax;
-    if (warp == 0) tc::tmem_alloc(tslot, L::tmem_cols);
-    if (tid < NPIPE) {
-        tc::mbar_init(&mbar[tid], 1);
-        tc::fence_mbar_init();
-    }
-    tc::fence_async_smem();
-    tc::fence_before();
     __syncthreads();
-    tc::fence_after();
     float bmax = 0.f;
     for (int w = 0; w < NT / 32; w++) bmax = fmaxf(bmax, red[w]);
-    // power-of-two scale: |x| 2^e <= 512, so a 64-point pass stays below 2^15;
-    // applied once to the staged spectrum (each thread rescales what it loaded)
     int e = bmax > 0.f ? (int)floorf(log2f(512.f / bmax)) : 0;
     e = max(-100, min(100, e));
     const float xscale = ldexpf(1.f, e);
-    const float oscale = scale_out * ldexpf(1.f, -2 * e);
-    const uint32_t tmem = *tslot;
+    const float oscale = it.scale_out * ldexpf(1.f, -2 * e);
     for (int i = tid; i < kM; i += NT) {
         float4 v = xs[i];
         xs[i] = make_float4(v.x * xscale, v.y * xscale, v.z * xscale, v.w * xscale);
@@ -173,22 +188,11 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     const uint32_t ph_taddr = tmem + lane_off + L::ph_col + 2 * JH * cg;
     if (pipe == 0) {
         uint32_t w[2 * JH];
-        if constexpr (UNIFORM) {
-            const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
-            #pragma unroll
-            for (int i = 0; i < JH; i++) {
-                const uint2 v = __ldg(p + (jbase + i) * 64 + jlo);
-                w[2 * i] = v.x;
-                w[2 * i + 1] = v.y;
-            }
-        } else {
-            const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
-            #pragma unroll
-            for (int i = 0; i < JH; i++) {
-                const uint2 v = __ldg(p + (jbase + i) * 64 + jlo);
-                w[2 * i] = v.x;
-                w[2 * i + 1] = v.y;
-            }
+        #pragma unroll
+        for (int i = 0; i < JH; i++) {
+            const uint2 v = __ldg(it.ph + (jbase + i) * 64 + jlo);
+            w[2 * i] = v.x;
+            w[2 * i + 1] = v.y;
         }
         if constexpr (JH == 16) tc::tmem_st32(ph_taddr, w);
         else tc::tmem_st16(ph_taddr, w);
@@ -201,11 +205,10 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
     uint8_t *ab = smem + L::off_a + pipe * L::abytes;
     uint64_t *mb = &mbar[pipe];
     const int bar_id = 1 + pipe;
-
+    const int ndt = it.ndt;
+    const int nd = it.nd, nint = it.nint;
     const int half = nd / 2;
     const int seglen = (kM - nd) / nint;
-    const int64_t rows = (int64_t)nsub * nchan;
-    const int64_t obase = (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
     const bool pow2 = (nint & (nint - 1)) == 0 && nint <= 32;
     const int rot = pow2 ? (((tid & 31) * nint) >> 5) : 0;
     const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);
@@ -217,7 +220,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         // ---- chirp, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
         {
             double dmv = 0.0;
-            if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
+            if constexpr (!UNIFORM) dmv = it.dms[d];
             uint32_t w[2 * JH];
             if constexpr (JH == 16) tc::tmem_ld32_async(ph_taddr, w);
             else tc::tmem_ld16_async(ph_taddr, w);
@@ -371,7 +374,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         tc::fence_before();
         tc::bar(bar_id, PT);
         tc::fence_after();
-        float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
+        float *orow = it.out + (int64_t)d * it.dm_stride;
         for (int u = q; u < seglen; u += PT) {
             const float *px = ib + half + u * nint;
             const float *py = px + kM;
@@ -388,11 +391,113 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         }
         tc::bar(bar_id, PT);
     }
-    if (!ok && q == 0) atomicExch(status, 1);
     tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    if (warp == 0) tc::tmem_free(tmem, L::tmem_cols);
+    return __syncthreads_and(ok) != 0;
+}
+
+// AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
+// FP16: three pipes of 256 threads, each carrying one DM at a time through its
+// own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of 512
+// threads (one hi/lo operand set fits).  Within a pipe the chirp stage is split
+// over all its threads, and each tensor-memory read-out is split by column
+// groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
+// One CTA per (DM tile, subband, segment, channel).
+template <bool UNIFORM, int AB>
+__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
+k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
+                const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
+                float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
+                int dm_tile, int nd, int nint, int64_t nout, float scale_out)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x;
+    // once any CTA has given up on a tensor-core wait, the rest of the launch
+    // returns at once (one read, block-uniform decision)
+    if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
+    int64_t item = blockIdx.x;
+    const int c = (int)(item % nchan); item /= nchan;
+    const int kk = (int)(item % kc); item /= kc;
+    const int s = (int)(item % nsub); item /= nsub;
+    const int tile = (int)item;
+    const int dm0 = tile * dm_tile;
+
+    TcItem it;
+    it.src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
+    if constexpr (UNIFORM) it.ph = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
+    else it.ph = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
+    it.dms = dm_list + dm0;
+    it.ndt = min(dm_tile, ndm - dm0);
+    const int seglen = (kM - nd) / nint;
+    const int64_t rows = (int64_t)nsub * nchan;
+    it.out = out + (int64_t)dm0 * rows * nout + (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+    it.dm_stride = rows * nout;
+    it.nd = nd;
+    it.nint = nint;
+    it.scale_out = scale_out;
+
+    const uint32_t tmem = tc_cta_setup<AB>(smem, bmat, twq);
+    const bool ok = tc_run_item<UNIFORM, AB>(it, smem, tmem);
+    if (!ok && tid == 0) atomicExch(status, 1);
+    tc_cta_teardown<AB>(tmem);
+}
+
+// Persistent form for batches of beams of uneven shapes (FP16, evenly spaced
+// DM lists): one CTA per SM takes items from a device queue until the round's
+// items are exhausted.  The round number is read from device memory, so one
+// captured graph serves every round.
+template <int AB>
+__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
+k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__restrict__ round_dev,
+                      int *__restrict__ queue, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
+                      int *__restrict__ status)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    int *next = reinterpret_cast<int *>(smem + TcLayout<AB>::off_misc + 192);
+    const int tid = threadIdx.x;
+    if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
+    const int round = *round_dev;
+    const uint32_t tmem = tc_cta_setup<AB>(smem, bmat, twq);
+    for (;;) {
+        if (tid == 0) *next = atomicAdd(queue, 1);
+        __syncthreads();
+        int64_t item = *next;
+        __syncthreads();
+        // find the beam of this item (items of this round, beam after beam)
+        int b = 0;
+        int64_t kc_b = 0;
+        for (; b < nbeam; b++) {
+            const TcBeam &B = beams[b];
+            const int64_t k0 = (int64_t)round * B.kc;
+            kc_b = k0 < B.nseg ? min((int64_t)B.kc, B.nseg - k0) : 0;
+            const int64_t n = (int64_t)B.ntile * B.nsub * kc_b * B.nchan;
+            if (item < n) break;
+            item -= n;
+        }
+        if (b >= nbeam) break;
+        const TcBeam &B = beams[b];
+        const int c = (int)(item % B.nchan); item /= B.nchan;
+        const int kk = (int)(item % kc_b); item /= kc_b;
+        const int s = (int)(item % B.nsub); item /= B.nsub;
+        const int tile = (int)item;
+        const int dm0 = tile * B.dm_tile;
+        TcItem it;
+        it.src = B.spec + (((int64_t)s * B.kc + kk) * B.nchan + c) * kM;
+        it.ph = B.nco + ((int64_t)tile * B.nsub + s) * (int64_t)B.nchan * kM + (int64_t)c * kM;
+        it.dms = nullptr;
+        it.ndt = min(B.dm_tile, B.ndm - dm0);
+        const int seglen = (kM - B.nd) / B.nint;
+        const int64_t rows = (int64_t)B.nsub * B.nchan;
+        it.out = B.out + (int64_t)dm0 * rows * B.out_stride + (int64_t)(s * B.nchan + c) * B.out_stride + kk * seglen;
+        it.dm_stride = rows * B.out_stride;
+        it.nd = B.nd;
+        it.nint = B.nint;
+        it.scale_out = B.scale;
+        if (!tc_run_item<true, AB>(it, smem, tmem)) {
+            if (tid == 0) atomicExch(status, 1);
+            break;
+        }
+    }
+    tc_cta_teardown<AB>(tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -409,7 +514,24 @@ cudaError_t tc_prepare(int ab)
 {
     cudaError_t e = ab ? set_attr<true, 1>() : set_attr<true, 0>();
     if (e != cudaSuccess) return e;
-    return ab ? set_attr<false, 1>() : set_attr<false, 0>();
+    e = ab ? set_attr<false, 1>() : set_attr<false, 0>();
+    if (e != cudaSuccess) return e;
+    return ab ? cudaFuncSetAttribute(k_dedisperse_tc_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TcLayout<1>::total)
+              : cudaFuncSetAttribute(k_dedisperse_tc_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TcLayout<0>::total);
+}
+
+cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev, int *queue, const uint4 *bmat,
+                            const float2 *twq, int *status, int ab, int nctas, cudaStream_t st)
+{
+    if (ab)
+        k_dedisperse_tc_batch<1><<<nctas, TcLayout<1>::nt, TcLayout<1>::total, st>>>(beams, nbeam, round_dev, queue,
+                                                                                   bmat, twq, status);
+    else
+        k_dedisperse_tc_batch<0><<<nctas, TcLayout<0>::nt, TcLayout<0>::total, st>>>(beams, nbeam, round_dev, queue,
+                                                                                   bmat, twq, status);
+    return cudaGetLastError();
 }
 
 template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
