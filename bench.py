@@ -392,13 +392,96 @@ def gpu_arm(args, w):
     return 0
 
 
+# ---------------------------------------------------------------- batch of uneven beams
+
+BATCH4 = [  # (nsub, log2 nsamp, ndm, nchan, nint): DMs k * 100 / ndm, k < ndm; 195.3125 kHz subbands at 135 MHz
+    (288, 23, 1024, 16, 8),
+    (160, 22, 512, 8, 4),
+    (96, 22, 512, 32, 16),
+    (32, 21, 256, 16, 8),
+]
+
+
+def batch_arm(args):
+    """Four beams of uneven shapes through the batch API: one graph launch per
+    round (forward stage of every beam + one persistent tensor-core launch).
+    A step = every round = the whole input of every beam."""
+    import torch
+
+    import paper_1607_00909_gb300 as cdmt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev)
+    ins, beams, units = [], [], 0.0
+    t0 = time.perf_counter()
+    for i, (nsub, lg, ndm, nchan, nint) in enumerate(BATCH4):
+        g.manual_seed(1000 + i)
+        x = torch.randn((nsub, 1 << lg, 4), generator=g, device=dev, dtype=torch.float32)
+        x.mul_(float(np.sqrt(0.5)))
+        ins.append(x)
+        beams.append(dict(nsub=nsub, nsamp=1 << lg, f_centre=135.0, bw_sub=0.1953125, dm_first=0.0,
+                          dm_step=100.0 / ndm, ndm=ndm, nchan=nchan, nint=nint, d_in=x.data_ptr()))
+    torch.cuda.synchronize(dev)
+    log(f"batch inputs ready in {time.perf_counter() - t0:.1f}s ({sum(x.numel() * 4 for x in ins) / 1e9:.1f} GB)")
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    batch = cdmt.Batch(beams, out_budget=24 << 30, autotune=args.autotune, stream=stream.cuda_stream)
+    log(f"batch planned in {time.perf_counter() - t0:.1f}s: {batch.nround} rounds")
+    per_beam = []
+    for b, inf in zip(beams, batch.infos):
+        units += inf.plan.units
+        per_beam.append({"nsub": b["nsub"], "nsamp": b["nsamp"], "ndm": b["ndm"], "nchan": b["nchan"],
+                         "nint": b["nint"], "nbin": inf.plan.nbin, "nd": inf.plan.nd, "nseg": inf.plan.nseg,
+                         "precision": ["fp32", "fp16", "bf16"][inf.tune.precision], "dm_tile": inf.tune.dm_tile,
+                         "tuned_units_per_s": inf.tune.units_per_s, "seg_per_round": inf.seg_per_round})
+    for _ in range(args.warmup):
+        batch.run_round(0, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    batch.status()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except AttributeError:
+        pass
+    with ClockSampler(bus) as clk:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            batch.run(stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    clocks = clk.summary()
+    batch.status()
+    ms = ev0.elapsed_time(ev1)
+    value = units * args.steps / (ms / 1e3) / 1e9
+    n_fp32 = sum(1 for p in per_beam if p["precision"] == "fp32")
+    launches_per_round = 1 + 2 * len(beams) + 1 + n_fp32
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 (FP32 accumulate)", "data": "synthetic",
+            "config": {"workload": "batch of 4 uneven beams (288/160/96/32 subbands, 2^23/2^22/2^22/2^21 samples, "
+                                   "1024/512/512/256 DMs over 0-100, 16/8/32/16 channels, nint 8/4/16/8)",
+                       "rounds": batch.nround, "beams": per_beam, "autotune": bool(args.autotune),
+                       "l2": "inputs (57 GB) larger than L2; no flush",
+                       "output": "each round's filterbanks are written to the batch's round buffers "
+                                 f"({batch.infos[0].out_bytes_total / 1e9:.1f} GB) and overwritten by the next round"},
+            "gpu_launches": launches_per_round * batch.nround * args.steps, "clocks": clocks,
+            "graph_launches_per_step": batch.nround}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdmt", choices=["cdmt", "reference"])
-    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny"])
+    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny", "batch4"])
+    ap.add_argument("--autotune", action="store_true", help="batch4: time candidates per beam")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
@@ -408,6 +491,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")
+    if args.workload == "batch4" and args.impl != "reference":
+        return batch_arm(args)
     w = workload(args.workload)
     if args.impl == "reference":
         return reference_arm(args, w)
