@@ -474,13 +474,124 @@ def batch_arm(args):
     return 0
 
 
+SERVE = dict(nsub=288, block_len=1 << 16, ndm=1024, dm_max=100.0, nchan=16, nint=8, f_centre=135.0, bw=0.1953125)
+
+
+def _serve_run(cdmt, srv, beams, host_blocks, scale, nblk, pace_s=0.0):
+    """Submit nblk blocks per beam (round-robin over beams; every pace_s seconds a
+    round when pacing), wait for each in submission order, release its slot."""
+    reqs = []
+    t0 = time.perf_counter()
+    for k in range(nblk):
+        if pace_s > 0:
+            dt = t0 + k * pace_s - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        for b in beams:
+            blk = host_blocks[(k + b) % len(host_blocks)]
+            reqs.append(srv.submit(b, blk.data_ptr(), scale.data_ptr() if scale is not None else 0))
+        if pace_s > 0:  # under pacing, drain what is done before the next round arrives
+            while reqs and srv.stats().blocks_running + srv.stats().blocks_queued < len(reqs):
+                srv.wait(reqs[0], 600.0)
+                srv.release(reqs.pop(0))
+    for r in reqs:
+        srv.wait(r, 600.0)
+        srv.release(r)
+
+
+def serve_arm(args):
+    """Streaming server: SERVE-shaped beams, blocks from pinned host memory.
+
+    Three runs through one server: every beam saturated (blocks queued ahead:
+    throughput and aggregate real-time factor), one beam saturated (its real-time
+    factor), one beam paced at the data rate (its latency when blocks arrive in
+    real time)."""
+    import torch
+
+    import paper_1607_00909_gb300 as cdmt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c = SERVE
+    i8 = args.int8
+    shape = (c["nsub"], c["block_len"], 4)
+    g = torch.Generator(device=dev)
+    host_blocks = []
+    for i in range(4):
+        g.manual_seed(5000 + i)
+        if i8:
+            d = torch.randint(-24, 25, shape, generator=g, device=dev, dtype=torch.int8)
+        else:
+            d = torch.randn(shape, generator=g, device=dev, dtype=torch.float32)
+        h = torch.empty(shape, dtype=d.dtype, pin_memory=True)
+        h.copy_(d)
+        host_blocks.append(h)
+    scale = torch.full((c["nsub"],), 0.05, dtype=torch.float32).pin_memory() if i8 else None
+    srv = cdmt.Server(hbm_budget=120 << 30)
+    t0 = time.perf_counter()
+    beams = [srv.add_beam(c["nsub"], c["block_len"], c["f_centre"], c["bw"], 0.0, c["dm_max"] / c["ndm"], c["ndm"],
+                          c["nchan"], c["nint"], precision=cdmt.CDMT_PREC_FP16,
+                          in_dtype=cdmt.CDMT_IN_I8 if i8 else cdmt.CDMT_IN_C64) for _ in range(args.beams)]
+    st0 = srv.stats()
+    log(f"{args.beams} beams admitted in {time.perf_counter() - t0:.1f}s: {st0.hbm_bytes / 1e9:.1f} GB, "
+        f"{st0.slots} output slots")
+    _serve_run(cdmt, srv, beams, host_blocks, scale, args.warmup)
+    torch.cuda.synchronize(dev)
+    srv.reset_stats()
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except AttributeError:
+        pass
+    with ClockSampler(bus) as clk:
+        _serve_run(cdmt, srv, beams, host_blocks, scale, args.steps)
+    clocks = clk.summary()
+    sat = srv.stats()
+    block_s = c["block_len"] / (c["bw"] * 1e6)
+    srv.reset_stats()
+    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(4, args.steps))
+    one = srv.stats()
+    srv.reset_stats()
+    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(8, args.steps), pace_s=block_s)
+    paced = srv.stats()
+    srv.close()
+    value = sat.units_per_s / 1e9
+    in_bytes = (4 if i8 else 16) * c["nsub"] * c["block_len"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sat.wall_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16 (FP32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"streaming server, {args.beams} beams x {c['nsub']} subbands, blocks of "
+                                   f"2^16 samples ({block_s * 1e3:.1f} ms of data), {c['ndm']} DMs 0-{c['dm_max']:g}, "
+                                   f"{c['nchan']} channels, nint {c['nint']}, "
+                                   + ("int8 input" if i8 else "complex64 input"),
+                       "step": "one block of every beam, from pinned host memory",
+                       "l2": "per-block inputs and outputs larger than L2; no flush",
+                       "hbm_bytes": sat.hbm_bytes, "output_slots": sat.slots},
+            "serving": {"all_beams": {"realtime_factor": sat.realtime_factor, "latency_p50_ms": sat.latency_p50_ms,
+                                      "latency_p99_ms": sat.latency_p99_ms, "blocks": sat.blocks_done,
+                                      "note": "blocks queued ahead (saturated); latency includes queueing"},
+                        "one_beam": {"realtime_factor": one.realtime_factor, "units_per_s": one.units_per_s,
+                                     "latency_p50_ms": one.latency_p50_ms, "latency_p99_ms": one.latency_p99_ms},
+                        "one_beam_paced": {"latency_p50_ms": paced.latency_p50_ms,
+                                           "latency_p99_ms": paced.latency_p99_ms,
+                                           "latency_max_ms": paced.latency_max_ms, "blocks": paced.blocks_done}},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": in_bytes * args.beams,
+                    "d2h_bytes_per_step": 0,
+                    "note": "host blocks in; the filterbanks stay in device slots for the consumer"},
+            "roofline": None, "gpu_launches": 4 * args.beams * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdmt", choices=["cdmt", "reference"])
-    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny", "batch4"])
+    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny", "batch4", "serve8"])
+    ap.add_argument("--beams", type=int, default=8, help="serve8: beams served at once")
+    ap.add_argument("--int8", action="store_true", help="serve8: int8 blocks (4 bytes per sample)")
     ap.add_argument("--autotune", action="store_true", help="batch4: time candidates per beam")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -493,6 +604,8 @@ def main():
         log("note: fewer than 3 warm-up steps")
     if args.workload == "batch4" and args.impl != "reference":
         return batch_arm(args)
+    if args.workload == "serve8" and args.impl != "reference":
+        return serve_arm(args)
     w = workload(args.workload)
     if args.impl == "reference":
         return reference_arm(args, w)

@@ -345,6 +345,98 @@ const char *cdmt_batch_last_error(cdmt_batch_t batch);
 /* cdmt_batch_destroy - free the batch (waits for the device first). */
 int cdmt_batch_destroy(cdmt_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Streaming server: real-time blocks of several beams, continuously batched.
+ *
+ * Each beam added to a server keeps its plan, its overlap tail (the input
+ * samples that do not yet complete an overlap-save segment, Sec. 2) and a
+ * block buffer resident on the device.  Submitted blocks are queued; a
+ * scheduler thread dispatches them in arrival order across beams whenever an
+ * output slot is free (blocks of one beam stay in order on that beam's CUDA
+ * stream; blocks of different beams overlap on the GPU).  The slot pool is sized
+ * from the HBM budget left after the resident beam state, so new blocks are
+ * admitted as slots and memory free up.  A block's filterbank holds every
+ * segment the block completes (Algorithm 1's block loop run per beam).
+ */
+typedef struct cdmt_server_s *cdmt_server_t;
+
+typedef struct cdmt_server_opts {
+    int64_t hbm_budget;    /* bytes the server may hold (0: 120 GiB) */
+    int32_t max_slots;     /* upper bound on output slots (0: 64) */
+    int32_t reserved0;
+    int64_t reserved[6];
+} cdmt_server_opts;
+
+typedef struct cdmt_stream_desc {
+    int32_t nsub, ndm;
+    int64_t block_len;     /* samples per subband per block */
+    double f_centre_mhz, bw_sub_mhz;
+    double dm_first, dm_step;
+    int32_t nchan, nint;
+    int32_t precision;     /* enum cdmt_precision */
+    int32_t in_dtype;      /* CDMT_IN_C64: 16-byte samples; CDMT_IN_I8: 4 int8 per sample + nsub float scales */
+    int64_t nbin;          /* 0: 4096 * nchan */
+    int32_t dm_tile;       /* DM trials per work item (0: the plan's choice) */
+    int32_t reserved0;
+    int64_t reserved[4];
+} cdmt_stream_desc;
+
+typedef struct cdmt_block_result {
+    int32_t beam;
+    int32_t reserved0;
+    int64_t index;         /* block number within the beam (submission order) */
+    float *d_out;          /* DEVICE slot: float32 [ndm][nsub*nchan][row_stride], this block's samples in
+                              columns [0, samples); valid until cdmt_server_release */
+    int64_t nseg;          /* overlap-save segments this block completed (0 while the stream fills) */
+    int64_t first_sample;  /* output-sample index (per channel, since the stream start) of column 0 */
+    int64_t samples;       /* output samples per row in this block = nseg * (M - nd) / nint */
+    int64_t row_stride;
+    double latency_ms;     /* submit -> completion */
+} cdmt_block_result;
+
+typedef struct cdmt_server_stats {
+    int64_t blocks_done, blocks_queued, blocks_running;
+    double latency_p50_ms, latency_p99_ms, latency_max_ms;
+    double wall_s;          /* first submit to last completion */
+    double data_s;          /* seconds of voltage data completed, summed over beams */
+    double realtime_factor; /* data_s / wall_s */
+    double units_per_s;     /* DM-trial x samples per second */
+    int64_t hbm_bytes;      /* resident beam state + output slots */
+    int32_t slots;
+    int32_t reserved0;
+} cdmt_server_stats;
+
+/* create / destroy a server (destroy waits for its GPU work; output slots and
+ * beam state are freed) */
+int cdmt_server_create(cdmt_server_t *server, const cdmt_server_opts *opts);
+int cdmt_server_destroy(cdmt_server_t server);
+
+/* cdmt_server_add_beam - admit a beam: plans it and allocates its resident
+ * state; CDMT_EBUDGET if that state plus one output slot does not fit the HBM
+ * budget.  *beam_id receives the beam's index. */
+int cdmt_server_add_beam(cdmt_server_t server, const cdmt_stream_desc *desc, int *beam_id);
+
+/* cdmt_server_submit - queue the next block of a beam.  block: [nsub][block_len]
+ * samples in host (pinned for asynchronous copies) or device memory; scale:
+ * nsub floats (host or device) for int8 blocks.  Both must stay valid until the
+ * block completes.  Returns at once with *request_id. */
+int cdmt_server_submit(cdmt_server_t server, int beam, const void *block, const float *scale, int64_t *request_id);
+
+/* cdmt_server_wait - wait up to timeout_s for a block (CDMT_ETIMEOUT after) and
+ * describe its output in *result (may be NULL). */
+int cdmt_server_wait(cdmt_server_t server, int64_t request_id, double timeout_s, cdmt_block_result *result);
+
+/* cdmt_server_release - give a completed block's output slot back. */
+int cdmt_server_release(cdmt_server_t server, int64_t request_id);
+
+/* cdmt_server_get_stats - latency percentiles, real-time factor and throughput of
+ * the blocks completed since the start (or the last reset). */
+int cdmt_server_get_stats(cdmt_server_t server, cdmt_server_stats *stats);
+int cdmt_server_reset_stats(cdmt_server_t server);
+
+/* cdmt_server_last_error - message of the last failure on the server. */
+const char *cdmt_server_last_error(cdmt_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

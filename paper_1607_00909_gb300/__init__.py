@@ -64,6 +64,33 @@ class cdmt_batch_beam_info(ctypes.Structure):
                 ("out_row_stride", ctypes.c_int64), ("out_bytes_total", ctypes.c_int64)]
 
 
+class cdmt_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
+class cdmt_stream_desc(ctypes.Structure):
+    _fields_ = [("nsub", ctypes.c_int32), ("ndm", ctypes.c_int32), ("block_len", ctypes.c_int64),
+                ("f_centre_mhz", ctypes.c_double), ("bw_sub_mhz", ctypes.c_double), ("dm_first", ctypes.c_double),
+                ("dm_step", ctypes.c_double), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("nbin", ctypes.c_int64),
+                ("dm_tile", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+
+
+class cdmt_block_result(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("index", ctypes.c_int64),
+                ("d_out", ctypes.c_void_p), ("nseg", ctypes.c_int64), ("first_sample", ctypes.c_int64),
+                ("samples", ctypes.c_int64), ("row_stride", ctypes.c_int64), ("latency_ms", ctypes.c_double)]
+
+
+class cdmt_server_stats(ctypes.Structure):
+    _fields_ = [("blocks_done", ctypes.c_int64), ("blocks_queued", ctypes.c_int64), ("blocks_running", ctypes.c_int64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double), ("wall_s", ctypes.c_double), ("data_s", ctypes.c_double),
+                ("realtime_factor", ctypes.c_double), ("units_per_s", ctypes.c_double), ("hbm_bytes", ctypes.c_int64),
+                ("slots", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
 class CdmtError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} [status {status}]")
@@ -86,6 +113,16 @@ def _load():
     lib.cdmt_destroy.argtypes = [P]
     lib.cdmt_set_timing.argtypes = [P, ctypes.c_int]
     lib.cdmt_device_status.argtypes = [P]
+    lib.cdmt_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(cdmt_server_opts)]
+    lib.cdmt_server_destroy.argtypes = [P]
+    lib.cdmt_server_add_beam.argtypes = [P, ctypes.POINTER(cdmt_stream_desc), ctypes.POINTER(ctypes.c_int)]
+    lib.cdmt_server_submit.argtypes = [P, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.cdmt_server_wait.argtypes = [P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(cdmt_block_result)]
+    lib.cdmt_server_release.argtypes = [P, ctypes.c_int64]
+    lib.cdmt_server_get_stats.argtypes = [P, ctypes.POINTER(cdmt_server_stats)]
+    lib.cdmt_server_reset_stats.argtypes = [P]
+    lib.cdmt_server_last_error.argtypes = [P]
+    lib.cdmt_server_last_error.restype = ctypes.c_char_p
     lib.cdmt_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(cdmt_beam),
                                       ctypes.POINTER(cdmt_batch_opts), P]
     lib.cdmt_batch_info.argtypes = [P, ctypes.c_int, ctypes.POINTER(cdmt_batch_beam_info)]
@@ -106,7 +143,9 @@ def _load():
     for f in ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
               "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status", "cdmt_execute_static",
               "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run", "cdmt_batch_status",
-              "cdmt_batch_destroy", "cdmt_batch_copy_out"):
+              "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
+              "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
+              "cdmt_server_get_stats", "cdmt_server_reset_stats"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -116,7 +155,10 @@ _lib = _load()
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
             "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
-            "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out")
+            "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
+            "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
+            "cdmt_server_wait", "cdmt_server_release", "cdmt_server_get_stats", "cdmt_server_reset_stats",
+            "cdmt_server_last_error")
 
 
 def lib():
@@ -262,6 +304,109 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             cdmt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cdmt_server_last_error(server=None) -> str:
+    return _lib.cdmt_server_last_error(server).decode()
+
+
+def _scheck(rc: int, server=None):
+    if rc != CDMT_OK:
+        raise CdmtError(rc, f"{cdmt_strerror(rc)}: {cdmt_server_last_error(server)}")
+
+
+def cdmt_server_create(opts: cdmt_server_opts | None = None):
+    h = ctypes.c_void_p()
+    _scheck(_lib.cdmt_server_create(ctypes.byref(h), ctypes.byref(opts) if opts else None))
+    return h.value
+
+
+def cdmt_server_destroy(server):
+    _scheck(_lib.cdmt_server_destroy(server))
+
+
+def cdmt_server_add_beam(server, desc: cdmt_stream_desc) -> int:
+    b = ctypes.c_int()
+    _scheck(_lib.cdmt_server_add_beam(server, ctypes.byref(desc), ctypes.byref(b)), server)
+    return b.value
+
+
+def cdmt_server_submit(server, beam: int, block: int, scale: int = 0) -> int:
+    r = ctypes.c_int64()
+    _scheck(_lib.cdmt_server_submit(server, beam, block, scale or None, ctypes.byref(r)), server)
+    return r.value
+
+
+def cdmt_server_wait(server, request: int, timeout_s: float = 60.0) -> cdmt_block_result:
+    res = cdmt_block_result()
+    _scheck(_lib.cdmt_server_wait(server, request, timeout_s, ctypes.byref(res)), server)
+    return res
+
+
+def cdmt_server_release(server, request: int):
+    _scheck(_lib.cdmt_server_release(server, request), server)
+
+
+def cdmt_server_get_stats(server) -> cdmt_server_stats:
+    st = cdmt_server_stats()
+    _scheck(_lib.cdmt_server_get_stats(server, ctypes.byref(st)), server)
+    return st
+
+
+def cdmt_server_reset_stats(server):
+    _scheck(_lib.cdmt_server_reset_stats(server), server)
+
+
+class Server:
+    """Owning wrapper of a streaming server."""
+
+    def __init__(self, hbm_budget=0, max_slots=0):
+        o = cdmt_server_opts()
+        o.hbm_budget, o.max_slots = int(hbm_budget), int(max_slots)
+        self.handle = cdmt_server_create(o)
+
+    def add_beam(self, nsub, block_len, f_centre, bw_sub, dm_first, dm_step, ndm, nchan, nint,
+                 precision=CDMT_PREC_FP16, in_dtype=CDMT_IN_C64, nbin=0, dm_tile=0) -> int:
+        d = cdmt_stream_desc(int(nsub), int(ndm), int(block_len), float(f_centre), float(bw_sub), float(dm_first),
+                             float(dm_step), int(nchan), int(nint), int(precision), int(in_dtype), int(nbin),
+                             int(dm_tile))
+        return cdmt_server_add_beam(self.handle, d)
+
+    def submit(self, beam, block_ptr, scale_ptr=0) -> int:
+        return cdmt_server_submit(self.handle, beam, block_ptr, scale_ptr)
+
+    def wait(self, request, timeout_s=60.0):
+        return cdmt_server_wait(self.handle, request, timeout_s)
+
+    def release(self, request):
+        cdmt_server_release(self.handle, request)
+
+    def stats(self):
+        return cdmt_server_get_stats(self.handle)
+
+    @staticmethod
+    def block_view(res: cdmt_block_result, ndm: int, rows: int):
+        """Zero-copy torch view [ndm][rows][samples] of a finished block's output slot (valid until release)."""
+        import torch
+
+        class _Slot:
+            __cuda_array_interface__ = {"shape": (ndm, rows, res.row_stride), "typestr": "<f4",
+                                        "data": (res.d_out, False), "version": 3, "strides": None}
+        return torch.as_tensor(_Slot(), device="cuda")[:, :, :res.samples]
+
+    def reset_stats(self):
+        cdmt_server_reset_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cdmt_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -234,6 +234,12 @@ int mark(cdmt_plan_s *p, cudaStream_t st)
     return CDMT_OK;
 }
 
+}  // namespace
+
+namespace cdmt {
+// Forward stage and DM stage of kc segments of `in` (segment kk at
+// in + (in_k0 + kk) * S, subbands in_stride samples apart) into `out`
+// (rows out_stride floats apart, segment kk at (out_k0 + kk) * seglen).
 int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
                   int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st)
 {
@@ -306,9 +312,7 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
     return CDMT_OK;
 }
 
-}  // namespace
 
-namespace cdmt {
 // lets other translation units of the library report an error before a plan exists
 void set_thread_error(const char *msg) { g_thread_error = msg; }
 

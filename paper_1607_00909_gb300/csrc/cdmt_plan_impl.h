@@ -59,4 +59,7 @@ struct cdmt_plan_s {
 namespace cdmt {
 // overlap n_d of Sec. 2 for a band (defined in cdmt_host.cu); -1 if none < M
 int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin);
+// forward stage + DM stage of kc segments (defined in cdmt_host.cu)
+int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
+                  int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st);
 }  // namespace cdmt

@@ -1,0 +1,129 @@
+"""Streaming server: blocks of several beams, continuously batched.
+
+A beam streamed block by block must give exactly the filterbank of the
+offline plan on its whole input (the same overlap-save segments through the
+same kernels, so bit-identical); a beam's results must be the same alone and
+in a mix with other beams whose blocks overlap on the GPU; int8 blocks must
+match their dequantised float equivalent; admission must refuse a beam that
+does not fit the HBM budget; a wait that cannot finish must time out.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+BW = 0.1953125
+
+
+@pytest.fixture(scope="module")
+def cdmt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1607_00909_gb300 as m
+    return m
+
+
+# block lengths below, at and above N, so that some blocks complete no segment
+BEAMS = [
+    dict(nsub=2, block_len=1 << 14, f_centre=135.0, dm_first=0.0, dm_step=2.0, ndm=6, nchan=8, nint=4, seed=51),
+    dict(nsub=3, block_len=3 << 13, f_centre=150.0, dm_first=1.0, dm_step=1.5, ndm=5, nchan=16, nint=8, seed=52),
+    dict(nsub=1, block_len=1 << 15, f_centre=120.0, dm_first=0.0, dm_step=5.0, ndm=3, nchan=8, nint=2, seed=53),
+]
+NBLK = 8
+
+
+def _serve(cdmt, beams, inputs, interleave=True, i8=False, scales=None, precision=None, max_slots=0):
+    import torch
+    precision = cdmt.CDMT_PREC_FP16 if precision is None else precision
+    srv = cdmt.Server(max_slots=max_slots)
+    ids = [srv.add_beam(b["nsub"], b["block_len"], b["f_centre"], BW, b["dm_first"], b["dm_step"], b["ndm"],
+                        b["nchan"], b["nint"], precision=precision,
+                        in_dtype=cdmt.CDMT_IN_I8 if i8 else cdmt.CDMT_IN_C64, dm_tile=b["ndm"]) for b in beams]
+    blocks = []
+    for b, x in zip(beams, inputs):
+        L = b["block_len"]
+        blocks.append([torch.from_numpy(np.ascontiguousarray(x[:, k * L:(k + 1) * L])).pin_memory()
+                       for k in range(NBLK)])
+    sc = [torch.from_numpy(s).pin_memory() for s in scales] if scales is not None else None
+    order = [(k, bi) for k in range(NBLK) for bi in range(len(beams))] if interleave else \
+        [(k, bi) for bi in range(len(beams)) for k in range(NBLK)]
+    reqs = [(bi, k, srv.submit(ids[bi], blocks[bi][k].data_ptr(), sc[bi].data_ptr() if sc else 0))
+            for k, bi in order]
+    parts = [dict() for _ in beams]
+    for bi, k, rid in reqs:
+        res = srv.wait(rid, 120.0)
+        b = beams[bi]
+        assert res.beam == ids[bi] and res.index == k
+        if res.samples > 0:
+            parts[bi][res.first_sample] = srv.block_view(res, b["ndm"], b["nsub"] * b["nchan"]).cpu().numpy()
+        srv.release(rid)
+    st = srv.stats()
+    srv.close()
+    out = []
+    for p in parts:
+        keys = sorted(p)
+        pos = 0
+        for k in keys:  # the blocks tile the output with no gap or overlap
+            assert k == pos
+            pos += p[k].shape[2]
+        out.append(np.concatenate([p[k] for k in keys], axis=2))
+    return out, st
+
+
+def _offline(cdmt, b, x, precision):
+    import torch
+    dms = [b["dm_first"] + i * b["dm_step"] for i in range(b["ndm"])]
+    p = cdmt.Plan(b["nsub"], x.shape[1], b["f_centre"], BW, dms, b["nchan"], b["nint"], nbin=4096 * b["nchan"],
+                  dm_tile=b["ndm"], precision=precision)
+    out = cdmt.run(p, torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
+    p.close()
+    return out
+
+
+def _inputs(beams):
+    xs = [synth.noise(b["seed"], b["nsub"], NBLK * b["block_len"]) for b in beams]
+    synth.add_pulses(xs[0], [synth.Pulse(0.4, 6.0, 1e-3, 0.5)], beams[0]["f_centre"], BW, beams[0]["seed"])
+    return xs
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp32"])
+def test_stream_equals_offline_and_mix_equals_alone(cdmt, prec):
+    precision = cdmt.CDMT_PREC_FP16 if prec == "fp16" else cdmt.CDMT_PREC_FP32
+    xs = _inputs(BEAMS)
+    # two output slots: blocks wait for a free slot, so dispatch order and slot reuse are exercised
+    mixed, st = _serve(cdmt, BEAMS, xs, interleave=True, precision=precision, max_slots=2)
+    assert st.blocks_done == NBLK * len(BEAMS) and st.slots == 2
+    assert 0 < st.latency_p50_ms <= st.latency_p99_ms <= st.latency_max_ms
+    assert st.realtime_factor > 0 and st.units_per_s > 0
+    for bi, (b, x) in enumerate(zip(BEAMS, xs)):
+        alone, _ = _serve(cdmt, [b], [x], interleave=False, precision=precision)
+        assert np.array_equal(alone[0], mixed[bi]), bi
+        off = _offline(cdmt, b, x, precision)
+        assert off.shape == mixed[bi].shape, (off.shape, mixed[bi].shape)
+        assert np.array_equal(off, mixed[bi]), bi
+
+
+def test_int8_blocks(cdmt):
+    b = BEAMS[0]
+    x = _inputs([b])[0]
+    scale = (np.abs(x).reshape(b["nsub"], -1).max(axis=1) / 127.0).astype(np.float32)
+    q = np.clip(np.rint(x / scale[:, None, None]), -127, 127).astype(np.int8)
+    deq = q.astype(np.float32) * scale[:, None, None]
+    got, _ = _serve(cdmt, [b], [q], interleave=False, i8=True, scales=[scale])
+    assert np.array_equal(got[0], _offline(cdmt, b, deq, cdmt.CDMT_PREC_FP16))
+
+
+def test_admission_and_errors(cdmt):
+    srv = cdmt.Server(hbm_budget=64 << 20)
+    with pytest.raises(cdmt.CdmtError) as e:
+        srv.add_beam(64, 1 << 16, 135.0, BW, 0.0, 0.5, 128, 16, 8)
+    assert e.value.status == cdmt.CDMT_EBUDGET
+    with pytest.raises(cdmt.CdmtError) as e:
+        srv.submit(0, 1)
+    assert e.value.status == cdmt.CDMT_EINVAL
+    with pytest.raises(cdmt.CdmtError) as e:
+        srv.wait(12345, 0.1)
+    assert e.value.status == cdmt.CDMT_EINVAL
+    srv.close()
