@@ -123,16 +123,22 @@ __device__ __forceinline__ double chirp_k(double f_centre, double bw, int nsub, 
 // 32-bit fixed-point fraction of x cycles (x * 2^32 rounded, modulo 2^32)
 __device__ __forceinline__ uint32_t fix32(double x) { return (uint32_t)(unsigned long long)llrint(x * 4294967296.0); }
 
+// shift != 0 (tensor-core form): the start words also carry a phase ramp of
+// shift * j / M cycles on bin j of each channel, which delays the channel's
+// backward DFT output by `shift` samples (exact: shift * j * 2^32 / 4096 is an
+// integer multiple of 2^20).
 __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, double f_centre, double bw, int nsub,
-                            int nchan, int64_t nbin, int ntile)
+                            int nchan, int64_t nbin, int ntile, int shift)
 {
+    const int64_t mbin = nbin / nchan;
     const int64_t total = (int64_t)ntile * nsub * nbin;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q % nbin;
         const int s = (int)((q / nbin) % nsub);
         const int tile = (int)(q / ((int64_t)nbin * nsub));
         const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i);
-        nco[q] = make_uint2(fix32(-dm_tile0[tile] * k), fix32(-ddm * k));
+        const uint32_t ramp = shift ? (uint32_t)((i % mbin) * shift) << 20 : 0u;
+        nco[q] = make_uint2(fix32(-dm_tile0[tile] * k) + ramp, fix32(-ddm * k));
     }
 }
 
@@ -421,6 +427,10 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)p->mbin);
     }
     p->r = (int)(p->mbin / 256);
+    if (p->precision != CDMT_PREC_FP32 && 32 % nint != 0) {
+        delete p;
+        return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need nint dividing 32 (got %d)", nint);
+    }
     if (p->precision != CDMT_PREC_FP32 && p->mbin != 4096) {
         delete p;
         return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need M_bin = 4096 (got %lld)", (long long)p->mbin);
@@ -526,7 +536,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     if (p->uniform) {
         TRYC(cudaMalloc(&d_tile0, sizeof(double) * p->ntile));
         TRYC(cudaMemcpy(d_tile0, tile0.data(), sizeof(double) * p->ntile, cudaMemcpyHostToDevice));
-        k_nco_table<<<1024, 256>>>(p->nco, d_tile0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile);
+        k_nco_table<<<1024, 256>>>(p->nco, d_tile0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile,
+                                   p->precision != CDMT_PREC_FP32 ? (int)(p->nd / 2) : 0);
     } else {
         k_k_table<<<1024, 256>>>(p->ktab, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin);
     }

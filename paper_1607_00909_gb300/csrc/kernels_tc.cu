@@ -4,14 +4,23 @@
 // j = 64 j_hi + j_lo, output m = m0 + 64 m1):
 //   pass A  for every j_lo:  y[m0] = sum_j_hi x[64 j_hi + j_lo] W_64^{j_hi m0},  y *= W_4096^{j_lo m0}
 //   pass B  for every m0:    z[m1] = sum_j_lo y_j_lo[m0] W_64^{j_lo m1}
-// Each pass is one real GEMM on the tensor cores: 128 rows (64 groups x 2
-// polarisations) by K = 128 (64 complex inputs, real and imaginary parts
-// interleaved) by N = 128 (64 complex outputs), with the 128 x 128 real form of
-// the 64-point DFT matrix as operand B, half-precision operands and an FP32
-// accumulator in tensor memory.  Between the passes each thread reads its own
-// GEMM row from tensor memory, applies the W_4096 twiddles in FP32 and writes
-// the row as a K-column of the next operand (MN-major layout), so the
-// transposition costs only 16-byte shared-memory stores.
+// Each pass is one real GEMM on the tensor cores, 128 x 128 x 128, with the
+// 128 x 128 real form of the 64-point DFT matrix F (real and imaginary parts
+// interleaved) as one operand, half-precision operands and an FP32
+// accumulator in tensor memory:
+//   pass A  D[(pol, j_lo)][(m0, re/im)]  = X[(pol, j_lo)][(j_hi, re/im)] . F
+//   pass B  D[(m1, re/im)][(pol, m0)]    = F^T . Y[(j_lo, re/im)][(pol, m0)]
+// Between the passes each thread reads its own pass-A row from tensor memory,
+// applies the W_4096 twiddles in FP32 and writes it as a K-row of pass B's
+// data operand (MN-major), so the transposition costs only 16-byte shared-memory
+// stores.  Pass B's orientation puts the real and imaginary parts of one time
+// sample in neighbouring TMEM lanes and both polarisations and consecutive
+// time samples in one thread's columns, so detection and integration run in
+// registers: one fused multiply-add per value, one shuffle per output.  The
+// time shift by n_d / 2 that drops the wrapped overlap (Sec. 2) is folded into
+// the chirp phase (a circular shift of the output is a phase ramp on the
+// bins, exact in the 32-bit fixed-point phase), so integration windows start
+// on multiples of nint; nint must divide 32.
 //
 // The chirp (Eq. 1, conjugated) and the data scaling run in FP32 before the
 // rounding to half precision; the chirp phase comes from the same FP64-derived
@@ -83,6 +92,61 @@ template <int AB> __device__ __forceinline__ uint32_t pk(float lo, float hi)
 
 // hi part of a bf16 split: round to bf16 and back
 __device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__float_as_uint(__uint_as_float(tc::pack_bf16(x, 0.f) << 16))); }
+
+// Detection and integration of one pass-B result, by the thread of TMEM lane
+// 2 m1 + ro (ro: 0 real, 1 imaginary part) and column group cg (m0 in
+// [32 cg, 32 cg + 32)).  Columns pol * 64 + m0 hold polarisation pol at time
+// m' = m0 + 64 m1, counted from the first valid sample.  Each thread sums the
+// squares of its part over both polarisations and N consecutive m0, then the
+// lane pair (re, im) adds its partial sums: ro = 0 keeps the first half of the
+// windows of a chunk and ro = 1 the second half, one shuffle per output.
+template <int N>
+__device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro, float *__restrict__ orow, int seglen,
+                                          float oscale)
+{
+    constexpr int WC = N >= 16 ? 1 : 16 / N;   // windows (or window halves, N = 32) per chunk of 16 m0
+    float carry = 0.f;
+    #pragma unroll
+    for (int h = 0; h < 2; h++) {
+        float acc[WC];
+        #pragma unroll
+        for (int c = 0; c < 2; c++) {   // 8 columns of each polarisation at a time
+            uint32_t bx[8], by[8];
+            tc::tmem_ld8_async(taddr + 32 * cg + 16 * h + 8 * c, bx);
+            tc::tmem_ld8_async(taddr + 64 + 32 * cg + 16 * h + 8 * c, by);
+            tc::tmem_wait();
+            #pragma unroll
+            for (int i8 = 0; i8 < 8; i8++) {
+                const int i = 8 * c + i8;
+                const float x = __uint_as_float(bx[i8]), y = __uint_as_float(by[i8]);
+                const int w = N >= 16 ? 0 : i / N;
+                acc[w] = (i % N == 0) ? x * x : fmaf(x, x, acc[w]);
+                acc[w] = fmaf(y, y, acc[w]);
+            }
+        }
+        if constexpr (N == 32) {
+            if (h == 0) {
+                carry = acc[0];
+                continue;
+            }
+            acc[0] += carry;
+        }
+        const int ubase = (64 * m1 + 32 * cg + (N == 32 ? 0 : 16 * h)) / N;
+        if constexpr (WC == 1) {
+            const float tot = acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
+            if (ro == 0 && ubase < seglen) orow[ubase] = tot * oscale;
+        } else {
+            #pragma unroll
+            for (int k = 0; k < WC / 2; k++) {
+                const float send = ro ? acc[k] : acc[k + WC / 2];
+                const float keep = ro ? acc[k + WC / 2] : acc[k];
+                const float tot = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+                const int u = ubase + ro * (WC / 2) + k;
+                if (u < seglen) orow[u] = tot * oscale;
+            }
+        }
+    }
+}
 
 }  // namespace
 
@@ -209,10 +273,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     const int nd = it.nd, nint = it.nint;
     const int half = nd / 2;
     const int seglen = (kM - nd) / nint;
-    const bool pow2 = (nint & (nint - 1)) == 0 && nint <= 32;
-    const int rot = pow2 ? (((tid & 31) * nint) >> 5) : 0;
-    const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);
-    const uint32_t id_b = tc::idesc(128, 128, AB, 1, 0);
+    const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);   // pass A: data (K-major) x F (K-major)
+    const uint32_t id_b = tc::idesc(128, 128, AB, 0, 1);   // pass B: F^T (K-major) x data (MN-major)
     const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
     uint32_t ok = 1;
 
@@ -240,7 +302,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                         const double kj = __hiloint2double((int)w[2 * b + 1], (int)w[2 * b]);
                         double cyc = dmv * kj;
                         cyc -= rint(cyc);
-                        __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
+                        const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << 20);
+                        __sincosf((float)(int32_t)pf * kTwoPiOver2p32, &sn, &cs);
                     }
                     const float4 v = xs[j];
                     const float xr = v.x * cs - v.y * sn, xi = v.x * sn + v.y * cs;
@@ -335,12 +398,12 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (q == 0) {
             #pragma unroll 1
             for (int ks = 0; ks < 8; ks++) {
-                const uint64_t bh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
-                tc::mma(dcol, tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB), bh, id_b, ks > 0);
+                const uint64_t fh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
+                const uint64_t yh = tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB);
+                tc::mma(dcol, fh, yh, id_b, ks > 0);
                 if constexpr (AB) {
-                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), bh, id_b, 1);
-                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB),
-                            tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), id_b, 1);
+                    tc::mma(dcol, fh, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), id_b, 1);
+                    tc::mma(dcol, tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), yh, id_b, 1);
                 }
             }
             tc::commit(mb);
@@ -349,47 +412,21 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (!ok) break;
         tc::fence_after();
 
-        // ---- detect: row = pol * 64 + m0 holds z[m1], time sample m = m0 + 64 m1
-        float *ib = reinterpret_cast<float *>(ab);   // [2][4096], the operand is consumed
-        {
-            const int pol = t >> 6, m0 = t & 63;
-            constexpr int NST = COLS / 16;
-            uint32_t buf[2][16];
-            #pragma unroll
-            for (int st = 0; st < NST; st++) {
-                if ((st & 1) == 0) {
-                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * st, buf[0]);
-                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * (st + 1), buf[1]);
-                    tc::tmem_wait();
-                }
-                const uint32_t *v = buf[st & 1];
-                const int m1b = (cg * COLS + 16 * st) / 2;
-                #pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const float a = __uint_as_float(v[2 * i]), b = __uint_as_float(v[2 * i + 1]);
-                    ib[pol * kM + m0 + 64 * (m1b + i)] = fmaf(a, a, b * b);
-                }
+        // ---- detect + integrate in registers (see the head of this file), by two
+        //      column groups of 32 m0 (BF16: the pipe's other two warpgroups skip)
+        if (NCG == 2 || cg < 2) {
+            float *orow = it.out + (int64_t)d * it.dm_stride;
+            const uint32_t taddr = dcol + lane_off;
+            const int m1 = t >> 1, ro = t & 1;
+            switch (nint) {
+            case 1: tc_detect<1>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 2: tc_detect<2>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 4: tc_detect<4>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 8: tc_detect<8>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 16: tc_detect<16>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            default: tc_detect<32>(taddr, cg, m1, ro, orow, seglen, oscale); break;
             }
         }
-        tc::fence_before();
-        tc::bar(bar_id, PT);
-        tc::fence_after();
-        float *orow = it.out + (int64_t)d * it.dm_stride;
-        for (int u = q; u < seglen; u += PT) {
-            const float *px = ib + half + u * nint;
-            const float *py = px + kM;
-            float acc = 0.f;
-            if (pow2) {
-                for (int qq = 0; qq < nint; qq++) {
-                    const int r = (qq + rot) & (nint - 1);
-                    acc += px[r] + py[r];
-                }
-            } else {
-                for (int qq = 0; qq < nint; qq++) acc += px[qq] + py[qq];
-            }
-            orow[u] = acc * oscale;
-        }
-        tc::bar(bar_id, PT);
     }
     tc::fence_before();
     return __syncthreads_and(ok) != 0;

@@ -117,6 +117,13 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t *r)
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
 }
+// 8 consecutive columns, issued without waiting (pair with tmem_wait)
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
 // store 32 / 16 consecutive 32-bit columns of this thread's lane (warp-collective), then wait
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r)
 {
