@@ -157,7 +157,7 @@ __global__ void k_tc_bmat(uint16_t *out, int ab)
 {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * 128; idx += gridDim.x * blockDim.x) {
         const int n = idx / 128, k = idx % 128;
-        const int m = n >> 1, ro = n & 1, j = k >> 1, ri = k & 1;
+        const int m = n & 63, ro = n >> 6, j = k >> 1, ri = k & 1;   // output part-major, input interleaved
         double sn, cs;
         sincospi(2.0 * (double)((j * m) % 64) / 64.0, &sn, &cs);
         const double v = ro == 0 ? (ri == 0 ? cs : -sn) : (ri == 0 ? sn : cs);
@@ -173,15 +173,17 @@ __global__ void k_tc_bmat(uint16_t *out, int ab)
     }
 }
 
-// W_4096^{j_lo m0} = exp(+2 pi i j_lo m0 / 4096) at [m0][j_lo]
+// W_4096^{j_lo m0} = exp(+2 pi i j_lo m0 / 4096) for consecutive pairs of m0:
+// [m0 / 2][j_lo] = (cos, cos', sin, sin') of m0 = 2i, 2i + 1
 __global__ void k_tc_twq(float2 *tw)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 4096) return;
-    const int m0 = idx / 64, jlo = idx % 64;
-    double sn, cs;
-    sincospi(2.0 * (double)(jlo * m0) / 4096.0, &sn, &cs);
-    tw[idx] = make_float2((float)cs, (float)sn);
+    if (idx >= 2048) return;
+    const int i = idx / 64, jlo = idx % 64;
+    double s0, c0, s1, c1;
+    sincospi(2.0 * (double)(jlo * (2 * i)) / 4096.0, &s0, &c0);
+    sincospi(2.0 * (double)(jlo * (2 * i + 1)) / 4096.0, &s1, &c1);
+    reinterpret_cast<float4 *>(tw)[idx] = make_float4((float)c0, (float)c1, (float)s0, (float)s1);
 }
 
 template <class T> int dalloc(cdmt_plan_s *p, T **ptr, size_t count)

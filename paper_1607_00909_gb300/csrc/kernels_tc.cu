@@ -8,12 +8,16 @@
 // 128 x 128 real form of the 64-point DFT matrix F (real and imaginary parts
 // interleaved) as one operand, half-precision operands and an FP32
 // accumulator in tensor memory:
-//   pass A  D[(pol, j_lo)][(m0, re/im)]  = X[(pol, j_lo)][(j_hi, re/im)] . F
+//   pass A  D[(j_lo, pol)][(re/im, m0)]  = X[(j_lo, pol)][(j_hi, re/im)] . F
 //   pass B  D[(m1, re/im)][(pol, m0)]    = F^T . Y[(j_lo, re/im)][(pol, m0)]
-// Between the passes each thread reads its own pass-A row from tensor memory,
-// applies the W_4096 twiddles in FP32 and writes it as a K-row of pass B's
-// data operand (MN-major), so the transposition costs only 16-byte shared-memory
-// stores.  Pass B's orientation puts the real and imaginary parts of one time
+// F sits in shared memory (output parts split: real parts of m = 0..63, then
+// imaginary parts) as pass A's B operand, and in tensor memory (output parts
+// interleaved) as pass B's A operand.  Between the passes each thread reads
+// its own pass-A row from tensor memory, applies the W_4096 twiddles with
+// packed FP32 pairs (two consecutive m0 per instruction) and writes the row as
+// a K-row of pass B's data operand (MN-major), so the transposition costs only
+// 16-byte shared-memory stores.  Pass-A rows pair the polarisations of one
+// j_lo in neighbouring lanes, which share their twiddle loads.  Pass B's orientation puts the real and imaginary parts of one time
 // sample in neighbouring TMEM lanes and both polarisations and consecutive
 // time samples in one thread's columns, so detection and integration run in
 // registers: one fused multiply-add per value, one shuffle per output.  The
@@ -46,7 +50,8 @@ namespace cdmt {
 namespace {
 
 constexpr int kM = 4096;
-constexpr uint32_t kLboA = 128, kSboA = 2048;    // pass-A operand, K-major
+constexpr uint32_t kLboA = 128, kSboA = 2048;    // DFT matrix F, K-major
+constexpr uint32_t kSboX = 2064;                 // pass-A data operand, K-major, row-core stride padded by 16 B
 constexpr uint32_t kLboB = 2064, kSboB = 128;    // pass-B operand, MN-major; K-core stride padded by 16 B
 constexpr uint32_t kAbuf = 33024;                // >= 15 * 2064 + 2048 and >= 2 * 4096 floats
 constexpr uint32_t kBmat = 32768;                // one 128 x 128 half-precision DFT matrix
@@ -71,8 +76,9 @@ template <int AB> struct TcLayout {
     static constexpr uint32_t abytes = na * kAbuf;
     static constexpr uint32_t off_misc = off_a + npipe * abytes;
     static constexpr uint32_t total = off_misc + 256;
-    static constexpr uint32_t tmem_cols = AB ? 256 : 512;            // power of two >= npipe * 128 + 64
-    static constexpr uint32_t ph_col = npipe * 128;                   // first phase-word column
+    static constexpr uint32_t tmem_cols = 512;
+    static constexpr uint32_t ph_col = npipe * 128;                   // first phase-word column (64 columns)
+    static constexpr uint32_t f_col = ph_col + 64;                    // F as pass B's A operand (64 columns; BF16 lo: 64 more)
 };
 
 __device__ __forceinline__ bool bar_and(int id, int count, bool v)
@@ -187,7 +193,32 @@ __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__r
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    return *tslot;
+    const uint32_t tmem = *tslot;
+    // F (and its BF16 lo part) into tensor memory as pass B's A operand: warp w < 4
+    // writes TMEM rows 32 w .. 32 w + 31; row 2 m1 + ro is shared-memory row
+    // 64 ro + m1, column c holds its K elements 2c, 2c + 1
+    if (warp < 4) {
+        const int r = 32 * warp + (tid & 31);
+        const int n = (r & 1) * 64 + (r >> 1);
+        #pragma unroll 1
+        for (uint32_t part = 0; part < L::nb; part++) {
+            #pragma unroll 1
+            for (int h = 0; h < 2; h++) {
+                uint32_t w[32];
+                #pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    const int k = 2 * (32 * h + c);
+                    w[c] = *reinterpret_cast<const uint32_t *>(bm + part * kBmat + (n / 8) * kSboA + (k / 8) * kLboA +
+                                                               (n % 8) * 16 + (k % 8) * 2);
+                }
+                tc::tmem_st32(tmem + ((uint32_t)(32 * warp) << 16) + L::f_col + 64 * part + 32 * h, w);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return tmem;
 }
 
 template <int AB> __device__ __forceinline__ void tc_cta_teardown(uint32_t tmem)
@@ -316,8 +347,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                     }
                 }
                 const int kcore = (jbase + 4 * c4) / 4;
-                const uint32_t ox = (uint32_t)(jlo / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
-                const uint32_t oy = (uint32_t)((64 + jlo) / 8) * kSboA + kcore * kLboA + (jlo % 8) * 16;
+                const uint32_t ox = (uint32_t)((2 * jlo) / 8) * kSboX + kcore * kLboA + ((2 * jlo) % 8) * 16;
+                const uint32_t oy = (uint32_t)((2 * jlo + 1) / 8) * kSboX + kcore * kLboA + ((2 * jlo + 1) % 8) * 16;
                 *reinterpret_cast<uint4 *>(ab + ox) = make_uint4(hx[0], hx[1], hx[2], hx[3]);
                 *reinterpret_cast<uint4 *>(ab + oy) = make_uint4(hy[0], hy[1], hy[2], hy[3]);
                 if constexpr (AB) {
@@ -334,10 +365,10 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             #pragma unroll 1
             for (int ks = 0; ks < 8; ks++) {
                 const uint64_t bh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
-                tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboA), bh, id_a, ks > 0);
+                tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboX), bh, id_a, ks > 0);
                 if constexpr (AB) {
-                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 256, kLboA, kSboA), bh, id_a, 1);
-                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboA),
+                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 256, kLboA, kSboX), bh, id_a, 1);
+                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboX),
                             tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), id_a, 1);
                 }
             }
@@ -347,29 +378,32 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (!ok) break;
         tc::fence_after();
 
-        // ---- pass-A rows -> twiddle -> pass-B operand (MN-major): row = pol * 64 + m0, k = 2 j_lo + (re, im).
-        // Two 16-column TMEM loads (8 complex m0 each) are issued together and
-        // waited for once; no loaded register is touched before the wait.
+        // ---- pass-A row (j_lo, pol) -> twiddle -> pass-B operand (MN-major): column pol * 64 + m0,
+        //      k = 2 j_lo + (re, im).  Eight m0 at a time: their real parts (TMEM columns m0)
+        //      and imaginary parts (64 + m0) are loaded together and waited for once.
         {
-            const int pol = t >> 6, rjlo = t & 63;     // pass-A row: (pol, j_lo)
-            constexpr int NST = COLS / 16;
-            uint32_t buf[2][16];
+            const int pol = t & 1, rjlo = t >> 1;
+            constexpr int MPT = 64 / NCG;             // m0 per thread
+            const float4 *tw4 = reinterpret_cast<const float4 *>(tws);
             #pragma unroll
-            for (int st = 0; st < NST; st++) {
-                if ((st & 1) == 0) {
-                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * st, buf[0]);
-                    tc::tmem_ld16_async(dcol + lane_off + cg * COLS + 16 * (st + 1), buf[1]);
-                    tc::tmem_wait();
-                }
-                const uint32_t *v = buf[st & 1];
-                const int m0b = (cg * COLS + 16 * st) / 2;   // first of 8 consecutive m0
+            for (int st = 0; st < MPT / 8; st++) {
+                const int m0b = cg * MPT + 8 * st;
+                uint32_t vr[8], vi[8];
+                tc::tmem_ld8_async(dcol + lane_off + m0b, vr);
+                tc::tmem_ld8_async(dcol + lane_off + 64 + m0b, vi);
+                tc::tmem_wait();
                 float re[8], im[8];
                 #pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const float2 w = tws[(m0b + i) * 64 + rjlo];
-                    const float2 z = cmul(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), w);
-                    re[i] = z.x;
-                    im[i] = z.y;
+                for (int i = 0; i < 4; i++) {
+                    // (wr, wr', wi, wi') of m0 = m0b + 2i, m0b + 2i + 1
+                    const float4 w = tw4[((m0b >> 1) + i) * 64 + rjlo];
+                    const uint64_t P = tc::f2_pack(__uint_as_float(vr[2 * i]), __uint_as_float(vr[2 * i + 1]));
+                    const uint64_t Q = tc::f2_pack(__uint_as_float(vi[2 * i]), __uint_as_float(vi[2 * i + 1]));
+                    const uint64_t WR = tc::f2_pack(w.x, w.y), WI = tc::f2_pack(w.z, w.w);
+                    const uint64_t R = tc::f2_sub(tc::f2_mul(P, WR), tc::f2_mul(Q, WI));
+                    const uint64_t I = tc::f2_fma(P, WI, tc::f2_mul(Q, WR));
+                    tc::f2_unpack(R, re[2 * i], re[2 * i + 1]);
+                    tc::f2_unpack(I, im[2 * i], im[2 * i + 1]);
                 }
                 const uint32_t o = (uint32_t)((pol * 64 + m0b) / 8) * kSboB + (uint32_t)(2 * rjlo / 8) * kLboB +
                                    (uint32_t)((2 * rjlo) % 8) * 16;
@@ -398,12 +432,12 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (q == 0) {
             #pragma unroll 1
             for (int ks = 0; ks < 8; ks++) {
-                const uint64_t fh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
+                const uint32_t fh = tmem + L::f_col + 8 * ks;
                 const uint64_t yh = tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB);
-                tc::mma(dcol, fh, yh, id_b, ks > 0);
+                tc::mma_ta(dcol, fh, yh, id_b, ks > 0);
                 if constexpr (AB) {
-                    tc::mma(dcol, fh, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), id_b, 1);
-                    tc::mma(dcol, tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), yh, id_b, 1);
+                    tc::mma_ta(dcol, fh, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), id_b, 1);
+                    tc::mma_ta(dcol, fh + 64, yh, id_b, 1);
                 }
             }
             tc::commit(mb);
