@@ -184,9 +184,9 @@ def kernel_source_hash():
 # dram__bytes_write.sum per launch / units per launch), valid for the kernel
 # source whose hash is recorded; null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16): 542.5 MB read + 2068.1 MB written
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16): 543.1 MB read + 2070.0 MB written
     # for 4.253e9 units (profiles/k_dedisperse_tc_fp16_lofar8.md)
-    "a3177c99f3585719:fp16": 0.6138,
+    "5e8675d3ac10b73a:fp16": 0.6144,
 }
 
 try:
