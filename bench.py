@@ -477,26 +477,65 @@ def batch_arm(args):
 SERVE = dict(nsub=288, block_len=1 << 16, ndm=1024, dm_max=100.0, nchan=16, nint=8, f_centre=135.0, bw=0.1953125)
 
 
-def _serve_run(cdmt, srv, beams, host_blocks, scale, nblk, pace_s=0.0):
+def _serve_run(cdmt, srv, beams, host_blocks, scale, nblk, pace_s=0.0, hist=None, probe=None):
     """Submit nblk blocks per beam (round-robin over beams; every pace_s seconds a
-    round when pacing), wait for each in submission order, release its slot."""
+    round when pacing), wait for each in submission order, release its slot.
+    hist[b] records the host block index of every block beam b received;
+    probe(b, block number, result) sees each result before its release."""
     reqs = []
     t0 = time.perf_counter()
+
+    def finish(item):
+        b, kb, rid = item
+        res = srv.wait(rid, 600.0)
+        if probe is not None:
+            probe(b, kb, res)
+        srv.release(rid)
+
     for k in range(nblk):
         if pace_s > 0:
             dt = t0 + k * pace_s - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
         for b in beams:
-            blk = host_blocks[(k + b) % len(host_blocks)]
-            reqs.append(srv.submit(b, blk.data_ptr(), scale.data_ptr() if scale is not None else 0))
+            i = (k + b) % len(host_blocks)
+            hist.setdefault(b, []).append(i)
+            reqs.append((b, len(hist[b]) - 1,
+                         srv.submit(b, host_blocks[i].data_ptr(), scale.data_ptr() if scale is not None else 0)))
         if pace_s > 0:  # under pacing, drain what is done before the next round arrives
             while reqs and srv.stats().blocks_running + srv.stats().blocks_queued < len(reqs):
-                srv.wait(reqs[0], 600.0)
-                srv.release(reqs.pop(0))
-    for r in reqs:
-        srv.wait(r, 600.0)
-        srv.release(r)
+                finish(reqs.pop(0))
+    for item in reqs:
+        finish(item)
+
+
+def _serve_error(c, host_blocks, scale, hist0, samples, i8):
+    """Sampled (subband, DM) tiles of beam 0's first segment in two blocks against
+    the FP64 oracle, from the same stream rebuilt from the host blocks."""
+    import oracle
+    dms = [i * c["dm_max"] / c["ndm"] for i in range(c["ndm"])]
+    nbin, nchan, nint, L = 4096 * c["nchan"], c["nchan"], c["nint"], c["block_len"]
+    nd = oracle.overlap(c["nsub"], c["f_centre"], c["bw"], dms, nchan, nint, nbin)
+    S = nbin - nd * nchan
+    gs, os_ = [], []
+    for (seg0, s, dmi, g) in samples:
+        t0 = seg0 * S
+        x = np.empty((1, nbin, 4), dtype=np.float32)
+        pos = t0
+        while pos < t0 + nbin:   # gather the segment from the blocks the beam received
+            blk, off = divmod(pos, L)
+            n = min(L - off, t0 + nbin - pos)
+            src = host_blocks[hist0[blk]][s, off:off + n].numpy()
+            x[0, pos - t0:pos - t0 + n] = (src.astype(np.float32) * np.float32(scale[s].item())) if i8 else src
+            pos += n
+        fc = c["f_centre"] + (s - (c["nsub"] - 1) / 2) * c["bw"]
+        o = oracle.tiles(x, fc, c["bw"], dms, nchan, nint, nbin, nd, [0], [0], [dmi])[0]
+        gs.append(g.astype(np.float64))
+        os_.append(o)
+    g, o = np.stack(gs), np.stack(os_)
+    d = g - o
+    return {"rel_max": float(np.max(np.abs(d)) / np.mean(o)), "rel_rms": float(np.linalg.norm(d) / np.linalg.norm(o)),
+            "tiles": len(samples), "beam": 0}
 
 
 def serve_arm(args):
@@ -534,9 +573,23 @@ def serve_arm(args):
     st0 = srv.stats()
     log(f"{args.beams} beams admitted in {time.perf_counter() - t0:.1f}s: {st0.hbm_bytes / 1e9:.1f} GB, "
         f"{st0.slots} output slots")
-    _serve_run(cdmt, srv, beams, host_blocks, scale, args.warmup)
+    hist, samples = {}, []
+    _serve_run(cdmt, srv, beams, host_blocks, scale, args.warmup, hist=hist)
     torch.cuda.synchronize(dev)
     srv.reset_stats()
+    rng = np.random.default_rng(7)
+    pick = {args.warmup + 1, args.warmup + args.steps - 1}
+    rows = c["nsub"] * c["nchan"]
+
+    def probe(b, kb, res):   # copy a few tiles of beam 0's results before their slots are released
+        if args.no_error or b != 0 or kb not in pick or res.nseg < 1:
+            return
+        view = cdmt.Server.block_view(res, c["ndm"], rows)
+        seglen = res.samples // res.nseg
+        for _ in range(4):
+            s_, d_ = int(rng.integers(0, c["nsub"])), int(rng.integers(0, c["ndm"]))
+            g = view[d_, s_ * c["nchan"]:(s_ + 1) * c["nchan"], :seglen].cpu().numpy()
+            samples.append((res.first_sample // seglen, s_, d_, g))
     props = torch.cuda.get_device_properties(dev)
     bus = None
     try:
@@ -544,17 +597,18 @@ def serve_arm(args):
     except AttributeError:
         pass
     with ClockSampler(bus) as clk:
-        _serve_run(cdmt, srv, beams, host_blocks, scale, args.steps)
+        _serve_run(cdmt, srv, beams, host_blocks, scale, args.steps, hist=hist, probe=probe)
     clocks = clk.summary()
     sat = srv.stats()
     block_s = c["block_len"] / (c["bw"] * 1e6)
     srv.reset_stats()
-    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(4, args.steps))
+    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(4, args.steps), hist=hist)
     one = srv.stats()
     srv.reset_stats()
-    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(8, args.steps), pace_s=block_s)
+    _serve_run(cdmt, srv, beams[:1], host_blocks, scale, max(8, args.steps), pace_s=block_s, hist=hist)
     paced = srv.stats()
     srv.close()
+    err = _serve_error(c, host_blocks, scale, hist[0], samples, i8) if samples else None
     value = sat.units_per_s / 1e9
     in_bytes = (4 if i8 else 16) * c["nsub"] * c["block_len"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -578,7 +632,8 @@ def serve_arm(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": in_bytes * args.beams,
                     "d2h_bytes_per_step": 0,
                     "note": "host blocks in; the filterbanks stay in device slots for the consumer"},
-            "roofline": None, "gpu_launches": 4 * args.beams * args.steps, "clocks": clocks}
+            "roofline": None, "gpu_launches": 4 * args.beams * args.steps, "clocks": clocks,
+            "error_vs_oracle": err}
     print(json.dumps(line), flush=True)
     return 0
 
