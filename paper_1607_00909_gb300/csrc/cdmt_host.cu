@@ -291,6 +291,7 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
         ta.ab = p->precision == CDMT_PREC_BF16 ? 1 : 0;
         ta.uniform = p->uniform;
         ta.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
+        ta.nsm = p->nsm;
         CK(p, tc_dedisperse(ta, st));
         if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
         return CDMT_OK;
@@ -462,6 +463,7 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
 
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    p->nsm = nsm;
     // DM tile: all DMs, unless that leaves too few work items to fill the GPU
     const int64_t items = (int64_t)nsub * p->nseg * nchan;
     const int64_t want_items = 4LL * nsm;

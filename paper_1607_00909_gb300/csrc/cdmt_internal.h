@@ -41,11 +41,12 @@ struct TcArgs {
     const double *ktab;
     const double *dm_list;
     const uint4 *bmat;    // 64-point DFT matrix in the K-major canonical layout (hi [, lo])
-    const float2 *twq;    // W_4096^{j_lo m0} at [m0][j_lo]
+    const float2 *twq;    // W_4096^{j_lo m0}, pairs of m0: [m0 / 2][j_lo] (cos, cos', sin, sin')
     float *out;
     int *status;          // set to 1 by a CTA whose tensor-core wait timed out
     int64_t k0, nout;
     int nsub, kc, nchan, ndm, dm_tile, nd, nint;
+    int nsm;              // SMs of the device: persistent grid size
     int ab;               // 0 FP16, 1 BF16 hi/lo
     bool uniform;
     float scale;

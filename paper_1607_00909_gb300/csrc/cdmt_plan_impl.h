@@ -22,6 +22,7 @@ struct Staging {
 
 struct cdmt_plan_s {
     int device = 0;
+    int nsm = 148;         // SMs of the device
     int nsub = 0, nchan = 0, nint = 0, ndm = 0;
     int64_t nsamp = 0;
     double f_centre = 0, bw = 0;

@@ -17,7 +17,8 @@
 // packed FP32 pairs (two consecutive m0 per instruction) and writes the row as
 // a K-row of pass B's data operand (MN-major), so the transposition costs only
 // 16-byte shared-memory stores.  Pass-A rows pair the polarisations of one
-// j_lo in neighbouring lanes, which share their twiddle loads.  Pass B's orientation puts the real and imaginary parts of one time
+// j_lo in neighbouring lanes, which share their twiddle loads.  Pass B's
+// orientation puts the real and imaginary parts of one time
 // sample in neighbouring TMEM lanes and both polarisations and consecutive
 // time samples in one thread's columns, so detection and integration run in
 // registers: one fused multiply-add per value, one shuffle per output.  The
@@ -41,6 +42,8 @@
 // BF16 mode both the data and the DFT matrix are split into hi + lo parts and
 // each K-step issues three MMAs (hi*hi + lo*hi + hi*lo); the CTA then runs one
 // DM at a time with all 512 threads (two operand sets do not fit).
+#include <algorithm>
+
 #include "cdmt_internal.h"
 #include "fft_core.cuh"
 #include "tc_ptx.cuh"
@@ -307,6 +310,10 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);   // pass A: data (K-major) x F (K-major)
     const uint32_t id_b = tc::idesc(128, 128, AB, 0, 1);   // pass B: F^T (K-major) x data (MN-major)
     const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
+    // The issuing thread builds each operand's descriptor of K step 0 once per GEMM;
+    // step ks adds ks * (byte step >> 4) to the address field (bits 0-13, no carry:
+    // every operand lies below 256 KB), so a GEMM costs it a few instructions per MMA.
+    constexpr uint64_t kStepK = 256 >> 4, kStepY = (2 * kLboB) >> 4;
     uint32_t ok = 1;
 
     for (int d = pipe; d < ndt; d += NPIPE) {
@@ -362,14 +369,19 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         tc::bar(bar_id, PT);
         tc::fence_after();
         if (q == 0) {
-            #pragma unroll 1
+            const uint32_t xa = tc::opaque(ab_addr), fa = tc::opaque(bm_addr);
+            const uint64_t dX = tc::sdesc(xa, kLboA, kSboX), dF = tc::sdesc(fa, kLboA, kSboA);
+            uint64_t dXl = 0, dFl = 0;
+            if constexpr (AB) {
+                dXl = tc::sdesc(xa + kAbuf, kLboA, kSboX);
+                dFl = tc::sdesc(fa + kBmat, kLboA, kSboA);
+            }
+            #pragma unroll
             for (int ks = 0; ks < 8; ks++) {
-                const uint64_t bh = tc::sdesc(bm_addr + ks * 256, kLboA, kSboA);
-                tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboX), bh, id_a, ks > 0);
+                tc::mma(dcol, dX + kStepK * ks, dF + kStepK * ks, id_a, ks > 0);
                 if constexpr (AB) {
-                    tc::mma(dcol, tc::sdesc(ab_addr + kAbuf + ks * 256, kLboA, kSboX), bh, id_a, 1);
-                    tc::mma(dcol, tc::sdesc(ab_addr + ks * 256, kLboA, kSboX),
-                            tc::sdesc(bm_addr + kBmat + ks * 256, kLboA, kSboA), id_a, 1);
+                    tc::mma(dcol, dXl + kStepK * ks, dF + kStepK * ks, id_a, 1);
+                    tc::mma(dcol, dX + kStepK * ks, dFl + kStepK * ks, id_a, 1);
                 }
             }
             tc::commit(mb);
@@ -430,14 +442,16 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         tc::bar(bar_id, PT);
         tc::fence_after();
         if (q == 0) {
-            #pragma unroll 1
+            const uint32_t ya = tc::opaque(ab_addr), f_taddr = tc::opaque(tmem) + L::f_col;
+            const uint64_t dY = tc::sdesc(ya, kLboB, kSboB);
+            uint64_t dYl = 0;
+            if constexpr (AB) dYl = tc::sdesc(ya + kAbuf, kLboB, kSboB);
+            #pragma unroll
             for (int ks = 0; ks < 8; ks++) {
-                const uint32_t fh = tmem + L::f_col + 8 * ks;
-                const uint64_t yh = tc::sdesc(ab_addr + ks * 2 * kLboB, kLboB, kSboB);
-                tc::mma_ta(dcol, fh, yh, id_b, ks > 0);
+                tc::mma_ta(dcol, f_taddr + 8 * ks, dY + kStepY * ks, id_b, ks > 0);
                 if constexpr (AB) {
-                    tc::mma_ta(dcol, fh, tc::sdesc(ab_addr + kAbuf + ks * 2 * kLboB, kLboB, kSboB), id_b, 1);
-                    tc::mma_ta(dcol, fh + 64, yh, id_b, 1);
+                    tc::mma_ta(dcol, f_taddr + 8 * ks, dYl + kStepY * ks, id_b, 1);
+                    tc::mma_ta(dcol, f_taddr + 64 + 8 * ks, dY + kStepY * ks, id_b, 1);
                 }
             }
             tc::commit(mb);
@@ -472,43 +486,56 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
 // threads (one hi/lo operand set fits).  Within a pipe the chirp stage is split
 // over all its threads, and each tensor-memory read-out is split by column
 // groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
-// One CTA per (DM tile, subband, segment, channel).
+// Persistent: one CTA per SM sets up once (DFT matrix and twiddles in shared
+// memory, F in tensor memory) and takes items (DM tile, subband, segment,
+// channel) blockIdx.x, + gridDim.x, ...; while it works on one item, the next
+// item's spectrum and phase words are prefetched into L2.
 template <bool UNIFORM, int AB>
 __global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
 k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
                 float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
-                int dm_tile, int nd, int nint, int64_t nout, float scale_out)
+                int dm_tile, int nd, int nint, int64_t nout, float scale_out, int64_t nitems)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     // once any CTA has given up on a tensor-core wait, the rest of the launch
     // returns at once (one read, block-uniform decision)
     if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
-    int64_t item = blockIdx.x;
-    const int c = (int)(item % nchan); item /= nchan;
-    const int kk = (int)(item % kc); item /= kc;
-    const int s = (int)(item % nsub); item /= nsub;
-    const int tile = (int)item;
-    const int dm0 = tile * dm_tile;
-
-    TcItem it;
-    it.src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
-    if constexpr (UNIFORM) it.ph = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
-    else it.ph = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
-    it.dms = dm_list + dm0;
-    it.ndt = min(dm_tile, ndm - dm0);
     const int seglen = (kM - nd) / nint;
     const int64_t rows = (int64_t)nsub * nchan;
-    it.out = out + (int64_t)dm0 * rows * nout + (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
-    it.dm_stride = rows * nout;
-    it.nd = nd;
-    it.nint = nint;
-    it.scale_out = scale_out;
-
+    auto make = [&](int64_t item) {
+        const int c = (int)(item % nchan); item /= nchan;
+        const int kk = (int)(item % kc); item /= kc;
+        const int s = (int)(item % nsub); item /= nsub;
+        const int tile = (int)item;
+        const int dm0 = tile * dm_tile;
+        TcItem it;
+        it.src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
+        if constexpr (UNIFORM) it.ph = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
+        else it.ph = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
+        it.dms = dm_list + dm0;
+        it.ndt = min(dm_tile, ndm - dm0);
+        it.out = out + (int64_t)dm0 * rows * nout + (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+        it.dm_stride = rows * nout;
+        it.nd = nd;
+        it.nint = nint;
+        it.scale_out = scale_out;
+        return it;
+    };
     const uint32_t tmem = tc_cta_setup<AB>(smem, bmat, twq);
-    const bool ok = tc_run_item<UNIFORM, AB>(it, smem, tmem);
-    if (!ok && tid == 0) atomicExch(status, 1);
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const TcItem it = make(item);
+        if (tid < 24 && item + gridDim.x < nitems) {   // 16 + 8 chunks of 4 KB
+            const TcItem nx = make(item + gridDim.x);
+            if (tid < 16) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
+            else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - 16), 4096);
+        }
+        if (!tc_run_item<UNIFORM, AB>(it, smem, tmem)) {
+            if (tid == 0) atomicExch(status, 1);
+            break;
+        }
+    }
     tc_cta_teardown<AB>(tmem);
 }
 
@@ -608,10 +635,11 @@ cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev
 template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
-    const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
+    const int64_t nitems = ntile * a.nsub * a.kc * a.nchan;
+    const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
     k_dedisperse_tc<U, AB><<<(unsigned)nblk, TcLayout<AB>::nt, TcLayout<AB>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan, a.ndm,
-        a.dm_tile, a.nd, a.nint, a.nout, a.scale);
+        a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems);
 }
 
 cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st)

@@ -18,6 +18,20 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// bring `bytes` (a multiple of 16) at p (16-byte aligned) into L2, asynchronously
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// v, opaque to the optimiser (keeps a cheap recomputation from being hoisted
+// out of a loop into a long-lived register)
+__device__ __forceinline__ uint32_t opaque(uint32_t v)
+{
+    asm volatile("mov.b32 %0, %0;" : "+r"(v));
+    return v;
+}
+
 // shared-memory matrix descriptor (no swizzle, relative LBO)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
