@@ -74,6 +74,8 @@ def _load():
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
                                       ctypes.POINTER(ctypes.c_int), dp, ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
+            lib.orc_redigitise.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_redigitise.restype = None
             lib.orc_max_threads.argtypes = []
             _lib = lib
     return _lib
@@ -177,6 +179,21 @@ def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthrea
     if rc:
         raise ValueError("oracle rejected the tile list")
     return out
+
+
+def redigitise(fb) -> tuple[np.ndarray, np.ndarray]:
+    """8-bit redigitisation of a float filterbank [ndm][rows][nt] (Sec. 3):
+    returns (codes uint8 [ndm][nt][rows] in decreasing frequency, stats float64
+    [ndm][rows][2] = (mean, standard deviation))."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    out = np.empty((ndm, nt, rows), dtype=np.uint8)
+    st = np.empty((ndm, rows, 2), dtype=np.float64)
+    _load().orc_redigitise(_fp(fb), ndm, rows, nt, out.ctypes.data, st.ctypes.data)
+    return out, st
+
+
+LEVELS = 16.0   # code steps per standard deviation (128 = the mean)
 
 
 def max_threads() -> int:

@@ -24,6 +24,10 @@
  *   5. nd/2 samples dropped at each edge, |y_X|^2 + |y_Y|^2 (Stokes I)
  *      (Sec. 3, "transpose, unpad and detect").
  *   6. nint consecutive samples summed into out[dm][s*nchan + c][t].
+ *   7. (orc_redigitise) per DM and channel, mean and standard deviation of the
+ *      block's samples, then 8-bit codes in decreasing-frequency, time-major
+ *      order (Sec. 3, "compute block sums", "compute channel statistics",
+ *      "redigitize").
  *
  * Readings where the paper is silent: D = 4.148808e3 MHz^2 pc^-1 cm^3 s
  * (the paper quotes 1/2.41e-4); transforms unitary; channel index increases
@@ -317,4 +321,50 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/*
+ * Redigitisation to 8 bits (Sec. 3, the steps "compute block sums", "compute
+ * channel statistics", "redigitize" of Algorithm 1).  For every DM trial and
+ * every channel row of a float filterbank fb[ndm][rows][nt] (one data block):
+ *   mu = (1/nt) sum_t I_t,  sigma = sqrt((1/nt) sum_t I_t^2 - mu^2)   (FP64);
+ * the offset and scale of the row are mu and g = LEVELS / sigma (g = 0 when
+ * sigma = 0), both rounded to FP32, and each sample becomes
+ *   code = clamp(rint(fmaf(I - mu, g, 128)), 0, 255)
+ * in FP32 (the paper leaves the mapping open: 128 is the mean and LEVELS = 16
+ * code steps span one sigma).  Codes are written in the paper's filterbank
+ * order (Sec. 3): per DM, time-major spectra in decreasing frequency,
+ * u8[ndm][nt][rows] with row r at position rows - 1 - r.
+ * stats (may be NULL) receives (mu, sigma) per (dm, row) in FP64.
+ */
+#define ORC_LEVELS 16.0f
+
+void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out, double *stats)
+{
+    for (int d = 0; d < ndm; d++) {
+        for (int r = 0; r < rows; r++) {
+            const float *row = fb + ((size_t)d * rows + r) * (size_t)nt;
+            double s1 = 0.0, s2 = 0.0;
+            for (int64_t t = 0; t < nt; t++) {
+                s1 += (double)row[t];
+                s2 += (double)row[t] * (double)row[t];
+            }
+            const double mu = nt > 0 ? s1 / (double)nt : 0.0;
+            double var = nt > 0 ? s2 / (double)nt - mu * mu : 0.0;
+            if (var < 0.0) var = 0.0;
+            const double sigma = sqrt(var);
+            if (stats) {
+                stats[2 * ((size_t)d * rows + r)] = mu;
+                stats[2 * ((size_t)d * rows + r) + 1] = sigma;
+            }
+            const float muf = (float)mu;
+            const float g = sigma > 0.0 ? (float)(ORC_LEVELS / sigma) : 0.0f;
+            for (int64_t t = 0; t < nt; t++) {
+                float x = rintf(fmaf(row[t] - muf, g, 128.0f));
+                if (x < 0.0f) x = 0.0f;
+                if (x > 255.0f) x = 255.0f;
+                out[((size_t)d * (size_t)nt + (size_t)t) * rows + (size_t)(rows - 1 - r)] = (uint8_t)x;
+            }
+        }
+    }
 }

@@ -37,6 +37,11 @@ MUTANTS = [
     ("overlap_uses_top_channel", "double lo = nu_s0 - 0.5 * bw;", "double lo = nu_s0 + 0.5 * bw - bw / (double)nchan;",
      None),
     ("segment_stride_wrong", "(size_t)(k * sv)) * 4;", "(size_t)(k * nbin)) * 4;", None),
+    ("redig_sample_sigma", "s2 / (double)nt - mu * mu", "(s2 - mu * s1) / (double)(nt - 1)", None),
+    ("redig_offset_127", "fmaf(row[t] - muf, g, 128.0f)", "fmaf(row[t] - muf, g, 127.0f)", None),
+    ("redig_truncate", "float x = rintf(", "float x = truncf(", None),
+    ("redig_increasing_order", "(size_t)(rows - 1 - r)] = (uint8_t)x;", "(size_t)r] = (uint8_t)x;", None),
+    ("redig_no_clip_high", "if (x > 255.0f) x = 255.0f;", "if (x > 255.0f) x = x - 256.0f;", None),
 ]
 
 PIN_CALLS = [
@@ -52,6 +57,12 @@ PIN_CALLS = [
     lambda o: pins.test_noise_mean_and_variance(o),
     lambda o: pins.test_overlap_rule_values(o),
     lambda o: pins.test_overlap_covers_every_channel_and_is_minimal(o),
+    lambda o: pins.test_redigitise_two_level_channel(o),
+    lambda o: pins.test_redigitise_constant_channel_is_the_mean_code(o),
+    lambda o: pins.test_redigitise_clips_an_outlier(o),
+    lambda o: pins.test_redigitise_gaussian_row_statistics(o),
+    lambda o: pins.test_redigitise_order_and_independence(o),
+    lambda o: pins.test_redigitise_scale_invariance(o),
 ]
 
 

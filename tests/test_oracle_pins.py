@@ -318,3 +318,64 @@ def test_overlap_covers_every_channel_and_is_minimal(orc):
     m = nbin // nchan
     assert nd >= need and nd % 2 == 0 and (m - nd) % nint == 0
     assert nd - 2 < need or (m - nd + 2) % nint != 0
+
+
+# ---------------------------------------------------------------- redigitisation (Sec. 3)
+# Offsets and scales come from each channel's mean and standard deviation over the
+# block; 128 is the mean and 16 code steps span one standard deviation.
+
+
+def test_redigitise_two_level_channel(orc):
+    # half the samples at a, half at b: mean (a+b)/2, sigma (b-a)/2, so a -> 128 - 16, b -> 128 + 16
+    fb = np.tile(np.array([10.0, 14.0], dtype=np.float32), 50)[None, None, :]
+    codes, st = orc.redigitise(fb)
+    assert st[0, 0, 0] == 12.0 and st[0, 0, 1] == 2.0
+    assert set(codes[0, 0::2, 0]) == {112} and set(codes[0, 1::2, 0]) == {144}
+
+
+def test_redigitise_constant_channel_is_the_mean_code(orc):
+    fb = np.full((2, 3, 40), 7.25, dtype=np.float32)
+    codes, st = orc.redigitise(fb)
+    assert np.all(codes == 128) and np.all(st[..., 1] == 0.0)
+
+
+def test_redigitise_clips_an_outlier(orc):
+    # N-1 zeros and one X: the outlier sits 16 sqrt(N-1) = 160 steps above the mean -> 255;
+    # the zeros sit 16 / sqrt(N-1) = 1.6 steps below -> 126
+    n = 101
+    fb = np.zeros((1, 1, n), dtype=np.float32)
+    fb[0, 0, 37] = 100.0
+    codes, _ = orc.redigitise(fb)
+    assert codes[0, 37, 0] == 255
+    assert set(np.delete(codes[0, :, 0], 37)) == {126}
+
+
+def test_redigitise_gaussian_row_statistics(orc):
+    g = np.random.default_rng(11)
+    fb = (40.0 + 3.0 * g.standard_normal((1, 1, 200000))).astype(np.float32)
+    codes, st = orc.redigitise(fb)
+    c = codes[0, :, 0].astype(np.float64)
+    assert abs(st[0, 0, 0] - 40.0) < 0.05 and abs(st[0, 0, 1] - 3.0) < 0.05
+    assert abs(c.mean() - 128.0) < 0.1 and abs(c.std() - 16.0) < 0.1
+
+
+def test_redigitise_order_and_independence(orc):
+    # each (DM, channel) is quantised on its own statistics, and channel r of the
+    # increasing-frequency rows lands at position rows - 1 - r (decreasing frequency)
+    g = np.random.default_rng(12)
+    fb = (g.random((3, 5, 64)) * (1.0 + np.arange(5))[None, :, None]).astype(np.float32)
+    codes, _ = orc.redigitise(fb)
+    assert codes.shape == (3, 64, 5)
+    for d in range(3):
+        for r in range(5):
+            one, _ = orc.redigitise(fb[d:d + 1, r:r + 1, :])
+            assert np.array_equal(codes[d, :, 5 - 1 - r], one[0, :, 0])
+
+
+def test_redigitise_scale_invariance(orc):
+    # scaling a channel by a power of two scales mean and sigma exactly: codes unchanged
+    g = np.random.default_rng(13)
+    fb = g.gamma(4.0, 2.0, (2, 4, 500)).astype(np.float32)
+    a, _ = orc.redigitise(fb)
+    b, _ = orc.redigitise(fb * np.float32(8.0))
+    assert np.array_equal(a, b)
