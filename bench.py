@@ -310,6 +310,33 @@ def gpu_arm(args, w):
     plan, info = R["plan"], R["info"]
     units = info["units"]
 
+    # 8-bit redigitisation of the headline form's filterbank (Sec. 3), timed on its own:
+    # a statistics pass reads the filterbank, a code pass reads it again and writes one byte per sample
+    redig = None
+    if not args.no_redigitise:
+        ndm_, rows_, nout_ = plan.out_shape()
+        u8 = torch.empty((ndm_, nout_, rows_), dtype=torch.uint8, device=dev)
+        st_ = stream.cuda_stream
+        for _ in range(max(3, args.warmup)):
+            plan.redigitise(out, u8, stream=st_)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.redigitise(out, u8, stream=st_)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rms = e0.elapsed_time(e1) / args.steps
+        nbytes = ndm_ * rows_ * nout_ * (4 + 4 + 1)
+        hbm = MEASURED.get("hbm_gbs")
+        redig = {"ms_per_launch": rms, "kernels": 2, "bytes_per_launch": nbytes,
+                 "achieved_gbs": nbytes / rms / 1e6, "peak_gbs": hbm,
+                 "frac": (nbytes / rms / 1e6) / hbm if hbm else None, "bound": "hbm",
+                 "output_bytes": ndm_ * rows_ * nout_, "levels_per_sigma": cdmt.REDIG_LEVELS,
+                 "note": "8-bit codes, per DM time-major spectra in decreasing frequency; not part of the step"}
+        del u8
+        log(f"rank {rank}: redigitise: {rms:.2f} ms per launch, {nbytes / rms / 1e6:.0f} GB/s")
+
     # ---- roofline of the dominant kernel of the headline form
     nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
     dd_avg_s = R["dd_ms"] / max(1, R["dd_n"]) / 1e3
@@ -381,6 +408,7 @@ def gpu_arm(args, w):
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "error_vs_oracle": R.get("error"),
+                "redigitise": redig,
                 "forms": {f: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
                               "dedisperse_ms_per_step": r["dd_ms"] / args.steps,
                               "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error")}
@@ -654,6 +682,7 @@ def main():
     ap.add_argument("--forms", default="fp32,fp16",
                     help="precision forms to time, comma-separated (fp32, fp16, bf16); the last is the headline")
     ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
+    ap.add_argument("--no-redigitise", action="store_true", help="skip timing the 8-bit redigitisation")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

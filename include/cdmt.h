@@ -200,6 +200,32 @@ int cdmt_set_timing(cdmt_plan_t plan, int on);
  * Errors: CDMT_EINVAL (NULL plan or ms), CDMT_ECUDA. */
 int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
 
+/* ------------------------------------------------------------------------
+ * Redigitisation to 8 bits (Sec. 3: "compute block sums", "compute channel
+ * statistics", "redigitize" of Algorithm 1).  The paper computes data offsets
+ * and scales from the mean and standard deviation of each channel's time
+ * series in the block and converts the floating-point filterbank to 8-bit
+ * integers packed as spectra in decreasing frequency order.
+ *
+ * For every DM trial d and channel row r (r = s*nchan + c, increasing
+ * frequency) of a plan's float32 filterbank fb[ndm][nsub*nchan][nout]:
+ *   mu, sigma = mean and (population) standard deviation of the row's nout
+ *               samples (sums of I and I^2; FP32 within a thread, FP64 across);
+ *   code      = clamp(rint(fmaf(I - mu, g, 128)), 0, 255),  g = CDMT_REDIG_LEVELS / sigma
+ *               (g = 0 for a constant row), in FP32 with mu and g rounded to FP32.
+ * The mapping is this library's choice (the paper leaves it open): 128 is the
+ * mean and 16 code steps span one sigma, so -8 .. +7.9 sigma are kept.
+ *
+ * cdmt_redigitise - d_fb: device, the plan's filterbank (as cdmt_execute
+ * writes it); d_u8: device, uint8 [ndm][nout][nsub*nchan] with row r at
+ * position nsub*nchan - 1 - r; d_stats: device float [ndm][nsub*nchan][2]
+ * (mu, sigma), or NULL.  Asynchronous on cuda_stream; the plan keeps an
+ * (mu, g) array of ndm*nsub*nchan float2.  Errors: CDMT_EINVAL (NULL
+ * pointers), CDMT_ENOMEM, CDMT_ENOTSUP (more than 65535 DM trials or 64-row
+ * tiles), CDMT_ECUDA. */
+#define CDMT_REDIG_LEVELS 16.0
+int cdmt_redigitise(cdmt_plan_t plan, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream);
+
 /* Bytes of the device array that backs cdmt_execute_static (64 MiB). */
 #define CDMT_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

@@ -136,6 +136,7 @@ def _load():
     lib.cdmt_execute_static.argtypes = [ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.cdmt_redigitise.argtypes = [P, P, P, P, P]
     lib.cdmt_strerror.argtypes = [ctypes.c_int]
     lib.cdmt_strerror.restype = ctypes.c_char_p
     lib.cdmt_last_error.argtypes = [P]
@@ -145,7 +146,7 @@ def _load():
               "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run", "cdmt_batch_status",
               "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
               "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
-              "cdmt_server_get_stats", "cdmt_server_reset_stats"):
+              "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -154,6 +155,7 @@ _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
+            "cdmt_redigitise",
             "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
@@ -434,6 +436,13 @@ def cdmt_stage_times(plan):
     return (ms[0], ms[1]), (n[0], n[1])
 
 
+def cdmt_redigitise(plan, d_fb: int, d_u8: int, d_stats: int = 0, stream: int = 0):
+    _check(_lib.cdmt_redigitise(plan, d_fb, d_u8, d_stats or None, stream or None), plan)
+
+
+REDIG_LEVELS = 16.0
+
+
 class Plan:
     """Owning wrapper of a cdmt plan."""
 
@@ -457,6 +466,19 @@ class Plan:
     def out_shape(self):
         i = self.info
         return (i["ndm"], i["nsub"] * i["nchan"], i["nout"])
+
+    def redigitise(self, fb, out=None, stats=None, stream=None):
+        """8-bit codes uint8 [ndm][nout][nsub*nchan] (decreasing frequency) of the
+        filterbank fb (a device tensor of out_shape()); stats, if given, receives
+        float32 [ndm][nsub*nchan][2] (mean, sigma)."""
+        import torch
+        ndm, rows, nout = self.out_shape()
+        assert tuple(fb.shape) == (ndm, rows, nout) and fb.dtype == torch.float32 and fb.is_contiguous()
+        if out is None:
+            out = torch.empty((ndm, nout, rows), dtype=torch.uint8, device=fb.device)
+        st = torch.cuda.current_stream(fb.device).cuda_stream if stream is None else stream
+        cdmt_redigitise(self.handle, fb.data_ptr(), out.data_ptr(), stats.data_ptr() if stats is not None else 0, st)
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -210,7 +210,7 @@ void release(cdmt_plan_s *p)
     cudaDeviceSynchronize();
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
-                    p->d_status};
+                    p->d_status, p->redig_mg};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {

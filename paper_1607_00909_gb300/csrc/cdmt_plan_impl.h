@@ -44,6 +44,7 @@ struct cdmt_plan_s {
     uint4 *tc_bmat = nullptr;
     float2 *tc_twq = nullptr;
     int *d_status = nullptr;
+    float2 *redig_mg = nullptr;   // redigitisation: (mean, levels / sigma) per (DM, channel)
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0;

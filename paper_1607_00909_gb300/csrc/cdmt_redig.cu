@@ -1,0 +1,184 @@
+// Redigitisation of a plan's filterbank to 8 bits (Sec. 3: after the
+// transpose, "compute block sums", "compute channel statistics" and
+// "redigitize" of Algorithm 1).  The data offsets and scales of every channel
+// follow from the mean and standard deviation of its samples in the block;
+// one kernel forms the sums and the statistics of each (DM, channel) row, a
+// second one converts the samples and writes them in the paper's filterbank
+// order: per DM, time-major spectra in decreasing frequency.
+//
+// The mapping (left open by the paper): code = clamp(rint((I - mu) * g + 128),
+// 0, 255) with g = 16 / sigma, evaluated in FP32 as one fused multiply-add.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/cdmt.h"
+#include "cdmt_plan_impl.h"
+
+namespace {
+
+constexpr int kTile = 64;
+
+// One CTA per (DM, channel) row of nt samples: sums of I and I^2 (FP32 within a
+// thread, FP64 across threads), then mean mu, standard deviation sigma, and the
+// row's (mu, g = levels / sigma) as FP32.  VEC: rows start 16-byte aligned
+// (nt % 4 == 0) and are read as float4, four loads in flight per thread.
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ fb, int64_t nt,
+                                                     float2 *__restrict__ mg, float *__restrict__ stats)
+{
+    const int64_t row = blockIdx.x;
+    const float *p = fb + row * nt;
+    float s1 = 0.f, s2 = 0.f;
+    if constexpr (VEC) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+        const int64_t n4 = nt / 4;
+        #pragma unroll 4
+        for (int64_t t = threadIdx.x; t < n4; t += blockDim.x) {
+            const float4 v = __ldg(p4 + t);
+            s1 += (v.x + v.y) + (v.z + v.w);
+            s2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s2))));
+        }
+    } else {
+        #pragma unroll 4
+        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
+            const float v = __ldg(p + t);
+            s1 += v;
+            s2 = fmaf(v, v, s2);
+        }
+    }
+    double d1 = s1, d2 = s2;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    __shared__ double r1[8], r2[8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        r1[w] = d1;
+        r2[w] = d2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            a += r1[i];
+            b += r2[i];
+        }
+        const double mu = nt > 0 ? a / (double)nt : 0.0;
+        const double var = nt > 0 ? fmax(b / (double)nt - mu * mu, 0.0) : 0.0;
+        const double sigma = sqrt(var);
+        mg[row] = make_float2((float)mu, sigma > 0.0 ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        if (stats) {
+            stats[2 * row] = (float)mu;
+            stats[2 * row + 1] = (float)sigma;
+        }
+    }
+}
+
+__device__ __forceinline__ uint8_t code8(float v, float2 m)
+{
+    const float x = rintf(fmaf(v - m.x, m.y, 128.f));
+    return (uint8_t)fminf(fmaxf(x, 0.f), 255.f);
+}
+
+// One CTA per (64-sample, 64-row) tile of one DM: codes into shared memory,
+// then each output spectrum's 64 bytes (rows reversed) in 4-byte words.  VEC:
+// full-width tiles of 16-byte aligned rows are read as float4 (4 per thread).
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ fb, const float2 *__restrict__ mg,
+                                                     uint8_t *__restrict__ out, int rows, int64_t nt)
+{
+    __shared__ uint8_t tile[kTile][kTile + 4];   // [sample][row]
+    const int dm = blockIdx.z;
+    const int r0 = blockIdx.y * kTile;
+    const int64_t t0 = (int64_t)blockIdx.x * kTile;
+    const int nr = min(kTile, rows - r0);
+    const int ntt = (int)(nt - t0 < kTile ? nt - t0 : kTile);
+    const float *src = fb + ((int64_t)dm * rows + r0) * nt + t0;
+    const float2 *g = mg + (int64_t)dm * rows + r0;
+    if (VEC && ntt == kTile) {
+        #pragma unroll
+        for (int k = 0; k < kTile * kTile / 4 / 256; k++) {
+            const int i = k * 256 + (int)threadIdx.x;
+            const int rr = i / (kTile / 4), tt = 4 * (i % (kTile / 4));
+            if (rr < nr) {
+                const float2 m = g[rr];
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (int64_t)rr * nt + tt));
+                tile[tt][rr] = code8(v.x, m);
+                tile[tt + 1][rr] = code8(v.y, m);
+                tile[tt + 2][rr] = code8(v.z, m);
+                tile[tt + 3][rr] = code8(v.w, m);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
+            const int rr = i / kTile, tt = i % kTile;
+            if (rr < nr && tt < ntt) tile[tt][rr] = code8(__ldg(src + (int64_t)rr * nt + tt), g[rr]);
+        }
+    }
+    __syncthreads();
+    // output position of row r0 + rr within a spectrum: rows - 1 - r0 - rr
+    uint8_t *dst = out + ((int64_t)dm * nt + t0) * rows + (rows - r0 - nr);
+    if (nr == kTile && (rows & 3) == 0) {
+        for (int i = threadIdx.x; i < ntt * (kTile / 4); i += blockDim.x) {
+            const int tt = i / (kTile / 4), wd = i % (kTile / 4);
+            const int rr = kTile - 1 - 4 * wd;   // rows rr, rr-1, rr-2, rr-3 at positions 4wd .. 4wd+3
+            const uint32_t v = (uint32_t)tile[tt][rr] | ((uint32_t)tile[tt][rr - 1] << 8) |
+                               ((uint32_t)tile[tt][rr - 2] << 16) | ((uint32_t)tile[tt][rr - 3] << 24);
+            *reinterpret_cast<uint32_t *>(dst + (int64_t)tt * rows + 4 * wd) = v;
+        }
+    } else {
+        for (int i = threadIdx.x; i < ntt * nr; i += blockDim.x) {
+            const int tt = i / nr, pos = i % nr;
+            dst[(int64_t)tt * rows + pos] = tile[tt][nr - 1 - pos];
+        }
+    }
+}
+
+int rfail(cdmt_plan_s *p, int code, const char *msg)
+{
+    p->last_error = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" int cdmt_redigitise(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream)
+{
+    if (!p) return CDMT_EINVAL;
+    if (!d_fb || !d_u8) return rfail(p, CDMT_EINVAL, "NULL filterbank or output pointer");
+    const int rows = p->nsub * p->nchan;
+    const int64_t nt = p->nout;
+    if (nt < 1) return rfail(p, CDMT_EINVAL, "the plan has no output samples");
+    if (p->ndm > 65535 || (rows + kTile - 1) / kTile > 65535)
+        return rfail(p, CDMT_ENOTSUP, "more than 65535 DM trials or 64-row tiles");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return rfail(p, CDMT_ECUDA, "cudaSetDevice failed");
+    if (!p->redig_mg) {
+        if (cudaMalloc((void **)&p->redig_mg, sizeof(float2) * (size_t)p->ndm * rows) != cudaSuccess) {
+            cudaGetLastError();
+            if (cur != p->device) cudaSetDevice(cur);
+            return rfail(p, CDMT_ENOMEM, "redigitisation statistics buffer");
+        }
+        p->bytes += (int64_t)sizeof(float2) * p->ndm * rows;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // float4 reads need every row to start 16-byte aligned
+    const bool vec = nt % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
+    const unsigned nrow = (unsigned)((int64_t)p->ndm * rows);
+    const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)p->ndm);
+    if (vec) {
+        k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, p->redig_mg, d_stats);
+        k_redig_codes<true><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt);
+    } else {
+        k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, p->redig_mg, d_stats);
+        k_redig_codes<false><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (cur != p->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(e));
+    return CDMT_OK;
+}

@@ -1,0 +1,98 @@
+"""8-bit redigitisation of the filterbank (Sec. 3) against the oracle.
+
+Both sides take each code in FP32 from the row's (mean, gain) rounded to FP32;
+the statistics differ only in their summation order (FP64 in the oracle, FP32
+partial sums per thread on the GPU), so a code may differ by one where the
+unrounded value sits on a rounding boundary.  The tests require identical codes
+everywhere else, at most 1e-4 of the samples on boundaries, and mean and sigma
+within 1e-5.
+"""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_filterbank
+
+pytestmark = pytest.mark.gpu
+BW = 0.1953125
+
+
+@pytest.fixture(scope="module")
+def cdmt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1607_00909_gb300 as m
+    return m
+
+
+def _check(orc, fb, codes, stats):
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    oc, ost = orc.redigitise(fb)
+    mu_g, sg_g = stats[..., 0].astype(np.float64), stats[..., 1].astype(np.float64)
+    scale = np.maximum(ost[..., 1], 1e-30)
+    assert np.max(np.abs(mu_g - ost[..., 0]) / (np.abs(ost[..., 0]) + scale)) <= 1e-5
+    assert np.max(np.abs(sg_g - ost[..., 1]) / (np.abs(ost[..., 0]) + scale)) <= 1e-5
+    diff = codes.astype(np.int32) - oc.astype(np.int32)
+    assert np.all(np.abs(diff) <= 1)
+    d, t, p = np.nonzero(diff)
+    r = rows - 1 - p
+    x = 128.0 + (fb[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / scale[d, r]
+    assert np.all(np.abs(x - np.floor(x) - 0.5) < 1e-3), "a code differs away from a rounding boundary"
+    assert len(d) <= max(1, 1e-4 * codes.size)
+    return len(d)
+
+
+def test_redigitise_tiny_workload(cdmt, orc):
+    import torch
+    w = synth.tiny()
+    x = w.voltages()
+    plan = cdmt.Plan(1, w.nsamp, w.f_centre, BW, w.dms, w.nchan, w.nint, nbin=w.nbin)
+    fb = cdmt.run(plan, torch.from_numpy(x).cuda())
+    stats = torch.empty((len(w.dms), w.nchan, 2), dtype=torch.float32, device="cuda")
+    codes = plan.redigitise(fb, stats=stats)
+    torch.cuda.synchronize()
+    _check(orc, fb.cpu().numpy(), codes.cpu().numpy(), stats.cpu().numpy())
+    plan.close()
+
+
+def test_redigitise_ragged_tiles_and_degenerate_rows(cdmt, orc):
+    import torch
+    # 3 subbands x 16 channels = 48 rows (< one 64-row tile), nout not a multiple of 64
+    nsamp = 3 * (1 << 16) + 999
+    plan = cdmt.Plan(3, nsamp, 150.0, BW, [0.0, 7.0, 14.0], 16, 8, nbin=1 << 16)
+    ndm, rows, nout = plan.out_shape()
+    assert rows % 64 and nout % 64
+    g = np.random.default_rng(3)
+    fb = g.gamma(8.0, 2.0, (ndm, rows, nout)).astype(np.float32)
+    fb[0, 5, :] = 3.5                     # constant row: every code 128
+    fb[1, 7, 123] = 1e4                   # an outlier clips at 255
+    fb[2, 9, :] = np.where(np.arange(nout) % 2 == 0, 10.0, 14.0)   # two levels: 112 / 144
+    fbt = torch.from_numpy(fb).cuda()
+    stats = torch.empty((ndm, rows, 2), dtype=torch.float32, device="cuda")
+    codes = plan.redigitise(fbt, stats=stats).cpu().numpy()
+    torch.cuda.synchronize()
+    _check(orc, fb, codes, stats.cpu().numpy())
+    assert np.all(codes[0, :, rows - 1 - 5] == 128)
+    assert codes[1, 123, rows - 1 - 7] == 255
+    assert set(codes[2, 0::2, rows - 1 - 9]) == {112} and set(codes[2, 1::2, rows - 1 - 9]) == {144}
+    plan.close()
+
+
+def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
+    import torch
+    # 8 subbands x 16 channels = 128 rows (two full tiles), FP16 tensor-core filterbank
+    nsub, nsamp = 8, 4 * (1 << 16)
+    x = synth.noise(41, nsub, nsamp)
+    dms = [0.0, 10.0, 20.0, 30.0]
+    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, dms, 16, 8, nbin=1 << 16, precision=cdmt.CDMT_PREC_FP16)
+    fb = cdmt.run(plan, torch.from_numpy(x).cuda())
+    stats = torch.empty((len(dms), nsub * 16, 2), dtype=torch.float32, device="cuda")
+    codes = plan.redigitise(fb, stats=stats)
+    torch.cuda.synchronize()
+    c = codes.cpu().numpy()
+    _check(orc, fb.cpu().numpy(), c, stats.cpu().numpy())
+    # detected noise: codes centred on 128 with 16 steps per sigma
+    assert abs(c.mean() - 128.0) < 0.5 and abs(c.astype(np.float64).std() - 16.0) < 0.5
+    plan.close()
