@@ -125,8 +125,8 @@ __device__ __forceinline__ uint32_t fix32(double x) { return (uint32_t)(unsigned
 
 // shift != 0 (tensor-core form): the start words also carry a phase ramp of
 // shift * j / M cycles on bin j of each channel, which delays the channel's
-// backward DFT output by `shift` samples (exact: shift * j * 2^32 / 4096 is an
-// integer multiple of 2^20).
+// backward DFT output by `shift` samples (exact: shift * j * 2^32 / M is an
+// integer for M a power of two <= 2^32).
 __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, double f_centre, double bw, int nsub,
                             int nchan, int64_t nbin, int ntile, int shift)
 {
@@ -137,7 +137,8 @@ __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, doub
         const int s = (int)((q / nbin) % nsub);
         const int tile = (int)(q / ((int64_t)nbin * nsub));
         const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i);
-        const uint32_t ramp = shift ? (uint32_t)((i % mbin) * shift) << 20 : 0u;
+        const int lm = 31 - __clz((int)mbin);   // shift * j * 2^32 / M = (shift * j) << (32 - log2 M)
+        const uint32_t ramp = shift ? (uint32_t)((i % mbin) * shift) << (32 - lm) : 0u;
         nco[q] = make_uint2(fix32(-dm_tile0[tile] * k) + ramp, fix32(-ddm * k));
     }
 }
@@ -149,40 +150,42 @@ __global__ void k_k_table(double *kt, double f_centre, double bw, int nsub, int 
         kt[q] = chirp_k(f_centre, bw, nsub, nchan, nbin, (int)(q / nbin), q % nbin);
 }
 
-// 128 x 128 real form of the backward 64-point DFT (W = exp(+2 pi i / 64)) in
-// the K-major canonical layout (SBO 2048 B, LBO 128 B): output n = 2 m + (re, im),
-// input k = 2 j + (re, im).  ab = 0: FP16; ab = 1: BF16 hi at [0, 16384) and
-// the BF16 rounding residue (lo) at [16384, 32768) (16-bit elements).
-__global__ void k_tc_bmat(uint16_t *out, int ab)
+// 2P x 2P real form of the backward P-point DFT (W = exp(+2 pi i / P)) in the
+// K-major canonical layout (SBO 32P B, LBO 128 B): output n = P ro + m (real
+// parts, then imaginary parts), input k = 2 j + (re, im).  ab = 0: FP16; ab = 1:
+// BF16 hi in the first (2P)^2 elements and the BF16 rounding residue (lo) in the
+// next (2P)^2 (16-bit elements).
+__global__ void k_tc_bmat(uint16_t *out, int ab, int P)
 {
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 128 * 128; idx += gridDim.x * blockDim.x) {
-        const int n = idx / 128, k = idx % 128;
-        const int m = n & 63, ro = n >> 6, j = k >> 1, ri = k & 1;   // output part-major, input interleaved
+    const int n2 = 4 * P * P;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += gridDim.x * blockDim.x) {
+        const int n = idx / (2 * P), k = idx % (2 * P);
+        const int m = n % P, ro = n / P, j = k >> 1, ri = k & 1;
         double sn, cs;
-        sincospi(2.0 * (double)((j * m) % 64) / 64.0, &sn, &cs);
+        sincospi(2.0 * (double)((j * m) % P) / (double)P, &sn, &cs);
         const double v = ro == 0 ? (ri == 0 ? cs : -sn) : (ri == 0 ? sn : cs);
-        const int off = (n / 8) * 1024 + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+        const int off = (n / 8) * (16 * P) + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
         if (ab == 0) {
             out[off] = __half_as_ushort(__double2half(v));
         } else {
             const __nv_bfloat16 hi = __double2bfloat16(v);
             const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
             out[off] = __bfloat16_as_ushort(hi);
-            out[16384 + off] = __bfloat16_as_ushort(lo);
+            out[n2 + off] = __bfloat16_as_ushort(lo);
         }
     }
 }
 
-// W_4096^{j_lo m0} = exp(+2 pi i j_lo m0 / 4096) for consecutive pairs of m0:
-// [m0 / 2][j_lo] = (cos, cos', sin, sin') of m0 = 2i, 2i + 1
-__global__ void k_tc_twq(float2 *tw)
+// W_M^{j_lo m0} = exp(+2 pi i j_lo m0 / M), m0 < M / 64, for consecutive pairs of
+// m0: [m0 / 2][j_lo] = (cos, cos', sin, sin') of m0 = 2i, 2i + 1
+__global__ void k_tc_twq(float2 *tw, int mbin)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2048) return;
+    if (idx >= mbin / 2) return;
     const int i = idx / 64, jlo = idx % 64;
     double s0, c0, s1, c1;
-    sincospi(2.0 * (double)(jlo * (2 * i)) / 4096.0, &s0, &c0);
-    sincospi(2.0 * (double)(jlo * (2 * i + 1)) / 4096.0, &s1, &c1);
+    sincospi(2.0 * (double)(jlo * (2 * i)) / (double)mbin, &s0, &c0);
+    sincospi(2.0 * (double)(jlo * (2 * i + 1)) / (double)mbin, &s1, &c1);
     reinterpret_cast<float4 *>(tw)[idx] = make_float4((float)c0, (float)c1, (float)s0, (float)s1);
 }
 
@@ -210,7 +213,7 @@ void release(cdmt_plan_s *p)
     cudaDeviceSynchronize();
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
-                    p->d_status, p->redig_mg};
+                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {
@@ -276,7 +279,9 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
         ta.ktab = p->ktab;
         ta.dm_list = p->d_dm;
         ta.bmat = p->tc_bmat;
+        ta.bmat64 = p->tc_bmat64;
         ta.twq = p->tc_twq;
+        ta.lm = p->mbin == 2048 ? 11 : 12;
         ta.out = out;
         ta.status = p->d_status;
         ta.k0 = out_k0;
@@ -426,17 +431,19 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     p->nbin = nbin;
     p->mbin = nbin / nchan;
     if (p->mbin < 512 || p->mbin > 4096) {
+        const long long mb = (long long)p->mbin;
         delete p;
-        return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)p->mbin);
+        return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", mb);
     }
     p->r = (int)(p->mbin / 256);
     if (p->precision != CDMT_PREC_FP32 && 32 % nint != 0) {
         delete p;
         return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need nint dividing 32 (got %d)", nint);
     }
-    if (p->precision != CDMT_PREC_FP32 && p->mbin != 4096) {
+    if (p->precision != CDMT_PREC_FP32 && p->mbin != 4096 && p->mbin != 2048) {
+        const long long mb = (long long)p->mbin;
         delete p;
-        return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need M_bin = 4096 (got %lld)", (long long)p->mbin);
+        return fail(nullptr, CDMT_ENOTSUP, "tensor-core precisions need M_bin = 2048 or 4096 (got %lld)", mb);
     }
     if (nsamp < nbin) {
         delete p;
@@ -444,9 +451,10 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     }
     p->nd = o.nd >= 0 ? o.nd : overlap_rule(*p, nbin);
     if (p->nd < 0 || p->nd % 2 || p->nd >= p->mbin || (p->mbin - p->nd) % nint) {
+        const long long nd = (long long)p->nd, mb = (long long)p->mbin;
         delete p;
         return fail(nullptr, CDMT_EINVAL, "overlap nd=%lld invalid for M=%lld, nint=%d (need even, < M, (M-nd) %% nint == 0)",
-                    (long long)p->nd, (long long)p->mbin, nint);
+                    nd, mb, nint);
     }
     p->nvalid = nbin - p->nd * nchan;
     p->nseg = (nsamp - nbin) / p->nvalid + 1;
@@ -510,8 +518,11 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     TRY(dalloc(p, &p->spec, (size_t)p->seg_chunk * nsub * nbin));
     TRY(dalloc(p, &p->d_status, 1));
     if (p->precision != CDMT_PREC_FP32) {
-        TRY(dalloc(p, &p->tc_bmat, (size_t)(p->precision == CDMT_PREC_BF16 ? 4096 : 2048)));
-        TRY(dalloc(p, &p->tc_twq, (size_t)4096));
+        const int P = (int)(p->mbin / 64), planes = p->precision == CDMT_PREC_BF16 ? 2 : 1;
+        TRY(dalloc(p, &p->tc_bmat, (size_t)planes * P * P / 2));   // (2P)^2 halves per plane, 8 per uint4
+        if (P != 64) TRY(dalloc(p, &p->tc_bmat64, (size_t)planes * 2048));
+        else p->tc_bmat64 = p->tc_bmat;
+        TRY(dalloc(p, &p->tc_twq, (size_t)p->mbin));
     }
 
     std::vector<double> tile0(p->ntile);
@@ -531,8 +542,10 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     TRYC(cudaMemcpy(p->d_dm, dm_list, sizeof(double) * ndm, cudaMemcpyHostToDevice));
     TRYC(cudaMemset(p->d_status, 0, sizeof(int)));
     if (p->precision != CDMT_PREC_FP32) {
-        k_tc_bmat<<<64, 256>>>(reinterpret_cast<uint16_t *>(p->tc_bmat), p->precision == CDMT_PREC_BF16 ? 1 : 0);
-        k_tc_twq<<<16, 256>>>(p->tc_twq);
+        const int ab = p->precision == CDMT_PREC_BF16 ? 1 : 0;
+        k_tc_bmat<<<64, 256>>>(reinterpret_cast<uint16_t *>(p->tc_bmat), ab, (int)(p->mbin / 64));
+        if (p->tc_bmat64 != p->tc_bmat) k_tc_bmat<<<64, 256>>>(reinterpret_cast<uint16_t *>(p->tc_bmat64), ab, 64);
+        k_tc_twq<<<(unsigned)((p->mbin / 2 + 255) / 256), 256>>>(p->tc_twq, (int)p->mbin);
     }
     k_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256>>>(p->tw_n, nbin, -1);
     k_twiddle_passes<<<64, 256>>>(p->tw_af, p->tw_bf, p->r, -1);

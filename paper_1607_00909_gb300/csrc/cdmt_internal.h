@@ -40,8 +40,10 @@ struct TcArgs {
     const uint2 *nco;
     const double *ktab;
     const double *dm_list;
-    const uint4 *bmat;    // 64-point DFT matrix in the K-major canonical layout (hi [, lo])
-    const float2 *twq;    // W_4096^{j_lo m0}, pairs of m0: [m0 / 2][j_lo] (cos, cos', sin, sin')
+    const uint4 *bmat;    // F_P, the (M/64)-point DFT matrix, K-major canonical layout (hi [, lo])
+    const uint4 *bmat64;  // F_64, the 64-point DFT matrix, same layout (equal to bmat when M = 4096)
+    const float2 *twq;    // W_M^{j_lo m0}, pairs of m0: [m0 / 2][j_lo] (cos, cos', sin, sin')
+    int lm;               // log2 M: 12 or 11
     float *out;
     int *status;          // set to 1 by a CTA whose tensor-core wait timed out
     int64_t k0, nout;
@@ -66,7 +68,7 @@ struct TcBeam {
 cudaError_t tc_prepare(int ab);
 cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev, int *queue, const uint4 *bmat,
                             const float2 *twq, int *status, int ab, int nctas, cudaStream_t st);
-size_t tc_smem(int ab);
+size_t tc_smem(int ab, int lm);
 cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st);
 
 cudaError_t fp32_prepare(int r);

@@ -41,7 +41,8 @@ struct cdmt_plan_s {
     double *ktab = nullptr, *d_dm = nullptr;
     float4 *spec = nullptr;
     // tensor-core form
-    uint4 *tc_bmat = nullptr;
+    uint4 *tc_bmat = nullptr;     // F_P, P = M / 64
+    uint4 *tc_bmat64 = nullptr;   // F_64 (the same buffer when M = 4096)
     float2 *tc_twq = nullptr;
     int *d_status = nullptr;
     float2 *redig_mg = nullptr;   // redigitisation: (mean, levels / sigma) per (DM, channel)

@@ -1,18 +1,18 @@
-// Tensor-core form of the DM stage (sm_103a tcgen05), for channels of M = 4096 bins.
+// Tensor-core form of the DM stage (sm_103a tcgen05), for channels of
+// M = 64 P bins, P = 64 (M = 4096) or P = 32 (M = 2048).
 //
-// The backward M-point DFT of each channel is split as M = 64 x 64 (input
-// j = 64 j_hi + j_lo, output m = m0 + 64 m1):
-//   pass A  for every j_lo:  y[m0] = sum_j_hi x[64 j_hi + j_lo] W_64^{j_hi m0},  y *= W_4096^{j_lo m0}
+// The backward M-point DFT of each channel is split as M = P x 64 (input
+// j = 64 j_hi + j_lo, output m = m0 + P m1):
+//   pass A  for every j_lo:  y[m0] = sum_j_hi x[64 j_hi + j_lo] W_P^{j_hi m0},  y *= W_M^{j_lo m0}
 //   pass B  for every m0:    z[m1] = sum_j_lo y_j_lo[m0] W_64^{j_lo m1}
-// Each pass is one real GEMM on the tensor cores, 128 x 128 x 128, with the
-// 128 x 128 real form of the 64-point DFT matrix F (real and imaginary parts
-// interleaved) as one operand, half-precision operands and an FP32
-// accumulator in tensor memory:
-//   pass A  D[(j_lo, pol)][(re/im, m0)]  = X[(j_lo, pol)][(j_hi, re/im)] . F
-//   pass B  D[(m1, re/im)][(pol, m0)]    = F^T . Y[(j_lo, re/im)][(pol, m0)]
-// F sits in shared memory (output parts split: real parts of m = 0..63, then
-// imaginary parts) as pass A's B operand, and in tensor memory (output parts
-// interleaved) as pass B's A operand.  Between the passes each thread reads
+// Each pass is one real GEMM on the tensor cores with the real form of a DFT
+// matrix (real and imaginary parts interleaved on its input side) as one
+// operand, half-precision operands and an FP32 accumulator in tensor memory:
+//   pass A  D[(j_lo, pol)][(re/im, m0)]  = X[(j_lo, pol)][(j_hi, re/im)] . F_P     128 x 2P x 2P
+//   pass B  D[(m1, re/im)][(pol, m0)]    = F_64^T . Y[(j_lo, re/im)][(pol, m0)]     128 x 2P x 128
+// F_P sits in shared memory (output parts split: real parts of m = 0..P-1,
+// then imaginary parts) as pass A's B operand, and F_64 in tensor memory
+// (output parts interleaved) as pass B's A operand.  Between the passes each thread reads
 // its own pass-A row from tensor memory, applies the W_4096 twiddles with
 // packed FP32 pairs (two consecutive m0 per instruction) and writes the row as
 // a K-row of pass B's data operand (MN-major), so the transposition costs only
@@ -25,7 +25,9 @@
 // time shift by n_d / 2 that drops the wrapped overlap (Sec. 2) is folded into
 // the chirp phase (a circular shift of the output is a phase ramp on the
 // bins, exact in the 32-bit fixed-point phase), so integration windows start
-// on multiples of nint; nint must divide 32.
+// on multiples of nint; nint must divide 32.  The two sizes differ in their
+// pipes: M = 4096 runs three pipes of 256 threads (128-column accumulators),
+// M = 2048 six pipes of 128 threads (64-column accumulators).
 //
 // The chirp (Eq. 1, conjugated) and the data scaling run in FP32 before the
 // rounding to half precision; the chirp phase comes from the same FP64-derived
@@ -52,36 +54,51 @@ namespace cdmt {
 
 namespace {
 
-constexpr int kM = 4096;
-constexpr uint32_t kLboA = 128, kSboA = 2048;    // DFT matrix F, K-major
-constexpr uint32_t kSboX = 2064;                 // pass-A data operand, K-major, row-core stride padded by 16 B
-constexpr uint32_t kLboB = 2064, kSboB = 128;    // pass-B operand, MN-major; K-core stride padded by 16 B
-constexpr uint32_t kAbuf = 33024;                // >= 15 * 2064 + 2048 and >= 2 * 4096 floats
-constexpr uint32_t kBmat = 32768;                // one 128 x 128 half-precision DFT matrix
+constexpr uint32_t kLboA = 128;                  // K-major operands: stride between 8-element K cores
+constexpr uint32_t kSboB = 128;                  // pass-B data (MN-major): stride between 8-element N cores
+constexpr uint32_t kF64Sbo = 2048;               // F_64 in global memory: K-major, 128 x 128 half
+constexpr uint32_t kF64Bytes = 32768;
 constexpr uint32_t kWaitPolls = 1u << 26;          // backstop on polls
 constexpr uint64_t kWaitNs = 50ull * 1000 * 1000;  // a GEMM batch takes microseconds; give up after 50 ms
 constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;
 
-// Shared-memory map and thread organisation.  The per-bin chirp-phase words
-// live in tensor memory (64 columns after the accumulators): the chirp-stage
-// thread q of every pipe reads TMEM lane q mod 128, and the bins a lane's
-// threads handle are the same in every pipe, so one copy serves all pipes.
-template <int AB> struct TcLayout {
-    static constexpr int npipe = AB ? 1 : 3;           // DMs in flight per CTA
-    static constexpr int pt = AB ? 512 : 256;          // threads per pipe
+// Sizes, shared-memory map, tensor-memory map and thread organisation for
+// M = 2^LM.  The per-bin chirp-phase words live in tensor memory after the
+// accumulators: the chirp-stage thread q of every pipe reads TMEM lane q mod
+// 128, and the bins a lane's threads handle are the same in every pipe, so one
+// copy serves all pipes.
+template <int AB, int LM> struct TcLayout {
+    static constexpr int M = 1 << LM;
+    static constexpr int P = M / 64;                    // pass-A DFT length
+    static constexpr int npipe = LM == 12 ? (AB ? 1 : 3) : (AB ? 2 : 6);   // DMs in flight per CTA
+    static constexpr int pt = LM == 12 ? (AB ? 512 : 256) : (AB ? 256 : 128);   // threads per pipe
     static constexpr int nt = npipe * pt;
-    static constexpr uint32_t nb = AB ? 2 : 1;         // B matrices (hi, lo)
-    static constexpr uint32_t na = AB ? 2 : 1;         // operand planes per pipe (hi, lo)
+    static constexpr int ncg = pt / 128;                // TMEM column groups of a pipe's read-outs
+    static constexpr int jh = M / pt;                   // chirp bins (j_hi values) per thread
+    static constexpr uint32_t nb = AB ? 2 : 1;          // F_P planes (hi, lo)
+    static constexpr uint32_t na = AB ? 2 : 1;          // operand planes per pipe (hi, lo)
+    static constexpr uint32_t sbo_f = 32 * P;           // F_P, K-major: stride between 8-row cores
+    static constexpr uint32_t fbytes = 8 * P * P;       // one 2P x 2P half-precision F_P
+    static constexpr uint32_t sbo_x = 32 * P + 16;      // pass-A data, K-major: row-core stride padded by 16 B
+    static constexpr uint32_t lbo_y = 32 * P + 16;      // pass-B data, MN-major: K-core stride padded by 16 B
+    static constexpr uint32_t abuf = 16 * lbo_y;        // one operand: 16 K cores, or 16 row cores of pass A
     static constexpr uint32_t off_b = 0;
-    static constexpr uint32_t off_x = off_b + nb * kBmat;
-    static constexpr uint32_t off_tw = off_x + 16 * kM;               // W_4096 twiddles [m0][j_lo]
-    static constexpr uint32_t off_a = off_tw + 8 * kM;
-    static constexpr uint32_t abytes = na * kAbuf;
+    static constexpr uint32_t off_x = off_b + nb * fbytes;
+    static constexpr uint32_t off_tw = off_x + 16 * M;  // W_M twiddle pairs [m0 / 2][j_lo]
+    static constexpr uint32_t off_a = off_tw + 8 * M;
+    static constexpr uint32_t abytes = na * abuf;
     static constexpr uint32_t off_misc = off_a + npipe * abytes;
-    static constexpr uint32_t total = off_misc + 256;
+    // misc: mbarriers (one per pipe, <= 8) at +0, TMEM slot at +64, one float per
+    // warp (<= 32) at +128, queue ticket at +256
+    static constexpr uint32_t m_tslot = 64, m_red = 128, m_next = 256;
+    static constexpr uint32_t total = off_misc + 320;
+    static_assert(npipe <= 8 && nt <= 1024, "misc area");
     static constexpr uint32_t tmem_cols = 512;
-    static constexpr uint32_t ph_col = npipe * 128;                   // first phase-word column (64 columns)
-    static constexpr uint32_t f_col = ph_col + 64;                    // F as pass B's A operand (64 columns; BF16 lo: 64 more)
+    static constexpr uint32_t acc_cols = 2 * P;         // one accumulator
+    static constexpr uint32_t ph_col = npipe * acc_cols;   // first phase-word column
+    static constexpr uint32_t f_col = ph_col + 2 * jh * ncg;   // F_64 as pass B's A operand (64 columns; BF16 lo: 64 more)
+    static_assert(f_col + 64 * nb <= tmem_cols, "tensor memory");
+    static_assert(total <= 232448, "shared memory");
 };
 
 __device__ __forceinline__ bool bar_and(int id, int count, bool v)
@@ -103,13 +120,13 @@ template <int AB> __device__ __forceinline__ uint32_t pk(float lo, float hi)
 __device__ __forceinline__ float bf16_round(float x) { return __uint_as_float(__float_as_uint(__uint_as_float(tc::pack_bf16(x, 0.f) << 16))); }
 
 // Detection and integration of one pass-B result, by the thread of TMEM lane
-// 2 m1 + ro (ro: 0 real, 1 imaginary part) and column group cg (m0 in
-// [32 cg, 32 cg + 32)).  Columns pol * 64 + m0 hold polarisation pol at time
-// m' = m0 + 64 m1, counted from the first valid sample.  Each thread sums the
+// 2 m1 + ro (ro: 0 real, 1 imaginary part) and detection group cg (m0 in
+// [32 cg, 32 cg + 32)).  Columns pol * P + m0 hold polarisation pol at time
+// m' = m0 + P m1, counted from the first valid sample.  Each thread sums the
 // squares of its part over both polarisations and N consecutive m0, then the
 // lane pair (re, im) adds its partial sums: ro = 0 keeps the first half of the
 // windows of a chunk and ro = 1 the second half, one shuffle per output.
-template <int N>
+template <int N, int P>
 __device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro, float *__restrict__ orow, int seglen,
                                           float oscale)
 {
@@ -122,7 +139,7 @@ __device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro
         for (int c = 0; c < 2; c++) {   // 8 columns of each polarisation at a time
             uint32_t bx[8], by[8];
             tc::tmem_ld8_async(taddr + 32 * cg + 16 * h + 8 * c, bx);
-            tc::tmem_ld8_async(taddr + 64 + 32 * cg + 16 * h + 8 * c, by);
+            tc::tmem_ld8_async(taddr + P + 32 * cg + 16 * h + 8 * c, by);
             tc::tmem_wait();
             #pragma unroll
             for (int i8 = 0; i8 < 8; i8++) {
@@ -140,7 +157,7 @@ __device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro
             }
             acc[0] += carry;
         }
-        const int ubase = (64 * m1 + 32 * cg + (N == 32 ? 0 : 16 * h)) / N;
+        const int ubase = (P * m1 + 32 * cg + (N == 32 ? 0 : 16 * h)) / N;
         if constexpr (WC == 1) {
             const float tot = acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
             if (ro == 0 && ubase < seglen) orow[ubase] = tot * oscale;
@@ -172,21 +189,21 @@ struct TcItem {
     float scale_out;
 };
 
-// Per-CTA set-up: DFT matrix and twiddles to shared memory, tensor memory,
+// Per-CTA set-up: F_P and twiddles to shared memory, F_64 to tensor memory,
 // mbarriers.  Returns the TMEM base address.
-template <int AB>
+template <int AB, int LM>
 __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__restrict__ bmat,
-                                                 const float2 *__restrict__ twq)
+                                                 const uint4 *__restrict__ bmat64, const float2 *__restrict__ twq)
 {
-    using L = TcLayout<AB>;
+    using L = TcLayout<AB, LM>;
     constexpr int NT = L::nt;
     const int tid = threadIdx.x, warp = tid >> 5;
     uint8_t *bm = smem + L::off_b;
     float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + 32);
-    for (int i = tid; i < (int)(L::nb * kBmat / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
-    for (int i = tid; i < kM; i += NT) tws[i] = __ldg(twq + i);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L::off_misc + L::m_tslot);
+    for (int i = tid; i < (int)(L::nb * L::fbytes / 16); i += NT) reinterpret_cast<uint4 *>(bm)[i] = bmat[i];
+    for (int i = tid; i < L::M; i += NT) tws[i] = __ldg(twq + i);
     if (warp == 0) tc::tmem_alloc(tslot, L::tmem_cols);
     if (tid < L::npipe) {
         tc::mbar_init(&mbar[tid], 1);
@@ -197,9 +214,10 @@ __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__r
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    // F (and its BF16 lo part) into tensor memory as pass B's A operand: warp w < 4
-    // writes TMEM rows 32 w .. 32 w + 31; row 2 m1 + ro is shared-memory row
-    // 64 ro + m1, column c holds its K elements 2c, 2c + 1
+    // F_64 (and its BF16 lo part) into tensor memory as pass B's A operand: warp
+    // w < 4 writes TMEM rows 32 w .. 32 w + 31; row 2 m1 + ro is row 64 ro + m1 of
+    // the K-major copy in global memory, column c holds its K elements 2c, 2c + 1
+    const uint8_t *f64 = reinterpret_cast<const uint8_t *>(bmat64);
     if (warp < 4) {
         const int r = 32 * warp + (tid & 31);
         const int n = (r & 1) * 64 + (r >> 1);
@@ -211,8 +229,8 @@ __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__r
                 #pragma unroll
                 for (int c = 0; c < 32; c++) {
                     const int k = 2 * (32 * h + c);
-                    w[c] = *reinterpret_cast<const uint32_t *>(bm + part * kBmat + (n / 8) * kSboA + (k / 8) * kLboA +
-                                                               (n % 8) * 16 + (k % 8) * 2);
+                    w[c] = __ldg(reinterpret_cast<const uint32_t *>(f64 + part * kF64Bytes + (n / 8) * kF64Sbo +
+                                                                    (k / 8) * kLboA + (n % 8) * 16 + (k % 8) * 2));
                 }
                 tc::tmem_st32(tmem + ((uint32_t)(32 * warp) << 16) + L::f_col + 64 * part + 32 * h, w);
             }
@@ -224,31 +242,33 @@ __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__r
     return tmem;
 }
 
-template <int AB> __device__ __forceinline__ void tc_cta_teardown(uint32_t tmem)
+template <int AB, int LM> __device__ __forceinline__ void tc_cta_teardown(uint32_t tmem)
 {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_free(tmem, TcLayout<AB>::tmem_cols);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_free(tmem, TcLayout<AB, LM>::tmem_cols);
 }
 
 // The DM stage of one item.  Must be called by every thread of the CTA;
 // returns false (for every thread) if a tensor-core wait gave up.
-template <bool UNIFORM, int AB>
+template <bool UNIFORM, int AB, int LM>
 __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uint32_t tmem)
 {
-    using L = TcLayout<AB>;
+    using L = TcLayout<AB, LM>;
+    constexpr int kM = L::M;
+    constexpr int P = L::P;
     constexpr int NT = L::nt;
     constexpr int NPIPE = L::npipe;
     constexpr int PT = L::pt;                // threads per pipe
-    constexpr int NCG = PT / 128;           // TMEM column groups per pipe
-    constexpr int COLS = 128 / NCG;         // accumulator columns read per thread per read-out
-    constexpr int JH = 4096 / PT;           // j_hi values per thread in the chirp stage
+    constexpr int NCG = L::ncg;             // TMEM column groups per pipe
+    constexpr int JH = L::jh;               // j_hi values per thread in the chirp stage
+    constexpr uint32_t kSboA = L::sbo_f, kSboX = L::sbo_x, kLboB = L::lbo_y, kAbuf = L::abuf, kBmat = L::fbytes;
     uint8_t *bm = smem + L::off_b;
     float4 *xs = reinterpret_cast<float4 *>(smem + L::off_x);
     float2 *tws = reinterpret_cast<float2 *>(smem + L::off_tw);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::off_misc);
-    float *red = reinterpret_cast<float *>(smem + L::off_misc + 64);   // one float per warp
+    float *red = reinterpret_cast<float *>(smem + L::off_misc + L::m_red);   // one float per warp
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int pipe = tid / PT;
@@ -299,7 +319,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     __syncthreads();
     tc::fence_after();
 
-    const uint32_t dcol = tmem + 128 * pipe;
+    const uint32_t dcol = tmem + L::acc_cols * pipe;
     uint8_t *ab = smem + L::off_a + pipe * L::abytes;
     uint64_t *mb = &mbar[pipe];
     const int bar_id = 1 + pipe;
@@ -307,8 +327,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     const int nd = it.nd, nint = it.nint;
     const int half = nd / 2;
     const int seglen = (kM - nd) / nint;
-    const uint32_t id_a = tc::idesc(128, 128, AB, 0, 0);   // pass A: data (K-major) x F (K-major)
-    const uint32_t id_b = tc::idesc(128, 128, AB, 0, 1);   // pass B: F^T (K-major) x data (MN-major)
+    const uint32_t id_a = tc::idesc(128, 2 * P, AB, 0, 0);   // pass A: data (K-major) x F_P (K-major)
+    const uint32_t id_b = tc::idesc(128, 2 * P, AB, 0, 1);   // pass B: F_64^T (K-major) x data (MN-major)
     const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
     // The issuing thread builds each operand's descriptor of K step 0 once per GEMM;
     // step ks adds ks * (byte step >> 4) to the address field (bits 0-13, no carry:
@@ -317,7 +337,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     uint32_t ok = 1;
 
     for (int d = pipe; d < ndt; d += NPIPE) {
-        // ---- chirp, round: pass-A operand, K-major, row = pol * 64 + j_lo, k = 2 j_hi + (re, im)
+        // ---- chirp, round: pass-A operand, K-major, row = 2 j_lo + pol, k = 2 j_hi + (re, im)
         {
             double dmv = 0.0;
             if constexpr (!UNIFORM) dmv = it.dms[d];
@@ -340,7 +360,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                         const double kj = __hiloint2double((int)w[2 * b + 1], (int)w[2 * b]);
                         double cyc = dmv * kj;
                         cyc -= rint(cyc);
-                        const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << 20);
+                        const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << (32 - LM));
                         __sincosf((float)(int32_t)pf * kTwoPiOver2p32, &sn, &cs);
                     }
                     const float4 v = xs[j];
@@ -377,7 +397,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                 dFl = tc::sdesc(fa + kBmat, kLboA, kSboA);
             }
             #pragma unroll
-            for (int ks = 0; ks < 8; ks++) {
+            for (int ks = 0; ks < P / 8; ks++) {   // K = 2P
                 tc::mma(dcol, dX + kStepK * ks, dF + kStepK * ks, id_a, ks > 0);
                 if constexpr (AB) {
                     tc::mma(dcol, dXl + kStepK * ks, dF + kStepK * ks, id_a, 1);
@@ -390,19 +410,19 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (!ok) break;
         tc::fence_after();
 
-        // ---- pass-A row (j_lo, pol) -> twiddle -> pass-B operand (MN-major): column pol * 64 + m0,
+        // ---- pass-A row (j_lo, pol) -> twiddle -> pass-B operand (MN-major): column pol * P + m0,
         //      k = 2 j_lo + (re, im).  Eight m0 at a time: their real parts (TMEM columns m0)
-        //      and imaginary parts (64 + m0) are loaded together and waited for once.
+        //      and imaginary parts (P + m0) are loaded together and waited for once.
         {
             const int pol = t & 1, rjlo = t >> 1;
-            constexpr int MPT = 64 / NCG;             // m0 per thread
+            constexpr int MPT = P / NCG;              // m0 per thread
             const float4 *tw4 = reinterpret_cast<const float4 *>(tws);
             #pragma unroll
             for (int st = 0; st < MPT / 8; st++) {
                 const int m0b = cg * MPT + 8 * st;
                 uint32_t vr[8], vi[8];
                 tc::tmem_ld8_async(dcol + lane_off + m0b, vr);
-                tc::tmem_ld8_async(dcol + lane_off + 64 + m0b, vi);
+                tc::tmem_ld8_async(dcol + lane_off + P + m0b, vi);
                 tc::tmem_wait();
                 float re[8], im[8];
                 #pragma unroll
@@ -417,7 +437,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                     tc::f2_unpack(R, re[2 * i], re[2 * i + 1]);
                     tc::f2_unpack(I, im[2 * i], im[2 * i + 1]);
                 }
-                const uint32_t o = (uint32_t)((pol * 64 + m0b) / 8) * kSboB + (uint32_t)(2 * rjlo / 8) * kLboB +
+                const uint32_t o = (uint32_t)((pol * P + m0b) / 8) * kSboB + (uint32_t)(2 * rjlo / 8) * kLboB +
                                    (uint32_t)((2 * rjlo) % 8) * 16;
                 *reinterpret_cast<uint4 *>(ab + o) =
                     make_uint4(pk<AB>(re[0], re[1]), pk<AB>(re[2], re[3]), pk<AB>(re[4], re[5]), pk<AB>(re[6], re[7]));
@@ -460,19 +480,19 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         if (!ok) break;
         tc::fence_after();
 
-        // ---- detect + integrate in registers (see the head of this file), by two
-        //      column groups of 32 m0 (BF16: the pipe's other two warpgroups skip)
-        if (NCG == 2 || cg < 2) {
+        // ---- detect + integrate in registers (see the head of this file), by P / 32
+        //      groups of 32 m0 (the pipe's other warpgroups, if any, skip)
+        if (cg < P / 32) {
             float *orow = it.out + (int64_t)d * it.dm_stride;
             const uint32_t taddr = dcol + lane_off;
             const int m1 = t >> 1, ro = t & 1;
             switch (nint) {
-            case 1: tc_detect<1>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 2: tc_detect<2>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 4: tc_detect<4>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 8: tc_detect<8>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 16: tc_detect<16>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            default: tc_detect<32>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 1: tc_detect<1, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 2: tc_detect<2, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 4: tc_detect<4, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 8: tc_detect<8, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 16: tc_detect<16, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            default: tc_detect<32, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
             }
         }
     }
@@ -481,22 +501,25 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
 }
 
 // AB: 0 = FP16 operands, 1 = BF16 hi/lo operands.
-// FP16: three pipes of 256 threads, each carrying one DM at a time through its
-// own operand buffer, TMEM columns and mbarrier.  BF16: one pipe of 512
-// threads (one hi/lo operand set fits).  Within a pipe the chirp stage is split
+// FP16: three pipes of 256 threads (M = 4096) or six of 128 (M = 2048), each
+// carrying one DM at a time through its own operand buffer, TMEM columns and
+// mbarrier.  BF16: one pipe of 512 threads (M = 4096; one hi/lo operand set
+// fits) or two of 256 (M = 2048).  Within a pipe the chirp stage is split
 // over all its threads, and each tensor-memory read-out is split by column
 // groups over its warpgroups (warp w reads TMEM lanes 32 (w % 4) .. + 31).
 // Persistent: one CTA per SM sets up once (DFT matrix and twiddles in shared
 // memory, F in tensor memory) and takes items (DM tile, subband, segment,
 // channel) blockIdx.x, + gridDim.x, ...; while it works on one item, the next
 // item's spectrum and phase words are prefetched into L2.
-template <bool UNIFORM, int AB>
-__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
+template <bool UNIFORM, int AB, int LM>
+__global__ void __launch_bounds__(TcLayout<AB, LM>::nt, 1)
 k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
-                const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
-                float *__restrict__ out, int *__restrict__ status, int nsub, int kc, int64_t k0, int nchan, int ndm,
-                int dm_tile, int nd, int nint, int64_t nout, float scale_out, int64_t nitems)
+                const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const uint4 *__restrict__ bmat64,
+                const float2 *__restrict__ twq, float *__restrict__ out, int *__restrict__ status, int nsub, int kc,
+                int64_t k0, int nchan, int ndm, int dm_tile, int nd, int nint, int64_t nout, float scale_out,
+                int64_t nitems)
 {
+    constexpr int kM = 1 << LM;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     // once any CTA has given up on a tensor-core wait, the rest of the launch
@@ -523,20 +546,21 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         it.scale_out = scale_out;
         return it;
     };
-    const uint32_t tmem = tc_cta_setup<AB>(smem, bmat, twq);
+    const uint32_t tmem = tc_cta_setup<AB, LM>(smem, bmat, bmat64, twq);
+    constexpr int kSrcChunks = kM / 256, kPhChunks = kM / 512;   // 4 KB chunks of 16 M and 8 M bytes
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const TcItem it = make(item);
-        if (tid < 24 && item + gridDim.x < nitems) {   // 16 + 8 chunks of 4 KB
+        if (tid < kSrcChunks + kPhChunks && item + gridDim.x < nitems) {
             const TcItem nx = make(item + gridDim.x);
-            if (tid < 16) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
-            else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - 16), 4096);
+            if (tid < kSrcChunks) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
+            else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - kSrcChunks), 4096);
         }
-        if (!tc_run_item<UNIFORM, AB>(it, smem, tmem)) {
+        if (!tc_run_item<UNIFORM, AB, LM>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
             break;
         }
     }
-    tc_cta_teardown<AB>(tmem);
+    tc_cta_teardown<AB, LM>(tmem);
 }
 
 // Persistent form for batches of beams of uneven shapes (FP16, evenly spaced
@@ -544,17 +568,18 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
 // items are exhausted.  The round number is read from device memory, so one
 // captured graph serves every round.
 template <int AB>
-__global__ void __launch_bounds__(TcLayout<AB>::nt, 1)
+__global__ void __launch_bounds__(TcLayout<AB, 12>::nt, 1)
 k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__restrict__ round_dev,
                       int *__restrict__ queue, const uint4 *__restrict__ bmat, const float2 *__restrict__ twq,
                       int *__restrict__ status)
 {
+    constexpr int kM = 4096;   // batched beams use channels of 4096 bins (F_P = F_64)
     extern __shared__ __align__(1024) uint8_t smem[];
-    int *next = reinterpret_cast<int *>(smem + TcLayout<AB>::off_misc + 192);
+    int *next = reinterpret_cast<int *>(smem + TcLayout<AB, 12>::off_misc + TcLayout<AB, 12>::m_next);
     const int tid = threadIdx.x;
     if (__syncthreads_or(tid == 0 ? *reinterpret_cast<volatile int *>(status) : 0)) return;
     const int round = *round_dev;
-    const uint32_t tmem = tc_cta_setup<AB>(smem, bmat, twq);
+    const uint32_t tmem = tc_cta_setup<AB, 12>(smem, bmat, bmat, twq);
     for (;;) {
         if (tid == 0) *next = atomicAdd(queue, 1);
         __syncthreads();
@@ -590,67 +615,79 @@ k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__
         it.nd = B.nd;
         it.nint = B.nint;
         it.scale_out = B.scale;
-        if (!tc_run_item<true, AB>(it, smem, tmem)) {
+        if (!tc_run_item<true, AB, 12>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
             break;
         }
     }
-    tc_cta_teardown<AB>(tmem);
+    tc_cta_teardown<AB, 12>(tmem);
 }
 
 // ---------------------------------------------------------------------------
 
-size_t tc_smem(int ab) { return ab ? TcLayout<1>::total : TcLayout<0>::total; }
-
-template <bool U, int AB> static cudaError_t set_attr()
+size_t tc_smem(int ab, int lm)
 {
-    return cudaFuncSetAttribute(k_dedisperse_tc<U, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TcLayout<AB>::total);
+    if (lm == 11) return ab ? TcLayout<1, 11>::total : TcLayout<0, 11>::total;
+    return ab ? TcLayout<1, 12>::total : TcLayout<0, 12>::total;
 }
 
-cudaError_t tc_prepare(int ab)
+template <bool U, int AB, int LM> static cudaError_t set_attr()
 {
-    cudaError_t e = ab ? set_attr<true, 1>() : set_attr<true, 0>();
-    if (e != cudaSuccess) return e;
-    e = ab ? set_attr<false, 1>() : set_attr<false, 0>();
-    if (e != cudaSuccess) return e;
-    return ab ? cudaFuncSetAttribute(k_dedisperse_tc_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TcLayout<1>::total)
-              : cudaFuncSetAttribute(k_dedisperse_tc_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TcLayout<0>::total);
+    return cudaFuncSetAttribute(k_dedisperse_tc<U, AB, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TcLayout<AB, LM>::total);
 }
+
+template <int AB> static cudaError_t prepare_ab()
+{
+    cudaError_t e = set_attr<true, AB, 12>();
+    if (e == cudaSuccess) e = set_attr<false, AB, 12>();
+    if (e == cudaSuccess) e = set_attr<true, AB, 11>();
+    if (e == cudaSuccess) e = set_attr<false, AB, 11>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dedisperse_tc_batch<AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcLayout<AB, 12>::total);
+    return e;
+}
+
+cudaError_t tc_prepare(int ab) { return ab ? prepare_ab<1>() : prepare_ab<0>(); }
 
 cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev, int *queue, const uint4 *bmat,
                             const float2 *twq, int *status, int ab, int nctas, cudaStream_t st)
 {
     if (ab)
-        k_dedisperse_tc_batch<1><<<nctas, TcLayout<1>::nt, TcLayout<1>::total, st>>>(beams, nbeam, round_dev, queue,
-                                                                                   bmat, twq, status);
+        k_dedisperse_tc_batch<1><<<nctas, TcLayout<1, 12>::nt, TcLayout<1, 12>::total, st>>>(
+            beams, nbeam, round_dev, queue, bmat, twq, status);
     else
-        k_dedisperse_tc_batch<0><<<nctas, TcLayout<0>::nt, TcLayout<0>::total, st>>>(beams, nbeam, round_dev, queue,
-                                                                                   bmat, twq, status);
+        k_dedisperse_tc_batch<0><<<nctas, TcLayout<0, 12>::nt, TcLayout<0, 12>::total, st>>>(
+            beams, nbeam, round_dev, queue, bmat, twq, status);
     return cudaGetLastError();
 }
 
-template <bool U, int AB> static void launch(const TcArgs &a, cudaStream_t st)
+template <bool U, int AB, int LM> static void launch(const TcArgs &a, cudaStream_t st)
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nitems = ntile * a.nsub * a.kc * a.nchan;
     const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
-    k_dedisperse_tc<U, AB><<<(unsigned)nblk, TcLayout<AB>::nt, TcLayout<AB>::total, st>>>(
-        a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan, a.ndm,
-        a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems);
+    k_dedisperse_tc<U, AB, LM><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
+        a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.bmat64, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan,
+        a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems);
+}
+
+template <int LM> static void launch_lm(const TcArgs &a, cudaStream_t st)
+{
+    if (a.uniform) {
+        if (a.ab) launch<true, 1, LM>(a, st);
+        else launch<true, 0, LM>(a, st);
+    } else {
+        if (a.ab) launch<false, 1, LM>(a, st);
+        else launch<false, 0, LM>(a, st);
+    }
 }
 
 cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st)
 {
-    if (a.uniform) {
-        if (a.ab) launch<true, 1>(a, st);
-        else launch<true, 0>(a, st);
-    } else {
-        if (a.ab) launch<false, 1>(a, st);
-        else launch<false, 0>(a, st);
-    }
+    if (a.lm == 11) launch_lm<11>(a, st);
+    else launch_lm<12>(a, st);
     return cudaGetLastError();
 }
 

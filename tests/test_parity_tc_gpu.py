@@ -103,10 +103,53 @@ def test_tc_strong_signal_scaling(cdmt, orc):
     assert emax <= TOL and erms <= TOL
 
 
-def test_tc_needs_4096_bins(cdmt):
+def test_tc_size_limits(cdmt):
+    # channels of 1024 bins, and an integration that does not divide 32, are not supported
     with pytest.raises(cdmt.CdmtError) as e:
-        cdmt.Plan(1, 1 << 17, 135.0, BW, [0.0, 5.0], 8, 4, nbin=1 << 14, precision=cdmt.CDMT_PREC_FP16)
+        cdmt.Plan(1, 1 << 17, 135.0, BW, [0.0, 5.0], 8, 4, nbin=1 << 13, precision=cdmt.CDMT_PREC_FP16)
     assert e.value.status == cdmt.CDMT_ENOTSUP
+    with pytest.raises(cdmt.CdmtError) as e:
+        cdmt.Plan(1, 1 << 17, 135.0, BW, [0.0, 5.0], 8, 3, nbin=1 << 15, precision=cdmt.CDMT_PREC_FP16)
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_tc_tiny_workload_own_shapes(cdmt, orc, name, prec):
+    # the tiny workload exactly as the FP32 path runs it: N = 2^14, 8 channels of M = 2048
+    w = synth.tiny()
+    x = w.voltages()
+    plan = cdmt.Plan(1, w.nsamp, w.f_centre, BW, w.dms, w.nchan, w.nint, nbin=w.nbin, precision=prec)
+    i = plan.info
+    assert i["mbin"] == 2048 and i["nd"] == 32
+    g = gpu_filterbank(plan, x)
+    plan.device_status()
+    assert np.all(np.isfinite(g))
+    o = orc.filterbank(x, w.f_centre, BW, w.dms, w.nchan, w.nint, w.nbin, i["nd"])
+    emax, erms = rel_errors(g, o)
+    print(f"{name} M=2048: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert emax <= TOL and erms <= TOL
+    p = w.pulses[0]
+    sg = pulse_snr(g, w.dms, p, w.f_centre, BW, 1, w.nchan, w.nint, i["nd"])
+    so = pulse_snr(o, w.dms, p, w.f_centre, BW, 1, w.nchan, w.nint, i["nd"])
+    print(f"{name} M=2048: S/N gpu {sg:.3f} oracle {so:.3f}")
+    assert so > 5 and abs(sg / so - 1) <= 0.01
+
+
+@pytest.mark.parametrize("nint", [16, 32])
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_tc_m2048_many_channels(cdmt, orc, name, prec, nint):
+    # 32 channels of 2048 bins (N = 2^16), 2 subbands, ragged tail, 7 DMs (six FP16 pipes, one idle on the last)
+    nsamp = 2 * (1 << 16) + 5001
+    dms = [0.0, 9.0, 18.0, 27.0, 36.0, 45.0, 54.0]
+    x = synth.noise(24, 2, nsamp)
+    plan = cdmt.Plan(2, nsamp, 140.0, BW, dms, 32, nint, nbin=1 << 16, precision=prec)
+    assert plan.info["mbin"] == 2048
+    g = gpu_filterbank(plan, x)
+    plan.device_status()
+    o = orc.filterbank(x, 140.0, BW, dms, 32, nint, 1 << 16, plan.info["nd"])
+    emax, erms = rel_errors(g, o)
+    print(f"{name} M=2048 nint {nint}: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert np.all(np.isfinite(g)) and emax <= TOL and erms <= TOL
 
 
 @pytest.mark.slow
