@@ -48,6 +48,8 @@ def workload(name):
         return synth.lofar64()
     if name == "lofar8":
         return synth.lofar64(nsub=8)
+    if name == "lofar64c32":
+        return synth.lofar64(nchan=32)
     if name == "tiny":
         return synth.tiny()
     raise SystemExit(f"unknown workload {name}")
@@ -672,7 +674,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdmt", choices=["cdmt", "reference"])
-    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "tiny", "batch4", "serve8"])
+    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "lofar64c32", "tiny", "batch4", "serve8"])
     ap.add_argument("--beams", type=int, default=8, help="serve8: beams served at once")
     ap.add_argument("--int8", action="store_true", help="serve8: int8 blocks (4 bytes per sample)")
     ap.add_argument("--autotune", action="store_true", help="batch4: time candidates per beam")

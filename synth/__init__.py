@@ -162,14 +162,16 @@ def tiny() -> Workload:
                     1 << 14, 1, (Pulse(0.30, 10.0, 1e-3, 0.5),))
 
 
-def lofar64(nsamp: int = 1 << 22, nsub: int = 64) -> Workload:
+def lofar64(nsamp: int = 1 << 22, nsub: int = 64, nchan: int = 16) -> Workload:
     """64 contiguous subbands 128.75-141.25 MHz, 2^22 samples, 5 pulses at
     DM ~ U(5, 60), widths U(0.2, 5) ms; N = 2^16, 128 DMs 0..63.5 step 0.5,
     16 channels, integrate 8.  ``nsub`` < 64 keeps the same per-subband work on
-    fewer subbands centred on 135 MHz (a small case for profiling)."""
+    fewer subbands centred on 135 MHz (a small case for profiling); ``nchan``
+    = 32 gives channels of 2048 bins at the same N."""
     g = np.random.default_rng(102)
     T = nsamp / 195312.5
     pulses = tuple(Pulse(float(g.uniform(1.0, max(1.5, T - 3.0))), float(g.uniform(5, 60)),
                          float(g.uniform(0.2e-3, 5e-3)), 0.5) for _ in range(5))
-    return Workload(f"lofar-{nsub}sub-2^{int(np.log2(nsamp))}", nsub, nsamp, 135.0, 0.1953125,
-                    tuple(0.5 * i for i in range(128)), 16, 8, 1 << 16, 2, pulses)
+    name = f"lofar-{nsub}sub-2^{int(np.log2(nsamp))}" + ("" if nchan == 16 else f"-{nchan}ch")
+    return Workload(name, nsub, nsamp, 135.0, 0.1953125, tuple(0.5 * i for i in range(128)), nchan, 8, 1 << 16, 2,
+                    pulses)
