@@ -55,6 +55,9 @@ def _load():
             lib.orc_overlap.restype = i64
             lib.orc_overlap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, i64]
+            lib.orc_overlap_m.restype = i64
+            lib.orc_overlap_m.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, i64, ctypes.c_int]
             lib.orc_fft.restype = None
             lib.orc_fft.argtypes = [dp, i64, ctypes.c_int]
             lib.orc_dft.restype = None
@@ -62,17 +65,24 @@ def _load():
             lib.orc_segment_channels.restype = None
             lib.orc_segment_channels.argtypes = [dp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, dp]
+            lib.orc_segment_channels_m.restype = None
+            lib.orc_segment_channels_m.argtypes = [dp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, dp, ctypes.c_int]
             lib.orc_grid.restype = ctypes.c_int
             lib.orc_grid.argtypes = [i64, i64, ctypes.c_int, i64, ctypes.c_int,
                                      ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
             lib.orc_filterbank.restype = ctypes.c_int
             lib.orc_filterbank.argtypes = [fp, ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, dp,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, dp, ctypes.c_int]
+            lib.orc_filterbank_m.restype = ctypes.c_int
+            lib.orc_filterbank_m.argtypes = lib.orc_filterbank.argtypes + [ctypes.c_int]
             lib.orc_tiles.restype = ctypes.c_int
             lib.orc_tiles.argtypes = [fp, ctypes.c_int, i64, ctypes.c_double, ctypes.c_double, dp,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
                                       ctypes.POINTER(ctypes.c_int), dp, ctypes.c_int]
+            lib.orc_tiles_m.restype = ctypes.c_int
+            lib.orc_tiles_m.argtypes = lib.orc_tiles.argtypes + [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             lib.orc_redigitise.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.restype = None
@@ -104,10 +114,11 @@ def channel_centre(nu_s: float, bw: float, nchan: int, c: int) -> float:
     return _load().orc_channel_centre(nu_s, bw, nchan, c)
 
 
-def overlap(nsub, f_centre, bw, dm_list, nchan, nint, nbin) -> int:
-    """Overlap nd of Sec. 2 (nd = r t_d / n_c, t_d of Eq. 2 for the lowest channel)."""
+def overlap(nsub, f_centre, bw, dm_list, nchan, nint, nbin, chirp: int = 0) -> int:
+    """Overlap nd of Sec. 2 (nd = r t_d / n_c, t_d of Eq. 2 for the lowest channel;
+    chirp = 1: for the lowest subband, whose single transfer function spans it)."""
     dm = np.ascontiguousarray(dm_list, dtype=np.float64)
-    return int(_load().orc_overlap(nsub, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin))
+    return int(_load().orc_overlap_m(nsub, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin, chirp))
 
 
 def grid(nsamp, nbin, nchan, nd, nint):
@@ -134,33 +145,34 @@ def dft(x, sign: int) -> np.ndarray:
     return y
 
 
-def segment_channels(x, nchan: int, nu_s: float, bw: float, dm: float) -> np.ndarray:
+def segment_channels(x, nchan: int, nu_s: float, bw: float, dm: float, chirp: int = 0) -> np.ndarray:
     """Channelised, dedispersed complex series [nchan][M] of one polarisation of
     one segment, before the overlap is discarded (Sec. 2 steps 3-5 of Fig. 2)."""
     a = np.ascontiguousarray(x, dtype=np.complex128)
     n = len(a)
     y = np.empty((nchan, n // nchan), dtype=np.complex128)
-    _load().orc_segment_channels(_dp(a.view(np.float64)), n, nchan, nu_s, bw, dm, _dp(y.view(np.float64)))
+    _load().orc_segment_channels_m(_dp(a.view(np.float64)), n, nchan, nu_s, bw, dm, _dp(y.view(np.float64)), chirp)
     return y
 
 
-def filterbank(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, nthreads: int = 0) -> np.ndarray:
+def filterbank(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, nthreads: int = 0, chirp: int = 0) -> np.ndarray:
     """Whole DM x channel x time filterbank (Algorithm 1 up to detection, plus
     integration over nint).  x: float32 [nsub][nsamp][4]; returns float64
-    [ndm][nsub*nchan][nout]."""
+    [ndm][nsub*nchan][nout].  chirp: 0 per-channel transfer functions, 1 one per subband."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     nsub, nsamp = x.shape[0], x.shape[1]
     dm = np.ascontiguousarray(dm_list, dtype=np.float64)
     _, _, nout = grid(nsamp, nbin, nchan, nd, nint)
     out = np.zeros((len(dm), nsub * nchan, nout), dtype=np.float64)
-    rc = _load().orc_filterbank(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint,
-                                nbin, nd, _dp(out), nthreads)
+    rc = _load().orc_filterbank_m(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint,
+                                  nbin, nd, _dp(out), nthreads, chirp)
     if rc:
         raise ValueError("oracle rejected the arguments")
     return out
 
 
-def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthreads: int = 0) -> np.ndarray:
+def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthreads: int = 0,
+          chirp: int = 0) -> np.ndarray:
     """Filterbank samples of the listed (subband, segment, DM index) tiles:
     float64 [ntile][nchan][(M - nd)/nint].  Equal to the matching slice of
     :func:`filterbank` (each segment is independent given its own input)."""
@@ -172,10 +184,10 @@ def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthrea
     dmi = np.ascontiguousarray(dmi, dtype=np.int32)
     m = nbin // nchan
     out = np.zeros((len(sub), nchan, (m - nd) // nint), dtype=np.float64)
-    rc = _load().orc_tiles(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin, nd,
-                           len(sub), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                           seg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                           dmi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out), nthreads)
+    rc = _load().orc_tiles_m(_fp(x), nsub, nsamp, f_centre, bw, _dp(dm), len(dm), nchan, nint, nbin, nd,
+                             len(sub), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                             seg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             dmi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out), nthreads, chirp)
     if rc:
         raise ValueError("oracle rejected the tile list")
     return out

@@ -16,7 +16,9 @@
  *      by the conjugate of Eq. 1 evaluated at the channel centre nu_c with
  *      offset nu = (j - M/2) * bw / N  (Sec. 2: each channel gets its own
  *      transfer function; Sec. 3: "complex multiplication with transfer
- *      function").  Dedispersion is the convolution with the INVERSE of the
+ *      function").  The *_m entry points also offer one transfer function
+ *      for the whole subband (chirp = 1: Eq. 1 about the subband centre), the
+ *      alternative that Sec. 2 sets the per-channel choice against.  Dedispersion is the convolution with the INVERSE of the
  *      ISM transfer function (Sec. 1, Sec. 2), i.e. multiplication by
  *      exp(-2 pi i phi), phi = 1e6 * D * DM * nu^2 / (nu_c^2 (nu_c + nu)).
  *   4. halves of each channel swapped back, unitary inverse DFT_M
@@ -74,16 +76,17 @@ double orc_channel_centre(double nu_s, double bw, int nchan, int c)
 /* Overlap rule of Sec. 2: nd = r t_d / nchan with t_d (Eq. 2) for the lowest
  * channel, at the largest |DM| of the list.  Rounded up to an even integer
  * and then up until (M - nd) is a multiple of nint.  Returns -1 if no nd < M
- * exists. */
-int64_t orc_overlap(int nsub, double f_centre, double bw, const double *dm,
-                    int ndm, int nchan, int nint, int64_t nbin)
+ * exists.  chirp = 1 (one transfer function for the whole subband): t_d is
+ * the sweep across the lowest subband. */
+int64_t orc_overlap_m(int nsub, double f_centre, double bw, const double *dm,
+                      int ndm, int nchan, int nint, int64_t nbin, int chirp)
 {
     double dmax = 0.0;
     for (int i = 0; i < ndm; i++)
         if (fabs(dm[i]) > dmax) dmax = fabs(dm[i]);
     double nu_s0 = orc_subband_centre(nsub, f_centre, bw, 0);
     double lo = nu_s0 - 0.5 * bw;
-    double hi = lo + bw / (double)nchan;
+    double hi = lo + (chirp ? bw : bw / (double)nchan);
     double td = orc_sweep(lo, hi, dmax);
     double r = bw * 1e6;
     double want = r * td / (double)nchan;
@@ -93,6 +96,12 @@ int64_t orc_overlap(int nsub, double f_centre, double bw, const double *dm,
     while (nd < m && (m - nd) % nint != 0) nd += 2;
     if (nd >= m) return -1;
     return nd;
+}
+
+int64_t orc_overlap(int nsub, double f_centre, double bw, const double *dm,
+                    int ndm, int nchan, int nint, int64_t nbin)
+{
+    return orc_overlap_m(nsub, f_centre, bw, dm, ndm, nchan, nint, nbin, 0);
 }
 
 /* In-place iterative radix-2 FFT, unnormalised, kernel exp(sign*2*pi*i*nk/n). */
@@ -148,14 +157,17 @@ static void spectrum(const cplx *x, cplx *xs, cplx *tmp, int64_t n)
 }
 
 /* Steps 3-4 for one channel: chirp multiply, swap halves back, unitary inverse
- * DFT_M.  xs: the swapped forward spectrum of the segment (length N). */
+ * DFT_M.  xs: the swapped forward spectrum of the segment (length N).  The
+ * chirp is Eq. 1 about the reference frequency nu_r; bin j of the channel lies
+ * at nu_r + dnu + (j - M/2) bw / N (per-channel chirp: nu_r = nu_c, dnu = 0;
+ * one chirp for the subband: nu_r = nu_s, dnu = nu_c - nu_s). */
 static void channel_series(const cplx *xs, int64_t n, int nchan, int c,
-                           double nu_c, double bw, double dm, cplx *y, cplx *w)
+                           double nu_r, double dnu, double bw, double dm, cplx *y, cplx *w)
 {
     int64_t m = n / nchan;
     for (int64_t j = 0; j < m; j++) {
-        double nu = ((double)j - 0.5 * (double)m) * bw / (double)n;
-        double phi = 1e6 * ORC_D * dm * nu * nu / (nu_c * nu_c * (nu_c + nu));
+        double nu = dnu + ((double)j - 0.5 * (double)m) * bw / (double)n;
+        double phi = 1e6 * ORC_D * dm * nu * nu / (nu_r * nu_r * (nu_r + nu));
         cplx h = cos(2.0 * ORC_PI * phi) - I * sin(2.0 * ORC_PI * phi); /* exp(-2 pi i phi) */
         y[j] = xs[(int64_t)c * m + j] * h;
     }
@@ -168,8 +180,8 @@ static void channel_series(const cplx *xs, int64_t n, int nchan, int c,
 /* Complex channelised, dedispersed time series of ONE polarisation of ONE
  * segment, before any samples are discarded (steps 2-4).
  * x: N complex samples; y: [nchan][M] complex output. */
-void orc_segment_channels(const cplx *x, int64_t n, int nchan, double nu_s,
-                          double bw, double dm, cplx *y)
+void orc_segment_channels_m(const cplx *x, int64_t n, int nchan, double nu_s,
+                            double bw, double dm, cplx *y, int chirp)
 {
     int64_t m = n / nchan;
     cplx *xs = malloc(sizeof(cplx) * (size_t)n);
@@ -177,10 +189,17 @@ void orc_segment_channels(const cplx *x, int64_t n, int nchan, double nu_s,
     spectrum(x, xs, tmp, n);
     for (int c = 0; c < nchan; c++) {
         double nu_c = orc_channel_centre(nu_s, bw, nchan, c);
-        channel_series(xs, n, nchan, c, nu_c, bw, dm, y + (int64_t)c * m, tmp);
+        channel_series(xs, n, nchan, c, chirp ? nu_s : nu_c, chirp ? nu_c - nu_s : 0.0, bw, dm,
+                       y + (int64_t)c * m, tmp);
     }
     free(xs);
     free(tmp);
+}
+
+void orc_segment_channels(const cplx *x, int64_t n, int nchan, double nu_s,
+                          double bw, double dm, cplx *y)
+{
+    orc_segment_channels_m(x, n, nchan, nu_s, bw, dm, y, 0);
 }
 
 /* Plan quantities (overlap-save segment grid). Returns 0 on success. */
@@ -204,7 +223,7 @@ static void segment_rows(const float *in, int nsub, int64_t nsamp, double f_cent
                          double bw, const double *dm, int ndm_total,
                          const int *dm_idx, int ndm_sel, int nchan, int nint,
                          int64_t nbin, int64_t nd, int s, int64_t k, double *out,
-                         int64_t nout)
+                         int64_t nout, int chirp)
 {
     int64_t m = nbin / nchan;
     int64_t sv = nbin - nd * nchan;
@@ -229,7 +248,8 @@ static void segment_rows(const float *in, int nsub, int64_t nsamp, double f_cent
             double nu_c = orc_channel_centre(nu_s, bw, nchan, c);
             for (int64_t i = 0; i < m; i++) pw[i] = 0.0;
             for (int p = 0; p < 2; p++) {
-                channel_series(xs[p], nbin, nchan, c, nu_c, bw, dm[idm], y, tmp);
+                channel_series(xs[p], nbin, nchan, c, chirp ? nu_s : nu_c, chirp ? nu_c - nu_s : 0.0, bw,
+                               dm[idm], y, tmp);
                 for (int64_t i = 0; i < m; i++) {
                     double re = creal(y[i]), im = cimag(y[i]);
                     pw[i] += re * re + im * im;
@@ -252,10 +272,11 @@ static void segment_rows(const float *in, int nsub, int64_t nsamp, double f_cent
 }
 
 /* Whole filterbank: out double [ndm][nsub*nchan][nout]. nthreads <= 0 means
- * the OpenMP default.  Returns 0 on success, -1 on bad arguments. */
-int orc_filterbank(const float *in, int nsub, int64_t nsamp, double f_centre,
-                   double bw, const double *dm, int ndm, int nchan, int nint,
-                   int64_t nbin, int64_t nd, double *out, int nthreads)
+ * the OpenMP default.  chirp: 0 per-channel transfer functions, 1 one per
+ * subband.  Returns 0 on success, -1 on bad arguments. */
+int orc_filterbank_m(const float *in, int nsub, int64_t nsamp, double f_centre,
+                     double bw, const double *dm, int ndm, int nchan, int nint,
+                     int64_t nbin, int64_t nd, double *out, int nthreads, int chirp)
 {
     int64_t sv, nseg, nout;
     if (nbin % nchan || orc_grid(nsamp, nbin, nchan, nd, nint, &sv, &nseg, &nout))
@@ -271,20 +292,27 @@ int orc_filterbank(const float *in, int nsub, int64_t nsamp, double f_centre,
         int s = (int)(pr / nseg);
         int64_t k = pr % nseg;
         segment_rows(in, nsub, nsamp, f_centre, bw, dm, ndm, idx, ndm, nchan, nint,
-                     nbin, nd, s, k, out, nout);
+                     nbin, nd, s, k, out, nout, chirp);
     }
     free(idx);
     return 0;
+}
+
+int orc_filterbank(const float *in, int nsub, int64_t nsamp, double f_centre,
+                   double bw, const double *dm, int ndm, int nchan, int nint,
+                   int64_t nbin, int64_t nd, double *out, int nthreads)
+{
+    return orc_filterbank_m(in, nsub, nsamp, f_centre, bw, dm, ndm, nchan, nint, nbin, nd, out, nthreads, 0);
 }
 
 /* Sampled tiles: for each tile t, the filterbank samples of segment seg[t] in
  * the rows of subband sub[t] and DM index dmi[t], written to
  * out[t][nchan][(M - nd)/nint].  Each tile depends only on its own segment of
  * input, so this reproduces the corresponding slice of orc_filterbank. */
-int orc_tiles(const float *in, int nsub, int64_t nsamp, double f_centre, double bw,
-              const double *dm, int ndm, int nchan, int nint, int64_t nbin,
-              int64_t nd, int ntile, const int *sub, const int64_t *seg,
-              const int *dmi, double *out, int nthreads)
+int orc_tiles_m(const float *in, int nsub, int64_t nsamp, double f_centre, double bw,
+                const double *dm, int ndm, int nchan, int nint, int64_t nbin,
+                int64_t nd, int ntile, const int *sub, const int64_t *seg,
+                const int *dmi, double *out, int nthreads, int chirp)
 {
     int64_t sv, nseg, nout;
     if (nbin % nchan || orc_grid(nsamp, nbin, nchan, nd, nint, &sv, &nseg, &nout))
@@ -306,12 +334,21 @@ int orc_tiles(const float *in, int nsub, int64_t nsamp, double f_centre, double 
                            (size_t)(seg[t] * sv) * 4;
         segment_rows(src, 1, nbin, orc_subband_centre(nsub, f_centre, bw, sub[t]),
                      bw, dm + dmi[t], 1, (const int[]){0}, 1, nchan, nint, nbin, nd,
-                     0, 0, scratch, l);
+                     0, 0, scratch, l, chirp);
         memcpy(out + (size_t)t * (size_t)nchan * (size_t)l, scratch,
                sizeof(double) * (size_t)nchan * (size_t)l);
         free(scratch);
     }
     return 0;
+}
+
+int orc_tiles(const float *in, int nsub, int64_t nsamp, double f_centre, double bw,
+              const double *dm, int ndm, int nchan, int nint, int64_t nbin,
+              int64_t nd, int ntile, const int *sub, const int64_t *seg,
+              const int *dmi, double *out, int nthreads)
+{
+    return orc_tiles_m(in, nsub, nsamp, f_centre, bw, dm, ndm, nchan, nint, nbin, nd, ntile, sub, seg, dmi, out,
+                       nthreads, 0);
 }
 
 int orc_max_threads(void)

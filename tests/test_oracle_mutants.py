@@ -3,7 +3,10 @@
 The mutants are textual edits of a COPY of oracle/cdmt_oracle.c, compiled into
 a temporary directory on the CPU; the oracle itself is never modified.  Every
 edit is a plausible slip (a flipped sign, a dropped term, a wrong index or
-centre); the pins in test_oracle_pins.py must reject each one.
+centre); the pins in test_oracle_pins.py must reject each one.  (Swapping the
+reference of the subband-wide chirp for the channel centre while keeping the
+absolute frequencies is not listed: it changes the phase only at second order,
+since the reference's linear terms cancel against the shifted 1/F term.)
 """
 import importlib.util
 import os
@@ -37,6 +40,8 @@ MUTANTS = [
     ("overlap_uses_top_channel", "double lo = nu_s0 - 0.5 * bw;", "double lo = nu_s0 + 0.5 * bw - bw / (double)nchan;",
      None),
     ("segment_stride_wrong", "(size_t)(k * sv)) * 4;", "(size_t)(k * nbin)) * 4;", None),
+    ("subband_chirp_no_offset", "chirp ? nu_c - nu_s : 0.0", "0.0", None),
+    ("subband_overlap_channel_width", "(chirp ? bw : bw / (double)nchan)", "(bw / (double)nchan)", None),
     ("redig_sample_sigma", "s2 / (double)nt - mu * mu", "(s2 - mu * s1) / (double)(nt - 1)", None),
     ("redig_offset_127", "fmaf(row[t] - muf, g, 128.0f)", "fmaf(row[t] - muf, g, 127.0f)", None),
     ("redig_truncate", "float x = rintf(", "float x = truncf(", None),
@@ -57,6 +62,10 @@ PIN_CALLS = [
     lambda o: pins.test_noise_mean_and_variance(o),
     lambda o: pins.test_overlap_rule_values(o),
     lambda o: pins.test_overlap_covers_every_channel_and_is_minimal(o),
+    lambda o: pins.test_subband_chirp_aligns_channels(o),
+    lambda o: pins.test_subband_chirp_is_the_channel_chirp_for_one_channel(o),
+    lambda o: pins.test_subband_overlap_covers_subband_sweep_and_is_minimal(o),
+    lambda o: pins.test_subband_chirp_is_unitary(o),
     lambda o: pins.test_redigitise_two_level_channel(o),
     lambda o: pins.test_redigitise_constant_channel_is_the_mean_code(o),
     lambda o: pins.test_redigitise_clips_an_outlier(o),

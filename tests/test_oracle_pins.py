@@ -320,6 +320,62 @@ def test_overlap_covers_every_channel_and_is_minimal(orc):
     assert nd - 2 < need or (m - nd + 2) % nint != 0
 
 
+# ---------------------------------------------------------------- one transfer function per subband
+# The alternative Sec. 2 sets the per-channel chirp against: Eq. 1 about the subband
+# centre for every bin.  It removes the dispersion across the whole subband, so all
+# channels of a subband line up, at the cost of an overlap that holds the subband's sweep.
+
+
+def test_subband_chirp_aligns_channels(orc):
+    fc, dm_true, nchan, nbin = 135.0, 10.0, 8, 1 << 14
+    dms = [0.0, 5.0, 10.0, 15.0]
+    nd = orc.overlap(1, fc, BW, dms, nchan, 1, nbin, chirp=1)
+    assert nd > orc.overlap(1, fc, BW, dms, nchan, 1, nbin)
+    nsamp, t0 = 1 << 15, 20000
+    x = _physical_impulse(nsamp, fc, dm_true, t0)
+    fb = orc.filterbank(x, fc, BW, dms, nchan, 1, nbin, nd, chirp=1)
+    t_exp = t0 / nchan - nd / 2    # the same output sample in every channel: no inter-channel delay
+    for c in range(nchan):
+        row = fb[2, c]
+        i0 = int(np.floor(t_exp))
+        assert abs(np.argmax(row) - t_exp) <= 1.0, (c, np.argmax(row), t_exp)
+        assert (row[i0] + row[i0 + 1]) / np.sum(row) >= 0.8
+        for idm in (0, 1, 3):
+            other = fb[idm, c]
+            j = int(np.argmax(other))
+            assert (other[j] + max(other[j - 1], other[j + 1])) / np.sum(other) < 0.6
+
+
+def test_subband_chirp_is_the_channel_chirp_for_one_channel(orc):
+    g = np.random.default_rng(21)
+    x = (g.standard_normal((2, 1 << 15, 4)) * 0.5).astype(np.float32)
+    dms = [0.0, 4.0, 9.0]
+    nd0 = orc.overlap(2, 135.0, BW, dms, 1, 2, 1 << 13)
+    assert 0 < nd0 and orc.overlap(2, 135.0, BW, dms, 1, 2, 1 << 13, chirp=1) == nd0
+    a = orc.filterbank(x, 135.0, BW, dms, 1, 2, 1 << 13, nd0)
+    b = orc.filterbank(x, 135.0, BW, dms, 1, 2, 1 << 13, nd0, chirp=1)
+    assert np.array_equal(a, b)
+
+
+def test_subband_overlap_covers_subband_sweep_and_is_minimal(orc):
+    nsub, fc, nchan, nint, nbin = 4, 60.0, 4, 2, 1 << 16
+    dms = [0.0, 37.0, 11.0]
+    nd = orc.overlap(nsub, fc, BW, dms, nchan, nint, nbin, chirp=1)
+    r = BW * 1e6
+    need = max(r * orc.sweep(orc.subband_centre(nsub, fc, BW, s) - BW / 2,
+                             orc.subband_centre(nsub, fc, BW, s) + BW / 2, max(dms)) / nchan for s in range(nsub))
+    m = nbin // nchan
+    assert nd >= need and nd % 2 == 0 and (m - nd) % nint == 0
+    assert nd - 2 < need or (m - nd + 2) % nint != 0
+
+
+def test_subband_chirp_is_unitary(orc):
+    g = np.random.default_rng(22)
+    x = g.standard_normal(4096) + 1j * g.standard_normal(4096)
+    y = orc.segment_channels(x, 8, 135.0, BW, 33.0, chirp=1)
+    assert np.isclose(np.sum(np.abs(y) ** 2), np.sum(np.abs(x) ** 2), rtol=1e-12)
+
+
 # ---------------------------------------------------------------- redigitisation (Sec. 3)
 # Offsets and scales come from each channel's mean and standard deviation over the
 # block; 128 is the mean and 16 code steps span one standard deviation.
