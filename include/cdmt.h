@@ -67,13 +67,23 @@ enum cdmt_in_dtype {
 
 /* Optional plan overrides (cdmt_plan_ex).  Zero-initialise, then set fields;
  * a zero / negative field means "let the planner choose". */
+/* Transfer functions (Sec. 2).  CDMT_CHIRP_CHANNEL: Eq. 1 evaluated about each
+ * channel's centre, the paper's choice; it removes the dispersion within each
+ * channel and leaves the inter-channel delays for a later incoherent stage, with
+ * an overlap that holds one channel's sweep.  CDMT_CHIRP_SUBBAND: Eq. 1 about
+ * the subband centre for every bin, the alternative the paper sets it against;
+ * it removes the dispersion across the whole subband (its channels line up in
+ * time) and needs an overlap that holds the whole subband's sweep (n_c^2 times
+ * the channel's, roughly). */
+enum cdmt_chirp { CDMT_CHIRP_CHANNEL = 0, CDMT_CHIRP_SUBBAND = 1 };
+
 typedef struct cdmt_opts {
     int64_t nbin;        /* forward FFT length N_bin (power of two); 0 = choose */
     int64_t nd;          /* overlap n_d in channel samples; < 0 = rule of Sec. 2 */
     int32_t dm_tile;     /* DM trials per work item (forward spectrum reuse); 0 = choose */
     int32_t precision;   /* enum cdmt_precision */
     int32_t in_dtype;    /* enum cdmt_in_dtype */
-    int32_t reserved0;
+    int32_t chirp;       /* enum cdmt_chirp: transfer function per channel (default) or per subband */
     int64_t seg_chunk;   /* segments per internal chunk (workspace size); 0 = choose */
     int64_t mem_budget;  /* bytes of device memory the plan may hold; 0 = no limit */
     int64_t reserved[6];

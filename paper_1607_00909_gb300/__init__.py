@@ -20,13 +20,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcdmt.so")
 
 CDMT_OK, CDMT_EINVAL, CDMT_ENOMEM, CDMT_ECUDA, CDMT_ETIMEOUT, CDMT_EBUDGET, CDMT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+CDMT_CHIRP_CHANNEL, CDMT_CHIRP_SUBBAND = 0, 1
 CDMT_PREC_FP32, CDMT_PREC_FP16, CDMT_PREC_BF16 = 0, 1, 2
 CDMT_IN_C64, CDMT_IN_I8 = 0, 1
 
 
 class cdmt_opts(ctypes.Structure):
     _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("chirp", ctypes.c_int32),
                 ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
 
 
@@ -447,10 +448,10 @@ class Plan:
     """Owning wrapper of a cdmt plan."""
 
     def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
-                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64):
+                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0):
         o = cdmt_opts()
         o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
-        o.precision, o.in_dtype = precision, in_dtype
+        o.precision, o.in_dtype, o.chirp = precision, in_dtype, chirp
         self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
         self.info = cdmt_plan_info(self.handle)
 

@@ -63,8 +63,10 @@ int64_t overlap_rule(const cdmt_plan_s &p, int64_t nbin)
     double dmax = 0;
     for (double d : p.dms) dmax = std::max(dmax, std::fabs(d));
     const double band_lo = p.f_centre - 0.5 * p.nsub * p.bw;
-    const double chan_bw = p.bw / p.nchan;
-    const double td = sweep(band_lo, band_lo + chan_bw, dmax);
+    // the overlap holds the chirp of the lowest channel, or of the lowest subband
+    // when one transfer function spans the subband
+    const double span = p.chirp == CDMT_CHIRP_SUBBAND ? p.bw : p.bw / p.nchan;
+    const double td = sweep(band_lo, band_lo + span, dmax);
     const double want = p.bw * 1e6 * td / p.nchan;
     int64_t nd = (int64_t)std::ceil(want);
     nd += nd & 1;
@@ -109,12 +111,17 @@ __global__ void k_twiddle_passes(float2 *ta, float2 *tb, int r, int sign)
 
 // K = 1e6 D nu^2 / (nu_c^2 (nu_c + nu)) in cycles per unit DM for shifted bin
 // i = c M + j of subband s (Eq. 1 per channel; nu = (j - M/2) bw / N).
-__device__ __forceinline__ double chirp_k(double f_centre, double bw, int nsub, int nchan, int64_t nbin, int s, int64_t i)
+__device__ __forceinline__ double chirp_k(double f_centre, double bw, int nsub, int nchan, int64_t nbin, int s, int64_t i,
+                                          int chirp)
 {
+    const double nu_s = f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
+    if (chirp == CDMT_CHIRP_SUBBAND) {   // Eq. 1 about the subband centre: bin i at (i - N/2) bw / N
+        const double nu = ((double)i - 0.5 * (double)nbin) * bw / (double)nbin;
+        return 1e6 * 4.148808e3 * nu * nu / (nu_s * nu_s * (nu_s + nu));
+    }
     const int64_t m = nbin / nchan;
     const int c = (int)(i / m);
     const int64_t j = i % m;
-    const double nu_s = f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
     const double nu_c = nu_s - 0.5 * bw + ((double)c + 0.5) * bw / (double)nchan;
     const double nu = ((double)j - 0.5 * (double)m) * bw / (double)nbin;
     return 1e6 * 4.148808e3 * nu * nu / (nu_c * nu_c * (nu_c + nu));
@@ -128,7 +135,7 @@ __device__ __forceinline__ uint32_t fix32(double x) { return (uint32_t)(unsigned
 // backward DFT output by `shift` samples (exact: shift * j * 2^32 / M is an
 // integer for M a power of two <= 2^32).
 __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, double f_centre, double bw, int nsub,
-                            int nchan, int64_t nbin, int ntile, int shift)
+                            int nchan, int64_t nbin, int ntile, int shift, int chirp)
 {
     const int64_t mbin = nbin / nchan;
     const int64_t total = (int64_t)ntile * nsub * nbin;
@@ -136,18 +143,18 @@ __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, doub
         const int64_t i = q % nbin;
         const int s = (int)((q / nbin) % nsub);
         const int tile = (int)(q / ((int64_t)nbin * nsub));
-        const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i);
+        const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i, chirp);
         const int lm = 31 - __clz((int)mbin);   // shift * j * 2^32 / M = (shift * j) << (32 - log2 M)
         const uint32_t ramp = shift ? (uint32_t)((i % mbin) * shift) << (32 - lm) : 0u;
         nco[q] = make_uint2(fix32(-dm_tile0[tile] * k) + ramp, fix32(-ddm * k));
     }
 }
 
-__global__ void k_k_table(double *kt, double f_centre, double bw, int nsub, int nchan, int64_t nbin)
+__global__ void k_k_table(double *kt, double f_centre, double bw, int nsub, int nchan, int64_t nbin, int chirp)
 {
     const int64_t total = (int64_t)nsub * nbin;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
-        kt[q] = chirp_k(f_centre, bw, nsub, nchan, nbin, (int)(q / nbin), q % nbin);
+        kt[q] = chirp_k(f_centre, bw, nsub, nchan, nbin, (int)(q / nbin), q % nbin, chirp);
 }
 
 // 2P x 2P real form of the backward P-point DFT (W = exp(+2 pi i / P)) in the
@@ -390,6 +397,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     if (o.precision != CDMT_PREC_FP32 && o.precision != CDMT_PREC_FP16 && o.precision != CDMT_PREC_BF16)
         return fail(nullptr, CDMT_ENOTSUP, "precision %d not available", o.precision);
     if (o.in_dtype != CDMT_IN_C64) return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
+    if (o.chirp != CDMT_CHIRP_CHANNEL && o.chirp != CDMT_CHIRP_SUBBAND)
+        return fail(nullptr, CDMT_EINVAL, "chirp %d is neither per channel nor per subband", o.chirp);
 
     auto *p = new cdmt_plan_s();
     cudaGetDevice(&p->device);
@@ -403,6 +412,7 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     p->nint = nint;
     p->precision = o.precision;
     p->in_dtype = o.in_dtype;
+    p->chirp = o.chirp;
     p->mem_budget = o.mem_budget;
 
     // N_bin: explicit, or the largest M in 512..4096 whose overlap wastes <= 1/4
@@ -554,9 +564,9 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         TRYC(cudaMalloc(&d_tile0, sizeof(double) * p->ntile));
         TRYC(cudaMemcpy(d_tile0, tile0.data(), sizeof(double) * p->ntile, cudaMemcpyHostToDevice));
         k_nco_table<<<1024, 256>>>(p->nco, d_tile0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile,
-                                   p->precision != CDMT_PREC_FP32 ? (int)(p->nd / 2) : 0);
+                                   p->precision != CDMT_PREC_FP32 ? (int)(p->nd / 2) : 0, p->chirp);
     } else {
-        k_k_table<<<1024, 256>>>(p->ktab, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin);
+        k_k_table<<<1024, 256>>>(p->ktab, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->chirp);
     }
     TRYC(cudaGetLastError());
     TRYC(cudaDeviceSynchronize());

@@ -34,6 +34,7 @@ struct cdmt_plan_s {
     int dm_tile = 0, ntile = 0;
     int64_t seg_chunk = 0;
     int precision = 0, in_dtype = 0;
+    int chirp = 0;         // enum cdmt_chirp
     int64_t mem_budget = 0;
     // device tables
     float2 *tw_n = nullptr, *tw_af = nullptr, *tw_bf = nullptr, *tw_ai = nullptr, *tw_bi = nullptr;
