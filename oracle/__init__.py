@@ -84,6 +84,10 @@ def _load():
             lib.orc_tiles_m.restype = ctypes.c_int
             lib.orc_tiles_m.argtypes = lib.orc_tiles.argtypes + [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
+            lib.orc_incoherent.restype = i64
+            lib.orc_incoherent.argtypes = [fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.restype = None
             lib.orc_max_threads.argtypes = []
@@ -205,7 +209,27 @@ def redigitise(fb) -> tuple[np.ndarray, np.ndarray]:
     return out, st
 
 
-LEVELS = 16.0   # code steps per standard deviation (128 = the mean)
+LEVELS = 16.0
+
+
+def incoherent(fb, nsub, nchan, f_centre, bw, nint, dm_c, ddm_lo, ddm_step, nk, chirp: int = 0):
+    """Incoherent dedispersion of coherent filterbanks fb [ndm][nsub*nchan][nt]
+    over nk fine trials dm_c[i] + ddm_lo + k ddm_step (Sec. 4).  Returns
+    (out float64 [ndm][nk][nt_out], delays int32 [ndm][nk][rows] relative to the
+    smallest)."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    dm = np.ascontiguousarray(dm_c, dtype=np.float64)
+    delays = np.empty((ndm, nk, rows), dtype=np.int32)
+    lib = _load()
+    nt_out = lib.orc_incoherent(_fp(fb), ndm, nsub, nchan, nt, f_centre, bw, nint, chirp, _dp(dm), ddm_lo,
+                                ddm_step, nk, None, delays.ctypes.data)
+    if nt_out < 1:
+        raise ValueError("no output sample survives the shifts")
+    out = np.empty((ndm, nk, nt_out), dtype=np.float64)
+    lib.orc_incoherent(_fp(fb), ndm, nsub, nchan, nt, f_centre, bw, nint, chirp, _dp(dm), ddm_lo, ddm_step, nk,
+                       out.ctypes.data, None)
+    return out, delays   # code steps per standard deviation (128 = the mean)
 
 
 def max_threads() -> int:

@@ -30,6 +30,8 @@
  *      block's samples, then 8-bit codes in decreasing-frequency, time-major
  *      order (Sec. 3, "compute block sums", "compute channel statistics",
  *      "redigitize").
+ *   8. (orc_incoherent) incoherent dedispersion of the coherent filterbanks
+ *      over fine DM trials (Sec. 4, semi-coherent search).
  *
  * Readings where the paper is silent: D = 4.148808e3 MHz^2 pc^-1 cm^3 s
  * (the paper quotes 1/2.41e-4); transforms unitary; channel index increases
@@ -404,4 +406,67 @@ void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out
             }
         }
     }
+}
+
+/*
+ * Incoherent dedispersion of the coherent filterbanks (Sec. 4, the
+ * semi-coherent search: each coherently dedispersed filterbank is
+ * incoherently dedispersed over fine DM trials around its coherent DM; Sec. 1
+ * describes incoherent dedispersion as shifting each channel's time series by
+ * its dispersive delay).  The channels of a coherent filterbank still carry
+ * the delays between their reference frequencies nu_r (channel centres, or
+ * subband centres for one transfer function per subband), so the shift of row
+ * r for total DM = DM_c + ddm_k, in output samples of t_samp seconds, is
+ *   d(c, k, r) = rint(D (DM_c + ddm_k) (nu_r^-2 - nu_top^-2) / t_samp),
+ * nu_top the highest reference frequency of the band.  With d_lo and d_hi the
+ * smallest and largest shift over all (c, k, r), the output is
+ *   out[c][k][t] = sum_r fb[c][r][t + d(c, k, r) - d_lo],  t < nt - (d_hi - d_lo)
+ * (sums in FP64).  delays (may be NULL) receives d(c, k, r) - d_lo as int32
+ * [ndm][nk][rows].  Returns nt_out, or -1 if no output sample remains.
+ */
+int64_t orc_incoherent(const float *fb, int ndm, int nsub, int nchan, int64_t nt, double f_centre, double bw,
+                       int nint, int chirp, const double *dm_c, double ddm_lo, double ddm_step, int nk,
+                       double *out, int32_t *delays)
+{
+    const int rows = nsub * nchan;
+    double *nu = malloc(sizeof(double) * (size_t)rows);
+    double top = 0.0;
+    for (int s = 0; s < nsub; s++) {
+        double nu_s = orc_subband_centre(nsub, f_centre, bw, s);
+        for (int c = 0; c < nchan; c++) {
+            nu[s * nchan + c] = chirp ? nu_s : orc_channel_centre(nu_s, bw, nchan, c);
+            if (nu[s * nchan + c] > top) top = nu[s * nchan + c];
+        }
+    }
+    const double tsamp = (double)nint * (double)nchan / (bw * 1e6);
+    const size_t nd_tab = (size_t)ndm * (size_t)nk * (size_t)rows;
+    int64_t *d = malloc(sizeof(int64_t) * nd_tab);
+    int64_t dlo = 0, dhi = 0;
+    for (int i = 0; i < ndm; i++)
+        for (int k = 0; k < nk; k++)
+            for (int r = 0; r < rows; r++) {
+                double dm = dm_c[i] + ddm_lo + (double)k * ddm_step;
+                int64_t v = (int64_t)llrint(ORC_D * dm * (1.0 / (nu[r] * nu[r]) - 1.0 / (top * top)) / tsamp);
+                d[((size_t)i * nk + k) * rows + r] = v;
+                if ((i | k | r) == 0 || v < dlo) dlo = v;
+                if ((i | k | r) == 0 || v > dhi) dhi = v;
+            }
+    const int64_t nt_out = nt - (dhi - dlo);
+    if (nt_out > 0 && out) {
+        for (int i = 0; i < ndm; i++)
+            for (int k = 0; k < nk; k++) {
+                double *o = out + ((size_t)i * nk + k) * (size_t)nt_out;
+                for (int64_t t = 0; t < nt_out; t++) o[t] = 0.0;
+                for (int r = 0; r < rows; r++) {
+                    const float *row = fb + ((size_t)i * rows + r) * (size_t)nt;
+                    const int64_t sh = d[((size_t)i * nk + k) * rows + r] - dlo;
+                    for (int64_t t = 0; t < nt_out; t++) o[t] += (double)row[t + sh];
+                }
+            }
+    }
+    if (delays)
+        for (size_t q = 0; q < nd_tab; q++) delays[q] = (int32_t)(d[q] - dlo);
+    free(d);
+    free(nu);
+    return nt_out > 0 ? nt_out : -1;
 }

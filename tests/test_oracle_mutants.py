@@ -42,6 +42,11 @@ MUTANTS = [
     ("segment_stride_wrong", "(size_t)(k * sv)) * 4;", "(size_t)(k * nbin)) * 4;", None),
     ("subband_chirp_no_offset", "chirp ? nu_c - nu_s : 0.0", "0.0", None),
     ("subband_overlap_channel_width", "(chirp ? bw : bw / (double)nchan)", "(bw / (double)nchan)", None),
+    ("incoh_delay_sign", "(1.0 / (nu[r] * nu[r]) - 1.0 / (top * top))", "(1.0 / (top * top) - 1.0 / (nu[r] * nu[r]))",
+     None),
+    ("incoh_no_coherent_dm", "double dm = dm_c[i] + ddm_lo", "double dm = ddm_lo", None),
+    ("incoh_tsamp_no_nint", "(double)nint * (double)nchan / (bw * 1e6)", "(double)nchan / (bw * 1e6)", None),
+    ("incoh_subband_freq_in_channel_mode", "chirp ? nu_s : orc_channel_centre(nu_s, bw, nchan, c)", "nu_s", None),
     ("redig_sample_sigma", "s2 / (double)nt - mu * mu", "(s2 - mu * s1) / (double)(nt - 1)", None),
     ("redig_offset_127", "fmaf(row[t] - muf, g, 128.0f)", "fmaf(row[t] - muf, g, 127.0f)", None),
     ("redig_truncate", "float x = rintf(", "float x = truncf(", None),
@@ -66,6 +71,11 @@ PIN_CALLS = [
     lambda o: pins.test_subband_chirp_is_the_channel_chirp_for_one_channel(o),
     lambda o: pins.test_subband_overlap_covers_subband_sweep_and_is_minimal(o),
     lambda o: pins.test_subband_chirp_is_unitary(o),
+    lambda o: pins.test_incoherent_zero_dm_is_the_channel_sum(o),
+    lambda o: pins.test_incoherent_dispersed_impulse_lines_up_at_its_dm(o, 0),
+    lambda o: pins.test_incoherent_dispersed_impulse_lines_up_at_its_dm(o, 1),
+    lambda o: pins.test_incoherent_delay_table(o),
+    lambda o: pins.test_incoherent_is_linear_and_shift_covariant(o),
     lambda o: pins.test_redigitise_two_level_channel(o),
     lambda o: pins.test_redigitise_constant_channel_is_the_mean_code(o),
     lambda o: pins.test_redigitise_clips_an_outlier(o),

@@ -435,3 +435,72 @@ def test_redigitise_scale_invariance(orc):
     a, _ = orc.redigitise(fb)
     b, _ = orc.redigitise(fb * np.float32(8.0))
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- incoherent stage (Sec. 4)
+# Each coherent filterbank is incoherently dedispersed over fine DM trials around its
+# coherent DM by shifting every channel by its dispersive delay and summing.
+
+INC = dict(nsub=3, nchan=4, f_centre=135.0, bw=BW, nint=2)
+
+
+def _row_freqs(nsub, nchan, f_centre, bw, chirp=0):
+    out = []
+    for s in range(nsub):
+        nus = f_centre + (s - (nsub - 1) / 2) * bw
+        for c in range(nchan):
+            out.append(nus if chirp else nus - bw / 2 + (c + 0.5) * bw / nchan)
+    return np.array(out)
+
+
+def test_incoherent_zero_dm_is_the_channel_sum(orc):
+    g = np.random.default_rng(31)
+    rows = INC["nsub"] * INC["nchan"]
+    fb = g.random((1, rows, 300)).astype(np.float32)
+    out, d = orc.incoherent(fb, INC["nsub"], INC["nchan"], INC["f_centre"], BW, INC["nint"], [0.5], -0.5, 0.002, 1)
+    assert np.all(d == 0) and out.shape == (1, 1, 300)
+    assert np.allclose(out[0, 0], fb[0].astype(np.float64).sum(axis=0), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("chirp", [0, 1])
+def test_incoherent_dispersed_impulse_lines_up_at_its_dm(orc, chirp):
+    # rows get a unit impulse at their arrival time for DM 2.4 (Eq. 2 delays relative to the
+    # top reference frequency, at the output sample time nint * nchan / bw); the trial at
+    # DM 2.4 collects all of them in one sample, every other trial fewer
+    nsub, nchan, fc, nint = INC["nsub"], INC["nchan"], INC["f_centre"], INC["nint"]
+    nu = _row_freqs(nsub, nchan, fc, BW, chirp)
+    tsamp = nint * nchan / (BW * 1e6)
+    dm_true, t0 = 2.4, 50
+    arr = np.rint(D * dm_true * (nu ** -2 - nu.max() ** -2) / tsamp).astype(int)
+    fb = np.zeros((1, len(nu), 400), np.float32)
+    fb[0, np.arange(len(nu)), t0 + arr] = 1.0
+    out, d = orc.incoherent(fb, nsub, nchan, fc, BW, nint, [2.0], -0.5, 0.05, 21, chirp=chirp)
+    k_true = 18   # 2.0 - 0.5 + 18 * 0.05 = 2.4
+    assert np.isclose(out[0, k_true].max(), len(nu))
+    best = out[0].max(axis=1)
+    assert np.argmax(best) == k_true and np.all(np.delete(best, k_true) < len(nu))
+
+
+def test_incoherent_delay_table(orc):
+    nsub, nchan, fc, nint = INC["nsub"], INC["nchan"], INC["f_centre"], INC["nint"]
+    fb = np.zeros((2, nsub * nchan, 4000), np.float32)
+    _, d = orc.incoherent(fb, nsub, nchan, fc, BW, nint, [3.0, 40.0], -0.5, 0.002, 500)
+    top = np.argmax(_row_freqs(nsub, nchan, fc, BW))
+    assert d.min() == 0
+    assert np.all(np.diff(d.astype(int), axis=1) >= 0)                 # more DM, more delay
+    assert np.all(d[..., top] == d[..., top][0, 0])                     # the top channel never moves
+    assert np.all(np.diff(d[:, :, ::-1].astype(int), axis=2) >= 0)      # lower channels arrive later
+
+
+def test_incoherent_is_linear_and_shift_covariant(orc):
+    g = np.random.default_rng(32)
+    nsub, nchan, fc, nint = INC["nsub"], INC["nchan"], INC["f_centre"], INC["nint"]
+    a = g.random((2, nsub * nchan, 600)).astype(np.float32)
+    b = g.random((2, nsub * nchan, 600)).astype(np.float32)
+    args = (nsub, nchan, fc, BW, nint, [1.0, 6.0], -0.5, 0.1, 11)
+    oa, _ = orc.incoherent(a, *args)
+    ob, _ = orc.incoherent(b, *args)
+    oab, _ = orc.incoherent(a + np.float32(2.0) * b, *args)
+    assert np.allclose(oab, oa + 2.0 * ob, rtol=1e-6)
+    sh, _ = orc.incoherent(np.roll(a, 5, axis=2), *args)
+    assert np.allclose(sh[..., 5:], oa[..., :-5], rtol=1e-12)
