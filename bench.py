@@ -339,6 +339,36 @@ def gpu_arm(args, w):
         del u8
         log(f"rank {rank}: redigitise: {rms:.2f} ms per launch, {nbytes / rms / 1e6:.0f} GB/s")
 
+    # incoherent dedispersion of the headline filterbank over 500 fine trials (-0.5 .. +0.498 in
+    # steps of 0.002) around every coherent DM (Sec. 4), timed on its own
+    incoh = None
+    if not args.no_incoherent:
+        lo_, step_, nk_ = -0.5, 0.002, 500
+        nt_o, _ = cdmt.cdmt_incoherent_info(plan.handle, lo_, step_, nk_)
+        ndm_, rows_, nout_ = plan.out_shape()
+        io = torch.empty((ndm_, nk_, nt_o), dtype=torch.float32, device=dev)
+        st_ = stream.cuda_stream
+        plan.incoherent(out, lo_, step_, nk_, io, st_)   # uploads the shift table
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_inc = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(n_inc):
+            plan.incoherent(out, lo_, step_, nk_, io, st_)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ims = e0.elapsed_time(e1) / n_inc
+        adds = ndm_ * nk_ * nt_o * rows_
+        peak_adds = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * (
+            (clocks or {}).get("sm_max_mhz") or MEASURED.get("sm_max_mhz") or 2070.0) * 1e6
+        incoh = {"ms_per_launch": ims, "trials": nk_, "ddm": [lo_, step_], "nt_out": nt_o,
+                 "adds_per_launch": adds, "g_adds_per_s": adds / ims / 1e6, "bound": "alu",
+                 "peak_g_adds_per_s": peak_adds / 1e9, "frac": adds / ims / 1e3 / peak_adds,
+                 "output_bytes": io.numel() * 4,
+                 "note": "FP32 adds of shifted channel rows; peak = SMs x 128 lanes x SM clock; not part of the step"}
+        del io
+        log(f"rank {rank}: incoherent: {ims:.2f} ms per launch, {adds / ims / 1e6:.0f} G adds/s")
+
     # ---- roofline of the dominant kernel of the headline form
     nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
     dd_avg_s = R["dd_ms"] / max(1, R["dd_n"]) / 1e3
@@ -411,6 +441,7 @@ def gpu_arm(args, w):
                 "gpu_launches": int(launches),
                 "error_vs_oracle": R.get("error"),
                 "redigitise": redig,
+                "incoherent": incoh,
                 "forms": {f: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
                               "dedisperse_ms_per_step": r["dd_ms"] / args.steps,
                               "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error")}
@@ -685,6 +716,7 @@ def main():
                     help="precision forms to time, comma-separated (fp32, fp16, bf16); the last is the headline")
     ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
     ap.add_argument("--no-redigitise", action="store_true", help="skip timing the 8-bit redigitisation")
+    ap.add_argument("--no-incoherent", action="store_true", help="skip timing the incoherent stage")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

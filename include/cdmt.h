@@ -236,6 +236,35 @@ int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
 #define CDMT_REDIG_LEVELS 16.0
 int cdmt_redigitise(cdmt_plan_t plan, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Incoherent dedispersion of the coherent filterbanks (Sec. 4: in the
+ * semi-coherent search every coherently dedispersed filterbank is then
+ * incoherently dedispersed at fine DM steps around its coherent DM; Sec. 1:
+ * incoherent dedispersion shifts each channel's time series by its delay).
+ *
+ * The channels of a coherent filterbank still carry the delays between their
+ * reference frequencies nu_r (channel centres; subband centres for
+ * CDMT_CHIRP_SUBBAND), so for coherent DM trial c (DM_c, the plan's list), fine
+ * trial k (total DM = DM_c + ddm_lo + k ddm_step) and row r the shift in output
+ * samples of t_samp = nint * nchan / (bw_sub * 1e6) seconds is
+ *     d(c, k, r) = rint(D (DM_c + ddm_lo + k ddm_step) (nu_r^-2 - nu_top^-2) / t_samp)
+ * (FP64 on the host; nu_top the highest reference frequency), and with d_lo,
+ * d_hi the extreme shifts over all (c, k, r):
+ *     out[c][k][t] = sum_r fb[c][r][t + d(c, k, r) - d_lo],   t < nt_out = nout - (d_hi - d_lo)
+ * summed in FP32.  Output sample t is at the top frequency's time t + d_lo.
+ *
+ * cdmt_incoherent_info - nt_out for the fine-trial grid, and (h_delays, host,
+ * may be NULL) the shifts d - d_lo as int32 [ndm][nk][nsub*nchan].
+ * cdmt_incoherent - d_fb: device, the plan's filterbank [ndm][nsub*nchan][nout]
+ * (as cdmt_execute writes it); d_out: device float32 [ndm][nk][nt_out].
+ * Asynchronous on cuda_stream, except that a new trial grid uploads the plan's
+ * shift table synchronously.  Errors: CDMT_EINVAL (NULL pointers, nk < 1, no
+ * output sample left), CDMT_ENOMEM, CDMT_ENOTSUP (more than 65535 coherent DMs
+ * or 1024-sample blocks), CDMT_ECUDA. */
+int cdmt_incoherent_info(cdmt_plan_t plan, double ddm_lo, double ddm_step, int nk, int64_t *nt_out, int32_t *h_delays);
+int cdmt_incoherent(cdmt_plan_t plan, const float *d_fb, double ddm_lo, double ddm_step, int nk, float *d_out,
+                    void *cuda_stream);
+
 /* Bytes of the device array that backs cdmt_execute_static (64 MiB). */
 #define CDMT_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

@@ -138,6 +138,9 @@ def _load():
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_redigitise.argtypes = [P, P, P, P, P]
+    lib.cdmt_incoherent_info.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64), P]
+    lib.cdmt_incoherent.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
     lib.cdmt_strerror.argtypes = [ctypes.c_int]
     lib.cdmt_strerror.restype = ctypes.c_char_p
     lib.cdmt_last_error.argtypes = [P]
@@ -147,7 +150,8 @@ def _load():
               "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run", "cdmt_batch_status",
               "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
               "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
-              "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise"):
+              "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise", "cdmt_incoherent_info",
+              "cdmt_incoherent"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -156,7 +160,7 @@ _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
-            "cdmt_redigitise",
+            "cdmt_redigitise", "cdmt_incoherent_info", "cdmt_incoherent",
             "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
@@ -444,6 +448,24 @@ def cdmt_redigitise(plan, d_fb: int, d_u8: int, d_stats: int = 0, stream: int = 
 REDIG_LEVELS = 16.0
 
 
+def cdmt_incoherent_info(plan, ddm_lo: float, ddm_step: float, nk: int, delays: bool = False):
+    """(nt_out, shifts int32 [ndm][nk][rows] or None) of the fine-trial grid."""
+    n = ctypes.c_int64()
+    tab = None
+    ptr = None
+    if delays:
+        import numpy as np
+        info = cdmt_plan_info(plan)
+        tab = np.empty((info["ndm"], nk, info["nsub"] * info["nchan"]), dtype=np.int32)
+        ptr = tab.ctypes.data
+    _check(_lib.cdmt_incoherent_info(plan, ddm_lo, ddm_step, nk, ctypes.byref(n), ptr), plan)
+    return n.value, tab
+
+
+def cdmt_incoherent(plan, d_fb: int, ddm_lo: float, ddm_step: float, nk: int, d_out: int, stream: int = 0):
+    _check(_lib.cdmt_incoherent(plan, d_fb, ddm_lo, ddm_step, nk, d_out, stream or None), plan)
+
+
 class Plan:
     """Owning wrapper of a cdmt plan."""
 
@@ -467,6 +489,18 @@ class Plan:
     def out_shape(self):
         i = self.info
         return (i["ndm"], i["nsub"] * i["nchan"], i["nout"])
+
+    def incoherent(self, fb, ddm_lo=-0.5, ddm_step=0.002, nk=500, out=None, stream=None):
+        """Incoherent dedispersion of the filterbank fb (device tensor of out_shape()) over
+        nk fine trials around every coherent DM: float32 [ndm][nk][nt_out]."""
+        import torch
+        nt_out, _ = cdmt_incoherent_info(self.handle, ddm_lo, ddm_step, nk)
+        if out is None:
+            out = torch.empty((self.info["ndm"], nk, nt_out), dtype=torch.float32, device=fb.device)
+        assert fb.is_contiguous() and tuple(fb.shape) == self.out_shape() and out.is_contiguous()
+        st = torch.cuda.current_stream(fb.device).cuda_stream if stream is None else stream
+        cdmt_incoherent(self.handle, fb.data_ptr(), ddm_lo, ddm_step, nk, out.data_ptr(), st)
+        return out
 
     def redigitise(self, fb, out=None, stats=None, stream=None):
         """8-bit codes uint8 [ndm][nout][nsub*nchan] (decreasing frequency) of the

@@ -220,7 +220,7 @@ void release(cdmt_plan_s *p)
     cudaDeviceSynchronize();
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
-                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr};
+                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {

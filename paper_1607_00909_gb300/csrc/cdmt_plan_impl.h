@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -47,6 +49,12 @@ struct cdmt_plan_s {
     float2 *tc_twq = nullptr;
     int *d_status = nullptr;
     float2 *redig_mg = nullptr;   // redigitisation: (mean, levels / sigma) per (DM, channel)
+    int32_t *inc_tab = nullptr;   // incoherent stage: shifts [ndm][nk][rows] of the last trial grid
+    size_t inc_bytes = 0;
+    double inc_key[2] = {NAN, NAN};   // (ddm_lo, ddm_step) of inc_tab
+    int inc_nk = 0;
+    int64_t inc_nt_out = 0;
+    size_t inc_off = 0, inc_chg = 0;   // byte offsets of the change offsets and changes in inc_tab
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0;
