@@ -185,6 +185,17 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * CDMT_IN_I8 input.
  * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_ECUDA.
  */
+/* cdmt_execute_host_u8 - the pipeline of Algorithm 1 up to "redigitize" and
+ * "copy to host": like cdmt_execute_host, but each chunk of segments is a data
+ * block whose filterbank is redigitised on the device (cdmt_redigitise: the
+ * mean and sigma of each (DM, channel) over the block) and copied back as
+ * 8-bit codes, 4x fewer bytes than float32.  h_u8: host (pinned for overlap)
+ * uint8 [ndm][nout][nsub*nchan], spectra in decreasing frequency.
+ * *block_segments (may be NULL) receives the segments per block (the last
+ * block may be shorter).  Errors as cdmt_execute_host. */
+int cdmt_execute_host_u8(cdmt_plan_t plan, const void *h_in, uint8_t *h_u8, int64_t *block_segments,
+                         void *cuda_stream);
+
 int cdmt_execute_host(cdmt_plan_t plan, const void *h_in, float *h_out, const float *h_scale,
                       void *cuda_stream);
 

@@ -138,6 +138,7 @@ def _load():
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_redigitise.argtypes = [P, P, P, P, P]
+    lib.cdmt_execute_host_u8.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int64), P]
     lib.cdmt_incoherent_info.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), P]
     lib.cdmt_incoherent.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
@@ -151,7 +152,7 @@ def _load():
               "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
               "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
               "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise", "cdmt_incoherent_info",
-              "cdmt_incoherent"):
+              "cdmt_incoherent", "cdmt_execute_host_u8"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -160,7 +161,7 @@ _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
-            "cdmt_redigitise", "cdmt_incoherent_info", "cdmt_incoherent",
+            "cdmt_redigitise", "cdmt_incoherent_info", "cdmt_incoherent", "cdmt_execute_host_u8",
             "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
@@ -441,6 +442,14 @@ def cdmt_stage_times(plan):
     return (ms[0], ms[1]), (n[0], n[1])
 
 
+def cdmt_execute_host_u8(plan, h_in: int, h_u8: int, stream: int = 0) -> int:
+    """8-bit codes of every block to host memory (Algorithm 1's redigitize + copy to host);
+    returns the segments per block."""
+    n = ctypes.c_int64()
+    _check(_lib.cdmt_execute_host_u8(plan, h_in, h_u8, ctypes.byref(n), stream or None), plan)
+    return n.value
+
+
 def cdmt_redigitise(plan, d_fb: int, d_u8: int, d_stats: int = 0, stream: int = 0):
     _check(_lib.cdmt_redigitise(plan, d_fb, d_u8, d_stats or None, stream or None), plan)
 
@@ -482,6 +491,10 @@ class Plan:
 
     def execute_host(self, h_in: int, h_out: int, h_scale: int = 0, stream: int = 0):
         cdmt_execute_host(self.handle, h_in, h_out, h_scale, stream)
+
+    def execute_host_u8(self, h_in: int, h_u8: int, stream: int = 0) -> int:
+        """8-bit codes [ndm][nout][nsub*nchan] to host memory; returns the segments per block."""
+        return cdmt_execute_host_u8(self.handle, h_in, h_u8, stream)
 
     def device_status(self):
         cdmt_device_status(self.handle)

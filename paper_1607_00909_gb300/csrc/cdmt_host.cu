@@ -226,6 +226,7 @@ void release(cdmt_plan_s *p)
     for (auto &st : p->stage) {
         if (st.in) cudaFree(st.in);
         if (st.out) cudaFree(st.out);
+        if (st.u8) cudaFree(st.u8);
         cudaEvent_t evs[] = {st.in_free, st.in_ready, st.out_ready, st.out_free};
         for (auto ev : evs)
             if (ev) cudaEventDestroy(ev);
@@ -625,36 +626,46 @@ int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_s
     return rc;
 }
 
-int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float *h_scale, void *cuda_stream)
+namespace {
+
+// Staging buffers, events and copy streams of the host pipeline (first host call)
+int host_setup(cdmt_plan_s *p, cudaStream_t st)
 {
-    (void)h_scale;
-    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
-    if (!h_in || !h_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (p->host_chunk) return CDMT_OK;
     const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
-    if (!p->host_chunk) {
-        // chunks small enough to pipeline, large enough to fill the GPU
-        int64_t kc = std::max<int64_t>(1, std::min<int64_t>(p->seg_chunk, (p->nseg + 7) / 8));
-        p->host_chunk = kc;
-        p->span_max = (kc - 1) * p->nvalid + p->nbin;
-        for (auto &sg : p->stage) {
-            int rc;
-            if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
-            if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
-            CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
-            CK(p, cudaEventCreateWithFlags(&sg.in_ready, cudaEventDisableTiming));
-            CK(p, cudaEventCreateWithFlags(&sg.out_ready, cudaEventDisableTiming));
-            CK(p, cudaEventCreateWithFlags(&sg.out_free, cudaEventDisableTiming));
-            CK(p, cudaEventRecord(sg.in_free, st));
-            CK(p, cudaEventRecord(sg.out_free, st));
-        }
-        CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
-        CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+    // chunks small enough to pipeline, large enough to fill the GPU
+    const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(p->seg_chunk, (p->nseg + 7) / 8));
+    p->span_max = (kc - 1) * p->nvalid + p->nbin;
+    for (auto &sg : p->stage) {
+        int rc;
+        if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
+        if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
+        CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
+        CK(p, cudaEventCreateWithFlags(&sg.in_ready, cudaEventDisableTiming));
+        CK(p, cudaEventCreateWithFlags(&sg.out_ready, cudaEventDisableTiming));
+        CK(p, cudaEventCreateWithFlags(&sg.out_free, cudaEventDisableTiming));
+        CK(p, cudaEventRecord(sg.in_free, st));
+        CK(p, cudaEventRecord(sg.out_free, st));
     }
+    CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+    CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+    p->host_chunk = kc;
+    return CDMT_OK;
+}
+
+// The host pipeline: per chunk of segments, H2D of its input span (copy stream),
+// the forward and DM stages (st), then D2H of its filterbank (copy stream); with
+// u8, the chunk is redigitised as one block and its codes are copied instead.
+int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8, cudaStream_t st)
+{
+    int rc;
+    if ((rc = host_setup(p, st)) != CDMT_OK) return rc;
+    const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
+    const int64_t nrow = (int64_t)p->nsub * p->nchan;
     const int64_t kcm = p->host_chunk;
+    if (h_u8)
+        for (auto &sg : p->stage)
+            if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)rows * kcm * p->seglen)) != CDMT_OK) return rc;
     const auto *src = static_cast<const float4 *>(h_in);
     int b = 0;
     for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, b ^= 1) {
@@ -667,19 +678,51 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
         CK(p, cudaEventRecord(sg.in_ready, p->s_h2d));
         CK(p, cudaStreamWaitEvent(st, sg.in_ready, 0));
         CK(p, cudaStreamWaitEvent(st, sg.out_free, 0));
-        int rc = enqueue_chunk(p, sg.in, p->span_max, 0, sg.out, kcm * p->seglen, 0, kc, st);
-        if (rc != CDMT_OK) return rc;
+        if ((rc = enqueue_chunk(p, sg.in, p->span_max, 0, sg.out, kcm * p->seglen, 0, kc, st)) != CDMT_OK) return rc;
         CK(p, cudaEventRecord(sg.in_free, st));
+        if (h_u8 && (rc = redig_enqueue(p, sg.out, kc * p->seglen, kcm * p->seglen, sg.u8, nullptr, st)) != CDMT_OK)
+            return rc;
         CK(p, cudaEventRecord(sg.out_ready, st));
         CK(p, cudaStreamWaitEvent(p->s_d2h, sg.out_ready, 0));
-        CK(p, cudaMemcpy2DAsync(h_out + k0 * p->seglen, p->nout * 4, sg.out, kcm * p->seglen * 4, kc * p->seglen * 4,
-                                rows, cudaMemcpyDeviceToHost, p->s_d2h));
+        if (h_u8)   // [ndm][kc * seglen][nrow] -> rows of [ndm][nout][nrow] from sample k0 * seglen
+            CK(p, cudaMemcpy2DAsync(h_u8 + k0 * p->seglen * nrow, p->nout * nrow, sg.u8, kc * p->seglen * nrow,
+                                    kc * p->seglen * nrow, p->ndm, cudaMemcpyDeviceToHost, p->s_d2h));
+        else
+            CK(p, cudaMemcpy2DAsync(h_out + k0 * p->seglen, p->nout * 4, sg.out, kcm * p->seglen * 4,
+                                    kc * p->seglen * 4, rows, cudaMemcpyDeviceToHost, p->s_d2h));
         CK(p, cudaEventRecord(sg.out_free, p->s_d2h));
     }
     CK(p, cudaStreamSynchronize(p->s_d2h));
     CK(p, cudaStreamSynchronize(st));
-    if (cur != p->device) cudaSetDevice(cur);
     return CDMT_OK;
+}
+
+}  // namespace
+
+int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float *h_scale, void *cuda_stream)
+{
+    (void)h_scale;
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    if (!h_in || !h_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    const int rc = host_pipeline(p, h_in, h_out, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
+}
+
+int cdmt_execute_host_u8(cdmt_plan_t p, const void *h_in, uint8_t *h_u8, int64_t *block_segments, void *cuda_stream)
+{
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    if (!h_in || !h_u8) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    const int rc = host_pipeline(p, h_in, nullptr, h_u8, static_cast<cudaStream_t>(cuda_stream));
+    if (rc == CDMT_OK && block_segments) *block_segments = p->host_chunk;
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
 }
 
 int cdmt_device_status(cdmt_plan_t p)

@@ -16,6 +16,7 @@ namespace cdmt {
 struct Staging {
     float4 *in = nullptr;   // [nsub][span_max] samples
     float *out = nullptr;   // [ndm][nsub*nchan][kc_max*seglen]
+    uint8_t *u8 = nullptr;  // [ndm][kc_max*seglen][nsub*nchan] codes (8-bit host output)
     cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free = nullptr;
 };
 
@@ -74,4 +75,7 @@ int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int
 // forward stage + DM stage of kc segments (defined in cdmt_host.cu)
 int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
                   int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st);
+// redigitisation of nt samples per row (rows `stride` floats apart) as one block (cdmt_redig.cu)
+int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
+                  cudaStream_t st);
 }  // namespace cdmt

@@ -24,11 +24,11 @@ constexpr int kTile = 64;
 // row's (mu, g = levels / sigma) as FP32.  VEC: rows start 16-byte aligned
 // (nt % 4 == 0) and are read as float4, four loads in flight per thread.
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ fb, int64_t nt,
+__global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ fb, int64_t nt, int64_t stride,
                                                      float2 *__restrict__ mg, float *__restrict__ stats)
 {
     const int64_t row = blockIdx.x;
-    const float *p = fb + row * nt;
+    const float *p = fb + row * stride;
     float s1 = 0.f, s2 = 0.f;
     if constexpr (VEC) {
         const float4 *p4 = reinterpret_cast<const float4 *>(p);
@@ -86,9 +86,10 @@ __device__ __forceinline__ uint8_t code8(float v, float2 m)
 // One CTA per (64-sample, 64-row) tile of one DM: codes into shared memory,
 // then each output spectrum's 64 bytes (rows reversed) in 4-byte words.  VEC:
 // full-width tiles of 16-byte aligned rows are read as float4 (4 per thread).
+// Rows of the filterbank are `stride` floats apart; nt samples of each are coded.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ fb, const float2 *__restrict__ mg,
-                                                     uint8_t *__restrict__ out, int rows, int64_t nt)
+                                                     uint8_t *__restrict__ out, int rows, int64_t nt, int64_t stride)
 {
     __shared__ uint8_t tile[kTile][kTile + 4];   // [sample][row]
     const int dm = blockIdx.z;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ f
     const int64_t t0 = (int64_t)blockIdx.x * kTile;
     const int nr = min(kTile, rows - r0);
     const int ntt = (int)(nt - t0 < kTile ? nt - t0 : kTile);
-    const float *src = fb + ((int64_t)dm * rows + r0) * nt + t0;
+    const float *src = fb + ((int64_t)dm * rows + r0) * stride + t0;
     const float2 *g = mg + (int64_t)dm * rows + r0;
     if (VEC && ntt == kTile) {
         #pragma unroll
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ f
             const int rr = i / (kTile / 4), tt = 4 * (i % (kTile / 4));
             if (rr < nr) {
                 const float2 m = g[rr];
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (int64_t)rr * nt + tt));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (int64_t)rr * stride + tt));
                 tile[tt][rr] = code8(v.x, m);
                 tile[tt + 1][rr] = code8(v.y, m);
                 tile[tt + 2][rr] = code8(v.z, m);
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ f
     } else {
         for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
             const int rr = i / kTile, tt = i % kTile;
-            if (rr < nr && tt < ntt) tile[tt][rr] = code8(__ldg(src + (int64_t)rr * nt + tt), g[rr]);
+            if (rr < nr && tt < ntt) tile[tt][rr] = code8(__ldg(src + (int64_t)rr * stride + tt), g[rr]);
         }
     }
     __syncthreads();
@@ -145,40 +146,50 @@ int rfail(cdmt_plan_s *p, int code, const char *msg)
 
 }  // namespace
 
-extern "C" int cdmt_redigitise(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream)
+namespace cdmt {
+
+// Redigitisation of a filterbank [ndm][nsub*nchan][stride] whose first nt samples per row form
+// one block, into d_u8 [ndm][nt][nsub*nchan] (decreasing frequency); plan-owned (mu, g) array.
+int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
+                  cudaStream_t st)
 {
-    if (!p) return CDMT_EINVAL;
-    if (!d_fb || !d_u8) return rfail(p, CDMT_EINVAL, "NULL filterbank or output pointer");
     const int rows = p->nsub * p->nchan;
-    const int64_t nt = p->nout;
-    if (nt < 1) return rfail(p, CDMT_EINVAL, "the plan has no output samples");
+    if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
     if (p->ndm > 65535 || (rows + kTile - 1) / kTile > 65535)
         return rfail(p, CDMT_ENOTSUP, "more than 65535 DM trials or 64-row tiles");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return rfail(p, CDMT_ECUDA, "cudaSetDevice failed");
     if (!p->redig_mg) {
         if (cudaMalloc((void **)&p->redig_mg, sizeof(float2) * (size_t)p->ndm * rows) != cudaSuccess) {
             cudaGetLastError();
-            if (cur != p->device) cudaSetDevice(cur);
             return rfail(p, CDMT_ENOMEM, "redigitisation statistics buffer");
         }
         p->bytes += (int64_t)sizeof(float2) * p->ndm * rows;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // float4 reads need every row to start 16-byte aligned
-    const bool vec = nt % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
+    const bool vec = nt % 4 == 0 && stride % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
     const unsigned nrow = (unsigned)((int64_t)p->ndm * rows);
     const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)p->ndm);
     if (vec) {
-        k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, p->redig_mg, d_stats);
-        k_redig_codes<true><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt);
+        k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        k_redig_codes<true><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     } else {
-        k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, p->redig_mg, d_stats);
-        k_redig_codes<false><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt);
+        k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        k_redig_codes<false><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     }
     const cudaError_t e = cudaGetLastError();
-    if (cur != p->device) cudaSetDevice(cur);
     if (e != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(e));
     return CDMT_OK;
+}
+
+}  // namespace cdmt
+
+extern "C" int cdmt_redigitise(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream)
+{
+    if (!p) return CDMT_EINVAL;
+    if (!d_fb || !d_u8) return rfail(p, CDMT_EINVAL, "NULL filterbank or output pointer");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return rfail(p, CDMT_ECUDA, "cudaSetDevice failed");
+    const int rc = cdmt::redig_enqueue(p, d_fb, p->nout, p->nout, d_u8, d_stats, static_cast<cudaStream_t>(cuda_stream));
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
 }

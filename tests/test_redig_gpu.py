@@ -96,3 +96,35 @@ def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
     # detected noise: codes centred on 128 with 16 steps per sigma
     assert abs(c.mean() - 128.0) < 0.5 and abs(c.astype(np.float64).std() - 16.0) < 0.5
     plan.close()
+
+
+def test_host_pipeline_8bit_blocks(cdmt, orc):
+    # Algorithm 1 up to "redigitize" and "copy to host": every chunk of segments is a block
+    # with its own statistics; codes must match the oracle applied block by block to the
+    # float filterbank of the same plan
+    import torch
+    nsub, nsamp = 2, 9 * (1 << 14) + 123
+    x = synth.noise(42, nsub, nsamp)
+    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, [0.0, 6.0, 12.0], 8, 4, nbin=1 << 14)
+    ndm, rows, nout = plan.out_shape()
+    fb = cdmt.run(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    xh = torch.from_numpy(x).pin_memory()
+    u8 = torch.empty((ndm, nout, rows), dtype=torch.uint8).pin_memory()
+    kb = plan.execute_host_u8(xh.data_ptr(), u8.data_ptr())
+    seglen = nout // plan.info["nseg"]
+    assert 1 <= kb < plan.info["nseg"]           # more than one block
+    codes = u8.numpy()
+    nbad = 0
+    for s0 in range(0, plan.info["nseg"], kb):
+        t0, t1 = s0 * seglen, min(plan.info["nseg"], s0 + kb) * seglen
+        block = np.ascontiguousarray(fb[:, :, t0:t1])
+        oc, ost = orc.redigitise(block)
+        diff = codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32)
+        assert np.all(np.abs(diff) <= 1)
+        d, t, p = np.nonzero(diff)
+        r = rows - 1 - p
+        xv = 128.0 + (block[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / ost[d, r, 1]
+        assert np.all(np.abs(xv - np.floor(xv) - 0.5) < 1e-3)
+        nbad += len(d)
+    assert nbad <= max(1, 1e-4 * codes.size)
+    plan.close()
