@@ -202,6 +202,24 @@ PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 DTYPE = {"fp32": "f32", "fp16": "f16 (FP32 accumulate)", "bf16": "bf16 hi/lo (FP32 accumulate)"}
 
 
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """The largest v over the ranks of the process group (v itself on one rank):
+    replicas are timed by their slowest member."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas (one beam each, same
+    shapes) in G units/s: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3) / 1e9
+
+
 def sampled_error(w, x, out, info, ntile=8, seed=5):
     """max |gpu - oracle| / mean(oracle) and the RMS ratio on ntile random
     (subband, segment, DM) tiles of this run's output."""
@@ -245,12 +263,9 @@ def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
     ms = ev0.elapsed_time(ev1)
     (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
     cdmt.cdmt_set_timing(plan.handle, False)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     return {"plan": plan, "info": info, "ms_max": ms_max, "fwd_ms": fwd_ms, "dd_ms": dd_ms, "fwd_n": fwd_n,
-            "dd_n": dd_n, "value": world * info["units"] * args.steps / (ms_max / 1e3) / 1e9}
+            "dd_n": dd_n, "value": replica_value(info["units"], args.steps, ms_max, world)}
 
 
 def gpu_arm(args, w):
@@ -413,12 +428,10 @@ def gpu_arm(args, w):
         torch.cuda.synchronize(dev)
         e_s = time.perf_counter() - e0
         plan.device_status()
-        te = torch.tensor([e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * units * ne / float(te.item()) / 1e9, "unit": UNIT,
+        e_max = max_over_ranks(e_s, world, dev)
+        e2e = {"value": replica_value(units, ne, e_max * 1e3, world), "unit": UNIT,
                "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
-               "steps": ne, "ms_per_step": float(te.item()) / ne * 1e3, "output": "float32 filterbank"}
+               "steps": ne, "ms_per_step": e_max / ne * 1e3, "output": "float32 filterbank"}
         del hout
         # the paper's pipeline (Algorithm 1): each block redigitised to 8 bits on the device, codes to host
         hu8 = torch.empty((plan.out_shape()[0], plan.out_shape()[2], plan.out_shape()[1]), dtype=torch.uint8,
@@ -432,12 +445,10 @@ def gpu_arm(args, w):
         torch.cuda.synchronize(dev)
         e_s = time.perf_counter() - e0
         plan.device_status()
-        te = torch.tensor([e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e["u8"] = {"value": world * units * ne / float(te.item()) / 1e9, "unit": UNIT,
+        e_max = max_over_ranks(e_s, world, dev)
+        e2e["u8"] = {"value": replica_value(units, ne, e_max * 1e3, world), "unit": UNIT,
                      "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hu8.numel()),
-                     "ms_per_step": float(te.item()) / ne * 1e3, "block_segments": kb,
+                     "ms_per_step": e_max / ne * 1e3, "block_segments": kb,
                      "output": "8-bit filterbank (statistics per block), decreasing frequency, time-major"}
         del hin, hu8
 
