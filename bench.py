@@ -397,14 +397,16 @@ def gpu_arm(args, w):
                     "flops_per_unit": fft_flops_unit,
                     "peak_basis": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
     else:
-        # the tensor-core GEMM work actually issued: 2 passes x 128 rows x 128 x 128 x 2 flops per (channel, DM)
-        # (x3 for the BF16 hi/lo products), per unit = that x n_c / S
+        # the tensor-core GEMM work actually issued per (channel, DM), with P = M / 64: pass A
+        # 128 x 2P x 2P and pass B 128 x 2P x 128, 2 flops per multiply-add (x3 for the BF16 hi/lo
+        # products); per unit = that x n_c / S.  M = 4096: 2 x 128^3 x 2.
         mult = 3 if head == "bf16" else 1
-        tc_flops_unit = mult * 2 * 128 * 128 * 128 * 2 * info["nchan"] / info["nvalid"]
+        P_ = mbin // 64
+        tc_flops_unit = mult * 2 * 128 * (2 * P_) * (2 * P_ + 128) * info["nchan"] / info["nvalid"]
         achieved = tc_flops_unit * units / dd_avg_s / 1e12
         peak = MEASURED.get("bf16_tflops_sustained") or 1703.7
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": "k_dedisperse_tc", "work": "tensor-core GEMM flops issued (DFT-64 as real 128x128 GEMMs)",
+                    "kernel": "k_dedisperse_tc", "work": "tensor-core GEMM flops issued (two real DFT GEMMs per channel and DM)",
                     "flops_per_unit": tc_flops_unit,
                     "nominal_fft_tflops": fft_flops_unit * units / dd_avg_s / 1e12,
                     "peak_basis": "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); FP16 dense rate equals BF16"}
@@ -661,7 +663,8 @@ def serve_arm(args):
     t0 = time.perf_counter()
     beams = [srv.add_beam(c["nsub"], c["block_len"], c["f_centre"], c["bw"], 0.0, c["dm_max"] / c["ndm"], c["ndm"],
                           c["nchan"], c["nint"], precision=cdmt.CDMT_PREC_FP16,
-                          in_dtype=cdmt.CDMT_IN_I8 if i8 else cdmt.CDMT_IN_C64) for _ in range(args.beams)]
+                          in_dtype=cdmt.CDMT_IN_I8 if i8 else cdmt.CDMT_IN_C64,
+                          out_dtype=cdmt.CDMT_OUT_U8 if args.u8 else cdmt.CDMT_OUT_F32) for _ in range(args.beams)]
     st0 = srv.stats()
     log(f"{args.beams} beams admitted in {time.perf_counter() - t0:.1f}s: {st0.hbm_bytes / 1e9:.1f} GB, "
         f"{st0.slots} output slots")
@@ -674,7 +677,7 @@ def serve_arm(args):
     rows = c["nsub"] * c["nchan"]
 
     def probe(b, kb, res):   # copy a few tiles of beam 0's results before their slots are released
-        if args.no_error or b != 0 or kb not in pick or res.nseg < 1:
+        if args.no_error or args.u8 or b != 0 or kb not in pick or res.nseg < 1:
             return
         view = cdmt.Server.block_view(res, c["ndm"], rows)
         seglen = res.samples // res.nseg
@@ -709,7 +712,8 @@ def serve_arm(args):
             "config": {"workload": f"streaming server, {args.beams} beams x {c['nsub']} subbands, blocks of "
                                    f"2^16 samples ({block_s * 1e3:.1f} ms of data), {c['ndm']} DMs 0-{c['dm_max']:g}, "
                                    f"{c['nchan']} channels, nint {c['nint']}, "
-                                   + ("int8 input" if i8 else "complex64 input"),
+                                   + ("int8 input" if i8 else "complex64 input")
+                                   + (", 8-bit output (redigitised per block)" if args.u8 else ", float32 output"),
                        "step": "one block of every beam, from pinned host memory",
                        "l2": "per-block inputs and outputs larger than L2; no flush",
                        "hbm_bytes": sat.hbm_bytes, "output_slots": sat.slots},
@@ -724,7 +728,7 @@ def serve_arm(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": in_bytes * args.beams,
                     "d2h_bytes_per_step": 0,
                     "note": "host blocks in; the filterbanks stay in device slots for the consumer"},
-            "roofline": None, "gpu_launches": 4 * args.beams * args.steps, "clocks": clocks,
+            "roofline": None, "gpu_launches": (6 if args.u8 else 4) * args.beams * args.steps, "clocks": clocks,
             "error_vs_oracle": err}
     print(json.dumps(line), flush=True)
     return 0
@@ -739,6 +743,7 @@ def main():
     ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "lofar64c32", "tiny", "batch4", "serve8"])
     ap.add_argument("--beams", type=int, default=8, help="serve8: beams served at once")
     ap.add_argument("--int8", action="store_true", help="serve8: int8 blocks (4 bytes per sample)")
+    ap.add_argument("--u8", action="store_true", help="serve8: blocks redigitised to 8 bits on the device")
     ap.add_argument("--autotune", action="store_true", help="batch4: time candidates per beam")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

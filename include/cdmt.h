@@ -432,7 +432,11 @@ int cdmt_batch_destroy(cdmt_batch_t batch);
  * stream; blocks of different beams overlap on the GPU).  The slot pool is sized
  * from the HBM budget left after the resident beam state, so new blocks are
  * admitted as slots and memory free up.  A block's filterbank holds every
- * segment the block completes (Algorithm 1's block loop run per beam).
+ * segment the block completes (Algorithm 1's block loop run per beam).  A beam
+ * with out_dtype CDMT_OUT_U8 runs Algorithm 1 through "redigitize" for every
+ * block: the float32 filterbank goes to a scratch slot of the pool, which is
+ * free again once the block completes, and the 8-bit codes and the row
+ * statistics occupy the output slot.
  */
 typedef struct cdmt_server_s *cdmt_server_t;
 
@@ -453,21 +457,36 @@ typedef struct cdmt_stream_desc {
     int32_t in_dtype;      /* CDMT_IN_C64: 16-byte samples; CDMT_IN_I8: 4 int8 per sample + nsub float scales */
     int64_t nbin;          /* 0: 4096 * nchan */
     int32_t dm_tile;       /* DM trials per work item (0: the plan's choice) */
-    int32_t reserved0;
+    int32_t out_dtype;     /* enum cdmt_out_dtype: the block's filterbank as float32, or redigitised to
+                              8 bits per block (Sec. 3, as cdmt_redigitise) */
     int64_t reserved[4];
 } cdmt_stream_desc;
+
+/* Output type of a served block. */
+enum cdmt_out_dtype {
+    CDMT_OUT_F32 = 0, /* float32 [ndm][nsub*nchan][row_stride] in d_out */
+    CDMT_OUT_U8 = 1   /* 8-bit codes [ndm][samples][nsub*nchan] (spectra in decreasing frequency) in d_u8,
+                         per-row (mean, sigma) of the block's samples in d_stats */
+};
 
 typedef struct cdmt_block_result {
     int32_t beam;
     int32_t reserved0;
     int64_t index;         /* block number within the beam (submission order) */
-    float *d_out;          /* DEVICE slot: float32 [ndm][nsub*nchan][row_stride], this block's samples in
-                              columns [0, samples); valid until cdmt_server_release */
+    float *d_out;          /* CDMT_OUT_F32 beams: DEVICE slot, float32 [ndm][nsub*nchan][row_stride], this
+                              block's samples in columns [0, samples); valid until cdmt_server_release.
+                              NULL for 8-bit beams */
     int64_t nseg;          /* overlap-save segments this block completed (0 while the stream fills) */
     int64_t first_sample;  /* output-sample index (per channel, since the stream start) of column 0 */
     int64_t samples;       /* output samples per row in this block = nseg * (M - nd) / nint */
-    int64_t row_stride;
+    int64_t row_stride;    /* floats between rows of d_out: max segments per block x (M - nd) / nint, rounded
+                              up to a multiple of 4 */
     double latency_ms;     /* submit -> completion */
+    uint8_t *d_u8;         /* CDMT_OUT_U8 beams: DEVICE slot, [ndm][samples][nsub*nchan] codes (row r of the
+                              filterbank at position nsub*nchan-1-r); NULL for float32 beams */
+    float *d_stats;        /* CDMT_OUT_U8 beams: DEVICE, [ndm][nsub*nchan][2] (mean, sigma) of each row over
+                              this block's samples; both valid until cdmt_server_release, and only when
+                              samples > 0 */
 } cdmt_block_result;
 
 typedef struct cdmt_server_stats {

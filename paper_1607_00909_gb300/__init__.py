@@ -23,6 +23,7 @@ CDMT_OK, CDMT_EINVAL, CDMT_ENOMEM, CDMT_ECUDA, CDMT_ETIMEOUT, CDMT_EBUDGET, CDMT
 CDMT_CHIRP_CHANNEL, CDMT_CHIRP_SUBBAND = 0, 1
 CDMT_PREC_FP32, CDMT_PREC_FP16, CDMT_PREC_BF16 = 0, 1, 2
 CDMT_IN_C64, CDMT_IN_I8 = 0, 1
+CDMT_OUT_F32, CDMT_OUT_U8 = 0, 1
 
 
 class cdmt_opts(ctypes.Structure):
@@ -75,13 +76,14 @@ class cdmt_stream_desc(ctypes.Structure):
                 ("f_centre_mhz", ctypes.c_double), ("bw_sub_mhz", ctypes.c_double), ("dm_first", ctypes.c_double),
                 ("dm_step", ctypes.c_double), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("nbin", ctypes.c_int64),
-                ("dm_tile", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+                ("dm_tile", ctypes.c_int32), ("out_dtype", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
 
 
 class cdmt_block_result(ctypes.Structure):
     _fields_ = [("beam", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("index", ctypes.c_int64),
                 ("d_out", ctypes.c_void_p), ("nseg", ctypes.c_int64), ("first_sample", ctypes.c_int64),
-                ("samples", ctypes.c_int64), ("row_stride", ctypes.c_int64), ("latency_ms", ctypes.c_double)]
+                ("samples", ctypes.c_int64), ("row_stride", ctypes.c_int64), ("latency_ms", ctypes.c_double),
+                ("d_u8", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
 
 
 class cdmt_server_stats(ctypes.Structure):
@@ -381,10 +383,10 @@ class Server:
         self.handle = cdmt_server_create(o)
 
     def add_beam(self, nsub, block_len, f_centre, bw_sub, dm_first, dm_step, ndm, nchan, nint,
-                 precision=CDMT_PREC_FP16, in_dtype=CDMT_IN_C64, nbin=0, dm_tile=0) -> int:
+                 precision=CDMT_PREC_FP16, in_dtype=CDMT_IN_C64, nbin=0, dm_tile=0, out_dtype=CDMT_OUT_F32) -> int:
         d = cdmt_stream_desc(int(nsub), int(ndm), int(block_len), float(f_centre), float(bw_sub), float(dm_first),
                              float(dm_step), int(nchan), int(nint), int(precision), int(in_dtype), int(nbin),
-                             int(dm_tile))
+                             int(dm_tile), int(out_dtype))
         return cdmt_server_add_beam(self.handle, d)
 
     def submit(self, beam, block_ptr, scale_ptr=0) -> int:
@@ -408,6 +410,21 @@ class Server:
             __cuda_array_interface__ = {"shape": (ndm, rows, res.row_stride), "typestr": "<f4",
                                         "data": (res.d_out, False), "version": 3, "strides": None}
         return torch.as_tensor(_Slot(), device="cuda")[:, :, :res.samples]
+
+    @staticmethod
+    def block_u8_view(res: cdmt_block_result, ndm: int, rows: int):
+        """Zero-copy torch views of an 8-bit block (valid until release): codes [ndm][samples][rows]
+        (spectra in decreasing frequency) and statistics [ndm][rows][2] (mean, sigma)."""
+        import torch
+        if not res.d_u8:
+            raise CdmtError(CDMT_EINVAL, "the block has no 8-bit output (float32 beam)")
+
+        def view(ptr, shape, typestr):
+            class _A:
+                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
+                                            "strides": None}
+            return torch.as_tensor(_A(), device="cuda")
+        return view(res.d_u8, (ndm, res.samples, rows), "|u1"), view(res.d_stats, (ndm, rows, 2), "<f4")
 
     def reset_stats(self):
         cdmt_server_reset_stats(self.handle)

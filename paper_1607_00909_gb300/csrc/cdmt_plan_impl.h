@@ -76,6 +76,8 @@ int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int
 int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
                   int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st);
 // redigitisation of nt samples per row (rows `stride` floats apart) as one block (cdmt_redig.cu)
+// Allocates the plan's per-row (mean, gain) array of the redigitisation if it is missing.
+int redig_reserve(cdmt_plan_s *p);
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
                   cudaStream_t st);
 }  // namespace cdmt

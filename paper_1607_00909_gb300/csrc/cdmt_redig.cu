@@ -19,10 +19,11 @@ namespace {
 
 constexpr int kTile = 64;
 
-// One CTA per (DM, channel) row of nt samples: sums of I and I^2 (FP32 within a
+// One CTA per (DM, channel) row of nt samples (rows of kShortRow samples or
+// more; shorter rows use k_redig_stats_rows): sums of I and I^2 (FP32 within a
 // thread, FP64 across threads), then mean mu, standard deviation sigma, and the
 // row's (mu, g = levels / sigma) as FP32.  VEC: rows start 16-byte aligned
-// (nt % 4 == 0) and are read as float4, four loads in flight per thread.
+// (stride % 4 == 0) and are read as float4, four loads in flight per thread.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ fb, int64_t nt, int64_t stride,
                                                      float2 *__restrict__ mg, float *__restrict__ stats)
@@ -38,6 +39,11 @@ __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ f
             const float4 v = __ldg(p4 + t);
             s1 += (v.x + v.y) + (v.z + v.w);
             s2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s2))));
+        }
+        for (int64_t t = 4 * n4 + threadIdx.x; t < nt; t += blockDim.x) {   // the last nt % 4 samples
+            const float v = __ldg(p + t);
+            s1 += v;
+            s2 = fmaf(v, v, s2);
         }
     } else {
         #pragma unroll 4
@@ -69,6 +75,59 @@ __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ f
         const double mu = nt > 0 ? a / (double)nt : 0.0;
         const double var = nt > 0 ? fmax(b / (double)nt - mu * mu, 0.0) : 0.0;
         const double sigma = sqrt(var);
+        mg[row] = make_float2((float)mu, sigma > 0.0 ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        if (stats) {
+            stats[2 * row] = (float)mu;
+            stats[2 * row + 1] = (float)sigma;
+        }
+    }
+}
+
+// Rows shorter than kShortRow samples (a served block holds one or two
+// segments per row): one warp per row, eight rows per CTA, with the same
+// statistics as k_redig_stats (FP32 within a lane, FP64 across lanes).
+constexpr int64_t kShortRow = 8192;
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_redig_stats_rows(const float *__restrict__ fb, int64_t nrow, int64_t nt,
+                                                          int64_t stride, float2 *__restrict__ mg,
+                                                          float *__restrict__ stats)
+{
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= nrow) return;
+    const int lane = threadIdx.x & 31;
+    const float *p = fb + row * stride;
+    float s1 = 0.f, s2 = 0.f;
+    if constexpr (VEC) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+        #pragma unroll 4
+        for (int64_t t = lane; t < nt / 4; t += 32) {
+            const float4 v = __ldg(p4 + t);
+            s1 += (v.x + v.y) + (v.z + v.w);
+            s2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s2))));
+        }
+        if (lane < nt % 4) {   // the last nt % 4 samples
+            const float v = __ldg(p + 4 * (nt / 4) + lane);
+            s1 += v;
+            s2 = fmaf(v, v, s2);
+        }
+    } else {
+        #pragma unroll 4
+        for (int64_t t = lane; t < nt; t += 32) {
+            const float v = __ldg(p + t);
+            s1 += v;
+            s2 = fmaf(v, v, s2);
+        }
+    }
+    double d1 = s1, d2 = s2;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    if (lane == 0) {
+        const double mu = d1 / (double)nt;
+        const double sigma = sqrt(fmax(d2 / (double)nt - mu * mu, 0.0));
         mg[row] = make_float2((float)mu, sigma > 0.0 ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
         if (stats) {
             stats[2 * row] = (float)mu;
@@ -150,11 +209,9 @@ namespace cdmt {
 
 // Redigitisation of a filterbank [ndm][nsub*nchan][stride] whose first nt samples per row form
 // one block, into d_u8 [ndm][nt][nsub*nchan] (decreasing frequency); plan-owned (mu, g) array.
-int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
-                  cudaStream_t st)
+int redig_reserve(cdmt_plan_s *p)
 {
     const int rows = p->nsub * p->nchan;
-    if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
     if (p->ndm > 65535 || (rows + kTile - 1) / kTile > 65535)
         return rfail(p, CDMT_ENOTSUP, "more than 65535 DM trials or 64-row tiles");
     if (!p->redig_mg) {
@@ -164,15 +221,28 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
         }
         p->bytes += (int64_t)sizeof(float2) * p->ndm * rows;
     }
-    // float4 reads need every row to start 16-byte aligned
-    const bool vec = nt % 4 == 0 && stride % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
+    return CDMT_OK;
+}
+
+int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
+                  cudaStream_t st)
+{
+    const int rows = p->nsub * p->nchan;
+    if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
+    const int rc = redig_reserve(p);
+    if (rc != CDMT_OK) return rc;
+    // float4 reads need every row to start 16-byte aligned (rows' last nt % 4 samples are read singly)
+    const bool vec = stride % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
     const unsigned nrow = (unsigned)((int64_t)p->ndm * rows);
     const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)p->ndm);
+    const unsigned nrow8 = (nrow + 7) / 8;
     if (vec) {
-        k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        if (nt < kShortRow) k_redig_stats_rows<true><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats);
+        else k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
         k_redig_codes<true><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     } else {
-        k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        if (nt < kShortRow) k_redig_stats_rows<false><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats);
+        else k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
         k_redig_codes<false><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     }
     const cudaError_t e = cudaGetLastError();

@@ -81,6 +81,7 @@ struct Req {
     double t_submit = 0, t_start = 0, t_done = 0;
     int state = 0;              // 0 queued, 1 running, 2 done, 3 failed
     int slot = -1;
+    int scratch = -1;           // 8-bit beams: slot holding the float32 filterbank until the block completes
     cudaEvent_t ev = nullptr;
     int64_t nseg = 0, seg0 = 0; // segments of this block's output and the global index of its first
 };
@@ -89,11 +90,14 @@ struct Beam {
     cdmt_stream_desc d{};
     cdmt_plan_t plan = nullptr;
     int64_t N = 0, S = 0, nd = 0, M = 0, seglen = 0, max_seg = 0, cap = 0, rows = 0;
+    int64_t stride = 0;         // floats between the rows of a block's float32 filterbank (a multiple of 4)
     float4 *stage[2] = {nullptr, nullptr};
     int cur = 0;
     int64_t tail = 0, seg_total = 0, next_index = 0;
     void *d_blk = nullptr;
     float *d_scale = nullptr;
+    int64_t fb_bytes = 0;       // one block's float32 filterbank (max_seg segments)
+    int64_t codes_bytes = 0;    // 8-bit beams: codes part of a slot (16-byte multiple); statistics follow
     cudaStream_t st = nullptr;
     std::deque<int64_t> fifo;
     int64_t bytes = 0;
@@ -102,7 +106,7 @@ struct Beam {
 };
 
 struct Slot {
-    float *p = nullptr;
+    uint8_t *p = nullptr;
     int64_t bytes = 0;
     int64_t owner = -1;   // request id, -1 when free
 };
@@ -149,16 +153,20 @@ void erase_slot(cdmt_server_s *v, size_t i)
     cudaFree(v->slots[i].p);
     v->slot_total -= v->slots[i].bytes;
     v->slots.erase(v->slots.begin() + (std::ptrdiff_t)i);
-    for (size_t j = i; j < v->slots.size(); j++) {
+    for (size_t j = i; j < v->slots.size(); j++) {   // the slot at j was at j + 1
         auto it = v->reqs.find(v->slots[j].owner);
-        if (it != v->reqs.end()) it->second.slot = (int)j;
+        if (it == v->reqs.end()) continue;
+        if (it->second.slot == (int)j + 1) it->second.slot = (int)j;
+        else if (it->second.scratch == (int)j + 1) it->second.scratch = (int)j;
     }
 }
 
-// A free output slot of at least `bytes` (lock held).  Takes the smallest free
-// one that fits; otherwise allocates one while the budget and the slot limit
-// allow, first freeing unused slots that are too small when they stand in the
-// way.  -1: the block has to wait for a release.
+// A free slot of at least `bytes` (lock held).  Takes the smallest free one
+// that fits if it is at most twice the size asked for; otherwise allocates one
+// of the size asked for while the budget and the slot limit allow, else takes
+// the larger free slot, else frees unused slots that are too small and stand in
+// the way (cudaFree waits for the device, so that is the last resort).  -1: the
+// block has to wait for a release.
 int take_slot(cdmt_server_s *v, int64_t bytes)
 {
     int best = -1;
@@ -166,11 +174,12 @@ int take_slot(cdmt_server_s *v, int64_t bytes)
         const Slot &sl = v->slots[i];
         if (sl.owner < 0 && sl.bytes >= bytes && (best < 0 || sl.bytes < v->slots[best].bytes)) best = (int)i;
     }
-    if (best >= 0) return best;
+    if (best >= 0 && v->slots[best].bytes <= 2 * bytes) return best;
     const int64_t max_slots = v->o.max_slots > 0 ? v->o.max_slots : 64;
     auto full = [&] {
         return (int64_t)v->slots.size() >= max_slots || v->resident + v->slot_total + bytes > v->o.hbm_budget;
     };
+    if (best >= 0 && full()) return best;
     while (full()) {
         int small = -1;
         for (size_t i = 0; i < v->slots.size(); i++)
@@ -222,8 +231,13 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
     int64_t nseg = avail >= b.N ? (avail - b.N) / b.S + 1 : 0;
     nseg = std::min(nseg, b.max_seg);
     if (nseg > 0) {
-        if (enqueue_chunk(b.plan, stage, b.cap, 0, v->slots[r.slot].p, b.max_seg * b.seglen, 0, (int)nseg, b.st) !=
-            CDMT_OK)
+        uint8_t *slot = v->slots[r.slot].p;
+        const bool u8 = b.d.out_dtype == CDMT_OUT_U8;
+        float *fb = reinterpret_cast<float *>(u8 ? v->slots[r.scratch].p : slot);
+        if (enqueue_chunk(b.plan, stage, b.cap, 0, fb, b.stride, 0, (int)nseg, b.st) != CDMT_OK)
+            return false;
+        if (u8 && redig_enqueue(b.plan, fb, nseg * b.seglen, b.stride, slot,
+                                reinterpret_cast<float *>(slot + b.codes_bytes), b.st) != CDMT_OK)
             return false;
     }
     const int64_t used = nseg * b.S;
@@ -259,6 +273,10 @@ void scheduler(cdmt_server_s *v)
                 const Beam &b = v->beams[r.beam];
                 v->data_s += (double)b.d.block_len / (b.d.bw_sub_mhz * 1e6);
                 v->units += (double)b.d.ndm * b.d.nsub * r.nseg * b.S;
+                if (r.scratch >= 0) {   // the float32 filterbank of an 8-bit block is no longer needed
+                    v->slots[r.scratch].owner = -1;
+                    r.scratch = -1;
+                }
                 progress = true;
             } else if (q != cudaErrorNotReady) {
                 r.state = 3;
@@ -276,11 +294,23 @@ void scheduler(cdmt_server_s *v)
             }
             if (!best) break;
             Beam &b = v->beams[best->beam];
+            // 8-bit beams: the float32 scratch slot first (the larger one), then the output slot
+            // (taking the second may move the first: erase_slot re-points the request)
+            if (b.d.out_dtype == CDMT_OUT_U8) {
+                const int scratch = take_slot(v, b.fb_bytes);
+                if (scratch < 0) break;
+                best->scratch = scratch;
+                v->slots[scratch].owner = best->id;
+            }
             const int slot = take_slot(v, b.out_bytes);
-            if (slot < 0) break;
-            b.fifo.pop_front();
+            if (slot < 0) {
+                if (best->scratch >= 0) v->slots[best->scratch].owner = -1;
+                best->scratch = -1;
+                break;
+            }
             best->slot = slot;
             v->slots[slot].owner = best->id;
+            b.fifo.pop_front();
             best->t_start = now_s();
             if (dispatch(v, b, *best)) best->state = 1;
             else {
@@ -329,6 +359,7 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     if (!v || !d || !beam_id) return sfail(v, CDMT_EINVAL, "NULL server, descriptor or id");
     if (d->block_len < 1 || d->nsub < 1 || d->ndm < 1) return sfail(v, CDMT_EINVAL, "bad stream descriptor");
     if (d->in_dtype != CDMT_IN_C64 && d->in_dtype != CDMT_IN_I8) return sfail(v, CDMT_ENOTSUP, "input dtype");
+    if (d->out_dtype != CDMT_OUT_F32 && d->out_dtype != CDMT_OUT_U8) return sfail(v, CDMT_ENOTSUP, "output dtype");
     Beam b;
     b.d = *d;
     const int64_t nbin = d->nbin > 0 ? d->nbin : 4096LL * d->nchan;
@@ -358,18 +389,31 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     cdmt_info inf;
     cdmt_plan_info(b.plan, &inf);
     const size_t es = d->in_dtype == CDMT_IN_I8 ? 4 : 16;
-    b.out_bytes = (int64_t)sizeof(float) * d->ndm * b.rows * b.max_seg * b.seglen;
+    const bool u8 = d->out_dtype == CDMT_OUT_U8;
+    b.stride = (b.max_seg * b.seglen + 3) / 4 * 4;   // rows 16-byte aligned
+    b.fb_bytes = (int64_t)sizeof(float) * d->ndm * b.rows * b.stride;
+    b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;
+    b.out_bytes = u8 ? b.codes_bytes + (int64_t)sizeof(float) * 2 * d->ndm * b.rows : b.fb_bytes;
     b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + (int64_t)es * d->nsub * d->block_len +
-              (int64_t)sizeof(float) * d->nsub;
-    // admission: resident state of every beam + the slots held + one slot for this beam's blocks
-    bool have_slot = false;
-    for (const Slot &sl : v->slots) have_slot |= sl.bytes >= b.out_bytes;
-    auto need = [&] { return v->resident + b.bytes + v->slot_total + (have_slot ? 0 : b.out_bytes); };
-    if (need() > v->o.hbm_budget) {
-        drop_free_slots(v);
-        have_slot = false;
-        for (const Slot &sl : v->slots) have_slot |= sl.bytes >= b.out_bytes;
-    }
+              (int64_t)sizeof(float) * d->nsub + (u8 ? (int64_t)sizeof(float) * 2 * d->ndm * b.rows : 0);
+    // admission: resident state of every beam + the slots held + the slots one block of this beam
+    // needs (an output slot; 8-bit beams also a float32 scratch slot) unless the pool has them
+    auto need = [&] {
+        int64_t big = 0, fit = 0;
+        for (const Slot &sl : v->slots) {
+            big += sl.bytes >= b.fb_bytes;
+            fit += sl.bytes >= b.out_bytes;
+        }
+        int64_t extra = 0;
+        if (u8) {
+            if (big < 1) extra += b.fb_bytes;
+            if (fit < 2) extra += b.out_bytes;
+        } else if (fit < 1) {
+            extra += b.out_bytes;
+        }
+        return v->resident + b.bytes + v->slot_total + extra;
+    };
+    if (need() > v->o.hbm_budget) drop_free_slots(v);
     if (need() > v->o.hbm_budget) {
         cdmt_destroy(b.plan);
         return sfail(v, CDMT_EBUDGET, "beam needs %lld resident bytes and a %lld-byte output slot; %lld of the "
@@ -380,6 +424,7 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaMalloc((void **)&b.stage[i], (size_t)d->nsub * b.cap * 16);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_blk, es * (size_t)d->nsub * (size_t)d->block_len);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b.d_scale, sizeof(float) * d->nsub);
+    if (e == cudaSuccess && u8 && redig_reserve(b.plan) != CDMT_OK) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_beam(b);
@@ -436,11 +481,17 @@ int cdmt_server_wait(cdmt_server_t v, int64_t id, double timeout_s, cdmt_block_r
         std::memset(res, 0, sizeof *res);
         res->beam = r.beam;
         res->index = r.index;
-        res->d_out = v->slots[r.slot].p;
+        uint8_t *slot = v->slots[r.slot].p;
+        if (b.d.out_dtype == CDMT_OUT_U8) {
+            res->d_u8 = slot;
+            res->d_stats = reinterpret_cast<float *>(slot + b.codes_bytes);
+        } else {
+            res->d_out = reinterpret_cast<float *>(slot);
+        }
         res->nseg = r.nseg;
         res->first_sample = r.seg0 * b.seglen;
         res->samples = r.nseg * b.seglen;
-        res->row_stride = b.max_seg * b.seglen;
+        res->row_stride = b.stride;
         res->latency_ms = (r.t_done - r.t_submit) * 1e3;
     }
     return CDMT_OK;
@@ -453,6 +504,7 @@ int cdmt_server_release(cdmt_server_t v, int64_t id)
     auto it = v->reqs.find(id);
     if (it == v->reqs.end() || it->second.state < 2) return sfail(v, CDMT_EINVAL, "request %lld is not done", (long long)id);
     if (it->second.slot >= 0) v->slots[it->second.slot].owner = -1;
+    if (it->second.scratch >= 0) v->slots[it->second.scratch].owner = -1;
     cudaEventDestroy(it->second.ev);
     v->reqs.erase(it);
     v->cv_work.notify_all();

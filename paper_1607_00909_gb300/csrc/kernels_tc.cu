@@ -135,19 +135,38 @@ __device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro
     #pragma unroll
     for (int h = 0; h < 2; h++) {
         float acc[WC];
+        uint64_t acc2[WC];
         #pragma unroll
         for (int c = 0; c < 2; c++) {   // 8 columns of each polarisation at a time
             uint32_t bx[8], by[8];
             tc::tmem_ld8_async(taddr + 32 * cg + 16 * h + 8 * c, bx);
             tc::tmem_ld8_async(taddr + P + 32 * cg + 16 * h + 8 * c, by);
             tc::tmem_wait();
+            if constexpr (N == 1) {
+                #pragma unroll
+                for (int i8 = 0; i8 < 8; i8++) {
+                    const float x = __uint_as_float(bx[i8]), y = __uint_as_float(by[i8]);
+                    acc[8 * c + i8] = fmaf(y, y, x * x);
+                }
+            } else {
+                // neighbouring columns (one window, N even) as packed FP32 pairs
+                #pragma unroll
+                for (int i8 = 0; i8 < 8; i8 += 2) {
+                    const int i = 8 * c + i8;
+                    const uint64_t X = tc::f2_pack(__uint_as_float(bx[i8]), __uint_as_float(bx[i8 + 1]));
+                    const uint64_t Y = tc::f2_pack(__uint_as_float(by[i8]), __uint_as_float(by[i8 + 1]));
+                    const int w = N >= 16 ? 0 : i / N;
+                    acc2[w] = (i % N == 0) ? tc::f2_mul(X, X) : tc::f2_fma(X, X, acc2[w]);
+                    acc2[w] = tc::f2_fma(Y, Y, acc2[w]);
+                }
+            }
+        }
+        if constexpr (N > 1) {
             #pragma unroll
-            for (int i8 = 0; i8 < 8; i8++) {
-                const int i = 8 * c + i8;
-                const float x = __uint_as_float(bx[i8]), y = __uint_as_float(by[i8]);
-                const int w = N >= 16 ? 0 : i / N;
-                acc[w] = (i % N == 0) ? x * x : fmaf(x, x, acc[w]);
-                acc[w] = fmaf(y, y, acc[w]);
+            for (int w = 0; w < WC; w++) {
+                float lo, hi;
+                tc::f2_unpack(acc2[w], lo, hi);
+                acc[w] = lo + hi;
             }
         }
         if constexpr (N == 32) {
@@ -282,11 +301,17 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
 
     // ---- the channel's spectrum, scaled by a power of two so that |x| 2^e <= 512
     //      (a 64-point pass then stays below 2^15); the scale is undone on the output
+    //      Staged as bin pairs (j_hi = 2 h, 2 h + 1 at one j_lo), one plane per polarisation:
+    //      xs[pol * M / 2 + 64 h + j_lo] = (re even, re odd, im even, im odd), so that the chirp
+    //      stage multiplies two bins per packed FP32-pair instruction.
     float vmax = 0.f;
-    for (int i = tid; i < kM; i += NT) {
-        float4 v = __ldg(it.src + i);
-        xs[i] = v;
-        vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    for (int i = tid; i < kM / 2; i += NT) {
+        const int jl = i & 63, h2 = i >> 6;
+        const float4 a = __ldg(it.src + 128 * h2 + jl), b = __ldg(it.src + 128 * h2 + 64 + jl);
+        xs[i] = make_float4(a.x, b.x, a.y, b.y);
+        xs[kM / 2 + i] = make_float4(a.z, b.z, a.w, b.w);
+        vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+        vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w))));
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -337,7 +362,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     uint32_t ok = 1;
 
     for (int d = pipe; d < ndt; d += NPIPE) {
-        // ---- chirp, round: pass-A operand, K-major, row = 2 j_lo + pol, k = 2 j_hi + (re, im)
+        // ---- chirp, round: pass-A operand, K-major, row = 2 j_lo + pol, k = 2 j_hi + (re, im);
+        //      two bins per packed FP32-pair multiply
         {
             double dmv = 0.0;
             if constexpr (!UNIFORM) dmv = it.dms[d];
@@ -349,28 +375,47 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             for (int c4 = 0; c4 < JH / 4; c4++) {
                 uint32_t hx[4], hy[4], lx[4], ly[4];
                 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int b = 4 * c4 + i;
-                    const int j = (jbase + b) * 64 + jlo;
-                    float sn, cs;
-                    if constexpr (UNIFORM) {
-                        const int32_t p = (int32_t)(w[2 * b] + (uint32_t)d * w[2 * b + 1]);
-                        __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
-                    } else {
-                        const double kj = __hiloint2double((int)w[2 * b + 1], (int)w[2 * b]);
-                        double cyc = dmv * kj;
-                        cyc -= rint(cyc);
-                        const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << (32 - LM));
-                        __sincosf((float)(int32_t)pf * kTwoPiOver2p32, &sn, &cs);
+                for (int i2 = 0; i2 < 2; i2++) {
+                    // bins j_hi = jbase + b and jbase + b + 1 (jbase and b even) of column j_lo
+                    const int b = 4 * c4 + 2 * i2;
+                    float sn[2], cs[2];
+                    #pragma unroll
+                    for (int e2 = 0; e2 < 2; e2++) {
+                        if constexpr (UNIFORM) {
+                            const int32_t p = (int32_t)(w[2 * (b + e2)] + (uint32_t)d * w[2 * (b + e2) + 1]);
+                            __sincosf((float)p * kTwoPiOver2p32, &sn[e2], &cs[e2]);
+                        } else {
+                            const int j = (jbase + b + e2) * 64 + jlo;
+                            const double kj = __hiloint2double((int)w[2 * (b + e2) + 1], (int)w[2 * (b + e2)]);
+                            double cyc = dmv * kj;
+                            cyc -= rint(cyc);
+                            const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << (32 - LM));
+                            __sincosf((float)(int32_t)pf * kTwoPiOver2p32, &sn[e2], &cs[e2]);
+                        }
                     }
-                    const float4 v = xs[j];
-                    const float xr = v.x * cs - v.y * sn, xi = v.x * sn + v.y * cs;
-                    const float yr = v.z * cs - v.w * sn, yi = v.z * sn + v.w * cs;
-                    hx[i] = pk<AB>(xr, xi);
-                    hy[i] = pk<AB>(yr, yi);
-                    if constexpr (AB) {
-                        lx[i] = tc::pack_bf16(xr - bf16_round(xr), xi - bf16_round(xi));
-                        ly[i] = tc::pack_bf16(yr - bf16_round(yr), yi - bf16_round(yi));
+                    const int pidx = ((jbase + b) >> 1) * 64 + jlo;
+                    const float4 vx = xs[pidx], vy = xs[kM / 2 + pidx];
+                    const uint64_t CS = tc::f2_pack(cs[0], cs[1]), SN = tc::f2_pack(sn[0], sn[1]);
+                    float xr[2], xi[2], yr[2], yi[2];
+                    {
+                        const uint64_t R = tc::f2_pack(vx.x, vx.y), I = tc::f2_pack(vx.z, vx.w);
+                        tc::f2_unpack(tc::f2_sub(tc::f2_mul(R, CS), tc::f2_mul(I, SN)), xr[0], xr[1]);
+                        tc::f2_unpack(tc::f2_fma(R, SN, tc::f2_mul(I, CS)), xi[0], xi[1]);
+                    }
+                    {
+                        const uint64_t R = tc::f2_pack(vy.x, vy.y), I = tc::f2_pack(vy.z, vy.w);
+                        tc::f2_unpack(tc::f2_sub(tc::f2_mul(R, CS), tc::f2_mul(I, SN)), yr[0], yr[1]);
+                        tc::f2_unpack(tc::f2_fma(R, SN, tc::f2_mul(I, CS)), yi[0], yi[1]);
+                    }
+                    #pragma unroll
+                    for (int e2 = 0; e2 < 2; e2++) {
+                        const int i = 2 * i2 + e2;
+                        hx[i] = pk<AB>(xr[e2], xi[e2]);
+                        hy[i] = pk<AB>(yr[e2], yi[e2]);
+                        if constexpr (AB) {
+                            lx[i] = tc::pack_bf16(xr[e2] - bf16_round(xr[e2]), xi[e2] - bf16_round(xi[e2]));
+                            ly[i] = tc::pack_bf16(yr[e2] - bf16_round(yr[e2]), yi[e2] - bf16_round(yi[e2]));
+                        }
                     }
                 }
                 const int kcore = (jbase + 4 * c4) / 4;
@@ -406,7 +451,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             }
             tc::commit(mb);
         }
-        ok = bar_and(bar_id, PT, tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
+        ok = bar_and(bar_id, PT, q >= 32 || tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
         if (!ok) break;
         tc::fence_after();
 
@@ -476,7 +521,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             }
             tc::commit(mb);
         }
-        ok = bar_and(bar_id, PT, tc::mbar_wait(mb, 1, kWaitNs, kWaitPolls));
+        ok = bar_and(bar_id, PT, q >= 32 || tc::mbar_wait(mb, 1, kWaitNs, kWaitPolls));
         if (!ok) break;
         tc::fence_after();
 

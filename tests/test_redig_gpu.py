@@ -128,3 +128,22 @@ def test_host_pipeline_8bit_blocks(cdmt, orc):
         nbad += len(d)
     assert nbad <= max(1, 1e-4 * codes.size)
     plan.close()
+
+
+@pytest.mark.parametrize("nsamp_segments", [3, 18])
+def test_redigitise_short_and_long_rows(cdmt, orc, nsamp_segments):
+    """Rows below 8192 samples take the warp-per-row statistics, longer rows the
+    CTA-per-row form: both against the oracle (3066 samples per row: scalar
+    loads; 18396: float4 loads)."""
+    import torch
+    nsamp = nsamp_segments * (1 << 16) + 777
+    plan = cdmt.Plan(1, nsamp, 140.0, BW, [0.0, 9.0], 16, 4, nbin=1 << 16)
+    ndm, rows, nout = plan.out_shape()
+    assert (nout < 8192) == (nsamp_segments == 3)
+    g = np.random.default_rng(nsamp_segments)
+    fb = g.gamma(4.0, 3.0, (ndm, rows, nout)).astype(np.float32)
+    stats = torch.empty((ndm, rows, 2), dtype=torch.float32, device="cuda")
+    codes = plan.redigitise(torch.from_numpy(fb).cuda(), stats=stats).cpu().numpy()
+    torch.cuda.synchronize()
+    _check(orc, fb, codes, stats.cpu().numpy())
+    plan.close()
