@@ -84,9 +84,19 @@ __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ f
 }
 
 // Rows shorter than kShortRow samples (a served block holds one or two
-// segments per row): one warp per row, eight rows per CTA, with the same
-// statistics as k_redig_stats (FP32 within a lane, FP64 across lanes).
+// segments per row): one warp per row, eight rows per CTA, all in FP32 (the
+// GPU's FP64 rate would make a per-row FP64 epilogue the bottleneck for
+// millions of short rows).  Two passes over the row (the second one hits the
+// cache): the mean, then the mean squared deviation from it, which has no
+// cancellation even when sigma << mu.
 constexpr int64_t kShortRow = 8192;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_stats_rows(const float *__restrict__ fb, int64_t nrow, int64_t nt,
@@ -97,41 +107,33 @@ __global__ void __launch_bounds__(256) k_redig_stats_rows(const float *__restric
     if (row >= nrow) return;
     const int lane = threadIdx.x & 31;
     const float *p = fb + row * stride;
-    float s1 = 0.f, s2 = 0.f;
-    if constexpr (VEC) {
-        const float4 *p4 = reinterpret_cast<const float4 *>(p);
-        #pragma unroll 4
-        for (int64_t t = lane; t < nt / 4; t += 32) {
-            const float4 v = __ldg(p4 + t);
-            s1 += (v.x + v.y) + (v.z + v.w);
-            s2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s2))));
-        }
-        if (lane < nt % 4) {   // the last nt % 4 samples
-            const float v = __ldg(p + 4 * (nt / 4) + lane);
-            s1 += v;
-            s2 = fmaf(v, v, s2);
-        }
-    } else {
-        #pragma unroll 4
-        for (int64_t t = lane; t < nt; t += 32) {
-            const float v = __ldg(p + t);
-            s1 += v;
-            s2 = fmaf(v, v, s2);
-        }
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+    const int64_t n4 = VEC ? nt / 4 : 0;   // float4 part; samples from 4 n4 on are read singly
+    float s1 = 0.f;
+    #pragma unroll 4
+    for (int64_t t = lane; t < n4; t += 32) {
+        const float4 v = __ldg(p4 + t);
+        s1 += (v.x + v.y) + (v.z + v.w);
     }
-    double d1 = s1, d2 = s2;
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    for (int64_t t = 4 * n4 + lane; t < nt; t += 32) s1 += __ldg(p + t);
+    const float mu = warp_sum(s1) / (float)nt;
+    float s2 = 0.f;
+    #pragma unroll 4
+    for (int64_t t = lane; t < n4; t += 32) {
+        const float4 v = __ldg(p4 + t);
+        const float a = v.x - mu, b = v.y - mu, c = v.z - mu, d = v.w - mu;
+        s2 = fmaf(a, a, fmaf(b, b, fmaf(c, c, fmaf(d, d, s2))));
     }
+    for (int64_t t = 4 * n4 + lane; t < nt; t += 32) {
+        const float a = __ldg(p + t) - mu;
+        s2 = fmaf(a, a, s2);
+    }
+    const float sigma = sqrtf(warp_sum(s2) / (float)nt);
     if (lane == 0) {
-        const double mu = d1 / (double)nt;
-        const double sigma = sqrt(fmax(d2 / (double)nt - mu * mu, 0.0));
-        mg[row] = make_float2((float)mu, sigma > 0.0 ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        mg[row] = make_float2(mu, sigma > 0.f ? (float)CDMT_REDIG_LEVELS / sigma : 0.f);
         if (stats) {
-            stats[2 * row] = (float)mu;
-            stats[2 * row + 1] = (float)sigma;
+            stats[2 * row] = mu;
+            stats[2 * row + 1] = sigma;
         }
     }
 }

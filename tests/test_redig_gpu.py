@@ -1,9 +1,10 @@
 """8-bit redigitisation of the filterbank (Sec. 3) against the oracle.
 
 Both sides take each code in FP32 from the row's (mean, gain) rounded to FP32;
-the statistics differ only in their summation order (FP64 in the oracle, FP32
-partial sums per thread on the GPU), so a code may differ by one where the
-unrounded value sits on a rounding boundary.  The tests require identical codes
+the statistics differ only in their arithmetic (FP64 in the oracle; on the GPU
+FP32 partial sums per thread with an FP64 combination for long rows, and FP32
+two-pass mean and deviation for rows under 8192 samples), so a code may differ
+by one where the unrounded value sits on a rounding boundary.  The tests require identical codes
 everywhere else, at most 1e-4 of the samples on boundaries, and mean and sigma
 within 1e-5.
 """
