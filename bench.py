@@ -186,9 +186,9 @@ def kernel_source_hash():
 # dram__bytes_write.sum per launch / units per launch), valid for the kernel
 # source whose hash is recorded; null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent): 546.9 MB read + 2083.0 MB
-    # written for 4.253e9 units (profiles/k_dedisperse_tc_fp16_lofar8.md)
-    "5319ae6d142740c8:fp16": 0.6183,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent): 545.3 MB read + 2074.9 MB
+    # written for 4.253e9 units (ncu --set full, 4th launch)
+    "8958702aa2f81dad:fp16": 0.6161,
 }
 
 try:
