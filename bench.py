@@ -241,7 +241,8 @@ def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
     """Plan one precision form, warm up, time args.steps executes; returns a dict."""
     import torch
     import torch.distributed as dist
-    plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, precision=PREC[prec])
+    plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, precision=PREC[prec],
+                     host_block=args.host_block)
     info = plan.info
     st = stream.cuda_stream
     for _ in range(args.warmup):
@@ -746,6 +747,8 @@ def main():
     ap.add_argument("--u8", action="store_true", help="serve8: blocks redigitised to 8 bits on the device")
     ap.add_argument("--autotune", action="store_true", help="batch4: time candidates per beam")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-block", type=int, default=0,
+                    help="segments per block of the host pipeline (e2e; 0: the plan's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
     ap.add_argument("--forms", default="fp32,fp16",

@@ -86,7 +86,11 @@ typedef struct cdmt_opts {
     int32_t chirp;       /* enum cdmt_chirp: transfer function per channel (default) or per subband */
     int64_t seg_chunk;   /* segments per internal chunk (workspace size); 0 = choose */
     int64_t mem_budget;  /* bytes of device memory the plan may hold; 0 = no limit */
-    int64_t reserved[6];
+    int64_t host_block;  /* segments per block of the host pipeline (cdmt_execute_host*): the unit of its
+                            copies and, for 8-bit output, the block the statistics cover (Sec. 3);
+                            0 = choose (about 4 blocks for float32 output, 16 for 8-bit output, each
+                            at least 16 work items per SM) */
+    int64_t reserved[5];
 } cdmt_opts;
 
 /* Derived sizes of a plan (cdmt_plan_info). */

@@ -29,7 +29,8 @@ CDMT_OUT_F32, CDMT_OUT_U8 = 0, 1
 class cdmt_opts(ctypes.Structure):
     _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("chirp", ctypes.c_int32),
-                ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+                ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("host_block", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 5)]
 
 
 class cdmt_info(ctypes.Structure):
@@ -496,10 +497,10 @@ class Plan:
     """Owning wrapper of a cdmt plan."""
 
     def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
-                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0):
+                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0, host_block=0):
         o = cdmt_opts()
         o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
-        o.precision, o.in_dtype, o.chirp = precision, in_dtype, chirp
+        o.precision, o.in_dtype, o.chirp, o.host_block = precision, in_dtype, chirp, host_block
         self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
         self.info = cdmt_plan_info(self.handle)
 

@@ -196,6 +196,15 @@ __global__ void k_tc_twq(float2 *tw, int mbin)
     reinterpret_cast<float4 *>(tw)[idx] = make_float4((float)c0, (float)c1, (float)s0, (float)s1);
 }
 
+// Frees a buffer from dalloc and gives its bytes back to the plan's count.
+template <class T> void dfree(cdmt_plan_s *p, T *&ptr, size_t count)
+{
+    if (!ptr) return;
+    cudaFree(ptr);
+    p->bytes -= (int64_t)(sizeof(T) * count);
+    ptr = nullptr;
+}
+
 template <class T> int dalloc(cdmt_plan_s *p, T **ptr, size_t count)
 {
     size_t b = sizeof(T) * count;
@@ -415,6 +424,7 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     p->in_dtype = o.in_dtype;
     p->chirp = o.chirp;
     p->mem_budget = o.mem_budget;
+    p->host_block_opt = o.host_block;
 
     // N_bin: explicit, or the largest M in 512..4096 whose overlap wastes <= 1/4
     int64_t nbin = o.nbin;
@@ -628,47 +638,83 @@ int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_s
 
 namespace {
 
-// Staging buffers, events and copy streams of the host pipeline (first host call)
-int host_setup(cdmt_plan_s *p, cudaStream_t st)
+// Segments per block of the host pipeline: the caller's choice, else by output
+// type.  The first block's copy-in and compute are not hidden, and the link to
+// the host moves 2D rows of a float32 block faster the longer they are (16 KB
+// rows ~170 GB/s, 64 KB ~194 GB/s on GB300): float32 output takes about 4
+// blocks, 8-bit output (4x fewer bytes back) about 16.  Every block holds at
+// least 16 work items per SM.
+int64_t host_block(const cdmt_plan_s *p, bool u8)
 {
-    if (p->host_chunk) return CDMT_OK;
+    int64_t kc;
+    if (p->host_block_opt > 0) {
+        kc = p->host_block_opt;
+    } else {
+        const int64_t ntile = (p->ndm + p->dm_tile - 1) / p->dm_tile;
+        const int64_t per_seg = std::max<int64_t>(1, ntile * p->nsub * p->nchan);
+        const int64_t fill = (16 * std::max(1, p->nsm) + per_seg - 1) / per_seg;
+        const int64_t nblk = u8 ? 16 : 4;
+        kc = std::max<int64_t>((p->nseg + nblk - 1) / nblk, fill);
+    }
+    return std::max<int64_t>(1, std::min<int64_t>(kc, std::min<int64_t>(p->seg_chunk, p->nseg)));
+}
+
+// Staging buffers for blocks of up to kc segments (grown when a call needs
+// more), events and copy streams of the host pipeline.
+int host_setup(cdmt_plan_s *p, int64_t kc, cudaStream_t st)
+{
     const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
-    // chunks small enough to pipeline, large enough to fill the GPU
-    const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(p->seg_chunk, (p->nseg + 7) / 8));
-    p->span_max = (kc - 1) * p->nvalid + p->nbin;
+    if (!p->s_h2d) {
+        for (auto &sg : p->stage) {
+            CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.in_ready, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.out_ready, cudaEventDisableTiming));
+            CK(p, cudaEventCreateWithFlags(&sg.out_free, cudaEventDisableTiming));
+        }
+        CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+        CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+    }
+    if (p->host_chunk < kc) {   // (the previous call ended with both copy streams drained)
+        const int64_t old = p->host_chunk;
+        for (auto &sg : p->stage) {
+            dfree(p, sg.in, (size_t)p->nsub * p->span_max);
+            dfree(p, sg.out, (size_t)rows * old * p->seglen);
+            dfree(p, sg.u8, (size_t)rows * old * p->seglen);
+        }
+        p->host_chunk = 0;
+        p->span_max = (kc - 1) * p->nvalid + p->nbin;
+        for (auto &sg : p->stage) {
+            int rc;
+            if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
+            if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
+        }
+        p->host_chunk = kc;
+    }
     for (auto &sg : p->stage) {
-        int rc;
-        if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
-        if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
-        CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
-        CK(p, cudaEventCreateWithFlags(&sg.in_ready, cudaEventDisableTiming));
-        CK(p, cudaEventCreateWithFlags(&sg.out_ready, cudaEventDisableTiming));
-        CK(p, cudaEventCreateWithFlags(&sg.out_free, cudaEventDisableTiming));
         CK(p, cudaEventRecord(sg.in_free, st));
         CK(p, cudaEventRecord(sg.out_free, st));
     }
-    CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
-    CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
-    p->host_chunk = kc;
     return CDMT_OK;
 }
 
-// The host pipeline: per chunk of segments, H2D of its input span (copy stream),
+// The host pipeline: per block of segments, H2D of its input span (copy stream),
 // the forward and DM stages (st), then D2H of its filterbank (copy stream); with
-// u8, the chunk is redigitised as one block and its codes are copied instead.
-int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8, cudaStream_t st)
+// u8, the block is redigitised on the device and its codes are copied instead.
+// Three blocks are in flight.  *kc_used receives the segments per block.
+int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8, int64_t *kc_used, cudaStream_t st)
 {
     int rc;
-    if ((rc = host_setup(p, st)) != CDMT_OK) return rc;
+    const int64_t kcm = host_block(p, h_u8 != nullptr);
+    if ((rc = host_setup(p, kcm, st)) != CDMT_OK) return rc;
     const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
     const int64_t nrow = (int64_t)p->nsub * p->nchan;
-    const int64_t kcm = p->host_chunk;
+    const int64_t cap = p->host_chunk;   // staging capacity in segments (>= kcm)
     if (h_u8)
         for (auto &sg : p->stage)
-            if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)rows * kcm * p->seglen)) != CDMT_OK) return rc;
+            if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)rows * cap * p->seglen)) != CDMT_OK) return rc;
     const auto *src = static_cast<const float4 *>(h_in);
     int b = 0;
-    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, b ^= 1) {
+    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, b = (b + 1) % 3) {
         Staging &sg = p->stage[b];
         const int kc = (int)std::min<int64_t>(kcm, p->nseg - k0);
         const int64_t span = (kc - 1) * p->nvalid + p->nbin;
@@ -694,6 +740,7 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
     }
     CK(p, cudaStreamSynchronize(p->s_d2h));
     CK(p, cudaStreamSynchronize(st));
+    if (kc_used) *kc_used = kcm;
     return CDMT_OK;
 }
 
@@ -707,7 +754,7 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    const int rc = host_pipeline(p, h_in, h_out, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    const int rc = host_pipeline(p, h_in, h_out, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }
@@ -719,8 +766,7 @@ int cdmt_execute_host_u8(cdmt_plan_t p, const void *h_in, uint8_t *h_u8, int64_t
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    const int rc = host_pipeline(p, h_in, nullptr, h_u8, static_cast<cudaStream_t>(cuda_stream));
-    if (rc == CDMT_OK && block_segments) *block_segments = p->host_chunk;
+    const int rc = host_pipeline(p, h_in, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }

@@ -58,8 +58,8 @@ struct cdmt_plan_s {
     size_t inc_off = 0, inc_chg = 0;   // byte offsets of the change offsets and changes in inc_tab
     int64_t bytes = 0;
     // host-execute pipeline
-    int64_t host_chunk = 0, span_max = 0;
-    cdmt::Staging stage[2];
+    int64_t host_chunk = 0, span_max = 0, host_block_opt = 0;
+    cdmt::Staging stage[3];        // host pipeline: three blocks in flight (copy in, compute, copy out)
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     // stage timing (cdmt_set_timing / cdmt_stage_times)
     bool timing = false;

@@ -99,21 +99,22 @@ def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
     plan.close()
 
 
-def test_host_pipeline_8bit_blocks(cdmt, orc):
-    # Algorithm 1 up to "redigitize" and "copy to host": every chunk of segments is a block
-    # with its own statistics; codes must match the oracle applied block by block to the
-    # float filterbank of the same plan
+@pytest.mark.parametrize("host_block", [2, 4])
+def test_host_pipeline_8bit_blocks(cdmt, orc, host_block):
+    # Algorithm 1 up to "redigitize" and "copy to host": every block of host_block segments
+    # (the last one shorter) has its own statistics; codes must match the oracle applied
+    # block by block to the float filterbank of the same plan
     import torch
     nsub, nsamp = 2, 9 * (1 << 14) + 123
     x = synth.noise(42, nsub, nsamp)
-    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, [0.0, 6.0, 12.0], 8, 4, nbin=1 << 14)
+    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, [0.0, 6.0, 12.0], 8, 4, nbin=1 << 14, host_block=host_block)
     ndm, rows, nout = plan.out_shape()
     fb = cdmt.run(plan, torch.from_numpy(x).cuda()).cpu().numpy()
     xh = torch.from_numpy(x).pin_memory()
     u8 = torch.empty((ndm, nout, rows), dtype=torch.uint8).pin_memory()
     kb = plan.execute_host_u8(xh.data_ptr(), u8.data_ptr())
     seglen = nout // plan.info["nseg"]
-    assert 1 <= kb < plan.info["nseg"]           # more than one block
+    assert kb == host_block and plan.info["nseg"] % kb   # several blocks, the last one shorter
     codes = u8.numpy()
     nbad = 0
     for s0 in range(0, plan.info["nseg"], kb):
@@ -147,4 +148,41 @@ def test_redigitise_short_and_long_rows(cdmt, orc, nsamp_segments):
     codes = plan.redigitise(torch.from_numpy(fb).cuda(), stats=stats).cpu().numpy()
     torch.cuda.synchronize()
     _check(orc, fb, codes, stats.cpu().numpy())
+    plan.close()
+
+
+def test_host_pipeline_block_choice_and_staging_growth(cdmt, orc):
+    """With host_block left to the plan, 8-bit output takes shorter blocks than
+    float32 output; the staging grows when a call needs longer blocks, and every
+    call still gives the same result: float32 equal to the device path, codes
+    equal between calls and to the oracle's redigitisation block by block."""
+    import torch
+    nsub, nsamp = 16, 17 * (1 << 14) + 99
+    x = synth.noise(77, nsub, nsamp)
+    dms = [0.0, 1.5, 3.0, 4.5, 6.0, 7.5, 9.0, 10.5, 12.0, 13.5]
+    plan = cdmt.Plan(nsub, nsamp, 140.0, BW, dms, 8, 4, nbin=1 << 14, dm_tile=1)
+    ndm, rows, nout = plan.out_shape()
+    nseg = plan.info["nseg"]
+    seglen = nout // nseg
+    fb = cdmt.run(plan, torch.from_numpy(x).cuda()).cpu().numpy()
+    xh = torch.from_numpy(x).pin_memory()
+    u8a = torch.empty((ndm, nout, rows), dtype=torch.uint8).pin_memory()
+    kb = plan.execute_host_u8(xh.data_ptr(), u8a.data_ptr())
+    # 10 tiles x 16 subbands x 8 channels = 1280 items per segment: two segments fill 152 SMs x 16
+    assert kb == max(2, -(-nseg // 16))
+    hout = torch.full((ndm, rows, nout), float("nan"), dtype=torch.float32).pin_memory()
+    plan.execute_host(xh.data_ptr(), hout.data_ptr(), 0, 0)   # float32: longer blocks, staging grows
+    assert np.array_equal(hout.numpy(), fb)
+    u8b = torch.empty_like(u8a)
+    assert plan.execute_host_u8(xh.data_ptr(), u8b.data_ptr()) == kb
+    assert np.array_equal(u8a.numpy(), u8b.numpy())
+    codes = u8a.numpy()
+    nbad = 0
+    for s0 in range(0, nseg, kb):
+        t0, t1 = s0 * seglen, min(nseg, s0 + kb) * seglen
+        oc, _ = orc.redigitise(np.ascontiguousarray(fb[:, :, t0:t1]))
+        diff = np.abs(codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32))
+        assert diff.max() <= 1
+        nbad += int(np.count_nonzero(diff))
+    assert nbad <= max(1, 1e-4 * codes.size)
     plan.close()
