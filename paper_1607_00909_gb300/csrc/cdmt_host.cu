@@ -268,8 +268,8 @@ namespace cdmt {
 // Forward stage and DM stage of kc segments of `in` (segment kk at
 // in + (in_k0 + kk) * S, subbands in_stride samples apart) into `out`
 // (rows out_stride floats apart, segment kk at (out_k0 + kk) * seglen).
-int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
-                  int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st)
+// The forward stage of kc segments (segment in_k0 of `in` first) into the plan's spectra.
+int enqueue_forward(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st)
 {
     ForwardArgs fa{};
     fa.in = in;
@@ -285,10 +285,16 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
     fa.kc = kc;
     fa.nsub = p->nsub;
     fa.r = p->r;
-    int rc;
-    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
     CK(p, fp32_forward(fa, st));
-    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    return CDMT_OK;
+}
+
+// The DM stage of the kc segments in the plan's spectra, for DMs dm_off .. dm_off + dm_cnt - 1
+// of every DM tile (dm_cnt 0: all), into out (row stride out_stride floats; segment kk at
+// (out_k0 + kk) * seglen; DM j of tile t's range at row block t * dm_cnt + j).
+int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, int kc, int dm_off, int dm_cnt,
+               cudaStream_t st)
+{
     if (p->precision != CDMT_PREC_FP32) {
         TcArgs ta{};
         ta.spec = p->spec;
@@ -314,8 +320,9 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
         ta.uniform = p->uniform;
         ta.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
         ta.nsm = p->nsm;
+        ta.dm_off = dm_off;
+        ta.dm_cnt = dm_cnt;
         CK(p, tc_dedisperse(ta, st));
-        if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
         return CDMT_OK;
     }
     DedispArgs da{};
@@ -338,7 +345,20 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
     da.r = p->r;
     da.uniform = p->uniform;
     da.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
+    da.dm_off = dm_off;
+    da.dm_cnt = dm_cnt;
     CK(p, fp32_dedisperse(da, st));
+    return CDMT_OK;
+}
+
+int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
+                  int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st)
+{
+    int rc;
+    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    if ((rc = enqueue_forward(p, in, in_stride, in_k0, kc, st)) != CDMT_OK) return rc;
+    if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
+    if ((rc = enqueue_dm(p, out, out_stride, out_k0, kc, 0, 0, st)) != CDMT_OK) return rc;
     if (p->timing && (rc = mark(p, st)) != CDMT_OK) return rc;
     return CDMT_OK;
 }
@@ -659,11 +679,10 @@ int64_t host_block(const cdmt_plan_s *p, bool u8)
     return std::max<int64_t>(1, std::min<int64_t>(kc, std::min<int64_t>(p->seg_chunk, p->nseg)));
 }
 
-// Staging buffers for blocks of up to kc segments (grown when a call needs
-// more), events and copy streams of the host pipeline.
-int host_setup(cdmt_plan_s *p, int64_t kc, cudaStream_t st)
+// Staging buffers (grown when a call needs more: input spans of kc segments,
+// out_floats per output slot), events and copy streams of the host pipeline.
+int host_setup(cdmt_plan_s *p, int64_t kc, int64_t out_floats, cudaStream_t st)
 {
-    const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
     if (!p->s_h2d) {
         for (auto &sg : p->stage) {
             CK(p, cudaEventCreateWithFlags(&sg.in_free, cudaEventDisableTiming));
@@ -674,21 +693,28 @@ int host_setup(cdmt_plan_s *p, int64_t kc, cudaStream_t st)
         CK(p, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
         CK(p, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
     }
-    if (p->host_chunk < kc) {   // (the previous call ended with both copy streams drained)
-        const int64_t old = p->host_chunk;
-        for (auto &sg : p->stage) {
-            dfree(p, sg.in, (size_t)p->nsub * p->span_max);
-            dfree(p, sg.out, (size_t)rows * old * p->seglen);
-            dfree(p, sg.u8, (size_t)rows * old * p->seglen);
-        }
+    // (the previous call ended with both copy streams drained, so the buffers are idle)
+    if (p->host_chunk < kc) {
+        for (auto &sg : p->stage) dfree(p, sg.in, (size_t)p->nsub * p->span_max);
         p->host_chunk = 0;
         p->span_max = (kc - 1) * p->nvalid + p->nbin;
         for (auto &sg : p->stage) {
-            int rc;
-            if ((rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max)) != CDMT_OK) return rc;
-            if ((rc = dalloc(p, &sg.out, (size_t)rows * kc * p->seglen)) != CDMT_OK) return rc;
+            const int rc = dalloc(p, &sg.in, (size_t)p->nsub * p->span_max);
+            if (rc != CDMT_OK) return rc;
         }
         p->host_chunk = kc;
+    }
+    if (p->host_out_cap < out_floats) {
+        for (auto &sg : p->stage) {
+            dfree(p, sg.out, (size_t)p->host_out_cap);
+            dfree(p, sg.u8, (size_t)p->host_out_cap);
+        }
+        p->host_out_cap = 0;
+        for (auto &sg : p->stage) {
+            const int rc = dalloc(p, &sg.out, (size_t)out_floats);
+            if (rc != CDMT_OK) return rc;
+        }
+        p->host_out_cap = out_floats;
     }
     for (auto &sg : p->stage) {
         CK(p, cudaEventRecord(sg.in_free, st));
@@ -700,43 +726,57 @@ int host_setup(cdmt_plan_s *p, int64_t kc, cudaStream_t st)
 // The host pipeline: per block of segments, H2D of its input span (copy stream),
 // the forward and DM stages (st), then D2H of its filterbank (copy stream); with
 // u8, the block is redigitised on the device and its codes are copied instead.
-// Three blocks are in flight.  *kc_used receives the segments per block.
+// Three input spans and three output slots are in flight.  For float32 output of
+// a plan with one DM tile, each block's DM stage runs in up to 4 DM ranges with
+// an output slot each, so the copy back of a block starts after a quarter of its
+// compute (the first one is the pipeline's fill) while its rows stay long.
+// *kc_used receives the segments per block.
 int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8, int64_t *kc_used, cudaStream_t st)
 {
     int rc;
-    const int64_t kcm = host_block(p, h_u8 != nullptr);
-    if ((rc = host_setup(p, kcm, st)) != CDMT_OK) return rc;
-    const int64_t rows = (int64_t)p->ndm * p->nsub * p->nchan;
+    const bool u8 = h_u8 != nullptr;
+    const int64_t kcm = host_block(p, u8);
     const int64_t nrow = (int64_t)p->nsub * p->nchan;
-    const int64_t cap = p->host_chunk;   // staging capacity in segments (>= kcm)
-    if (h_u8)
+    const int64_t ntile = (p->ndm + p->dm_tile - 1) / p->dm_tile;
+    const int nq = (!u8 && ntile == 1) ? (int)std::max<int64_t>(1, std::min<int64_t>(4, p->ndm / 32)) : 1;
+    const int qdm = (p->ndm + nq - 1) / nq;   // DMs per range
+    if ((rc = host_setup(p, kcm, (int64_t)qdm * nrow * kcm * p->seglen, st)) != CDMT_OK) return rc;
+    if (u8)
         for (auto &sg : p->stage)
-            if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)rows * cap * p->seglen)) != CDMT_OK) return rc;
+            if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)p->host_out_cap)) != CDMT_OK) return rc;
     const auto *src = static_cast<const float4 *>(h_in);
-    int b = 0;
-    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, b = (b + 1) % 3) {
-        Staging &sg = p->stage[b];
+    const int64_t ostride = kcm * p->seglen;   // floats per row of an output slot
+    int bi = 0, bo = 0;
+    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, bi = (bi + 1) % 3) {
+        Staging &si = p->stage[bi];
         const int kc = (int)std::min<int64_t>(kcm, p->nseg - k0);
         const int64_t span = (kc - 1) * p->nvalid + p->nbin;
-        CK(p, cudaStreamWaitEvent(p->s_h2d, sg.in_free, 0));
-        CK(p, cudaMemcpy2DAsync(sg.in, p->span_max * 16, src + k0 * p->nvalid, p->nsamp * 16, span * 16, p->nsub,
+        CK(p, cudaStreamWaitEvent(p->s_h2d, si.in_free, 0));
+        CK(p, cudaMemcpy2DAsync(si.in, p->span_max * 16, src + k0 * p->nvalid, p->nsamp * 16, span * 16, p->nsub,
                                 cudaMemcpyHostToDevice, p->s_h2d));
-        CK(p, cudaEventRecord(sg.in_ready, p->s_h2d));
-        CK(p, cudaStreamWaitEvent(st, sg.in_ready, 0));
-        CK(p, cudaStreamWaitEvent(st, sg.out_free, 0));
-        if ((rc = enqueue_chunk(p, sg.in, p->span_max, 0, sg.out, kcm * p->seglen, 0, kc, st)) != CDMT_OK) return rc;
-        CK(p, cudaEventRecord(sg.in_free, st));
-        if (h_u8 && (rc = redig_enqueue(p, sg.out, kc * p->seglen, kcm * p->seglen, sg.u8, nullptr, st)) != CDMT_OK)
-            return rc;
-        CK(p, cudaEventRecord(sg.out_ready, st));
-        CK(p, cudaStreamWaitEvent(p->s_d2h, sg.out_ready, 0));
-        if (h_u8)   // [ndm][kc * seglen][nrow] -> rows of [ndm][nout][nrow] from sample k0 * seglen
-            CK(p, cudaMemcpy2DAsync(h_u8 + k0 * p->seglen * nrow, p->nout * nrow, sg.u8, kc * p->seglen * nrow,
-                                    kc * p->seglen * nrow, p->ndm, cudaMemcpyDeviceToHost, p->s_d2h));
-        else
-            CK(p, cudaMemcpy2DAsync(h_out + k0 * p->seglen, p->nout * 4, sg.out, kcm * p->seglen * 4,
-                                    kc * p->seglen * 4, rows, cudaMemcpyDeviceToHost, p->s_d2h));
-        CK(p, cudaEventRecord(sg.out_free, p->s_d2h));
+        CK(p, cudaEventRecord(si.in_ready, p->s_h2d));
+        CK(p, cudaStreamWaitEvent(st, si.in_ready, 0));
+        if ((rc = enqueue_forward(p, si.in, p->span_max, 0, kc, st)) != CDMT_OK) return rc;
+        CK(p, cudaEventRecord(si.in_free, st));
+        for (int q = 0; q < nq; q++, bo = (bo + 1) % 3) {
+            Staging &so = p->stage[bo];
+            const int dm_lo = q * qdm, cnt = std::min(qdm, p->ndm - dm_lo);
+            CK(p, cudaStreamWaitEvent(st, so.out_free, 0));
+            if ((rc = enqueue_dm(p, so.out, ostride, 0, kc, nq > 1 ? dm_lo : 0, nq > 1 ? cnt : 0, st)) != CDMT_OK)
+                return rc;
+            if (u8 && (rc = redig_enqueue(p, so.out, kc * p->seglen, ostride, so.u8, nullptr, st)) != CDMT_OK)
+                return rc;
+            CK(p, cudaEventRecord(so.out_ready, st));
+            CK(p, cudaStreamWaitEvent(p->s_d2h, so.out_ready, 0));
+            if (u8)   // [ndm][kc * seglen][nrow] -> rows of [ndm][nout][nrow] from sample k0 * seglen
+                CK(p, cudaMemcpy2DAsync(h_u8 + k0 * p->seglen * nrow, p->nout * nrow, so.u8, kc * p->seglen * nrow,
+                                        kc * p->seglen * nrow, p->ndm, cudaMemcpyDeviceToHost, p->s_d2h));
+            else   // DMs dm_lo .. dm_lo + cnt - 1: cnt * nrow rows of the host filterbank
+                CK(p, cudaMemcpy2DAsync(h_out + (int64_t)dm_lo * nrow * p->nout + k0 * p->seglen, p->nout * 4,
+                                        so.out, ostride * 4, kc * p->seglen * 4, (int64_t)cnt * nrow,
+                                        cudaMemcpyDeviceToHost, p->s_d2h));
+            CK(p, cudaEventRecord(so.out_free, p->s_d2h));
+        }
     }
     CK(p, cudaStreamSynchronize(p->s_d2h));
     CK(p, cudaStreamSynchronize(st));

@@ -33,6 +33,9 @@ struct DedispArgs {
     float scale;
     const int *round_dev = nullptr;  // batches: skip segments round * kc + kk >= nseg
     int64_t nseg = 0;
+    // DM range: DMs dm_off .. dm_off + dm_cnt - 1 of every tile (dm_cnt 0: the whole tile); output
+    // row of DM j of tile t's range: t * dm_cnt + j
+    int dm_off = 0, dm_cnt = 0;
 };
 
 struct TcArgs {
@@ -52,6 +55,7 @@ struct TcArgs {
     int ab;               // 0 FP16, 1 BF16 hi/lo
     bool uniform;
     float scale;
+    int dm_off = 0, dm_cnt = 0;   // DM range within every tile, as in DedispArgs
 };
 
 // one beam of a batch, as the persistent tensor-core kernel sees it

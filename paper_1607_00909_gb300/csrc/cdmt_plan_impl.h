@@ -15,7 +15,7 @@ namespace cdmt {
 
 struct Staging {
     float4 *in = nullptr;   // [nsub][span_max] samples
-    float *out = nullptr;   // [ndm][nsub*nchan][kc_max*seglen]
+    float *out = nullptr;   // [DMs of a range][nsub*nchan][kc_max*seglen]
     uint8_t *u8 = nullptr;  // [ndm][kc_max*seglen][nsub*nchan] codes (8-bit host output)
     cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free = nullptr;
 };
@@ -59,6 +59,7 @@ struct cdmt_plan_s {
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0, host_block_opt = 0;
+    int64_t host_out_cap = 0;      // floats per output slot of the host pipeline (u8 slots: bytes)
     cdmt::Staging stage[3];        // host pipeline: three blocks in flight (copy in, compute, copy out)
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     // stage timing (cdmt_set_timing / cdmt_stage_times)

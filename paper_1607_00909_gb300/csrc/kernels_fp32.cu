@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
 k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
              const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
              float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
-             int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg)
+             int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg, int dm_off,
+             int dm_cnt)
 {
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T, NT = 2 * T;
@@ -156,8 +157,9 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
     const int kk = (int)(item % kc); item /= kc;
     const int s = (int)(item % nsub); item /= nsub;
     const int tile = (int)item;
-    const int dm0 = tile * dm_tile;
-    const int ndt = min(dm_tile, ndm - dm0);
+    const int dm0 = tile * dm_tile + dm_off;          // first DM of this tile's range
+    const int ndt = min(dm_cnt, ndm - dm0);
+    if (ndt <= 0) return;
     // batches: this chunk's segments start at round * kc; none past the end of the input
     if (round_dev && (int64_t)(*round_dev) * kc + kk >= nseg) return;
 
@@ -199,7 +201,7 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
             float sn, cs;
             if constexpr (UNIFORM) {
                 uint2 ab = ph[j];
-                int32_t p = (int32_t)(ab.x + (uint32_t)d * ab.y);
+                int32_t p = (int32_t)(ab.x + (uint32_t)(dm_off + d) * ab.y);
                 __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
             } else {
                 double kj = __hiloint2double((int)ph[j].y, (int)ph[j].x);
@@ -215,7 +217,7 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
         __syncthreads();
         F::template pass_c1<+1>(exp_, t, [&](int m, float2 a) { ibp[m] = fmaf(a.x, a.x, a.y * a.y); });
         __syncthreads();
-        float *orow = out + (int64_t)(dm0 + d) * rows * nout + obase;
+        float *orow = out + ((int64_t)tile * dm_cnt + d) * rows * nout + obase;
         for (int u = tid; u < seglen; u += NT) {
             const float *px = ib + half + u * nint;
             const float *py = px + M;
@@ -317,7 +319,7 @@ template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStre
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
     k_dedisperse<R, U><<<(unsigned)nblk, 2 * Fft3<R>::T, smem_dedisp<R>(), st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
-        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg);
+        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile);
 }
 
 cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)

@@ -200,8 +200,9 @@ __device__ __forceinline__ void tc_detect(uint32_t taddr, int cg, int m1, int ro
 struct TcItem {
     const float4 *src;     // M bins, (X re, X im, Y re, Y im)
     const uint2 *ph;       // per-bin words: uniform DM list (a, b) of this tile, otherwise K as double
-    const double *dms;     // DM values from the tile's first DM (uneven lists)
-    int ndt;               // DMs in the tile
+    const double *dms;     // DM values from the item's first DM (uneven lists)
+    int ndt;               // DMs of the item
+    int dbase;             // index of the item's first DM within its tile (the phase step count)
     float *out;            // output of the tile's first DM at this channel row and segment offset
     int64_t dm_stride;     // floats between the rows of consecutive DMs
     int nd, nint;
@@ -382,7 +383,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                     #pragma unroll
                     for (int e2 = 0; e2 < 2; e2++) {
                         if constexpr (UNIFORM) {
-                            const int32_t p = (int32_t)(w[2 * (b + e2)] + (uint32_t)d * w[2 * (b + e2) + 1]);
+                            const int32_t p = (int32_t)(w[2 * (b + e2)] + (uint32_t)(d + it.dbase) * w[2 * (b + e2) + 1]);
                             __sincosf((float)p * kTwoPiOver2p32, &sn[e2], &cs[e2]);
                         } else {
                             const int j = (jbase + b + e2) * 64 + jlo;
@@ -562,7 +563,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const uint4 *__restrict__ bmat64,
                 const float2 *__restrict__ twq, float *__restrict__ out, int *__restrict__ status, int nsub, int kc,
                 int64_t k0, int nchan, int ndm, int dm_tile, int nd, int nint, int64_t nout, float scale_out,
-                int64_t nitems)
+                int64_t nitems, int dm_off, int dm_cnt)
 {
     constexpr int kM = 1 << LM;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -577,14 +578,15 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         const int kk = (int)(item % kc); item /= kc;
         const int s = (int)(item % nsub); item /= nsub;
         const int tile = (int)item;
-        const int dm0 = tile * dm_tile;
+        const int dm0 = tile * dm_tile + dm_off;   // the item's DMs: dm_off .. dm_off + dm_cnt - 1 of the tile
         TcItem it;
         it.src = spec + (((int64_t)s * kc + kk) * nchan + c) * kM;
         if constexpr (UNIFORM) it.ph = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * kM + (int64_t)c * kM;
         else it.ph = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * kM);
         it.dms = dm_list + dm0;
-        it.ndt = min(dm_tile, ndm - dm0);
-        it.out = out + (int64_t)dm0 * rows * nout + (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
+        it.ndt = min(dm_cnt, ndm - dm0);
+        it.dbase = dm_off;
+        it.out = out + (int64_t)tile * dm_cnt * rows * nout + (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
         it.dm_stride = rows * nout;
         it.nd = nd;
         it.nint = nint;
@@ -653,6 +655,7 @@ k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__
         it.ph = B.nco + ((int64_t)tile * B.nsub + s) * (int64_t)B.nchan * kM + (int64_t)c * kM;
         it.dms = nullptr;
         it.ndt = min(B.dm_tile, B.ndm - dm0);
+        it.dbase = 0;
         const int seglen = (kM - B.nd) / B.nint;
         const int64_t rows = (int64_t)B.nsub * B.nchan;
         it.out = B.out + (int64_t)dm0 * rows * B.out_stride + (int64_t)(s * B.nchan + c) * B.out_stride + kk * seglen;
@@ -715,7 +718,7 @@ template <bool U, int AB, int LM> static void launch(const TcArgs &a, cudaStream
     const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
     k_dedisperse_tc<U, AB, LM><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.bmat64, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan,
-        a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems);
+        a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile);
 }
 
 template <int LM> static void launch_lm(const TcArgs &a, cudaStream_t st)

@@ -120,6 +120,30 @@ def test_execute_host_matches_execute(cdmt):
     assert np.array_equal(hout2, dev)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("uniform", [True, False])
+def test_execute_host_dm_ranges(cdmt, prec, uniform):
+    """float32 host output of a plan with one DM tile runs each block's DM stage in
+    DM ranges (here 2 of 35 DMs, 3 blocks of 3 segments): bit-identical to the
+    device path, for evenly spaced (phase steps from the range's offset) and
+    uneven DM lists."""
+    import torch
+    nsub, nsamp = 2, 9 * (1 << 14) + 5
+    x = synth.noise(91, nsub, nsamp)
+    dms = [0.25 * i for i in range(70)]
+    if not uniform:
+        dms = sorted(np.random.default_rng(5).uniform(0.0, 17.0, 70).tolist())
+    precision = cdmt.CDMT_PREC_FP16 if prec == "fp16" else cdmt.CDMT_PREC_FP32
+    plan = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, dm_tile=70, precision=precision, host_block=3)
+    assert plan.info["nseg"] == 9
+    dev = gpu_filterbank(plan, x)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.full(plan.out_shape(), float("nan"), dtype=torch.float32).pin_memory()
+    plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, 0)
+    assert np.array_equal(hout.numpy(), dev)
+    plan.close()
+
+
 def test_repeatable_and_stream_ordered(cdmt):
     import torch
     w = synth.tiny()
