@@ -90,6 +90,14 @@ def _load():
                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.restype = None
+            lib.orc_sk_sigma.argtypes = [i64, ctypes.c_int]
+            lib.orc_sk_sigma.restype = ctypes.c_double
+            lib.orc_spectral_kurtosis.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_spectral_kurtosis.restype = None
+            lib.orc_redigitise_sk.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_redigitise_sk.restype = None
             lib.orc_max_threads.argtypes = []
             _lib = lib
     return _lib
@@ -210,6 +218,37 @@ def redigitise(fb) -> tuple[np.ndarray, np.ndarray]:
 
 
 LEVELS = 16.0
+
+
+def sk_sigma(n: int, k: int) -> float:
+    """Large-n standard deviation of the spectral-kurtosis estimator for n samples
+    that are each a sum of k squared magnitudes."""
+    return _load().orc_sk_sigma(n, k)
+
+
+def spectral_kurtosis(fb, k: int, nsigma: float = 3.0) -> tuple[np.ndarray, np.ndarray]:
+    """Generalised spectral kurtosis of every row of fb [ndm][rows][nt] whose
+    samples each sum k squared magnitudes (k = 2 nint), and the RFI flags
+    |SK - 1| > nsigma * sk_sigma(nt, k) (Sec. 6): (sk float64 [ndm][rows],
+    flags uint8 [ndm][rows])."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    sk = np.empty((ndm, rows), dtype=np.float64)
+    fl = np.empty((ndm, rows), dtype=np.uint8)
+    _load().orc_spectral_kurtosis(_fp(fb), ndm, rows, nt, k, nsigma, sk.ctypes.data, fl.ctypes.data)
+    return sk, fl
+
+
+def redigitise_sk(fb, k: int, nsigma: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """redigitise() with spectral-kurtosis flagging: flagged rows are coded 128.
+    Returns (codes, stats, flags)."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    out = np.empty((ndm, nt, rows), dtype=np.uint8)
+    st = np.empty((ndm, rows, 2), dtype=np.float64)
+    fl = np.empty((ndm, rows), dtype=np.uint8)
+    _load().orc_redigitise_sk(_fp(fb), ndm, rows, nt, k, nsigma, out.ctypes.data, st.ctypes.data, fl.ctypes.data)
+    return out, st, fl
 
 
 def incoherent(fb, nsub, nchan, f_centre, bw, nint, dm_c, ddm_lo, ddm_step, nk, chirp: int = 0):

@@ -32,6 +32,9 @@
  *      "redigitize").
  *   8. (orc_incoherent) incoherent dedispersion of the coherent filterbanks
  *      over fine DM trials (Sec. 4, semi-coherent search).
+ *   9. (orc_spectral_kurtosis, orc_redigitise_sk) spectral-kurtosis flags of
+ *      the rows of a block and redigitisation with flagged rows set to 128
+ *      (Sec. 6, future work; generalised SK estimator).
  *
  * Readings where the paper is silent: D = 4.148808e3 MHz^2 pc^-1 cm^3 s
  * (the paper quotes 1/2.41e-4); transforms unitary; channel index increases
@@ -406,6 +409,66 @@ void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out
             }
         }
     }
+}
+
+/*
+ * Spectral-kurtosis RFI flags.  Sec. 6 names spectral kurtosis for RFI
+ * excision in the statistics step as future work and gives no definition;
+ * this takes the generalised spectral-kurtosis estimator.  For one (DM,
+ * channel) row of a block of n filterbank samples I_t, each the sum of k
+ * squared magnitudes (k = 2 nint: two polarisations, nint time samples),
+ *   SK = (n k + 1) / (n - 1) * (n S2 / S1^2 - 1),   S1 = sum I, S2 = sum I^2.
+ * For Gaussian voltages I ~ Gamma(k) and SK is 1 on average, with standard
+ * deviation sqrt(2 (k + 1) / (k n)) for large n (delta method on the sample
+ * variance over the squared sample mean).  A row is flagged when
+ * |SK - 1| > nsigma times that deviation.  Rows without power (S1 = 0) have
+ * SK = 0; rows of fewer than two samples are never flagged (SK = 1).
+ */
+double orc_sk_sigma(int64_t n, int k)
+{
+    return sqrt(2.0 * (double)(k + 1) / ((double)k * (double)n));
+}
+
+void orc_spectral_kurtosis(const float *fb, int ndm, int rows, int64_t nt, int k, double nsigma, double *sk,
+                           uint8_t *flags)
+{
+    const double thr = nt > 1 ? nsigma * orc_sk_sigma(nt, k) : 0.0;
+    for (int d = 0; d < ndm; d++) {
+        for (int r = 0; r < rows; r++) {
+            const float *row = fb + ((size_t)d * rows + r) * (size_t)nt;
+            double s1 = 0.0, s2 = 0.0;
+            for (int64_t t = 0; t < nt; t++) {
+                s1 += (double)row[t];
+                s2 += (double)row[t] * (double)row[t];
+            }
+            double v = 1.0;
+            if (nt > 1) {
+                const double n = (double)nt;
+                v = s1 > 0.0 ? (n * k + 1.0) / (n - 1.0) * (n * s2 / (s1 * s1) - 1.0) : 0.0;
+            }
+            const size_t i = (size_t)d * rows + r;
+            if (sk) sk[i] = v;
+            if (flags) flags[i] = (uint8_t)(nt > 1 && fabs(v - 1.0) > thr);
+        }
+    }
+}
+
+/* orc_redigitise with spectral-kurtosis flagging: flagged rows get gain 0,
+ * i.e. every code 128 (the row's mean). */
+void orc_redigitise_sk(const float *fb, int ndm, int rows, int64_t nt, int k, double nsigma, uint8_t *out,
+                       double *stats, uint8_t *flags)
+{
+    orc_redigitise(fb, ndm, rows, nt, out, stats);
+    uint8_t *fl = (uint8_t *)malloc((size_t)ndm * rows);
+    orc_spectral_kurtosis(fb, ndm, rows, nt, k, nsigma, NULL, fl);
+    for (int d = 0; d < ndm; d++)
+        for (int r = 0; r < rows; r++) {
+            const size_t i = (size_t)d * rows + r;
+            if (flags) flags[i] = fl[i];
+            if (!fl[i]) continue;
+            for (int64_t t = 0; t < nt; t++) out[((size_t)d * (size_t)nt + (size_t)t) * rows + (size_t)(rows - 1 - r)] = 128;
+        }
+    free(fl);
 }
 
 /*

@@ -52,6 +52,11 @@ MUTANTS = [
     ("redig_truncate", "float x = rintf(", "float x = truncf(", None),
     ("redig_increasing_order", "(size_t)(rows - 1 - r)] = (uint8_t)x;", "(size_t)r] = (uint8_t)x;", None),
     ("redig_no_clip_high", "if (x > 255.0f) x = 255.0f;", "if (x > 255.0f) x = x - 256.0f;", None),
+    ("sk_shape_factor_dropped", "(n * k + 1.0) / (n - 1.0)", "(n + 1.0) / (n - 1.0)", None),
+    ("sk_sigma_without_k_plus_1", "sqrt(2.0 * (double)(k + 1) / ((double)k * (double)n))",
+     "sqrt(2.0 / ((double)k * (double)n))", None),
+    ("sk_mean_not_squared", "(n * s2 / (s1 * s1) - 1.0)", "(s2 / s1 - 1.0)", None),
+    ("sk_one_sided", "fabs(v - 1.0) > thr", "v - 1.0 > thr", None),
 ]
 
 PIN_CALLS = [
@@ -82,6 +87,11 @@ PIN_CALLS = [
     lambda o: pins.test_redigitise_gaussian_row_statistics(o),
     lambda o: pins.test_redigitise_order_and_independence(o),
     lambda o: pins.test_redigitise_scale_invariance(o),
+    lambda o: pins.test_sk_gamma_noise_mean_and_spread(o, 1),
+    lambda o: pins.test_sk_gamma_noise_mean_and_spread(o, 16),
+    lambda o: pins.test_sk_equals_brute_force_moments(o),
+    lambda o: pins.test_sk_flags_impulsive_and_steady_rows(o),
+    lambda o: pins.test_redigitise_sk_zaps_flagged_rows_only(o),
 ]
 
 

@@ -504,3 +504,70 @@ def test_incoherent_is_linear_and_shift_covariant(orc):
     assert np.allclose(oab, oa + 2.0 * ob, rtol=1e-6)
     sh, _ = orc.incoherent(np.roll(a, 5, axis=2), *args)
     assert np.allclose(sh[..., 5:], oa[..., :-5], rtol=1e-12)
+
+
+# ---- spectral kurtosis (Sec. 6, future work: generalised SK estimator)
+
+@pytest.mark.parametrize("k", [1, 16])
+def test_sk_gamma_noise_mean_and_spread(orc, k):
+    # rows of Gamma(k) samples (each a sum of k exponential powers): SK averages 1 and spreads
+    # by sqrt(2 (k + 1) / (k n)); k = 1 is the classic estimator, whose variance is 4 / n
+    g = np.random.default_rng(21 + k)
+    n, nrow = 800, 3000
+    fb = g.gamma(float(k), 2.5, (1, nrow, n)).astype(np.float32)
+    sk, fl = orc.spectral_kurtosis(fb, k, 3.0)
+    s = orc.sk_sigma(n, k)
+    assert abs(s - np.sqrt(2.0 * (k + 1) / (k * n))) < 1e-15
+    if k == 1:
+        assert abs(s * s - 4.0 / n) < 1e-15
+    assert abs(sk.mean() - 1.0) < 4.0 * s / np.sqrt(nrow)
+    assert abs(sk.std() / s - 1.0) < 0.08
+    assert fl.mean() < 0.01          # a 3-sigma test flags a few rows in a thousand
+
+
+def test_sk_equals_brute_force_moments(orc):
+    # SK from the definition with numpy sums in FP64, on a ragged row length
+    g = np.random.default_rng(31)
+    fb = g.gamma(8.0, 1.0, (2, 3, 37)).astype(np.float32)
+    sk, _ = orc.spectral_kurtosis(fb, 8, 3.0)
+    x = fb.astype(np.float64)
+    n = x.shape[2]
+    s1, s2 = x.sum(axis=2), (x * x).sum(axis=2)
+    want = (n * 8 + 1.0) / (n - 1.0) * (n * s2 / (s1 * s1) - 1.0)
+    assert np.allclose(sk, want, rtol=1e-12, atol=0)
+
+
+def test_sk_flags_impulsive_and_steady_rows(orc):
+    g = np.random.default_rng(41)
+    k, n = 16, 2000
+    fb = g.gamma(float(k), 1.0, (1, 4, n)).astype(np.float32)
+    fb[0, 1, ::20] *= 30.0                       # impulsive RFI in 5 % of the samples: SK >> 1
+    fb[0, 2] = 100.0 + 0.01 * g.standard_normal(n).astype(np.float32)   # a steady carrier: SK << 1
+    fb[0, 3] = 0.0                               # a dead channel: SK = 0
+    sk, fl = orc.spectral_kurtosis(fb, k, 3.0)
+    assert fl[0, 0] == 0 and abs(sk[0, 0] - 1.0) < 3.0 * orc.sk_sigma(n, k)
+    assert fl[0, 1] == 1 and sk[0, 1] > 5.0
+    assert fl[0, 2] == 1 and sk[0, 2] < 0.01
+    assert fl[0, 3] == 1 and sk[0, 3] == 0.0
+    # single-sample rows are never flagged
+    _, f1 = orc.spectral_kurtosis(fb[:, :, :1], k, 3.0)
+    assert not f1.any()
+
+
+def test_redigitise_sk_zaps_flagged_rows_only(orc):
+    g = np.random.default_rng(51)
+    k, n, rows = 16, 1000, 6
+    fb = g.gamma(float(k), 1.0, (2, rows, n)).astype(np.float32)
+    fb[1, 4, ::10] *= 50.0
+    codes, st, fl = orc.redigitise_sk(fb, k, 3.0)
+    c0, st0 = orc.redigitise(fb)
+    assert np.array_equal(st, st0)
+    _, f2 = orc.spectral_kurtosis(fb, k, 3.0)
+    assert np.array_equal(fl, f2) and fl[1, 4] == 1
+    for d in range(2):
+        for r in range(rows):
+            col = rows - 1 - r
+            if fl[d, r]:
+                assert np.all(codes[d, :, col] == 128)
+            else:
+                assert np.array_equal(codes[d, :, col], c0[d, :, col])
