@@ -90,7 +90,9 @@ typedef struct cdmt_opts {
                             copies and, for 8-bit output, the block the statistics cover (Sec. 3);
                             0 = choose (about 4 blocks for float32 output, 16 for 8-bit output, each
                             at least 16 work items per SM) */
-    int64_t reserved[5];
+    double sk_nsigma;    /* cdmt_execute_host_u8: spectral-kurtosis RFI flagging of each block's rows
+                            (see cdmt_redigitise_sk); 0 = off */
+    int64_t reserved[4];
 } cdmt_opts;
 
 /* Derived sizes of a plan (cdmt_plan_info). */
@@ -250,6 +252,22 @@ int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
  * tiles), CDMT_ECUDA. */
 #define CDMT_REDIG_LEVELS 16.0
 int cdmt_redigitise(cdmt_plan_t plan, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream);
+
+/* cdmt_redigitise_sk - cdmt_redigitise with spectral-kurtosis RFI flagging
+ * (Sec. 6 names spectral kurtosis for the statistics step as future work and
+ * gives no definition; this is the generalised SK estimator).  For every
+ * (DM, channel) row of n = nout samples, each a sum of k = 2 nint squared
+ * magnitudes (two polarisations, nint time samples),
+ *   SK = (n k + 1) / (n - 1) * (n S2 / S1^2 - 1),  S1 = sum I, S2 = sum I^2,
+ * which averages 1 for Gaussian voltages with a large-n standard deviation of
+ * sqrt(2 (k + 1) / (k n)).  A row with |SK - 1| > sk_nsigma times that
+ * deviation is flagged: all its codes are 128 (its mean) and d_flags[dm][row]
+ * is 1 (0 otherwise).  Rows without power have SK = 0; rows of fewer than two
+ * samples are never flagged.  sk_nsigma = 0 disables flagging (then this is
+ * cdmt_redigitise).  d_flags: DEVICE uint8 [ndm][nsub*nchan], may be NULL.
+ * Errors: as cdmt_redigitise; CDMT_EINVAL for a negative or NaN sk_nsigma. */
+int cdmt_redigitise_sk(cdmt_plan_t plan, const float *d_fb, uint8_t *d_u8, float *d_stats, double sk_nsigma,
+                       uint8_t *d_flags, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Incoherent dedispersion of the coherent filterbanks (Sec. 4: in the
@@ -463,7 +481,9 @@ typedef struct cdmt_stream_desc {
     int32_t dm_tile;       /* DM trials per work item (0: the plan's choice) */
     int32_t out_dtype;     /* enum cdmt_out_dtype: the block's filterbank as float32, or redigitised to
                               8 bits per block (Sec. 3, as cdmt_redigitise) */
-    int64_t reserved[4];
+    double sk_nsigma;      /* CDMT_OUT_U8: spectral-kurtosis flagging of each block's rows, as
+                              cdmt_redigitise_sk (0 = off) */
+    int64_t reserved[3];
 } cdmt_stream_desc;
 
 /* Output type of a served block. */
@@ -491,6 +511,8 @@ typedef struct cdmt_block_result {
     float *d_stats;        /* CDMT_OUT_U8 beams: DEVICE, [ndm][nsub*nchan][2] (mean, sigma) of each row over
                               this block's samples; both valid until cdmt_server_release, and only when
                               samples > 0 */
+    uint8_t *d_flags;      /* CDMT_OUT_U8 beams: DEVICE, [ndm][nsub*nchan] spectral-kurtosis flags of this
+                              block's rows (all 0 when sk_nsigma is 0); NULL for float32 beams */
 } cdmt_block_result;
 
 typedef struct cdmt_server_stats {

@@ -30,7 +30,7 @@ class cdmt_opts(ctypes.Structure):
     _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("chirp", ctypes.c_int32),
                 ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("host_block", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 5)]
+                ("sk_nsigma", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
 
 
 class cdmt_info(ctypes.Structure):
@@ -77,14 +77,15 @@ class cdmt_stream_desc(ctypes.Structure):
                 ("f_centre_mhz", ctypes.c_double), ("bw_sub_mhz", ctypes.c_double), ("dm_first", ctypes.c_double),
                 ("dm_step", ctypes.c_double), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("nbin", ctypes.c_int64),
-                ("dm_tile", ctypes.c_int32), ("out_dtype", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+                ("dm_tile", ctypes.c_int32), ("out_dtype", ctypes.c_int32), ("sk_nsigma", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class cdmt_block_result(ctypes.Structure):
     _fields_ = [("beam", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("index", ctypes.c_int64),
                 ("d_out", ctypes.c_void_p), ("nseg", ctypes.c_int64), ("first_sample", ctypes.c_int64),
                 ("samples", ctypes.c_int64), ("row_stride", ctypes.c_int64), ("latency_ms", ctypes.c_double),
-                ("d_u8", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
+                ("d_u8", ctypes.c_void_p), ("d_stats", ctypes.c_void_p), ("d_flags", ctypes.c_void_p)]
 
 
 class cdmt_server_stats(ctypes.Structure):
@@ -141,6 +142,7 @@ def _load():
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P, P]
     lib.cdmt_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_redigitise.argtypes = [P, P, P, P, P]
+    lib.cdmt_redigitise_sk.argtypes = [P, P, P, P, ctypes.c_double, P, P]
     lib.cdmt_execute_host_u8.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int64), P]
     lib.cdmt_incoherent_info.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), P]
@@ -155,7 +157,7 @@ def _load():
               "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
               "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
               "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise", "cdmt_incoherent_info",
-              "cdmt_incoherent", "cdmt_execute_host_u8"):
+              "cdmt_incoherent", "cdmt_execute_host_u8", "cdmt_redigitise_sk"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -164,8 +166,8 @@ _lib = _load()
 
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
-            "cdmt_redigitise", "cdmt_incoherent_info", "cdmt_incoherent", "cdmt_execute_host_u8",
-            "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
+            "cdmt_redigitise", "cdmt_redigitise_sk", "cdmt_incoherent_info", "cdmt_incoherent",
+            "cdmt_execute_host_u8", "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
             "cdmt_server_wait", "cdmt_server_release", "cdmt_server_get_stats", "cdmt_server_reset_stats",
@@ -384,10 +386,11 @@ class Server:
         self.handle = cdmt_server_create(o)
 
     def add_beam(self, nsub, block_len, f_centre, bw_sub, dm_first, dm_step, ndm, nchan, nint,
-                 precision=CDMT_PREC_FP16, in_dtype=CDMT_IN_C64, nbin=0, dm_tile=0, out_dtype=CDMT_OUT_F32) -> int:
+                 precision=CDMT_PREC_FP16, in_dtype=CDMT_IN_C64, nbin=0, dm_tile=0, out_dtype=CDMT_OUT_F32,
+                 sk_nsigma=0.0) -> int:
         d = cdmt_stream_desc(int(nsub), int(ndm), int(block_len), float(f_centre), float(bw_sub), float(dm_first),
                              float(dm_step), int(nchan), int(nint), int(precision), int(in_dtype), int(nbin),
-                             int(dm_tile), int(out_dtype))
+                             int(dm_tile), int(out_dtype), float(sk_nsigma))
         return cdmt_server_add_beam(self.handle, d)
 
     def submit(self, beam, block_ptr, scale_ptr=0) -> int:
@@ -415,7 +418,8 @@ class Server:
     @staticmethod
     def block_u8_view(res: cdmt_block_result, ndm: int, rows: int):
         """Zero-copy torch views of an 8-bit block (valid until release): codes [ndm][samples][rows]
-        (spectra in decreasing frequency) and statistics [ndm][rows][2] (mean, sigma)."""
+        (spectra in decreasing frequency), statistics [ndm][rows][2] (mean, sigma) and
+        spectral-kurtosis flags [ndm][rows]."""
         import torch
         if not res.d_u8:
             raise CdmtError(CDMT_EINVAL, "the block has no 8-bit output (float32 beam)")
@@ -425,7 +429,8 @@ class Server:
                 __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
                                             "strides": None}
             return torch.as_tensor(_A(), device="cuda")
-        return view(res.d_u8, (ndm, res.samples, rows), "|u1"), view(res.d_stats, (ndm, rows, 2), "<f4")
+        return (view(res.d_u8, (ndm, res.samples, rows), "|u1"), view(res.d_stats, (ndm, rows, 2), "<f4"),
+                view(res.d_flags, (ndm, rows), "|u1"))
 
     def reset_stats(self):
         cdmt_server_reset_stats(self.handle)
@@ -472,6 +477,12 @@ def cdmt_redigitise(plan, d_fb: int, d_u8: int, d_stats: int = 0, stream: int = 
     _check(_lib.cdmt_redigitise(plan, d_fb, d_u8, d_stats or None, stream or None), plan)
 
 
+def cdmt_redigitise_sk(plan, d_fb: int, d_u8: int, d_stats: int = 0, sk_nsigma: float = 0.0, d_flags: int = 0,
+                       stream: int = 0):
+    _check(_lib.cdmt_redigitise_sk(plan, d_fb, d_u8, d_stats or None, float(sk_nsigma), d_flags or None,
+                                   stream or None), plan)
+
+
 REDIG_LEVELS = 16.0
 
 
@@ -497,10 +508,11 @@ class Plan:
     """Owning wrapper of a cdmt plan."""
 
     def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
-                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0, host_block=0):
+                 seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0, host_block=0,
+                 sk_nsigma=0.0):
         o = cdmt_opts()
         o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
-        o.precision, o.in_dtype, o.chirp, o.host_block = precision, in_dtype, chirp, host_block
+        o.precision, o.in_dtype, o.chirp, o.host_block, o.sk_nsigma = precision, in_dtype, chirp, host_block, sk_nsigma
         self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
         self.info = cdmt_plan_info(self.handle)
 
@@ -533,17 +545,19 @@ class Plan:
         cdmt_incoherent(self.handle, fb.data_ptr(), ddm_lo, ddm_step, nk, out.data_ptr(), st)
         return out
 
-    def redigitise(self, fb, out=None, stats=None, stream=None):
+    def redigitise(self, fb, out=None, stats=None, stream=None, sk_nsigma=0.0, flags=None):
         """8-bit codes uint8 [ndm][nout][nsub*nchan] (decreasing frequency) of the
         filterbank fb (a device tensor of out_shape()); stats, if given, receives
-        float32 [ndm][nsub*nchan][2] (mean, sigma)."""
+        float32 [ndm][nsub*nchan][2] (mean, sigma).  sk_nsigma > 0 flags rows by
+        spectral kurtosis (codes 128; flags, if given, uint8 [ndm][nsub*nchan])."""
         import torch
         ndm, rows, nout = self.out_shape()
         assert tuple(fb.shape) == (ndm, rows, nout) and fb.dtype == torch.float32 and fb.is_contiguous()
         if out is None:
             out = torch.empty((ndm, nout, rows), dtype=torch.uint8, device=fb.device)
         st = torch.cuda.current_stream(fb.device).cuda_stream if stream is None else stream
-        cdmt_redigitise(self.handle, fb.data_ptr(), out.data_ptr(), stats.data_ptr() if stats is not None else 0, st)
+        cdmt_redigitise_sk(self.handle, fb.data_ptr(), out.data_ptr(), stats.data_ptr() if stats is not None else 0,
+                           sk_nsigma, flags.data_ptr() if flags is not None else 0, st)
         return out
 
     def close(self):

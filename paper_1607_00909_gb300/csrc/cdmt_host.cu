@@ -445,6 +445,7 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     p->chirp = o.chirp;
     p->mem_budget = o.mem_budget;
     p->host_block_opt = o.host_block;
+    p->sk_nsigma = o.sk_nsigma > 0.0 ? o.sk_nsigma : 0.0;
 
     // N_bin: explicit, or the largest M in 512..4096 whose overlap wastes <= 1/4
     int64_t nbin = o.nbin;
@@ -764,7 +765,8 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
             CK(p, cudaStreamWaitEvent(st, so.out_free, 0));
             if ((rc = enqueue_dm(p, so.out, ostride, 0, kc, nq > 1 ? dm_lo : 0, nq > 1 ? cnt : 0, st)) != CDMT_OK)
                 return rc;
-            if (u8 && (rc = redig_enqueue(p, so.out, kc * p->seglen, ostride, so.u8, nullptr, st)) != CDMT_OK)
+            if (u8 && (rc = redig_enqueue(p, so.out, kc * p->seglen, ostride, so.u8, nullptr, st, p->sk_nsigma)) !=
+                          CDMT_OK)
                 return rc;
             CK(p, cudaEventRecord(so.out_ready, st));
             CK(p, cudaStreamWaitEvent(p->s_d2h, so.out_ready, 0));

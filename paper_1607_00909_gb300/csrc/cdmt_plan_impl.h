@@ -59,7 +59,8 @@ struct cdmt_plan_s {
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0, host_block_opt = 0;
-    int64_t host_out_cap = 0;      // floats per output slot of the host pipeline (u8 slots: bytes)
+    int64_t host_out_cap = 0;
+    double sk_nsigma = 0.0;        // spectral-kurtosis flagging of the 8-bit host output (0: off)      // floats per output slot of the host pipeline (u8 slots: bytes)
     cdmt::Staging stage[3];        // host pipeline: three blocks in flight (copy in, compute, copy out)
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     // stage timing (cdmt_set_timing / cdmt_stage_times)
@@ -80,5 +81,5 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
 // Allocates the plan's per-row (mean, gain) array of the redigitisation if it is missing.
 int redig_reserve(cdmt_plan_s *p);
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
-                  cudaStream_t st);
+                  cudaStream_t st, double sk_nsigma = 0.0, uint8_t *d_flags = nullptr);
 }  // namespace cdmt

@@ -19,6 +19,34 @@ namespace {
 
 constexpr int kTile = 64;
 
+// Spectral-kurtosis flag of a row of n samples, each a sum of k squared
+// magnitudes, from its mean and (population) standard deviation: the
+// generalised estimator SK = (n k + 1) / (n - 1) * sigma^2 / mu^2 (n S2 / S1^2
+// - 1 = sigma^2 / mu^2), flagged when |SK - 1| > nsigma sqrt(2 (k + 1) / (k n)),
+// its large-n deviation for Gaussian voltages; mu = 0 gives SK = 0 and fewer
+// than two samples are never flagged.  nsigma <= 0: no flagging.
+struct SkRule {
+    float nsigma = 0.f;
+    int k = 1;
+    uint8_t *flags = nullptr;   // [rows of the launch] (may be NULL)
+};
+
+__device__ __forceinline__ bool sk_flag(double mu, double sigma, int64_t n, const SkRule &sk)
+{
+    if (!(sk.nsigma > 0.f) || n < 2) return false;
+    const double nn = (double)n, k = (double)sk.k;
+    const double v = mu > 0.0 ? (nn * k + 1.0) / (nn - 1.0) * (sigma * sigma) / (mu * mu) : 0.0;
+    return fabs(v - 1.0) > (double)sk.nsigma * sqrt(2.0 * (k + 1.0) / (k * nn));
+}
+
+__device__ __forceinline__ bool sk_flag_f(float mu, float sigma, int64_t n, const SkRule &sk)
+{
+    if (!(sk.nsigma > 0.f) || n < 2) return false;
+    const float nn = (float)n, k = (float)sk.k;
+    const float v = mu > 0.f ? (nn * k + 1.f) / (nn - 1.f) * (sigma * sigma) / (mu * mu) : 0.f;
+    return fabsf(v - 1.f) > sk.nsigma * sqrtf(2.f * (k + 1.f) / (k * nn));
+}
+
 // One CTA per (DM, channel) row of nt samples (rows of kShortRow samples or
 // more; shorter rows use k_redig_stats_rows): sums of I and I^2 (FP32 within a
 // thread, FP64 across threads), then mean mu, standard deviation sigma, and the
@@ -26,7 +54,7 @@ constexpr int kTile = 64;
 // (stride % 4 == 0) and are read as float4, four loads in flight per thread.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ fb, int64_t nt, int64_t stride,
-                                                     float2 *__restrict__ mg, float *__restrict__ stats)
+                                                     float2 *__restrict__ mg, float *__restrict__ stats, SkRule sk)
 {
     const int64_t row = blockIdx.x;
     const float *p = fb + row * stride;
@@ -75,7 +103,9 @@ __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ f
         const double mu = nt > 0 ? a / (double)nt : 0.0;
         const double var = nt > 0 ? fmax(b / (double)nt - mu * mu, 0.0) : 0.0;
         const double sigma = sqrt(var);
-        mg[row] = make_float2((float)mu, sigma > 0.0 ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        const bool flag = sk_flag(mu, sigma, nt, sk);
+        mg[row] = make_float2((float)mu, sigma > 0.0 && !flag ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        if (sk.flags) sk.flags[row] = flag;
         if (stats) {
             stats[2 * row] = (float)mu;
             stats[2 * row + 1] = (float)sigma;
@@ -101,7 +131,7 @@ __device__ __forceinline__ float warp_sum(float v)
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_stats_rows(const float *__restrict__ fb, int64_t nrow, int64_t nt,
                                                           int64_t stride, float2 *__restrict__ mg,
-                                                          float *__restrict__ stats)
+                                                          float *__restrict__ stats, SkRule sk)
 {
     const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= nrow) return;
@@ -130,7 +160,9 @@ __global__ void __launch_bounds__(256) k_redig_stats_rows(const float *__restric
     }
     const float sigma = sqrtf(warp_sum(s2) / (float)nt);
     if (lane == 0) {
-        mg[row] = make_float2(mu, sigma > 0.f ? (float)CDMT_REDIG_LEVELS / sigma : 0.f);
+        const bool flag = sk_flag_f(mu, sigma, nt, sk);
+        mg[row] = make_float2(mu, sigma > 0.f && !flag ? (float)CDMT_REDIG_LEVELS / sigma : 0.f);
+        if (sk.flags) sk.flags[row] = flag;
         if (stats) {
             stats[2 * row] = mu;
             stats[2 * row + 1] = sigma;
@@ -227,7 +259,7 @@ int redig_reserve(cdmt_plan_s *p)
 }
 
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
-                  cudaStream_t st)
+                  cudaStream_t st, double sk_nsigma, uint8_t *d_flags)
 {
     const int rows = p->nsub * p->nchan;
     if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
@@ -238,13 +270,17 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
     const unsigned nrow = (unsigned)((int64_t)p->ndm * rows);
     const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)p->ndm);
     const unsigned nrow8 = (nrow + 7) / 8;
+    SkRule sk;
+    sk.nsigma = sk_nsigma > 0.0 ? (float)sk_nsigma : 0.f;
+    sk.k = 2 * p->nint;
+    sk.flags = d_flags;
     if (vec) {
-        if (nt < kShortRow) k_redig_stats_rows<true><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats);
-        else k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        if (nt < kShortRow) k_redig_stats_rows<true><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats, sk);
+        else k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats, sk);
         k_redig_codes<true><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     } else {
-        if (nt < kShortRow) k_redig_stats_rows<false><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats);
-        else k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats);
+        if (nt < kShortRow) k_redig_stats_rows<false><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats, sk);
+        else k_redig_stats<false><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats, sk);
         k_redig_codes<false><<<grid, 256, 0, st>>>(d_fb, p->redig_mg, d_u8, rows, nt, stride);
     }
     const cudaError_t e = cudaGetLastError();
@@ -254,14 +290,22 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
 
 }  // namespace cdmt
 
-extern "C" int cdmt_redigitise(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream)
+extern "C" int cdmt_redigitise_sk(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, double sk_nsigma,
+                                  uint8_t *d_flags, void *cuda_stream)
 {
     if (!p) return CDMT_EINVAL;
     if (!d_fb || !d_u8) return rfail(p, CDMT_EINVAL, "NULL filterbank or output pointer");
+    if (!(sk_nsigma >= 0.0)) return rfail(p, CDMT_EINVAL, "sk_nsigma must be >= 0");
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return rfail(p, CDMT_ECUDA, "cudaSetDevice failed");
-    const int rc = cdmt::redig_enqueue(p, d_fb, p->nout, p->nout, d_u8, d_stats, static_cast<cudaStream_t>(cuda_stream));
+    const int rc = cdmt::redig_enqueue(p, d_fb, p->nout, p->nout, d_u8, d_stats, static_cast<cudaStream_t>(cuda_stream),
+                                       sk_nsigma, d_flags);
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
+}
+
+extern "C" int cdmt_redigitise(cdmt_plan_t p, const float *d_fb, uint8_t *d_u8, float *d_stats, void *cuda_stream)
+{
+    return cdmt_redigitise_sk(p, d_fb, d_u8, d_stats, 0.0, nullptr, cuda_stream);
 }

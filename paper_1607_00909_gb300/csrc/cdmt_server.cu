@@ -97,7 +97,8 @@ struct Beam {
     void *d_blk = nullptr;
     float *d_scale = nullptr;
     int64_t fb_bytes = 0;       // one block's float32 filterbank (max_seg segments)
-    int64_t codes_bytes = 0;    // 8-bit beams: codes part of a slot (16-byte multiple); statistics follow
+    int64_t codes_bytes = 0;    // 8-bit beams: codes part of a slot (16-byte multiple); statistics follow,
+    int64_t stats_bytes = 0;    // then one flag byte per row
     cudaStream_t st = nullptr;
     std::deque<int64_t> fifo;
     int64_t bytes = 0;
@@ -237,7 +238,8 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
         if (enqueue_chunk(b.plan, stage, b.cap, 0, fb, b.stride, 0, (int)nseg, b.st) != CDMT_OK)
             return false;
         if (u8 && redig_enqueue(b.plan, fb, nseg * b.seglen, b.stride, slot,
-                                reinterpret_cast<float *>(slot + b.codes_bytes), b.st) != CDMT_OK)
+                                reinterpret_cast<float *>(slot + b.codes_bytes), b.st, b.d.sk_nsigma,
+                                slot + b.codes_bytes + b.stats_bytes) != CDMT_OK)
             return false;
     }
     const int64_t used = nseg * b.S;
@@ -360,6 +362,7 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     if (d->block_len < 1 || d->nsub < 1 || d->ndm < 1) return sfail(v, CDMT_EINVAL, "bad stream descriptor");
     if (d->in_dtype != CDMT_IN_C64 && d->in_dtype != CDMT_IN_I8) return sfail(v, CDMT_ENOTSUP, "input dtype");
     if (d->out_dtype != CDMT_OUT_F32 && d->out_dtype != CDMT_OUT_U8) return sfail(v, CDMT_ENOTSUP, "output dtype");
+    if (!(d->sk_nsigma >= 0.0)) return sfail(v, CDMT_EINVAL, "sk_nsigma must be >= 0");
     Beam b;
     b.d = *d;
     const int64_t nbin = d->nbin > 0 ? d->nbin : 4096LL * d->nchan;
@@ -393,7 +396,8 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     b.stride = (b.max_seg * b.seglen + 3) / 4 * 4;   // rows 16-byte aligned
     b.fb_bytes = (int64_t)sizeof(float) * d->ndm * b.rows * b.stride;
     b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;
-    b.out_bytes = u8 ? b.codes_bytes + (int64_t)sizeof(float) * 2 * d->ndm * b.rows : b.fb_bytes;
+    b.stats_bytes = (int64_t)sizeof(float) * 2 * d->ndm * b.rows;
+    b.out_bytes = u8 ? b.codes_bytes + b.stats_bytes + (int64_t)d->ndm * b.rows : b.fb_bytes;
     b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + (int64_t)es * d->nsub * d->block_len +
               (int64_t)sizeof(float) * d->nsub + (u8 ? (int64_t)sizeof(float) * 2 * d->ndm * b.rows : 0);
     // admission: resident state of every beam + the slots held + the slots one block of this beam
@@ -485,6 +489,7 @@ int cdmt_server_wait(cdmt_server_t v, int64_t id, double timeout_s, cdmt_block_r
         if (b.d.out_dtype == CDMT_OUT_U8) {
             res->d_u8 = slot;
             res->d_stats = reinterpret_cast<float *>(slot + b.codes_bytes);
+            res->d_flags = slot + b.codes_bytes + b.stats_bytes;
         } else {
             res->d_out = reinterpret_cast<float *>(slot);
         }

@@ -99,15 +99,16 @@ def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
     plan.close()
 
 
-@pytest.mark.parametrize("host_block", [2, 4])
-def test_host_pipeline_8bit_blocks(cdmt, orc, host_block):
+@pytest.mark.parametrize("host_block,sk_nsigma", [(2, 0.0), (4, 0.0), (4, 2.0)])
+def test_host_pipeline_8bit_blocks(cdmt, orc, host_block, sk_nsigma):
     # Algorithm 1 up to "redigitize" and "copy to host": every block of host_block segments
     # (the last one shorter) has its own statistics; codes must match the oracle applied
     # block by block to the float filterbank of the same plan
     import torch
     nsub, nsamp = 2, 9 * (1 << 14) + 123
     x = synth.noise(42, nsub, nsamp)
-    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, [0.0, 6.0, 12.0], 8, 4, nbin=1 << 14, host_block=host_block)
+    plan = cdmt.Plan(nsub, nsamp, 135.0, BW, [0.0, 6.0, 12.0], 8, 4, nbin=1 << 14, host_block=host_block,
+                     sk_nsigma=sk_nsigma)
     ndm, rows, nout = plan.out_shape()
     fb = cdmt.run(plan, torch.from_numpy(x).cuda()).cpu().numpy()
     xh = torch.from_numpy(x).pin_memory()
@@ -116,19 +117,28 @@ def test_host_pipeline_8bit_blocks(cdmt, orc, host_block):
     seglen = nout // plan.info["nseg"]
     assert kb == host_block and plan.info["nseg"] % kb   # several blocks, the last one shorter
     codes = u8.numpy()
-    nbad = 0
+    nbad = nflag = 0
     for s0 in range(0, plan.info["nseg"], kb):
         t0, t1 = s0 * seglen, min(plan.info["nseg"], s0 + kb) * seglen
         block = np.ascontiguousarray(fb[:, :, t0:t1])
         oc, ost = orc.redigitise(block)
         diff = codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32)
-        assert np.all(np.abs(diff) <= 1)
+        if sk_nsigma > 0:   # flagged rows (k = 2 nint = 8) are all 128; rows at the threshold are not compared
+            oc, _, of = orc.redigitise_sk(block, 8, sk_nsigma)
+            sk, _ = orc.spectral_kurtosis(block, 8, sk_nsigma)
+            thr = sk_nsigma * orc.sk_sigma(t1 - t0, 8)
+            near = np.abs(np.abs(sk - 1.0) - thr) < 1e-4 * thr
+            diff = codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32)
+            diff[:, :, ::-1][np.broadcast_to(near[:, None, :], diff.shape)] = 0
+            nflag += int(of.sum())
         d, t, p = np.nonzero(diff)
         r = rows - 1 - p
         xv = 128.0 + (block[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / ost[d, r, 1]
         assert np.all(np.abs(xv - np.floor(xv) - 0.5) < 1e-3)
         nbad += len(d)
     assert nbad <= max(1, 1e-4 * codes.size)
+    if sk_nsigma > 0:
+        assert nflag >= 1   # a 2-sigma rule flags a few noise rows out of 3 blocks x 3 DMs x 16 rows
     plan.close()
 
 
@@ -185,4 +195,62 @@ def test_host_pipeline_block_choice_and_staging_growth(cdmt, orc):
         assert diff.max() <= 1
         nbad += int(np.count_nonzero(diff))
     assert nbad <= max(1, 1e-4 * codes.size)
+    plan.close()
+
+
+def _check_sk(orc, fb, codes, stats, flags, k, nsigma):
+    """Flags equal to the oracle's except where |SK - 1| lies within 1e-4 of the
+    threshold (the two sides take SK from statistics rounded differently); codes
+    of rows both sides flag are all 128, other rows as _check."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    sk, of = orc.spectral_kurtosis(fb, k, nsigma)
+    thr = nsigma * orc.sk_sigma(nt, k)
+    near = np.abs(np.abs(sk - 1.0) - thr) < 1e-4 * thr
+    assert np.all((flags == of) | near)
+    both = (flags == 1) & (of == 1)
+    for d, r in zip(*np.nonzero(both)):
+        assert np.all(codes[d, :, rows - 1 - r] == 128)
+    keep = (flags == 0) & (of == 0)
+    fb2 = fb.copy()
+    c2 = codes.copy()
+    for d, r in zip(*np.nonzero(~keep)):   # compare the remaining rows only: blank the others
+        fb2[d, r, :] = 1.0
+        c2[d, :, rows - 1 - r] = 128
+    st2 = stats.copy()
+    st2[~keep] = (1.0, 0.0)
+    _check(orc, fb2, c2, st2)
+    return int(of.sum())
+
+
+@pytest.mark.parametrize("nsamp_segments", [3, 18])
+def test_redigitise_sk_flags(cdmt, orc, nsamp_segments):
+    """Spectral-kurtosis flagging on the warp-per-row (3066 samples) and
+    CTA-per-row (18396 samples) statistics: Gamma(2 nint) rows plus impulsive,
+    steady and dead rows, against the oracle."""
+    import torch
+    nsamp = nsamp_segments * (1 << 16) + 777
+    nint = 4
+    plan = cdmt.Plan(1, nsamp, 140.0, BW, [0.0, 9.0, 18.0], 16, nint, nbin=1 << 16)
+    ndm, rows, nout = plan.out_shape()
+    k = 2 * nint
+    g = np.random.default_rng(60 + nsamp_segments)
+    fb = g.gamma(float(k), 1.5, (ndm, rows, nout)).astype(np.float32)
+    fb[0, 3, ::25] *= 40.0                     # impulsive RFI
+    fb[1, 7] = 12.0 + 0.001 * g.standard_normal(nout).astype(np.float32)   # steady carrier
+    fb[2, 11] = 0.0                            # dead channel
+    stats = torch.empty((ndm, rows, 2), dtype=torch.float32, device="cuda")
+    flags = torch.full((ndm, rows), 7, dtype=torch.uint8, device="cuda")
+    codes = plan.redigitise(torch.from_numpy(fb).cuda(), stats=stats, sk_nsigma=3.0, flags=flags)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()
+    assert set(np.unique(f)) <= {0, 1}
+    assert f[0, 3] == 1 and f[1, 7] == 1 and f[2, 11] == 1
+    nflag = _check_sk(orc, fb, codes.cpu().numpy(), stats.cpu().numpy(), f, k, 3.0)
+    assert nflag <= 3 + max(2, 0.02 * ndm * rows)
+    # sk_nsigma = 0 flags nothing and gives the plain redigitisation
+    c0 = plan.redigitise(torch.from_numpy(fb).cuda(), sk_nsigma=0.0, flags=flags)
+    torch.cuda.synchronize()
+    assert not flags.cpu().numpy().any()
+    assert np.array_equal(c0.cpu().numpy(), plan.redigitise(torch.from_numpy(fb).cuda()).cpu().numpy())
     plan.close()

@@ -130,30 +130,32 @@ def test_admission_and_errors(cdmt):
 
 
 def test_u8_blocks_are_the_redigitised_float_blocks(cdmt, orc):
-    """A CDMT_OUT_U8 beam carries, per block, the codes and row statistics that
-    the redigitisation (Sec. 3) gives for the float32 filterbank of the same
-    block: checked against the oracle's redigitisation of a float32 twin beam
-    fed the same blocks on the same server."""
+    """A CDMT_OUT_U8 beam carries, per block, the codes, row statistics and
+    spectral-kurtosis flags that the redigitisation (Sec. 3, with the flagging of
+    Sec. 6) gives for the float32 filterbank of the same block: checked against
+    the oracle's redigitisation of a float32 twin beam fed the same blocks on the
+    same server."""
     import torch
-    from test_redig_gpu import _check
+    from test_redig_gpu import _check_sk
     b = BEAMS[1]
     x = _inputs([b])[0]
     rows, L = b["nsub"] * b["nchan"], b["block_len"]
     srv = cdmt.Server(max_slots=3)
     ids = [srv.add_beam(b["nsub"], L, b["f_centre"], BW, b["dm_first"], b["dm_step"], b["ndm"], b["nchan"], b["nint"],
-                        dm_tile=b["ndm"], out_dtype=od) for od in (cdmt.CDMT_OUT_F32, cdmt.CDMT_OUT_U8)]
+                        dm_tile=b["ndm"], out_dtype=od, sk_nsigma=2.5)
+           for od in (cdmt.CDMT_OUT_F32, cdmt.CDMT_OUT_U8)]
     blocks = [torch.from_numpy(np.ascontiguousarray(x[:, k * L:(k + 1) * L])).pin_memory() for k in range(NBLK)]
     reqs = [(k, [srv.submit(i, blocks[k].data_ptr()) for i in ids]) for k in range(NBLK)]
     checked = 0
     for k, (rf, ru) in reqs:
         a, u = srv.wait(rf, 120.0), srv.wait(ru, 120.0)
         assert (a.first_sample, a.samples) == (u.first_sample, u.samples)
-        assert a.d_u8 is None and u.d_out is None
+        assert a.d_u8 is None and a.d_flags is None and u.d_out is None
         if u.samples > 0:
             fb = srv.block_view(a, b["ndm"], rows).cpu().numpy()
-            codes, stats = (t.cpu().numpy() for t in srv.block_u8_view(u, b["ndm"], rows))
+            codes, stats, flags = (t.cpu().numpy() for t in srv.block_u8_view(u, b["ndm"], rows))
             assert codes.shape == (b["ndm"], u.samples, rows)
-            _check(orc, fb, codes, stats)
+            _check_sk(orc, fb, codes, stats, flags, 2 * b["nint"], 2.5)
             checked += 1
         else:
             with pytest.raises(cdmt.CdmtError):
