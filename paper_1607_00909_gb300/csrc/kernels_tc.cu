@@ -368,12 +368,17 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
         {
             double dmv = 0.0;
             if constexpr (!UNIFORM) dmv = it.dms[d];
-            uint32_t w[2 * JH];
-            if constexpr (JH == 16) tc::tmem_ld32_async(ph_taddr, w);
-            else tc::tmem_ld16_async(ph_taddr, w);
-            tc::tmem_wait();
+            // phase words (a, b) of the thread's bins, 8 bins (16 words) per tensor-memory load:
+            // half the registers of loading all 16 bins at once, for one more wait
+            constexpr int CH = JH / 4 < 2 ? JH / 4 : 2;   // 4-bin groups per load
+            uint32_t wl[8 * CH];
             #pragma unroll
             for (int c4 = 0; c4 < JH / 4; c4++) {
+                if (c4 % CH == 0) {
+                    if constexpr (CH == 2) tc::tmem_ld16_async(ph_taddr + 8 * c4, wl);
+                    else tc::tmem_ld8_async(ph_taddr + 8 * c4, wl);
+                    tc::tmem_wait();
+                }
                 uint32_t hx[4], hy[4], lx[4], ly[4];
                 #pragma unroll
                 for (int i2 = 0; i2 < 2; i2++) {
@@ -383,11 +388,13 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                     #pragma unroll
                     for (int e2 = 0; e2 < 2; e2++) {
                         if constexpr (UNIFORM) {
-                            const int32_t p = (int32_t)(w[2 * (b + e2)] + (uint32_t)(d + it.dbase) * w[2 * (b + e2) + 1]);
+                            const int q = 8 * (c4 % CH) + 2 * (2 * i2 + e2);   // bin b + e2 in wl
+                            const int32_t p = (int32_t)(wl[q] + (uint32_t)(d + it.dbase) * wl[q + 1]);
                             __sincosf((float)p * kTwoPiOver2p32, &sn[e2], &cs[e2]);
                         } else {
                             const int j = (jbase + b + e2) * 64 + jlo;
-                            const double kj = __hiloint2double((int)w[2 * (b + e2) + 1], (int)w[2 * (b + e2)]);
+                            const int q = 8 * (c4 % CH) + 2 * (2 * i2 + e2);
+                            const double kj = __hiloint2double((int)wl[q + 1], (int)wl[q]);
                             double cyc = dmv * kj;
                             cyc -= rint(cyc);
                             const uint32_t pf = (uint32_t)(long long)llrint(-cyc * 4294967296.0) + ((uint32_t)(j * half) << (32 - LM));
