@@ -459,6 +459,8 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             }
             tc::commit(mb);
         }
+        // warp 0 of the pipe polls the mbarrier (bounded); the other warps wait at the pipe's named
+        // barrier, which takes no issue slots, and the vote makes a timeout pipe-uniform
         ok = bar_and(bar_id, PT, q >= 32 || tc::mbar_wait(mb, 0, kWaitNs, kWaitPolls));
         if (!ok) break;
         tc::fence_after();
