@@ -95,3 +95,46 @@ def test_null_handles(cdmt):
     assert lib.cdmt_execute_host(None, None, None, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_destroy(None) == cdmt.CDMT_OK
     assert lib.cdmt_plan_ex(None, 1, 1, 1.0, 1.0, None, 0, 8, 1, None) == cdmt.CDMT_EINVAL
+
+
+def test_null_handles_of_the_8bit_and_incoherent_entry_points(cdmt):
+    lib = cdmt.lib()
+    assert lib.cdmt_redigitise(None, None, None, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_redigitise_sk(None, None, None, None, 3.0, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_execute_host_u8(None, None, None, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_incoherent(None, None, 0.0, 0.0, 1, None, None) == cdmt.CDMT_EINVAL
+
+
+def test_struct_layouts_match_the_header(cdmt, tmp_path):
+    """Every ctypes mirror of a header struct has the size and field offsets that
+    the C compiler gives include/cdmt.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = [cdmt.cdmt_opts, cdmt.cdmt_info, cdmt.cdmt_beam, cdmt.cdmt_batch_opts, cdmt.cdmt_batch_tune,
+               cdmt.cdmt_batch_beam_info, cdmt.cdmt_stream_desc, cdmt.cdmt_block_result, cdmt.cdmt_server_opts,
+               cdmt.cdmt_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cdmt.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        n, f, v = line.split()
+        got[(n, f)] = int(v)
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "size")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
