@@ -94,8 +94,12 @@ struct Beam {
     float4 *stage[2] = {nullptr, nullptr};
     int cur = 0;
     int64_t tail = 0, seg_total = 0, next_index = 0;
-    void *d_blk = nullptr;
-    float *d_scale = nullptr;
+    // two block buffers: the copy of the next block (own stream) overlaps the compute of this one
+    void *d_blk[2] = {nullptr, nullptr};
+    float *d_scale[2] = {nullptr, nullptr};
+    cudaStream_t cp = nullptr;
+    cudaEvent_t blk_ready[2] = {nullptr, nullptr}, blk_free[2] = {nullptr, nullptr};
+    int cb = 0;                 // block buffer of the next block
     int64_t fb_bytes = 0;       // one block's float32 filterbank (max_seg segments)
     int64_t codes_bytes = 0;    // 8-bit beams: codes part of a slot (16-byte multiple); statistics follow,
     int64_t stats_bytes = 0;    // then one flag byte per row
@@ -215,19 +219,27 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
     cudaPointerAttributes pa{};
     const bool on_device = cudaPointerGetAttributes(&pa, r.block) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
     cudaGetLastError();
-    if (!on_device) {
-        if (cudaMemcpyAsync(b.d_blk, r.block, bytes, cudaMemcpyHostToDevice, b.st) != cudaSuccess) return false;
-        src = b.d_blk;
-    }
-    const float *scale = b.d_scale;
-    if (b.d.in_dtype == CDMT_IN_I8) {
-        if (cudaMemcpyAsync(b.d_scale, r.scale, sizeof(float) * b.d.nsub, cudaMemcpyDefault, b.st) != cudaSuccess)
+    // the block (and its int8 scales) into block buffer i on the copy stream, once the block that used
+    // the buffer before has been appended; the beam's stream waits for the copy
+    const int i = b.cb;
+    b.cb ^= 1;
+    const bool i8 = b.d.in_dtype == CDMT_IN_I8;
+    if (!on_device || i8) {
+        if (cudaStreamWaitEvent(b.cp, b.blk_free[i], 0) != cudaSuccess) return false;
+        if (!on_device) {
+            if (cudaMemcpyAsync(b.d_blk[i], r.block, bytes, cudaMemcpyHostToDevice, b.cp) != cudaSuccess) return false;
+            src = b.d_blk[i];
+        }
+        if (i8 && cudaMemcpyAsync(b.d_scale[i], r.scale, sizeof(float) * b.d.nsub, cudaMemcpyDefault, b.cp) !=
+                      cudaSuccess)
             return false;
+        if (cudaEventRecord(b.blk_ready[i], b.cp) != cudaSuccess) return false;
+        if (cudaStreamWaitEvent(b.st, b.blk_ready[i], 0) != cudaSuccess) return false;
     }
     float4 *stage = b.stage[b.cur];
-    k_append<<<512, 256, 0, b.st>>>(stage, b.cap, b.tail, src, scale, b.d.block_len, b.d.nsub,
-                                    b.d.in_dtype == CDMT_IN_I8);
+    k_append<<<512, 256, 0, b.st>>>(stage, b.cap, b.tail, src, b.d_scale[i], b.d.block_len, b.d.nsub, i8);
     if (cudaGetLastError() != cudaSuccess) return false;
+    if (cudaEventRecord(b.blk_free[i], b.st) != cudaSuccess) return false;
     const int64_t avail = b.tail + b.d.block_len;
     int64_t nseg = avail >= b.N ? (avail - b.N) / b.S + 1 : 0;
     nseg = std::min(nseg, b.max_seg);
@@ -329,11 +341,17 @@ void scheduler(cdmt_server_s *v)
 void free_beam(Beam &b)
 {
     if (b.st) cudaStreamSynchronize(b.st);
+    if (b.cp) cudaStreamSynchronize(b.cp);
     if (b.plan) cdmt_destroy(b.plan);
     for (float4 *p : b.stage)
         if (p) cudaFree(p);
-    if (b.d_blk) cudaFree(b.d_blk);
-    if (b.d_scale) cudaFree(b.d_scale);
+    for (int i = 0; i < 2; i++) {
+        if (b.d_blk[i]) cudaFree(b.d_blk[i]);
+        if (b.d_scale[i]) cudaFree(b.d_scale[i]);
+        if (b.blk_ready[i]) cudaEventDestroy(b.blk_ready[i]);
+        if (b.blk_free[i]) cudaEventDestroy(b.blk_free[i]);
+    }
+    if (b.cp) cudaStreamDestroy(b.cp);
     if (b.st) cudaStreamDestroy(b.st);
     b = Beam{};
     b.active = false;
@@ -398,8 +416,8 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;
     b.stats_bytes = (int64_t)sizeof(float) * 2 * d->ndm * b.rows;
     b.out_bytes = u8 ? b.codes_bytes + b.stats_bytes + (int64_t)d->ndm * b.rows : b.fb_bytes;
-    b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + (int64_t)es * d->nsub * d->block_len +
-              (int64_t)sizeof(float) * d->nsub + (u8 ? (int64_t)sizeof(float) * 2 * d->ndm * b.rows : 0);
+    b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + 2 * (int64_t)es * d->nsub * d->block_len +
+              2 * (int64_t)sizeof(float) * d->nsub + (u8 ? (int64_t)sizeof(float) * 2 * d->ndm * b.rows : 0);
     // admission: resident state of every beam + the slots held + the slots one block of this beam
     // needs (an output slot; 8-bit beams also a float32 scratch slot) unless the pool has them
     auto need = [&] {
@@ -426,8 +444,13 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaMalloc((void **)&b.stage[i], (size_t)d->nsub * b.cap * 16);
-    if (e == cudaSuccess) e = cudaMalloc(&b.d_blk, es * (size_t)d->nsub * (size_t)d->block_len);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b.d_scale, sizeof(float) * d->nsub);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        e = cudaMalloc(&b.d_blk[i], es * (size_t)d->nsub * (size_t)d->block_len);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&b.d_scale[i], sizeof(float) * d->nsub);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_ready[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_free[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b.cp, cudaStreamNonBlocking);
     if (e == cudaSuccess && u8 && redig_reserve(b.plan) != CDMT_OK) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
