@@ -748,9 +748,17 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
     const auto *src = static_cast<const float4 *>(h_in);
     const int64_t ostride = kcm * p->seglen;   // floats per row of an output slot
     int bi = 0, bo = 0;
-    for (int64_t k0 = 0; k0 < p->nseg; k0 += kcm, bi = (bi + 1) % 3) {
+    // float32 output chosen by the plan: the first block is a quarter of the others (at least the
+    // 16 items per SM of a full GPU), so the pipeline fills after a short copy-in and compute
+    int64_t first = kcm;
+    if (!u8 && p->host_block_opt <= 0) {
+        const int64_t per_seg = std::max<int64_t>(1, ntile * p->nsub * p->nchan);
+        const int64_t fill = (16 * std::max(1, p->nsm) + per_seg - 1) / per_seg;
+        first = std::max<int64_t>(1, std::min<int64_t>(kcm, std::max<int64_t>(kcm / 4, fill)));
+    }
+    for (int64_t k0 = 0; k0 < p->nseg; k0 += (k0 == 0 ? first : kcm), bi = (bi + 1) % 3) {
         Staging &si = p->stage[bi];
-        const int kc = (int)std::min<int64_t>(kcm, p->nseg - k0);
+        const int kc = (int)std::min<int64_t>(k0 == 0 ? first : kcm, p->nseg - k0);
         const int64_t span = (kc - 1) * p->nvalid + p->nbin;
         CK(p, cudaStreamWaitEvent(p->s_h2d, si.in_free, 0));
         CK(p, cudaMemcpy2DAsync(si.in, p->span_max * 16, src + k0 * p->nvalid, p->nsamp * 16, span * 16, p->nsub,
