@@ -121,20 +121,20 @@ def test_execute_host_matches_execute(cdmt):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("uniform", [True, False])
-def test_execute_host_dm_ranges(cdmt, prec, uniform):
+@pytest.mark.parametrize("uniform,ndm", [(True, 70), (False, 70), (True, 97)])
+def test_execute_host_dm_ranges(cdmt, prec, uniform, ndm):
     """float32 host output of a plan with one DM tile runs each block's DM stage in
-    DM ranges (here 2 of 35 DMs, 3 blocks of 3 segments): bit-identical to the
-    device path, for evenly spaced (phase steps from the range's offset) and
-    uneven DM lists."""
+    DM ranges (70 DMs: 2 of 35; 97 DMs: 33, 33 and 31; 3 blocks of 3 segments):
+    bit-identical to the device path, for evenly spaced (phase steps from the
+    range's offset) and uneven DM lists."""
     import torch
     nsub, nsamp = 2, 9 * (1 << 14) + 5
     x = synth.noise(91, nsub, nsamp)
-    dms = [0.25 * i for i in range(70)]
+    dms = [17.0 * i / ndm for i in range(ndm)]
     if not uniform:
-        dms = sorted(np.random.default_rng(5).uniform(0.0, 17.0, 70).tolist())
+        dms = sorted(np.random.default_rng(5).uniform(0.0, 17.0, ndm).tolist())
     precision = cdmt.CDMT_PREC_FP16 if prec == "fp16" else cdmt.CDMT_PREC_FP32
-    plan = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, dm_tile=70, precision=precision, host_block=3)
+    plan = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, dm_tile=ndm, precision=precision, host_block=3)
     assert plan.info["nseg"] == 9
     dev = gpu_filterbank(plan, x)
     hin = torch.from_numpy(x).pin_memory()
