@@ -81,5 +81,9 @@ int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t i
 // Allocates the plan's per-row (mean, gain) array of the redigitisation if it is missing.
 int redig_reserve(cdmt_plan_s *p);
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
-                  cudaStream_t st, double sk_nsigma = 0.0, uint8_t *d_flags = nullptr);
+                  cudaStream_t st, double sk_nsigma = 0.0, uint8_t *d_flags = nullptr, int ndm_r = 0);
+// The forward stage, and the DM stage of a DM range of every tile (cdmt_host.cu).
+int enqueue_forward(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st);
+int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, int kc, int dm_off, int dm_cnt,
+               cudaStream_t st);
 }  // namespace cdmt

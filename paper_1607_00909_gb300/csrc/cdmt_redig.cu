@@ -259,16 +259,17 @@ int redig_reserve(cdmt_plan_s *p)
 }
 
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
-                  cudaStream_t st, double sk_nsigma, uint8_t *d_flags)
+                  cudaStream_t st, double sk_nsigma, uint8_t *d_flags, int ndm_r)
 {
     const int rows = p->nsub * p->nchan;
+    const int ndm = ndm_r > 0 ? ndm_r : p->ndm;   // DMs in d_fb (a range of the plan's)
     if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
     const int rc = redig_reserve(p);
     if (rc != CDMT_OK) return rc;
     // float4 reads need every row to start 16-byte aligned (rows' last nt % 4 samples are read singly)
     const bool vec = stride % 4 == 0 && (reinterpret_cast<uintptr_t>(d_fb) & 15) == 0;
-    const unsigned nrow = (unsigned)((int64_t)p->ndm * rows);
-    const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)p->ndm);
+    const unsigned nrow = (unsigned)((int64_t)ndm * rows);
+    const dim3 grid((unsigned)((nt + kTile - 1) / kTile), (unsigned)((rows + kTile - 1) / kTile), (unsigned)ndm);
     const unsigned nrow8 = (nrow + 7) / 8;
     SkRule sk;
     sk.nsigma = sk_nsigma > 0.0 ? (float)sk_nsigma : 0.f;

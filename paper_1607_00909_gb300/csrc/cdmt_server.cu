@@ -100,7 +100,8 @@ struct Beam {
     cudaStream_t cp = nullptr;
     cudaEvent_t blk_ready[2] = {nullptr, nullptr}, blk_free[2] = {nullptr, nullptr};
     int cb = 0;                 // block buffer of the next block
-    int64_t fb_bytes = 0;       // one block's float32 filterbank (max_seg segments)
+    int64_t fb_bytes = 0;       // float32 filterbank of one block (8-bit beams: of one DM range of a block)
+    int nq = 1, qdm = 0;        // 8-bit beams: DM ranges per block and DMs per range
     int64_t codes_bytes = 0;    // 8-bit beams: codes part of a slot (16-byte multiple); statistics follow,
     int64_t stats_bytes = 0;    // then one flag byte per row
     cudaStream_t st = nullptr;
@@ -245,14 +246,28 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
     nseg = std::min(nseg, b.max_seg);
     if (nseg > 0) {
         uint8_t *slot = v->slots[r.slot].p;
-        const bool u8 = b.d.out_dtype == CDMT_OUT_U8;
-        float *fb = reinterpret_cast<float *>(u8 ? v->slots[r.scratch].p : slot);
-        if (enqueue_chunk(b.plan, stage, b.cap, 0, fb, b.stride, 0, (int)nseg, b.st) != CDMT_OK)
-            return false;
-        if (u8 && redig_enqueue(b.plan, fb, nseg * b.seglen, b.stride, slot,
-                                reinterpret_cast<float *>(slot + b.codes_bytes), b.st, b.d.sk_nsigma,
-                                slot + b.codes_bytes + b.stats_bytes) != CDMT_OK)
-            return false;
+        if (b.d.out_dtype != CDMT_OUT_U8) {
+            if (enqueue_chunk(b.plan, stage, b.cap, 0, reinterpret_cast<float *>(slot), b.stride, 0, (int)nseg, b.st) !=
+                CDMT_OK)
+                return false;
+        } else {
+            // 8-bit: the DM stage range by range into the scratch slot, each range redigitised into its
+            // part of the output slot (codes [ndm][samples][rows], then (mu, sigma), then flags)
+            if (enqueue_forward(b.plan, stage, b.cap, 0, (int)nseg, b.st) != CDMT_OK) return false;
+            float *fb = reinterpret_cast<float *>(v->slots[r.scratch].p);
+            const int64_t samples = nseg * b.seglen;
+            for (int q = 0; q < b.nq; q++) {
+                const int lo = q * b.qdm, cnt = std::min(b.qdm, b.d.ndm - lo);
+                if (enqueue_dm(b.plan, fb, b.stride, 0, (int)nseg, b.nq > 1 ? lo : 0, b.nq > 1 ? cnt : 0, b.st) !=
+                    CDMT_OK)
+                    return false;
+                if (redig_enqueue(b.plan, fb, samples, b.stride, slot + (int64_t)lo * samples * b.rows,
+                                  reinterpret_cast<float *>(slot + b.codes_bytes) + (int64_t)lo * b.rows * 2, b.st,
+                                  b.d.sk_nsigma, slot + b.codes_bytes + b.stats_bytes + (int64_t)lo * b.rows, cnt) !=
+                    CDMT_OK)
+                    return false;
+            }
+        }
     }
     const int64_t used = nseg * b.S;
     const int64_t tail = avail - used;
@@ -412,7 +427,11 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     const size_t es = d->in_dtype == CDMT_IN_I8 ? 4 : 16;
     const bool u8 = d->out_dtype == CDMT_OUT_U8;
     b.stride = (b.max_seg * b.seglen + 3) / 4 * 4;   // rows 16-byte aligned
-    b.fb_bytes = (int64_t)sizeof(float) * d->ndm * b.rows * b.stride;
+    // 8-bit beams of a plan with one DM tile: the block's DM stage in up to 4 ranges of at least 32
+    // DMs, so the float32 scratch of a block in flight is a quarter of its filterbank
+    b.nq = u8 && inf.dm_tile >= d->ndm ? std::max(1, std::min(4, d->ndm / 32)) : 1;
+    b.qdm = (d->ndm + b.nq - 1) / b.nq;
+    b.fb_bytes = (int64_t)sizeof(float) * (u8 ? b.qdm : d->ndm) * b.rows * b.stride;
     b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;
     b.stats_bytes = (int64_t)sizeof(float) * 2 * d->ndm * b.rows;
     b.out_bytes = u8 ? b.codes_bytes + b.stats_bytes + (int64_t)d->ndm * b.rows : b.fb_bytes;
