@@ -180,6 +180,88 @@ __device__ __forceinline__ uint8_t code8(float v, float2 m)
 // then each output spectrum's 64 bytes (rows reversed) in 4-byte words.  VEC:
 // full-width tiles of 16-byte aligned rows are read as float4 (4 per thread).
 // Rows of the filterbank are `stride` floats apart; nt samples of each are coded.
+// Short rows in one pass: one CTA per R rows of one DM stages them in shared
+// memory by asynchronous copies (R x nt floats, row stride nt + 1 so that the
+// code pass's column reads meet distinct banks), takes each row's statistics from there (as
+// k_redig_stats_rows: FP32 mean, then mean squared deviation; spectral-kurtosis
+// flag) and writes the R rows' codes of every sample, rows reversed, as 4-byte
+// words: one read of the filterbank instead of two.
+template <int R>
+__global__ void __launch_bounds__(256) k_redig_fused(const float *__restrict__ fb, int rows, int64_t nt,
+                                                     int64_t stride, uint8_t *__restrict__ out,
+                                                     float *__restrict__ stats, SkRule sk)
+{
+    extern __shared__ float sm[];
+    const int ldr = (int)nt + 1;
+    float *tile = sm;               // [R][ldr]
+    float *mus = sm + R * ldr;      // [R]
+    float *gs = mus + R;            // [R]
+    const int dm = blockIdx.y;
+    const int r0 = blockIdx.x * R;
+    const int nr = min(R, rows - r0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float *src = fb + ((int64_t)dm * rows + r0) * stride;
+    // the tile by asynchronous 4-byte copies (all of a thread's copies in flight at once)
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    for (int r = warp; r < nr; r += 8) {
+        const float *row = src + (int64_t)r * stride;
+        for (int t = lane; t < nt; t += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tile_s + 4u * (uint32_t)(r * ldr + t)),
+                         "l"(row + t)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (int r = warp; r < nr; r += 8) {
+        const float *x = tile + r * ldr;
+        float s1 = 0.f;
+        for (int t = lane; t < nt; t += 32) s1 += x[t];
+        const float mu = warp_sum(s1) / (float)nt;
+        float s2 = 0.f;
+        for (int t = lane; t < nt; t += 32) {
+            const float a = x[t] - mu;
+            s2 = fmaf(a, a, s2);
+        }
+        const float sigma = sqrtf(warp_sum(s2) / (float)nt);
+        if (lane == 0) {
+            const bool flag = sk_flag_f(mu, sigma, nt, sk);
+            mus[r] = mu;
+            gs[r] = sigma > 0.f && !flag ? (float)CDMT_REDIG_LEVELS / sigma : 0.f;
+            const int64_t g = (int64_t)dm * rows + r0 + r;
+            if (sk.flags) sk.flags[g] = flag;
+            if (stats) {
+                stats[2 * g] = mu;
+                stats[2 * g + 1] = sigma;
+            }
+        }
+    }
+    __syncthreads();
+    // spectrum t of this DM: row r0 + rr at position rows - 1 - r0 - rr
+    uint8_t *dst = out + (int64_t)dm * nt * rows + (rows - r0 - nr);
+    if (nr == R && (rows & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 3) == 0) {
+        constexpr int W = R / 4;    // 4-byte words of the R rows in one spectrum
+        for (int64_t i = threadIdx.x; i < nt * W; i += blockDim.x) {
+            const int t = (int)(i / W), wd = (int)(i % W);
+            const int rr = R - 1 - 4 * wd;   // rows rr, rr-1, rr-2, rr-3 at positions 4wd .. 4wd+3
+            uint32_t v = 0;
+            #pragma unroll
+            for (int b = 0; b < 4; b++)
+                v |= (uint32_t)code8(tile[(rr - b) * ldr + t], make_float2(mus[rr - b], gs[rr - b])) << (8 * b);
+            *reinterpret_cast<uint32_t *>(dst + (int64_t)t * rows + 4 * wd) = v;
+        }
+    } else {
+        for (int64_t i = threadIdx.x; i < nt * nr; i += blockDim.x) {
+            const int t = (int)(i / nr), pos = (int)(i % nr);
+            const int rr = nr - 1 - pos;
+            dst[(int64_t)t * rows + pos] = code8(tile[rr * ldr + t], make_float2(mus[rr], gs[rr]));
+        }
+    }
+}
+
+// Dynamic shared memory of k_redig_fused<R> for rows of nt samples.
+constexpr size_t fused_smem(int r, int64_t nt) { return sizeof(float) * ((size_t)r * (size_t)(nt + 1) + 2 * (size_t)r); }
+constexpr size_t kFusedSmemMax = 200 * 1024;
+
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ fb, const float2 *__restrict__ mg,
                                                      uint8_t *__restrict__ out, int rows, int64_t nt, int64_t stride)
@@ -275,6 +357,27 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
     sk.nsigma = sk_nsigma > 0.0 ? (float)sk_nsigma : 0.f;
     sk.k = 2 * p->nint;
     sk.flags = d_flags;
+    // short rows: one pass, 32 (or 16) rows of a DM staged in shared memory
+    const int fr = fused_smem(32, nt) <= kFusedSmemMax ? 32 : fused_smem(16, nt) <= kFusedSmemMax ? 16 : 0;
+    if (fr) {
+        const size_t smem = fused_smem(fr, nt);
+        static bool attr32 = false, attr16 = false;
+        bool &attr = fr == 32 ? attr32 : attr16;
+        if (!attr) {
+            const cudaError_t ea = fr == 32 ? cudaFuncSetAttribute(k_redig_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                   (int)kFusedSmemMax)
+                                            : cudaFuncSetAttribute(k_redig_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                   (int)kFusedSmemMax);
+            if (ea != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(ea));
+            attr = true;
+        }
+        const dim3 fg((unsigned)((rows + fr - 1) / fr), (unsigned)ndm);
+        if (fr == 32) k_redig_fused<32><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk);
+        else k_redig_fused<16><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(e));
+        return CDMT_OK;
+    }
     if (vec) {
         if (nt < kShortRow) k_redig_stats_rows<true><<<nrow8, 256, 0, st>>>(d_fb, nrow, nt, stride, p->redig_mg, d_stats, sk);
         else k_redig_stats<true><<<nrow, 256, 0, st>>>(d_fb, nt, stride, p->redig_mg, d_stats, sk);
