@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(256) k_redig_fused(const float *__restrict__ f
 
 // Dynamic shared memory of k_redig_fused<R> for rows of nt samples.
 constexpr size_t fused_smem(int r, int64_t nt) { return sizeof(float) * ((size_t)r * (size_t)(nt + 1) + 2 * (size_t)r); }
-constexpr size_t kFusedSmemMax = 200 * 1024;
+// at most 110 KB, so that two CTAs share an SM (one CTA per SM leaves too few copies in flight)
+constexpr size_t kFusedSmemMax = 110 * 1024;
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_redig_codes(const float *__restrict__ fb, const float2 *__restrict__ mg,
