@@ -427,9 +427,15 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     const size_t es = d->in_dtype == CDMT_IN_I8 ? 4 : 16;
     const bool u8 = d->out_dtype == CDMT_OUT_U8;
     b.stride = (b.max_seg * b.seglen + 3) / 4 * 4;   // rows 16-byte aligned
-    // 8-bit beams of a plan with one DM tile: the block's DM stage in up to 4 ranges of at least 32
-    // DMs, so the float32 scratch of a block in flight is a quarter of its filterbank
-    b.nq = u8 && inf.dm_tile >= d->ndm ? std::max(1, std::min(4, d->ndm / 32)) : 1;
+    // 8-bit beams of a plan with one DM tile: when a block's float32 filterbank would take more than a
+    // sixth of the HBM budget as scratch, the block's DM stage runs in 2 or 4 ranges (of at least 32
+    // DMs) through a scratch of one range (one launch is faster when memory allows: 436.6 against
+    // 426.7 DM-trial Gsamples/s on 8 beams of 288 subbands)
+    b.nq = 1;
+    if (u8 && inf.dm_tile >= d->ndm) {
+        const int64_t full = (int64_t)sizeof(float) * d->ndm * b.rows * b.stride;
+        while (b.nq < 4 && full / b.nq > v->o.hbm_budget / 6 && d->ndm / (2 * b.nq) >= 32) b.nq *= 2;
+    }
     b.qdm = (d->ndm + b.nq - 1) / b.nq;
     b.fb_bytes = (int64_t)sizeof(float) * (u8 ? b.qdm : d->ndm) * b.rows * b.stride;
     b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;

@@ -164,3 +164,43 @@ def test_u8_blocks_are_the_redigitised_float_blocks(cdmt, orc):
         srv.release(ru)
     srv.close()
     assert checked >= 2   # 8 blocks of 24576 samples complete 3 segments of N = 65536
+
+
+def test_u8_blocks_in_dm_ranges_under_a_small_budget(cdmt, orc):
+    """An 8-bit beam whose block filterbank would take more than a sixth of the HBM
+    budget runs each block's DM stage in 2 ranges through a half-size scratch:
+    its codes, statistics and flags equal the oracle's redigitisation of a float32
+    twin beam (on a server with the default budget) fed the same blocks."""
+    import torch
+    from test_redig_gpu import _check_sk
+    b = dict(nsub=2, block_len=1 << 14, f_centre=140.0, dm_first=0.0, dm_step=0.25, ndm=64, nchan=8, nint=4, seed=57)
+    rows, L, nbin = b["nsub"] * b["nchan"], b["block_len"], 4096 * b["nchan"]
+    dms = [b["dm_first"] + i * b["dm_step"] for i in range(b["ndm"])]
+    nd = orc.overlap(b["nsub"], b["f_centre"], BW, dms, b["nchan"], b["nint"], nbin)
+    S = nbin - nd * b["nchan"]
+    seglen = (nbin // b["nchan"] - nd) // b["nint"]
+    max_seg = L // S + 1
+    stride = (max_seg * seglen + 3) // 4 * 4
+    full = 4 * b["ndm"] * rows * stride              # one block's float32 filterbank
+    budget = 5 * full                                # full > budget / 6 >= full / 2: two ranges
+    x = _inputs([b])[0]
+    blocks = [torch.from_numpy(np.ascontiguousarray(x[:, k * L:(k + 1) * L])).pin_memory() for k in range(NBLK)]
+    servers = [cdmt.Server(), cdmt.Server(hbm_budget=budget)]
+    ids = [srv.add_beam(b["nsub"], L, b["f_centre"], BW, b["dm_first"], b["dm_step"], b["ndm"], b["nchan"],
+                        b["nint"], dm_tile=b["ndm"], out_dtype=od, sk_nsigma=2.5)
+           for srv, od in zip(servers, (cdmt.CDMT_OUT_F32, cdmt.CDMT_OUT_U8))]
+    checked = 0
+    for k in range(NBLK):
+        ra, ru = (srv.submit(i, blocks[k].data_ptr()) for srv, i in zip(servers, ids))
+        a, u = servers[0].wait(ra, 120.0), servers[1].wait(ru, 120.0)
+        assert (a.first_sample, a.samples) == (u.first_sample, u.samples)
+        if u.samples > 0:
+            fb = servers[0].block_view(a, b["ndm"], rows).cpu().numpy()
+            codes, stats, flags = (t.cpu().numpy() for t in servers[1].block_u8_view(u, b["ndm"], rows))
+            _check_sk(orc, fb, codes, stats, flags, 2 * b["nint"], 2.5)
+            checked += 1
+        servers[0].release(ra)
+        servers[1].release(ru)
+    for srv in servers:
+        srv.close()
+    assert checked >= 4
