@@ -379,7 +379,7 @@ def gpu_arm(args, w):
             (clocks or {}).get("sm_max_mhz") or MEASURED.get("sm_max_mhz") or 2070.0) * 1e6
         incoh = {"ms_per_launch": ims, "trials": nk_, "ddm": [lo_, step_], "nt_out": nt_o,
                  "adds_per_launch": adds, "g_adds_per_s": adds / ims / 1e6, "bound": "alu",
-                 "peak_g_adds_per_s": peak_adds / 1e9, "frac": adds / ims / 1e3 / peak_adds,
+                 "peak_g_adds_per_s": peak_adds / 1e9, "frac": (adds / (ims / 1e3)) / peak_adds,
                  "output_bytes": io.numel() * 4,
                  "note": "FP32 adds of shifted channel rows; peak = SMs x 128 lanes x SM clock; not part of the step"}
         del io
