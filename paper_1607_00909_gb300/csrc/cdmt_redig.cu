@@ -181,39 +181,48 @@ __device__ __forceinline__ uint8_t code8(float v, float2 m)
 // full-width tiles of 16-byte aligned rows are read as float4 (4 per thread).
 // Rows of the filterbank are `stride` floats apart; nt samples of each are coded.
 // Short rows in one pass: one CTA per R rows of one DM stages them in shared
-// memory by asynchronous copies (R x nt floats, row stride nt + 1 so that the
-// code pass's column reads meet distinct banks), takes each row's statistics from there (as
-// k_redig_stats_rows: FP32 mean, then mean squared deviation; spectral-kurtosis
-// flag) and writes the R rows' codes of every sample, rows reversed, as 4-byte
-// words: one read of the filterbank instead of two.
+// memory by asynchronous copies (16-byte chunks where rows are 16-byte aligned),
+// takes each row's statistics from there (as k_redig_stats_rows: FP32 mean,
+// then mean squared deviation; spectral-kurtosis flag) and writes the R rows'
+// codes of every sample, rows reversed, as 4-byte words: one read of the
+// filterbank instead of two.  Row r starts at r * ldr + 4 ((r / 4) mod 8)
+// floats (ldr a multiple of 32): the code pass reads 8 rows 4 apart at 4
+// consecutive samples per instruction, which then meet 32 distinct banks.
+__host__ __device__ constexpr int fused_ldr(int64_t nt) { return (int)((nt + 31) / 32 * 32) + 32; }
+
 template <int R>
 __global__ void __launch_bounds__(256) k_redig_fused(const float *__restrict__ fb, int rows, int64_t nt,
                                                      int64_t stride, uint8_t *__restrict__ out,
-                                                     float *__restrict__ stats, SkRule sk)
+                                                     float *__restrict__ stats, SkRule sk, bool vec)
 {
-    extern __shared__ float sm[];
-    const int ldr = (int)nt + 1;
+    extern __shared__ __align__(16) float sm[];
+    const int ldr = fused_ldr(nt);
     float *tile = sm;               // [R][ldr]
     float *mus = sm + R * ldr;      // [R]
     float *gs = mus + R;            // [R]
+    auto at = [&](int r, int t) { return r * ldr + 4 * ((r >> 2) & 7) + t; };
     const int dm = blockIdx.y;
     const int r0 = blockIdx.x * R;
     const int nr = min(R, rows - r0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float *src = fb + ((int64_t)dm * rows + r0) * stride;
-    // the tile by asynchronous 4-byte copies (all of a thread's copies in flight at once)
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    const int n4 = vec ? (int)(nt / 4) : 0;   // 16-byte chunks per row; samples from 4 n4 on singly
     for (int r = warp; r < nr; r += 8) {
         const float *row = src + (int64_t)r * stride;
-        for (int t = lane; t < nt; t += 32)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tile_s + 4u * (uint32_t)(r * ldr + t)),
+        for (int c = lane; c < n4; c += 32)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tile_s + 4u * (uint32_t)at(r, 4 * c)),
+                         "l"(row + 4 * c)
+                         : "memory");
+        for (int t = 4 * n4 + lane; t < nt; t += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tile_s + 4u * (uint32_t)at(r, t)),
                          "l"(row + t)
                          : "memory");
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     for (int r = warp; r < nr; r += 8) {
-        const float *x = tile + r * ldr;
+        const float *x = tile + at(r, 0);
         float s1 = 0.f;
         for (int t = lane; t < nt; t += 32) s1 += x[t];
         const float mu = warp_sum(s1) / (float)nt;
@@ -246,20 +255,20 @@ __global__ void __launch_bounds__(256) k_redig_fused(const float *__restrict__ f
             uint32_t v = 0;
             #pragma unroll
             for (int b = 0; b < 4; b++)
-                v |= (uint32_t)code8(tile[(rr - b) * ldr + t], make_float2(mus[rr - b], gs[rr - b])) << (8 * b);
+                v |= (uint32_t)code8(tile[at(rr - b, t)], make_float2(mus[rr - b], gs[rr - b])) << (8 * b);
             *reinterpret_cast<uint32_t *>(dst + (int64_t)t * rows + 4 * wd) = v;
         }
     } else {
         for (int64_t i = threadIdx.x; i < nt * nr; i += blockDim.x) {
             const int t = (int)(i / nr), pos = (int)(i % nr);
             const int rr = nr - 1 - pos;
-            dst[(int64_t)t * rows + pos] = code8(tile[rr * ldr + t], make_float2(mus[rr], gs[rr]));
+            dst[(int64_t)t * rows + pos] = code8(tile[at(rr, t)], make_float2(mus[rr], gs[rr]));
         }
     }
 }
 
 // Dynamic shared memory of k_redig_fused<R> for rows of nt samples.
-constexpr size_t fused_smem(int r, int64_t nt) { return sizeof(float) * ((size_t)r * (size_t)(nt + 1) + 2 * (size_t)r); }
+constexpr size_t fused_smem(int r, int64_t nt) { return sizeof(float) * ((size_t)r * (size_t)fused_ldr(nt) + 2 * (size_t)r); }
 // at most 110 KB, so that two CTAs share an SM (one CTA per SM leaves too few copies in flight)
 constexpr size_t kFusedSmemMax = 110 * 1024;
 
@@ -373,8 +382,8 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
             attr = true;
         }
         const dim3 fg((unsigned)((rows + fr - 1) / fr), (unsigned)ndm);
-        if (fr == 32) k_redig_fused<32><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk);
-        else k_redig_fused<16><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk);
+        if (fr == 32) k_redig_fused<32><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk, vec);
+        else k_redig_fused<16><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk, vec);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(e));
         return CDMT_OK;
