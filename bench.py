@@ -237,6 +237,65 @@ def sampled_error(w, x, out, info, ntile=8, seed=5):
             "rel_rms": float(np.linalg.norm(d) / np.linalg.norm(o)), "tiles": ntile}
 
 
+def time_cufft_unfused(w, xin, out, info, dev, stream, args):
+    """The paper's own design on the same GPU, as a timed comparison (not the product path):
+    batched cuFFT transforms (torch.fft, unitary) with the chirp multiply, the per-channel swap and
+    backward FFT, detection and integration as separate passes through device memory for every DM
+    (Sec. 3, Algorithm 1 with cuFFT).  Chirp phases DM K are reduced modulo 1 in FP64 per DM.
+    Returns throughput, time per step and the largest difference from the headline filterbank."""
+    import torch
+    nsub, nchan, nint = w.nsub, w.nchan, w.nint
+    N, M, nd, S, nseg = info["nbin"], info["mbin"], info["nd"], info["nvalid"], info["nseg"]
+    bw = w.bw
+    seglen = (M - nd) // nint
+    D = 4.148808e3
+    # K [nsub][N] in cycles per unit DM (Eq. 1, per channel), FP64 on the host
+    s_idx = np.arange(nsub)[:, None, None]
+    c_idx = np.arange(nchan)[None, :, None]
+    j = np.arange(M)[None, None, :]
+    nu_s = w.f_centre + (s_idx - 0.5 * (nsub - 1)) * bw
+    nu_c = nu_s - 0.5 * bw + (c_idx + 0.5) * bw / nchan
+    nu = (j - M / 2) * bw / N
+    K = torch.from_numpy((1e6 * D * nu * nu / (nu_c * nu_c * (nu_c + nu))).reshape(nsub, N)).to(dev)
+    xc = torch.view_as_complex(xin.view(nsub, w.nsamp, 2, 2))            # [nsub][nsamp][pol]
+    dms = [float(v) for v in w.dms]
+    o = torch.empty((len(dms), nsub * nchan, nseg * seglen), dtype=torch.float32, device=dev)
+
+    def step():
+        seg = xc.transpose(1, 2).unfold(2, N, S)                           # [nsub][pol][nseg][N]
+        X = torch.fft.fftshift(torch.fft.fft(seg, norm="ortho"), dim=-1)
+        for d, dm in enumerate(dms):
+            ph = dm * K
+            ph = ph - torch.round(ph)
+            H = torch.polar(torch.ones_like(ph, dtype=torch.float32), (-2.0 * np.pi * ph).to(torch.float32))
+            Y = (X * H[:, None, None, :]).view(nsub, 2, nseg, nchan, M)
+            y = torch.fft.ifft(torch.fft.ifftshift(Y, dim=-1), norm="ortho")
+            P = (y.real * y.real + y.imag * y.imag).sum(dim=1)             # [nsub][nseg][nchan][M]
+            I = P[..., nd // 2: M - nd // 2].reshape(nsub, nseg, nchan, seglen, nint).sum(dim=-1)
+            o[d] = I.permute(0, 2, 1, 3).reshape(nsub * nchan, nseg * seglen)
+
+    with torch.cuda.stream(stream):
+        step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nstep = 2
+        for _ in range(nstep):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / nstep
+    units = len(dms) * nsub * nseg * S
+    diff = float((o - out).abs().max() / out.mean())
+    del o, K
+    torch.cuda.empty_cache()
+    return {"value": units / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "max_rel_diff_vs_headline": diff,
+            "note": "the paper's unfused design: cuFFT (torch.fft) forward and backward FFTs, chirp multiply, "
+                    "detection and integration as separate device-memory passes per DM; a comparison, "
+                    "not the product path"}
+
+
 def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
     """Plan one precision form, warm up, time args.steps executes; returns a dict."""
     import torch
@@ -385,6 +444,13 @@ def gpu_arm(args, w):
         del io
         log(f"rank {rank}: incoherent: {ims:.2f} ms per launch, {adds / ims / 1e6:.0f} G adds/s")
 
+    # the paper's unfused cuFFT design on the same GPU, beside the fused kernels (rank 0)
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        cufft = time_cufft_unfused(w, xin, out, info, dev, stream, args)
+        log(f"rank {rank}: cuFFT unfused comparison: {cufft['value']:.2f} {UNIT}, {cufft['ms_per_step']:.1f} ms/step, "
+            f"max rel diff vs headline {cufft['max_rel_diff_vs_headline']:.2e}")
+
     # ---- roofline of the dominant kernel of the headline form
     nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
     dd_avg_s = R["dd_ms"] / max(1, R["dd_n"]) / 1e3
@@ -476,6 +542,7 @@ def gpu_arm(args, w):
                 "error_vs_oracle": R.get("error"),
                 "redigitise": redig,
                 "incoherent": incoh,
+                "comparisons": {"cufft_unfused": cufft},
                 "forms": {f: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
                               "dedisperse_ms_per_step": r["dd_ms"] / args.steps,
                               "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error")}
@@ -756,6 +823,7 @@ def main():
     ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
     ap.add_argument("--no-redigitise", action="store_true", help="skip timing the 8-bit redigitisation")
     ap.add_argument("--no-incoherent", action="store_true", help="skip timing the incoherent stage")
+    ap.add_argument("--no-cufft", action="store_true", help="skip timing the unfused cuFFT comparison pipeline")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")
