@@ -165,16 +165,18 @@ int cdmt_plan_info(cdmt_plan_t plan, cdmt_info *info);
  * unpad, detection (Sec. 3) and nint-sample integration.
  *
  *   d_in         DEVICE pointer to the input block (layout above), caller-owned,
- *                16-byte aligned; read only
+ *                16-byte aligned (CDMT_IN_I8: 4-byte aligned); read only
  *   d_out        DEVICE pointer to float32 [ndm][nsub*nchan][nout], caller-owned,
  *                4-byte aligned; fully overwritten
- *   d_scale      DEVICE pointer to nsub float scales for CDMT_IN_I8 input
- *                (ignored, may be NULL, for CDMT_IN_C64)
+ *   d_scale      DEVICE pointer to nsub float scales for CDMT_IN_I8 input: sample
+ *                value = int8 value x scale[subband], in FP32 (required; ignored,
+ *                may be NULL, for CDMT_IN_C64)
  *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream)
  * Asynchronous with respect to the host: returns after enqueueing.  The plan's
  * workspace is reused by every execute, so executes of ONE plan must not
  * overlap on different streams.
- * Errors: CDMT_EINVAL (NULL pointers, misaligned input), CDMT_ECUDA.
+ * Errors: CDMT_EINVAL (NULL pointers, misaligned input, int8 input without
+ * scales), CDMT_ECUDA.
  */
 int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *d_scale,
                  void *cuda_stream);
@@ -188,17 +190,21 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * should be page-locked (cudaHostAlloc / cudaHostRegister) for full speed;
  * pageable memory works but the copies are then synchronous.  Blocks until
  * h_out holds the result.  h_scale is a host array of nsub floats for
- * CDMT_IN_I8 input.
+ * CDMT_IN_I8 input (required then; the input is then 4 bytes per sample, so
+ * its copy to the device is 4x smaller).
  * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_ECUDA.
  */
 /* cdmt_execute_host_u8 - the pipeline of Algorithm 1 up to "redigitize" and
- * "copy to host": like cdmt_execute_host, but each chunk of segments is a data
- * block whose filterbank is redigitised on the device (cdmt_redigitise: the
- * mean and sigma of each (DM, channel) over the block) and copied back as
- * 8-bit codes, 4x fewer bytes than float32.  h_u8: host (pinned for overlap)
- * uint8 [ndm][nout][nsub*nchan], spectra in decreasing frequency.
- * *block_segments (may be NULL) receives the segments per block (the last
- * block may be shorter).  Errors as cdmt_execute_host. */
+ * "copy to host": like cdmt_execute_host, but each block of segments
+ * (cdmt_opts.host_block, or the plan's choice) is a data block whose filterbank
+ * is redigitised on the device (cdmt_redigitise: the mean and sigma of each
+ * (DM, channel) over the block; with cdmt_opts.sk_nsigma > 0 also the
+ * spectral-kurtosis flagging of cdmt_redigitise_sk, flagged rows coded 128)
+ * and copied back as 8-bit codes, 4x fewer bytes than float32.  h_u8: host
+ * (pinned for overlap) uint8 [ndm][nout][nsub*nchan], spectra in decreasing
+ * frequency.  *block_segments (may be NULL) receives the segments per block
+ * (the last block may be shorter).  Errors as cdmt_execute_host, and
+ * CDMT_ENOTSUP for a CDMT_IN_I8 plan (this entry point takes no scales). */
 int cdmt_execute_host_u8(cdmt_plan_t plan, const void *h_in, uint8_t *h_u8, int64_t *block_segments,
                          void *cuda_stream);
 

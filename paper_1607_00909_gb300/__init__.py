@@ -578,13 +578,18 @@ class Plan:
             pass
 
 
-def run(plan: Plan, x, out=None, stream=None):
+def run(plan: Plan, x, out=None, stream=None, scale=None):
     """Convenience for torch CUDA tensors: x float32 [nsub][nsamp][4] on the
-    plan's device, out float32 [ndm][nsub*nchan][nout] (allocated if None).
+    plan's device (int8 [nsub][nsamp][4] with scale float32 [nsub] for a
+    CDMT_IN_I8 plan), out float32 [ndm][nsub*nchan][nout] (allocated if None).
     Enqueues on `stream` (default: torch's current stream) and returns out."""
     import torch
-    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
-        raise ValueError("x must be a contiguous float32 CUDA tensor [nsub][nsamp][4]")
+    i8 = plan.info["in_dtype"] == CDMT_IN_I8
+    want = torch.int8 if i8 else torch.float32
+    if not (x.is_cuda and x.dtype == want and x.is_contiguous()):
+        raise ValueError(f"x must be a contiguous {want} CUDA tensor [nsub][nsamp][4]")
+    if i8 and (scale is None or not (scale.is_cuda and scale.dtype == torch.float32 and scale.numel() == x.shape[0])):
+        raise ValueError("an int8 plan needs scale, a float32 CUDA tensor of nsub values")
     i = plan.info
     if tuple(x.shape) != (i["nsub"], i["nsamp"], 4):
         raise ValueError(f"x has shape {tuple(x.shape)}, plan wants {(i['nsub'], i['nsamp'], 4)}")
@@ -593,5 +598,5 @@ def run(plan: Plan, x, out=None, stream=None):
     if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape) == plan.out_shape()):
         raise ValueError("out must be a contiguous float32 CUDA tensor of the plan's output shape")
     st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
-    plan.execute(x.data_ptr(), out.data_ptr(), 0, st)
+    plan.execute(x.data_ptr(), out.data_ptr(), scale.data_ptr() if i8 else 0, st)
     return out

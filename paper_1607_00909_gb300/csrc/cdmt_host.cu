@@ -229,7 +229,8 @@ void release(cdmt_plan_s *p)
     cudaDeviceSynchronize();
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
-                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab};
+                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab,
+                    p->d_scale_buf};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {
@@ -269,7 +270,7 @@ namespace cdmt {
 // in + (in_k0 + kk) * S, subbands in_stride samples apart) into `out`
 // (rows out_stride floats apart, segment kk at (out_k0 + kk) * seglen).
 // The forward stage of kc segments (segment in_k0 of `in` first) into the plan's spectra.
-int enqueue_forward(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st)
+int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st)
 {
     ForwardArgs fa{};
     fa.in = in;
@@ -285,6 +286,8 @@ int enqueue_forward(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t
     fa.kc = kc;
     fa.nsub = p->nsub;
     fa.r = p->r;
+    fa.i8 = p->in_dtype == CDMT_IN_I8;
+    fa.scale = p->scale_dev;
     CK(p, fp32_forward(fa, st));
     return CDMT_OK;
 }
@@ -351,7 +354,7 @@ int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, i
     return CDMT_OK;
 }
 
-int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
+int enqueue_chunk(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_k0, float *out,
                   int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st)
 {
     int rc;
@@ -426,7 +429,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     if (!(band_lo > 0)) return fail(nullptr, CDMT_EINVAL, "lowest frequency %.6g MHz must be > 0", band_lo);
     if (o.precision != CDMT_PREC_FP32 && o.precision != CDMT_PREC_FP16 && o.precision != CDMT_PREC_BF16)
         return fail(nullptr, CDMT_ENOTSUP, "precision %d not available", o.precision);
-    if (o.in_dtype != CDMT_IN_C64) return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
+    if (o.in_dtype != CDMT_IN_C64 && o.in_dtype != CDMT_IN_I8)
+        return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
     if (o.chirp != CDMT_CHIRP_CHANNEL && o.chirp != CDMT_CHIRP_SUBBAND)
         return fail(nullptr, CDMT_EINVAL, "chirp %d is neither per channel nor per subband", o.chirp);
 
@@ -639,10 +643,13 @@ int cdmt_plan_info(cdmt_plan_t p, cdmt_info *info)
 
 int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_scale, void *cuda_stream)
 {
-    (void)d_scale;
     if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
     if (!d_in || !d_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
-    if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(p, CDMT_EINVAL, "input must be 16-byte aligned");
+    const bool i8 = p->in_dtype == CDMT_IN_I8;
+    if (i8 && !d_scale) return fail(p, CDMT_EINVAL, "int8 input needs the per-subband scales");
+    if (reinterpret_cast<uintptr_t>(d_in) % (i8 ? 4 : 16))
+        return fail(p, CDMT_EINVAL, "input must be %d-byte aligned", i8 ? 4 : 16);
+    p->scale_dev = d_scale;
     if (reinterpret_cast<uintptr_t>(d_out) % 4) return fail(p, CDMT_EINVAL, "output must be 4-byte aligned");
     int cur = 0;
     cudaGetDevice(&cur);
@@ -651,7 +658,7 @@ int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_s
     int rc = CDMT_OK;
     for (int64_t k0 = 0; k0 < p->nseg && rc == CDMT_OK; k0 += p->seg_chunk) {
         const int kc = (int)std::min<int64_t>(p->seg_chunk, p->nseg - k0);
-        rc = enqueue_chunk(p, static_cast<const float4 *>(d_in), p->nsamp, k0, d_out, p->nout, k0, kc, st);
+        rc = enqueue_chunk(p, d_in, p->nsamp, k0, d_out, p->nout, k0, kc, st);
     }
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
@@ -732,10 +739,14 @@ int host_setup(cdmt_plan_s *p, int64_t kc, int64_t out_floats, cudaStream_t st)
 // an output slot each, so the copy back of a block starts after a quarter of its
 // compute (the first one is the pipeline's fill) while its rows stay long.
 // *kc_used receives the segments per block.
-int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8, int64_t *kc_used, cudaStream_t st)
+int host_pipeline(cdmt_plan_s *p, const void *h_in, const float *h_scale, float *h_out, uint8_t *h_u8,
+                  int64_t *kc_used, cudaStream_t st)
 {
     int rc;
     const bool u8 = h_u8 != nullptr;
+    const bool i8 = p->in_dtype == CDMT_IN_I8;
+    const size_t es = i8 ? 4 : 16;   // bytes per input sample
+    if (i8 && !h_scale) return fail(p, CDMT_EINVAL, "int8 input needs the per-subband scales");
     const int64_t kcm = host_block(p, u8);
     const int64_t nrow = (int64_t)p->nsub * p->nchan;
     const int64_t ntile = (p->ndm + p->dm_tile - 1) / p->dm_tile;
@@ -745,7 +756,12 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
     if (u8)
         for (auto &sg : p->stage)
             if (!sg.u8 && (rc = dalloc(p, &sg.u8, (size_t)p->host_out_cap)) != CDMT_OK) return rc;
-    const auto *src = static_cast<const float4 *>(h_in);
+    const auto *src = static_cast<const char *>(h_in);
+    if (i8) {   // the scales go first on the copy stream, so block 0's copy event covers them
+        if (!p->d_scale_buf && (rc = dalloc(p, &p->d_scale_buf, (size_t)p->nsub)) != CDMT_OK) return rc;
+        CK(p, cudaMemcpyAsync(p->d_scale_buf, h_scale, sizeof(float) * p->nsub, cudaMemcpyHostToDevice, p->s_h2d));
+        p->scale_dev = p->d_scale_buf;
+    }
     const int64_t ostride = kcm * p->seglen;   // floats per row of an output slot
     int bi = 0, bo = 0;
     // float32 output chosen by the plan: the first block is a quarter of the others (at least the
@@ -761,8 +777,8 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
         const int kc = (int)std::min<int64_t>(k0 == 0 ? first : kcm, p->nseg - k0);
         const int64_t span = (kc - 1) * p->nvalid + p->nbin;
         CK(p, cudaStreamWaitEvent(p->s_h2d, si.in_free, 0));
-        CK(p, cudaMemcpy2DAsync(si.in, p->span_max * 16, src + k0 * p->nvalid, p->nsamp * 16, span * 16, p->nsub,
-                                cudaMemcpyHostToDevice, p->s_h2d));
+        CK(p, cudaMemcpy2DAsync(si.in, p->span_max * es, src + k0 * p->nvalid * es, p->nsamp * es, span * es,
+                                p->nsub, cudaMemcpyHostToDevice, p->s_h2d));
         CK(p, cudaEventRecord(si.in_ready, p->s_h2d));
         CK(p, cudaStreamWaitEvent(st, si.in_ready, 0));
         if ((rc = enqueue_forward(p, si.in, p->span_max, 0, kc, st)) != CDMT_OK) return rc;
@@ -798,13 +814,12 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, float *h_out, uint8_t *h_u8,
 
 int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float *h_scale, void *cuda_stream)
 {
-    (void)h_scale;
     if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
     if (!h_in || !h_out) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    const int rc = host_pipeline(p, h_in, h_out, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    const int rc = host_pipeline(p, h_in, h_scale, h_out, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }
@@ -816,7 +831,11 @@ int cdmt_execute_host_u8(cdmt_plan_t p, const void *h_in, uint8_t *h_u8, int64_t
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    const int rc = host_pipeline(p, h_in, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
+    if (p->in_dtype == CDMT_IN_I8) {
+        if (cur != p->device) cudaSetDevice(cur);
+        return fail(p, CDMT_ENOTSUP, "int8 input: cdmt_execute_host_u8 takes no scales (use cdmt_execute_host)");
+    }
+    const int rc = host_pipeline(p, h_in, nullptr, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }

@@ -7,7 +7,8 @@
 namespace cdmt {
 
 struct ForwardArgs {
-    const float4 *in;  // first sample of the block's subband 0 (segment 0 of the chunk at in + k0 * nvalid)
+    const void *in;    // first sample of the block's subband 0 (segment 0 of the chunk at in + k0 * nvalid):
+                       // float4 samples, or char4 samples when i8 (times scale[subband])
     float4 *spec;      // [nsub][kc][nchan][M] float4 workspace
     const float2 *tw_a, *tw_b, *tw_n;
     int64_t nsamp;     // samples between consecutive subbands in `in`
@@ -17,6 +18,8 @@ struct ForwardArgs {
     int nchan, kc, nsub, r;
     const int *round_dev = nullptr;  // batches: first segment = *round_dev * kc (k0 ignored)
     int64_t nseg = 0;                // batches: segments of the whole input
+    bool i8 = false;                 // int8 samples (X re, X im, Y re, Y im) ...
+    const float *scale = nullptr;    // ... times a DEVICE per-subband scale
 };
 
 struct DedispArgs {

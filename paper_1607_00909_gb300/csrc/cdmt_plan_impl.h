@@ -60,7 +60,9 @@ struct cdmt_plan_s {
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0, host_block_opt = 0;
     int64_t host_out_cap = 0;
-    double sk_nsigma = 0.0;        // spectral-kurtosis flagging of the 8-bit host output (0: off)      // floats per output slot of the host pipeline (u8 slots: bytes)
+    double sk_nsigma = 0.0;        // spectral-kurtosis flagging of the 8-bit host output (0: off)
+    const float *scale_dev = nullptr;  // int8 input: DEVICE per-subband scales of the current call
+    float *d_scale_buf = nullptr;      // int8 input from host memory: the scales on the device      // floats per output slot of the host pipeline (u8 slots: bytes)
     cdmt::Staging stage[3];        // host pipeline: three blocks in flight (copy in, compute, copy out)
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     // stage timing (cdmt_set_timing / cdmt_stage_times)
@@ -75,7 +77,7 @@ namespace cdmt {
 // overlap n_d of Sec. 2 for a band (defined in cdmt_host.cu); -1 if none < M
 int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin);
 // forward stage + DM stage of kc segments (defined in cdmt_host.cu)
-int enqueue_chunk(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, float *out,
+int enqueue_chunk(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_k0, float *out,
                   int64_t out_stride, int64_t out_k0, int kc, cudaStream_t st);
 // redigitisation of nt samples per row (rows `stride` floats apart) as one block (cdmt_redig.cu)
 // Allocates the plan's per-row (mean, gain) array of the redigitisation if it is missing.
@@ -83,7 +85,7 @@ int redig_reserve(cdmt_plan_s *p);
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
                   cudaStream_t st, double sk_nsigma = 0.0, uint8_t *d_flags = nullptr, int ndm_r = 0);
 // The forward stage, and the DM stage of a DM range of every tile (cdmt_host.cu).
-int enqueue_forward(cdmt_plan_s *p, const float4 *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st);
+int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st);
 int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, int kc, int dm_off, int dm_cnt,
                cudaStream_t st);
 }  // namespace cdmt

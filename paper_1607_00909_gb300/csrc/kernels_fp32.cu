@@ -37,11 +37,13 @@ namespace cdmt {
 constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;  // 2 pi / 2^32
 
 // ---------------------------------------------------------------------------
-template <int R>
+// I8: char4 samples (X re, X im, Y re, Y im) times the subband's scale, in FP32.
+template <int R, bool I8>
 __global__ void __launch_bounds__(16 * R)
-k_forward_decimated(const float4 *__restrict__ in, float4 *__restrict__ spec, const float2 *__restrict__ tw_a,
-                    const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n, int64_t nsamp,
-                    int64_t nvalid, int nchan, int64_t k0, int kc, const int *__restrict__ round_dev, int64_t nseg)
+k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale, float4 *__restrict__ spec,
+                    const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n,
+                    int64_t nsamp, int64_t nvalid, int nchan, int64_t k0, int kc, const int *__restrict__ round_dev,
+                    int64_t nseg)
 {
     // batches: the chunk's first segment is round * kc, read from device memory;
     // segments past the end of the input are skipped
@@ -61,13 +63,27 @@ k_forward_decimated(const float4 *__restrict__ in, float4 *__restrict__ spec, co
     for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
     for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
 
-    const float4 *src = in + (int64_t)s * nsamp + (k0 + kk) * nvalid + n1;
+    const int64_t s0 = (int64_t)s * nsamp + (k0 + kk) * nvalid + n1;
     float2 x[16], y[16];
-    #pragma unroll
-    for (int j2 = 0; j2 < 16; j2++) {
-        float4 v = __ldg(src + (int64_t)nchan * (j2 * T + t));
-        x[j2] = make_float2(v.x, v.y);
-        y[j2] = make_float2(v.z, v.w);
+    if constexpr (I8) {
+        const char4 *src = static_cast<const char4 *>(in) + s0;
+        const float sc = __ldg(scale + s);
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            // products rounded on their own (never contracted into the FFT's additions), so the
+            // result equals that of the dequantised float32 voltages
+            const char4 v = __ldg(src + (int64_t)nchan * (j2 * T + t));
+            x[j2] = make_float2(__fmul_rn((float)v.x, sc), __fmul_rn((float)v.y, sc));
+            y[j2] = make_float2(__fmul_rn((float)v.z, sc), __fmul_rn((float)v.w, sc));
+        }
+    } else {
+        const float4 *src = static_cast<const float4 *>(in) + s0;
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            const float4 v = __ldg(src + (int64_t)nchan * (j2 * T + t));
+            x[j2] = make_float2(v.x, v.y);
+            y[j2] = make_float2(v.z, v.w);
+        }
     }
     __syncthreads();  // twiddles in place
     F::template pass_a<-1>(x, y, ex, ta, t);
@@ -247,7 +263,11 @@ template <int R> static size_t smem_dedisp()
 
 template <int R> static cudaError_t set_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_forward_decimated<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forward<R>());
+    cudaError_t e = cudaFuncSetAttribute(k_forward_decimated<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_forward<R>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_forward_decimated<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_forward<R>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
     if (e != cudaSuccess) return e;
@@ -279,9 +299,13 @@ size_t fp32_dedisp_smem(int r)
 template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t st)
 {
     dim3 g(a.nchan, a.kc, a.nsub);
-    k_forward_decimated<R><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(a.in, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp,
-                                                                    a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
-                                                                    a.round_dev ? a.nseg : INT64_MAX);
+    const int64_t nseg = a.round_dev ? a.nseg : INT64_MAX;
+    if (a.i8)
+        k_forward_decimated<R, true><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(
+            a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev, nseg);
+    else
+        k_forward_decimated<R, false><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(
+            a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev, nseg);
 }
 
 template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t st)

@@ -212,3 +212,41 @@ def test_lofar64_full_size_sampled_tiles(cdmt, orc):
     emax, erms = rel_errors(gt, o)
     print(f"lofar64 tiles: rel_max {emax:.3e} rel_rms {erms:.3e}")
     assert emax <= TOL_MAX and erms <= TOL_RMS
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_int8_input_equals_dequantised_float(cdmt, prec):
+    """CDMT_IN_I8 plans read 4-byte samples times a per-subband scale (the paper's
+    8-bit voltages): bit-identical to a float32 plan on the dequantised voltages,
+    on the device and through the host pipeline; the scales are required, and the
+    8-bit host entry point, which takes none, refuses int8 plans."""
+    import torch
+    nsub, nsamp = 3, 4 * (1 << 14) + 77
+    x = synth.noise(71, nsub, nsamp)
+    scale = (np.abs(x).reshape(nsub, -1).max(axis=1) / 127.0).astype(np.float32)
+    q = np.clip(np.rint(x / scale[:, None, None]), -127, 127).astype(np.int8)
+    deq = q.astype(np.float32) * scale[:, None, None]
+    precision = cdmt.CDMT_PREC_FP16 if prec == "fp16" else cdmt.CDMT_PREC_FP32
+    dms = [0.0, 3.0, 6.0]
+    pf = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, precision=precision)
+    want = gpu_filterbank(pf, deq)
+    pf.close()
+    pi = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, precision=precision, in_dtype=cdmt.CDMT_IN_I8,
+               host_block=2)
+    assert pi.info["in_dtype"] == cdmt.CDMT_IN_I8
+    qd, sd = torch.from_numpy(q).cuda(), torch.from_numpy(scale).cuda()
+    got = cdmt.run(pi, qd, scale=sd)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), want)
+    hin, hsc = torch.from_numpy(q).pin_memory(), torch.from_numpy(scale)
+    hout = torch.full(pi.out_shape(), float("nan"), dtype=torch.float32).pin_memory()
+    pi.execute_host(hin.data_ptr(), hout.data_ptr(), hsc.data_ptr(), 0)
+    assert np.array_equal(hout.numpy(), want)
+    with pytest.raises(cdmt.CdmtError) as e:
+        pi.execute(qd.data_ptr(), got.data_ptr(), 0, 0)
+    assert e.value.status == cdmt.CDMT_EINVAL
+    u8 = torch.empty((len(dms), pi.out_shape()[2], pi.out_shape()[1]), dtype=torch.uint8).pin_memory()
+    with pytest.raises(cdmt.CdmtError) as e:
+        pi.execute_host_u8(hin.data_ptr(), u8.data_ptr())
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+    pi.close()
