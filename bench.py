@@ -174,21 +174,24 @@ def reference_arm(args, w):
 # ---------------------------------------------------------------- GPU leg
 
 
-def kernel_source_hash():
+def kernel_source_hash(form="fp16"):
+    """Hash of the sources the form's DM-stage kernel is compiled from (the key of its traffic figure)."""
+    files = ("kernels_fp32.cu", "fft_core.cuh", "cdmt_internal.h") if form == "fp32" else \
+        ("kernels_tc.cu", "fft_core.cuh", "tc_ptx.cuh", "cdmt_internal.h")
     h = hashlib.sha256()
-    for f in ("kernels_fp32.cu", "kernels_tc.cu", "fft_core.cuh", "tc_ptx.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1607_00909_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-# DRAM bytes per DM-trial x sample of k_dedisperse from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch / units per launch), valid for the kernel
-# source whose hash is recorded; null otherwise.
+# DRAM bytes per DM-trial x sample of the DM-stage kernel from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
+# whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
     # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent): 544.5 MB read + 2071.6 MB
     # written for 4.253e9 units (ncu --set full, 4th launch)
-    "9967aa3bac6e92d8:fp16": 0.6151,
+    "587da1c0029d0c5f:fp16": 0.6151,
 }
 
 try:
@@ -477,7 +480,7 @@ def gpu_arm(args, w):
                     "flops_per_unit": tc_flops_unit,
                     "nominal_fft_tflops": fft_flops_unit * units / dd_avg_s / 1e12,
                     "peak_basis": "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); FP16 dense rate equals BF16"}
-    tr = NCU_TRAFFIC.get(kernel_source_hash() + ":" + head)
+    tr = NCU_TRAFFIC.get(kernel_source_hash(head) + ":" + head)
     roofline.update({"traffic": tr * units if tr else None, "kernel_ms_per_launch": dd_avg_s * 1e3,
                      "share_of_step": R["dd_ms"] / max(1e-9, R["dd_ms"] + R["fwd_ms"])})
 
