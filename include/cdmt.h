@@ -203,10 +203,17 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * and copied back as 8-bit codes, 4x fewer bytes than float32.  h_u8: host
  * (pinned for overlap) uint8 [ndm][nout][nsub*nchan], spectra in decreasing
  * frequency.  *block_segments (may be NULL) receives the segments per block
- * (the last block may be shorter).  Errors as cdmt_execute_host, and
- * CDMT_ENOTSUP for a CDMT_IN_I8 plan (this entry point takes no scales). */
+ * (the last block may be shorter).  Errors as cdmt_execute_host (a
+ * CDMT_IN_I8 plan needs cdmt_execute_host_u8_ex, which takes the scales). */
 int cdmt_execute_host_u8(cdmt_plan_t plan, const void *h_in, uint8_t *h_u8, int64_t *block_segments,
                          void *cuda_stream);
+
+/* cdmt_execute_host_u8_ex - cdmt_execute_host_u8 with h_scale, a host array of
+ * nsub floats for CDMT_IN_I8 input (ignored, may be NULL, for CDMT_IN_C64):
+ * the paper's own I/O, 8-bit voltages in and an 8-bit filterbank out.  Errors
+ * as cdmt_execute_host. */
+int cdmt_execute_host_u8_ex(cdmt_plan_t plan, const void *h_in, const float *h_scale, uint8_t *h_u8,
+                            int64_t *block_segments, void *cuda_stream);
 
 int cdmt_execute_host(cdmt_plan_t plan, const void *h_in, float *h_out, const float *h_scale,
                       void *cuda_stream);

@@ -144,6 +144,7 @@ def _load():
     lib.cdmt_redigitise.argtypes = [P, P, P, P, P]
     lib.cdmt_redigitise_sk.argtypes = [P, P, P, P, ctypes.c_double, P, P]
     lib.cdmt_execute_host_u8.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+    lib.cdmt_execute_host_u8_ex.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
     lib.cdmt_incoherent_info.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int64), P]
     lib.cdmt_incoherent.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
@@ -157,7 +158,7 @@ def _load():
               "cdmt_batch_destroy", "cdmt_batch_copy_out", "cdmt_server_create", "cdmt_server_destroy",
               "cdmt_server_add_beam", "cdmt_server_submit", "cdmt_server_wait", "cdmt_server_release",
               "cdmt_server_get_stats", "cdmt_server_reset_stats", "cdmt_redigitise", "cdmt_incoherent_info",
-              "cdmt_incoherent", "cdmt_execute_host_u8", "cdmt_redigitise_sk"):
+              "cdmt_incoherent", "cdmt_execute_host_u8", "cdmt_redigitise_sk", "cdmt_execute_host_u8_ex"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -167,7 +168,7 @@ _lib = _load()
 EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
             "cdmt_redigitise", "cdmt_redigitise_sk", "cdmt_incoherent_info", "cdmt_incoherent",
-            "cdmt_execute_host_u8", "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
+            "cdmt_execute_host_u8", "cdmt_execute_host_u8_ex", "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
             "cdmt_server_wait", "cdmt_server_release", "cdmt_server_get_stats", "cdmt_server_reset_stats",
@@ -465,11 +466,18 @@ def cdmt_stage_times(plan):
     return (ms[0], ms[1]), (n[0], n[1])
 
 
-def cdmt_execute_host_u8(plan, h_in: int, h_u8: int, stream: int = 0) -> int:
+def cdmt_execute_host_u8_ex(plan, h_in: int, h_scale: int, h_u8: int, stream: int = 0) -> int:
     """8-bit codes of every block to host memory (Algorithm 1's redigitize + copy to host);
-    returns the segments per block."""
+    h_scale: host nsub floats for int8 input (0 for complex64).  Returns the segments per block."""
     n = ctypes.c_int64()
-    _check(_lib.cdmt_execute_host_u8(plan, h_in, h_u8, ctypes.byref(n), stream or None), plan)
+    _check(_lib.cdmt_execute_host_u8_ex(plan, h_in, h_scale or None, h_u8, ctypes.byref(n), stream or None), plan)
+    return n.value
+
+
+def cdmt_execute_host_u8(plan, h_in: int, h_u8: int, stream: int = 0, h_scale: int = 0) -> int:
+    """As cdmt_execute_host_u8_ex (h_scale for int8 input)."""
+    n = ctypes.c_int64()
+    _check(_lib.cdmt_execute_host_u8_ex(plan, h_in, h_scale or None, h_u8, ctypes.byref(n), stream or None), plan)
     return n.value
 
 
@@ -522,9 +530,10 @@ class Plan:
     def execute_host(self, h_in: int, h_out: int, h_scale: int = 0, stream: int = 0):
         cdmt_execute_host(self.handle, h_in, h_out, h_scale, stream)
 
-    def execute_host_u8(self, h_in: int, h_u8: int, stream: int = 0) -> int:
-        """8-bit codes [ndm][nout][nsub*nchan] to host memory; returns the segments per block."""
-        return cdmt_execute_host_u8(self.handle, h_in, h_u8, stream)
+    def execute_host_u8(self, h_in: int, h_u8: int, stream: int = 0, h_scale: int = 0) -> int:
+        """8-bit codes [ndm][nout][nsub*nchan] to host memory (h_scale: host nsub floats for int8
+        input); returns the segments per block."""
+        return cdmt_execute_host_u8(self.handle, h_in, h_u8, stream, h_scale)
 
     def device_status(self):
         cdmt_device_status(self.handle)

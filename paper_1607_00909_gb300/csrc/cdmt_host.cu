@@ -824,20 +824,22 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     return rc;
 }
 
-int cdmt_execute_host_u8(cdmt_plan_t p, const void *h_in, uint8_t *h_u8, int64_t *block_segments, void *cuda_stream)
+int cdmt_execute_host_u8_ex(cdmt_plan_t p, const void *h_in, const float *h_scale, uint8_t *h_u8,
+                            int64_t *block_segments, void *cuda_stream)
 {
     if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
     if (!h_in || !h_u8) return fail(p, CDMT_EINVAL, "NULL input or output pointer");
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    if (p->in_dtype == CDMT_IN_I8) {
-        if (cur != p->device) cudaSetDevice(cur);
-        return fail(p, CDMT_ENOTSUP, "int8 input: cdmt_execute_host_u8 takes no scales (use cdmt_execute_host)");
-    }
-    const int rc = host_pipeline(p, h_in, nullptr, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
+    const int rc = host_pipeline(p, h_in, h_scale, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
+}
+
+int cdmt_execute_host_u8(cdmt_plan_t p, const void *h_in, uint8_t *h_u8, int64_t *block_segments, void *cuda_stream)
+{
+    return cdmt_execute_host_u8_ex(p, h_in, nullptr, h_u8, block_segments, cuda_stream);
 }
 
 int cdmt_device_status(cdmt_plan_t p)

@@ -218,8 +218,8 @@ def test_lofar64_full_size_sampled_tiles(cdmt, orc):
 def test_int8_input_equals_dequantised_float(cdmt, prec):
     """CDMT_IN_I8 plans read 4-byte samples times a per-subband scale (the paper's
     8-bit voltages): bit-identical to a float32 plan on the dequantised voltages,
-    on the device and through the host pipeline; the scales are required, and the
-    8-bit host entry point, which takes none, refuses int8 plans."""
+    on the device and through the host pipeline (float32 and 8-bit output); the scales are
+    required."""
     import torch
     nsub, nsamp = 3, 4 * (1 << 14) + 77
     x = synth.noise(71, nsub, nsamp)
@@ -245,8 +245,16 @@ def test_int8_input_equals_dequantised_float(cdmt, prec):
     with pytest.raises(cdmt.CdmtError) as e:
         pi.execute(qd.data_ptr(), got.data_ptr(), 0, 0)
     assert e.value.status == cdmt.CDMT_EINVAL
-    u8 = torch.empty((len(dms), pi.out_shape()[2], pi.out_shape()[1]), dtype=torch.uint8).pin_memory()
+    # 8-bit in, 8-bit out (the paper's own I/O): the codes equal those of the float32 plan on the
+    # dequantised voltages; without scales the int8 plan is refused
+    shape8 = (len(dms), pi.out_shape()[2], pi.out_shape()[1])
+    u8, ref8 = torch.empty(shape8, dtype=torch.uint8).pin_memory(), torch.empty(shape8, dtype=torch.uint8).pin_memory()
+    assert pi.execute_host_u8(hin.data_ptr(), u8.data_ptr(), 0, hsc.data_ptr()) == 2
+    pf = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, precision=precision, host_block=2)
+    pf.execute_host_u8(torch.from_numpy(deq).pin_memory().data_ptr(), ref8.data_ptr())
+    pf.close()
+    assert np.array_equal(u8.numpy(), ref8.numpy())
     with pytest.raises(cdmt.CdmtError) as e:
         pi.execute_host_u8(hin.data_ptr(), u8.data_ptr())
-    assert e.value.status == cdmt.CDMT_ENOTSUP
+    assert e.value.status == cdmt.CDMT_EINVAL
     pi.close()
