@@ -183,6 +183,64 @@ def filterbank(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, nthreads: int = 
     return out
 
 
+def dm_groups(ndm: int, groups: int) -> list[tuple[int, int]]:
+    """Contiguous DM-index ranges (first, count) of `groups` near-equal parts of
+    the list: part g holds indices [g ndm / groups, (g + 1) ndm / groups)."""
+    if not 1 <= groups <= ndm:
+        raise ValueError("need 1 <= groups <= ndm")
+    return [(g * ndm // groups, (g + 1) * ndm // groups - g * ndm // groups) for g in range(groups)]
+
+
+def grouped_layout(nsub, nsamp, f_centre, bw, dm_list, nchan, nint, nbin, groups, chirp: int = 0, nd: int = -1):
+    """Overlap per DM group (digifil's per-DM overlap, Sec. 5, taken per group of
+    trials).  nd_max is Sec. 2's overlap for the whole list (or `nd`), and the
+    grouped filterbank keeps its time axis and length nout: a group whose
+    overlap is nd_g starts its overlap-save segments off_g = (nd_max - nd_g) n_c / 2
+    input samples later, so that its first kept sample (nd_g / 2 channel samples
+    into segment 0) is channel sample nd_max / 2 of the input, as with nd_max.
+    nd_g is the smallest overlap that is at least Sec. 2's overlap for the
+    group's own largest |DM|, satisfies the rule's parity and nint conditions and
+    whose segments still cover nout (nd_max always does).
+    Returns ([(first, count, nd_g, off_g)], nd_max, nout)."""
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    nd_max = nd if nd >= 0 else overlap(nsub, f_centre, bw, dm, nchan, nint, nbin, chirp)
+    if nd_max < 0:
+        raise ValueError("no overlap < M")
+    nout = grid(nsamp, nbin, nchan, nd_max, nint)[2]
+    m = nbin // nchan
+
+    def covers(nd_g):
+        off = (nd_max - nd_g) * nchan // 2
+        return nsamp - off >= nbin and grid(nsamp - off, nbin, nchan, nd_g, nint)[2] >= nout
+
+    out = []
+    for first, count in dm_groups(len(dm), groups):
+        nd_g = min(overlap(nsub, f_centre, bw, dm[first:first + count], nchan, nint, nbin, chirp), nd_max)
+        while not covers(nd_g):
+            nd_g += 2
+            while (m - nd_g) % nint:
+                nd_g += 2
+        out.append((first, count, nd_g, (nd_max - nd_g) * nchan // 2))
+    return out, nd_max, nout
+
+
+def filterbank_grouped(x, f_centre, bw, dm_list, nchan, nint, nbin, groups, nthreads: int = 0, chirp: int = 0,
+                       nd: int = -1) -> np.ndarray:
+    """The filterbank of :func:`filterbank` with each DM group's own overlap
+    (:func:`grouped_layout`): group g's rows are the filterbank of the input from
+    sample off_g on, with overlap nd_g, cut to the ungrouped length nout.
+    float64 [ndm][nsub*nchan][nout], on the ungrouped time axis."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    nsub, nsamp = x.shape[0], x.shape[1]
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    layout, _, nout = grouped_layout(nsub, nsamp, f_centre, bw, dm, nchan, nint, nbin, groups, chirp, nd)
+    out = np.empty((len(dm), nsub * nchan, nout), dtype=np.float64)
+    for first, count, nd_g, off in layout:
+        fb = filterbank(x[:, off:], f_centre, bw, dm[first:first + count], nchan, nint, nbin, nd_g, nthreads, chirp)
+        out[first:first + count] = fb[:, :, :nout]
+    return out
+
+
 def tiles(x, f_centre, bw, dm_list, nchan, nint, nbin, nd, sub, seg, dmi, nthreads: int = 0,
           chirp: int = 0) -> np.ndarray:
     """Filterbank samples of the listed (subband, segment, DM index) tiles:

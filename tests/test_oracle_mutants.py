@@ -1,7 +1,8 @@
 """Planted mistakes: each mutant of the oracle must fail at least one pin.
 
-The mutants are textual edits of a COPY of oracle/cdmt_oracle.c, compiled into
-a temporary directory on the CPU; the oracle itself is never modified.  Every
+The mutants are textual edits of a COPY of oracle/cdmt_oracle.c (or of the
+module's own composition code in oracle/__init__.py), compiled into a temporary
+directory on the CPU; the oracle itself is never modified.  Every
 edit is a plausible slip (a flipped sign, a dropped term, a wrong index or
 centre); the pins in test_oracle_pins.py must reject each one.  (Swapping the
 reference of the subband-wide chirp for the channel centre while keeping the
@@ -95,13 +96,35 @@ PIN_CALLS = [
 ]
 
 
-def _load_mutant(tmp_path, name, old, new):
-    src = open(os.path.join(ORACLE_DIR, "cdmt_oracle.c")).read()
-    assert old in src, f"mutation anchor for {name} not found"
+# mistakes in the composition that the Python module does itself (DM groups)
+MUTANTS_PY = [
+    ("grouped_no_offset", "off = (nd_max - nd_g) * nchan // 2", "off = 0", None),
+    ("grouped_offset_sign", "(nd_max - nd_g) * nchan // 2", "(nd_g - nd_max) * nchan // 2", None),
+    ("grouped_offset_not_halved", "(nd_max - nd_g) * nchan // 2", "(nd_max - nd_g) * nchan", None),
+    ("grouped_no_coverage_step", "while not covers(nd_g):", "while False:", None),
+    ("grouped_overlap_of_first_dm", "dm[first:first + count], nchan, nint, nbin, chirp), nd_max)",
+     "dm[first:first + 1], nchan, nint, nbin, chirp), nd_max)", None),
+    ("grouped_all_nd_max", "nd_g = min(overlap(", "nd_g = max(overlap(", None),
+]
+
+GROUPED_PIN_CALLS = [
+    lambda o: pins.test_grouped_overlaps_cover_their_group_and_are_minimal(o, 0, 2),
+    lambda o: pins.test_grouped_overlaps_cover_their_group_and_are_minimal(o, 1, 4),
+    lambda o: pins.test_grouped_overlaps_cover_their_group_and_are_minimal(o, 1, 3),
+    lambda o: pins.test_grouped_filterbank_keeps_the_ungrouped_time_axis(o),
+    lambda o: pins.test_grouped_impulse_at_the_closed_form_time(o, 5.0),
+    lambda o: pins.test_grouped_impulse_at_the_closed_form_time(o, 10.0),
+]
+
+
+def _load_mutant(tmp_path, name, old, new, target="cdmt_oracle.c"):
+    srcs = {f: open(os.path.join(ORACLE_DIR, f)).read() for f in ("cdmt_oracle.c", "__init__.py")}
+    assert old in srcs[target], f"mutation anchor for {name} not found"
+    srcs[target] = srcs[target].replace(old, new)
     d = tmp_path / f"oracle_{name}"
     d.mkdir()
-    shutil.copy(os.path.join(ORACLE_DIR, "__init__.py"), d / "__init__.py")
-    (d / "cdmt_oracle.c").write_text(src.replace(old, new))
+    for f, text in srcs.items():
+        (d / f).write_text(text)
     spec = importlib.util.spec_from_file_location(f"oracle_{name}", d / "__init__.py",
                                                   submodule_search_locations=[str(d)])
     mod = importlib.util.module_from_spec(spec)
@@ -115,6 +138,18 @@ def test_mutant_is_caught(tmp_path, name, old, new, occ):
     mod = _load_mutant(tmp_path, name, old, new)
     caught = []
     for i, call in enumerate(PIN_CALLS):
+        try:
+            call(mod)
+        except (AssertionError, ValueError, IndexError):
+            caught.append(i)
+    assert caught, f"mutant {name} passed every pin"
+
+
+@pytest.mark.parametrize("name,old,new,occ", MUTANTS_PY, ids=[m[0] for m in MUTANTS_PY])
+def test_python_mutant_is_caught(tmp_path, name, old, new, occ):
+    mod = _load_mutant(tmp_path, name, old, new, target="__init__.py")
+    caught = []
+    for i, call in enumerate(GROUPED_PIN_CALLS):
         try:
             call(mod)
         except (AssertionError, ValueError, IndexError):

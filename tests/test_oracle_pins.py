@@ -571,3 +571,102 @@ def test_redigitise_sk_zaps_flagged_rows_only(orc):
                 assert np.all(codes[d, :, col] == 128)
             else:
                 assert np.array_equal(codes[d, :, col], c0[d, :, col])
+
+
+# ---------------------------------------------------------------- overlap per DM group
+# Sec. 5: digifil picks the overlap per DM, where cdmt sizes one overlap for the
+# largest DM of the list.  Grouped plans give each contiguous group of trials the
+# overlap its own largest DM needs, and keep the ungrouped time axis and length.
+
+
+def _grouped_need(orc, nsub, fc, nchan, dm_abs, chirp):
+    # r t_d / n_c for the widest sweep of any channel (chirp 0) or subband (chirp 1), Eq. 2
+    r, need = BW * 1e6, 0.0
+    for s in range(nsub):
+        nus = orc.subband_centre(nsub, fc, BW, s)
+        spans = [(nus - BW / 2, nus + BW / 2)] if chirp else [
+            (orc.channel_centre(nus, BW, nchan, c) - BW / nchan / 2, orc.channel_centre(nus, BW, nchan, c) + BW / nchan / 2)
+            for c in range(nchan)]
+        for lo, hi in spans:
+            need = max(need, r * orc.sweep(lo, hi, dm_abs) / nchan)
+    return need
+
+
+@pytest.mark.parametrize("chirp,groups", [(0, 2), (1, 4), (1, 3)])
+def test_grouped_overlaps_cover_their_group_and_are_minimal(orc, chirp, groups):
+    # Invariants of each group's overlap: even, (M - nd_g) divisible by nint, at least
+    # r t_d / n_c for the group's largest |DM| (Eq. 2 over every channel or subband), its
+    # segments (starting off_g = (nd_max - nd_g) n_c / 2 samples in) cover the ungrouped
+    # length, and the next smaller candidate fails one of these.  The group holding the
+    # largest |DM| has nd_max and no offset.
+    nsub, fc, nchan, nint, nbin = 2, 60.0, 8, 2, 1 << 13
+    nsamp = 6 * nbin + 1000
+    dms = np.linspace(0.0, 4.2, 8) if chirp else np.linspace(0.0, 30.0, 7)
+    layout, nd_max, nout = orc.grouped_layout(nsub, nsamp, fc, BW, dms, nchan, nint, nbin, groups, chirp)
+    m = nbin // nchan
+    assert [g[0] for g in layout] == [g * len(dms) // groups for g in range(groups)]
+    assert sum(g[1] for g in layout) == len(dms)
+    assert nd_max >= _grouped_need(orc, nsub, fc, nchan, dms.max(), chirp)
+    assert nout == (((nsamp - nbin) // (nbin - nd_max * nchan)) + 1) * ((m - nd_max) // nint)
+
+    def covers(nd_g):
+        off = (nd_max - nd_g) * nchan // 2
+        sv = nbin - nd_g * nchan
+        return nsamp - off >= nbin and ((nsamp - off - nbin) // sv + 1) * ((m - nd_g) // nint) >= nout
+
+    for first, count, nd_g, off in layout:
+        need = _grouped_need(orc, nsub, fc, nchan, np.abs(dms[first:first + count]).max(), chirp)
+        assert nd_g % 2 == 0 and (m - nd_g) % nint == 0 and nd_g <= nd_max
+        assert nd_g >= need and covers(nd_g)
+        assert off == (nd_max - nd_g) * nchan // 2
+        cand = nd_g - 2
+        while cand >= 0 and (cand % 2 or (m - cand) % nint):
+            cand -= 2
+        assert cand < 0 or cand < need or not covers(cand)
+    assert layout[-1][2] == nd_max and layout[-1][3] == 0
+    assert layout[0][2] < nd_max   # the grouping does save overlap here
+
+
+def test_grouped_filterbank_keeps_the_ungrouped_time_axis(orc):
+    # Noise in: one group is the ungrouped filterbank exactly; with four groups the
+    # group of the largest DM is the ungrouped rows exactly, and the other rows differ
+    # from them only by the wrap-around leakage of the shorter overlaps (about 1 %
+    # rms), while one output sample of misalignment would differ by about 60 %.
+    nsub, fc, nchan, nint, nbin = 2, 60.0, 8, 2, 1 << 13
+    nsamp = 6 * nbin + 1000
+    dms = np.linspace(0.0, 4.2, 8)
+    x = np.random.default_rng(5).standard_normal((nsub, nsamp, 4)).astype(np.float32)
+    nd = orc.overlap(nsub, fc, BW, dms, nchan, nint, nbin, 1)
+    plain = orc.filterbank(x, fc, BW, dms, nchan, nint, nbin, nd, chirp=1)
+    assert np.array_equal(orc.filterbank_grouped(x, fc, BW, dms, nchan, nint, nbin, 1, chirp=1), plain)
+    g = orc.filterbank_grouped(x, fc, BW, dms, nchan, nint, nbin, 4, chirp=1)
+    assert g.shape == plain.shape
+    assert np.array_equal(g[6:], plain[6:])
+    for i in range(6):
+        rel = np.sqrt(np.mean((g[i] - plain[i]) ** 2) / np.mean(plain[i] ** 2))
+        assert rel < 0.03, (i, rel)
+        shifted = np.sqrt(np.mean((g[i][:, 1:] - plain[i][:, :-1]) ** 2) / np.mean(plain[i] ** 2))
+        assert shifted > 0.3, (i, shifted)
+
+
+@pytest.mark.parametrize("dm_true", [5.0, 10.0])
+def test_grouped_impulse_at_the_closed_form_time(orc, dm_true):
+    # A physical impulse dispersed at dm_true (a DM in a group with a shorter overlap
+    # and an input offset): at its DM row, channel c peaks at the closed-form time of
+    # the ungrouped axis, t0 / n_c + D DM (nu_c^-2 - nu_s^-2) r / n_c - nd_max / 2, with
+    # >= 0.8 of the row's energy in the two nearest samples.
+    fc, nchan, nbin = 135.0, 8, 1 << 14
+    nsamp, t0, r = 1 << 15, 20000, BW * 1e6
+    x = _physical_impulse(nsamp, fc, dm_true, t0)
+    dms = [0.0, 5.0, 10.0, 15.0, 40.0, 45.0]
+    layout, nd_max, _ = orc.grouped_layout(1, nsamp, fc, BW, dms, nchan, 1, nbin, 3)
+    gi = [g for g, (first, count, _, _) in enumerate(layout) if first <= dms.index(dm_true) < first + count][0]
+    assert layout[gi][3] > 0   # the DM's group starts its segments later
+    fb = orc.filterbank_grouped(x, fc, BW, dms, nchan, 1, nbin, 3)
+    for c in range(nchan):
+        nuc = fc - BW / 2 + (c + 0.5) * BW / nchan
+        t_exp = t0 / nchan + D * dm_true * (1 / nuc ** 2 - 1 / fc ** 2) * r / nchan - nd_max / 2
+        row = fb[dms.index(dm_true), c]
+        i0 = int(np.floor(t_exp))
+        assert abs(np.argmax(row) - t_exp) <= 1.0, (c, np.argmax(row), t_exp)
+        assert (row[i0] + row[i0 + 1]) / np.sum(row) >= 0.8
