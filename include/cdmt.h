@@ -92,7 +92,13 @@ typedef struct cdmt_opts {
                             at least 16 work items per SM) */
     double sk_nsigma;    /* cdmt_execute_host_u8: spectral-kurtosis RFI flagging of each block's rows
                             (see cdmt_redigitise_sk); 0 = off */
-    int64_t reserved[4];
+    int32_t dm_groups;   /* > 1: split the DM list into this many contiguous groups of near-equal size
+                            (group g: DMs g*ndm/G .. (g+1)*ndm/G - 1), each with the overlap its own
+                            largest |DM| needs (the per-DM overlap of Sec. 5, taken per group), the
+                            ungrouped time axis and length kept (see cdmt_plan_group); 0 or 1 = one
+                            overlap for the whole list */
+    int32_t reserved32;
+    int64_t reserved[3];
 } cdmt_opts;
 
 /* Derived sizes of a plan (cdmt_plan_info). */
@@ -114,7 +120,9 @@ typedef struct cdmt_info {
     int32_t uniform_dm;   /* 1 if the DM list is evenly spaced (integer phase accumulator) */
     int32_t precision, in_dtype;
     int32_t device;
-    int32_t reserved[7];
+    int32_t dm_groups;    /* DM groups with their own overlap (1: none); nd, nvalid and nseg above are
+                             then those of the group with the largest overlap, nd of the whole list */
+    int32_t reserved[6];
 } cdmt_info;
 
 /*
@@ -155,6 +163,30 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
 /* cdmt_plan_info - copy the derived sizes of a plan into *info (host memory).
  * Errors: CDMT_EINVAL if plan or info is NULL. */
 int cdmt_plan_info(cdmt_plan_t plan, cdmt_info *info);
+
+/* cdmt_plan_group - the layout of DM group g of a plan made with
+ * cdmt_opts.dm_groups > 1 (g < cdmt_info.dm_groups; a plan without groups has
+ * one group, g = 0, of all DMs with the plan's overlap and no offset).
+ *
+ * Sec. 2 sizes the overlap n_d for the largest |DM| of the list; digifil
+ * (Sec. 5) sizes it per DM.  A grouped plan gives group g the smallest overlap
+ * nd_g that (a) holds the sweep of its own largest |DM| by the rule of Sec. 2
+ * (even, (M - nd_g) divisible by nint), and (b) whose segments cover the whole
+ * ungrouped output length; nd_g <= n_d of the whole list, which satisfies both.
+ * The filterbank keeps the ungrouped time axis: group g's overlap-save segments
+ * start off_g = (n_d - nd_g) * nchan / 2 input samples into each subband, so
+ * that its first kept sample is the ungrouped first kept sample.  The rows of
+ * group g are its own overlap-save filterbank; they differ from the ungrouped
+ * rows by the wrap-around of the shorter segments (about 1 % rms, largest at
+ * small overlaps), and the DM stage runs on nseg_g = (nsamp - off_g - N_bin) /
+ * (N_bin - nd_g * nchan) + 1 segments of S_g = N_bin - nd_g * nchan instead.
+ *
+ *   dm_first, ndm  out (may be NULL): the group's first DM index and DM count
+ *   nd, offset     out (may be NULL): nd_g (channel samples) and off_g (input samples)
+ *   nseg           out (may be NULL): segments the group's DM stage runs on per execute
+ * Errors: CDMT_EINVAL for a NULL plan or g out of range. */
+int cdmt_plan_group(cdmt_plan_t plan, int g, int *dm_first, int *ndm, int64_t *nd, int64_t *offset,
+                    int64_t *nseg);
 
 /*
  * cdmt_execute - compute the whole filterbank of one input block.

@@ -30,7 +30,8 @@ class cdmt_opts(ctypes.Structure):
     _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("chirp", ctypes.c_int32),
                 ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("host_block", ctypes.c_int64),
-                ("sk_nsigma", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
+                ("sk_nsigma", ctypes.c_double), ("dm_groups", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class cdmt_info(ctypes.Structure):
@@ -41,7 +42,7 @@ class cdmt_info(ctypes.Structure):
                 ("nsub", ctypes.c_int32), ("nchan", ctypes.c_int32), ("nint", ctypes.c_int32),
                 ("ndm", ctypes.c_int32), ("dm_tile", ctypes.c_int32), ("uniform_dm", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("dm_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class cdmt_beam(ctypes.Structure):
@@ -113,6 +114,9 @@ def _load():
                               ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.cdmt_plan_ex.argtypes = lib.cdmt_plan.argtypes + [ctypes.POINTER(cdmt_opts)]
     lib.cdmt_plan_info.argtypes = [P, ctypes.POINTER(cdmt_info)]
+    lib.cdmt_plan_group.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_execute.argtypes = [P, P, P, P, P]
     lib.cdmt_execute_host.argtypes = [P, P, P, P, P]
     lib.cdmt_destroy.argtypes = [P]
@@ -165,7 +169,7 @@ def _load():
 
 _lib = _load()
 
-EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
+EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
             "cdmt_redigitise", "cdmt_redigitise_sk", "cdmt_incoherent_info", "cdmt_incoherent",
             "cdmt_execute_host_u8", "cdmt_execute_host_u8_ex", "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
@@ -211,6 +215,16 @@ def cdmt_plan_info(plan) -> dict:
     _check(_lib.cdmt_plan_info(plan, ctypes.byref(info)), plan)
     return {name: (list(getattr(info, name)) if name == "reserved" else getattr(info, name))
             for name, _ in cdmt_info._fields_ if name != "reserved"}
+
+
+def cdmt_plan_group(plan, g: int) -> dict:
+    """Layout of DM group g (cdmt_opts.dm_groups): first DM, DM count, overlap nd_g,
+    input offset in samples and the segments its DM stage runs on."""
+    first, n = ctypes.c_int(), ctypes.c_int()
+    nd, off, nseg = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.cdmt_plan_group(plan, g, ctypes.byref(first), ctypes.byref(n), ctypes.byref(nd), ctypes.byref(off),
+                                ctypes.byref(nseg)), plan)
+    return {"dm_first": first.value, "ndm": n.value, "nd": nd.value, "offset": off.value, "nseg": nseg.value}
 
 
 def cdmt_execute(plan, d_in: int, d_out: int, d_scale: int = 0, stream: int = 0):
@@ -517,10 +531,11 @@ class Plan:
 
     def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
                  seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0, host_block=0,
-                 sk_nsigma=0.0):
+                 sk_nsigma=0.0, dm_groups=0):
         o = cdmt_opts()
         o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
         o.precision, o.in_dtype, o.chirp, o.host_block, o.sk_nsigma = precision, in_dtype, chirp, host_block, sk_nsigma
+        o.dm_groups = dm_groups
         self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
         self.info = cdmt_plan_info(self.handle)
 
@@ -537,6 +552,10 @@ class Plan:
 
     def device_status(self):
         cdmt_device_status(self.handle)
+
+    def groups(self) -> list[dict]:
+        """Layout of the plan's DM groups: dm_first, ndm, nd, offset (input samples), nseg."""
+        return [cdmt_plan_group(self.handle, g) for g in range(self.info["dm_groups"])]
 
     def out_shape(self):
         i = self.info

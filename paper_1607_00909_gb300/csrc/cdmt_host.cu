@@ -223,6 +223,8 @@ template <class T> int dalloc(cdmt_plan_s *p, T **ptr, size_t count)
 void release(cdmt_plan_s *p)
 {
     if (!p) return;
+    for (auto &g : p->groups) cdmt_destroy(g.plan);
+    p->groups.clear();
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
@@ -325,6 +327,7 @@ int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, i
         ta.nsm = p->nsm;
         ta.dm_off = dm_off;
         ta.dm_cnt = dm_cnt;
+        ta.tlim = p->out_tlim;
         CK(p, tc_dedisperse(ta, st));
         return CDMT_OK;
     }
@@ -350,6 +353,7 @@ int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, i
     da.scale = (float)(1.0 / ((double)p->nbin * (double)p->mbin));
     da.dm_off = dm_off;
     da.dm_cnt = dm_cnt;
+    da.tlim = p->out_tlim;
     CK(p, fp32_dedisperse(da, st));
     return CDMT_OK;
 }
@@ -366,6 +370,60 @@ int enqueue_chunk(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_
     return CDMT_OK;
 }
 
+
+// DM groups (cdmt_opts.dm_groups): child plans over contiguous parts of the DM
+// list, each with the smallest overlap that holds its own largest |DM| (Sec. 2's
+// rule) and whose segments, started (nd - nd_g) * nchan / 2 input samples in,
+// still cover the parent's nout: the parent's time axis and length are kept.
+// Steps along the overlaps the rule allows (even, (M - nd_g) % nint == 0) end
+// at the parent's nd, which covers nout with no offset.
+int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
+{
+    const int G = o.dm_groups;
+    const int64_t ndm = p->ndm;
+    auto covers = [&](int64_t ndg) {
+        const int64_t off = (p->nd - ndg) * p->nchan / 2;
+        if (p->nsamp - off < p->nbin) return false;
+        const int64_t nseg = (p->nsamp - off - p->nbin) / (p->nbin - ndg * p->nchan) + 1;
+        return nseg * ((p->mbin - ndg) / p->nint) >= p->nout;
+    };
+    for (int g = 0; g < G; g++) {
+        const int first = (int)(g * ndm / G), count = (int)((g + 1) * ndm / G) - first;
+        cdmt_plan_s part;
+        part.nsub = p->nsub;
+        part.f_centre = p->f_centre;
+        part.bw = p->bw;
+        part.nchan = p->nchan;
+        part.nint = p->nint;
+        part.chirp = p->chirp;
+        part.dms.assign(dm_list + first, dm_list + first + count);
+        int64_t ndg = overlap_rule(part, p->nbin);
+        if (ndg < 0 || ndg > p->nd) ndg = p->nd;
+        while (!covers(ndg)) {
+            ndg += 2;
+            while ((p->mbin - ndg) % p->nint) ndg += 2;
+        }
+        const int64_t off = (p->nd - ndg) * p->nchan / 2;
+        cdmt_opts co = o;
+        co.nbin = p->nbin;
+        co.nd = ndg;
+        co.dm_groups = 0;
+        co.mem_budget = o.mem_budget > 0 ? o.mem_budget / G : 0;
+        cdmt_plan_s *child = nullptr;
+        const int rc = cdmt_plan_ex(&child, p->nsub, p->nsamp - off, p->f_centre, p->bw, dm_list + first, count,
+                                    p->nchan, p->nint, &co);
+        if (rc != CDMT_OK) {
+            p->last_error = g_thread_error;
+            return rc;
+        }
+        const int64_t seglen = (p->mbin - ndg) / p->nint;
+        child->out_tlim = p->nout;
+        p->groups.push_back({child, first, off, (p->nout + seglen - 1) / seglen});
+    }
+    p->dm_tile = p->groups.back().plan->dm_tile;
+    p->ntile = 0;
+    return CDMT_OK;
+}
 
 // lets other translation units of the library report an error before a plan exists
 void set_thread_error(const char *msg) { g_thread_error = msg; }
@@ -433,6 +491,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         return fail(nullptr, CDMT_ENOTSUP, "input dtype %d not available", o.in_dtype);
     if (o.chirp != CDMT_CHIRP_CHANNEL && o.chirp != CDMT_CHIRP_SUBBAND)
         return fail(nullptr, CDMT_EINVAL, "chirp %d is neither per channel nor per subband", o.chirp);
+    if (o.dm_groups < 0 || o.dm_groups > ndm)
+        return fail(nullptr, CDMT_EINVAL, "dm_groups must be in 0..ndm (got %d)", o.dm_groups);
 
     auto *p = new cdmt_plan_s();
     cudaGetDevice(&p->device);
@@ -518,6 +578,16 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
     p->nsm = nsm;
+    if (o.dm_groups > 1) {
+        const int rc = make_groups(p, o, dm_list);
+        if (rc != CDMT_OK) {
+            release(p);
+            delete p;
+            return rc;
+        }
+        *plan = p;
+        return CDMT_OK;
+    }
     // DM tile: all DMs, unless that leaves too few work items to fill the GPU
     const int64_t items = (int64_t)nsub * p->nseg * nchan;
     const int64_t want_items = 4LL * nsm;
@@ -638,6 +708,30 @@ int cdmt_plan_info(cdmt_plan_t p, cdmt_info *info)
     info->precision = p->precision;
     info->in_dtype = p->in_dtype;
     info->device = p->device;
+    info->dm_groups = p->groups.empty() ? 1 : (int32_t)p->groups.size();
+    for (auto &g : p->groups) info->workspace_bytes += g.plan->bytes;
+    return CDMT_OK;
+}
+
+int cdmt_plan_group(cdmt_plan_t p, int g, int *dm_first, int *ndm, int64_t *nd, int64_t *offset, int64_t *nseg)
+{
+    if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
+    const int ng = p->groups.empty() ? 1 : (int)p->groups.size();
+    if (g < 0 || g >= ng) return fail(p, CDMT_EINVAL, "group %d outside 0..%d", g, ng - 1);
+    if (p->groups.empty()) {
+        if (dm_first) *dm_first = 0;
+        if (ndm) *ndm = p->ndm;
+        if (nd) *nd = p->nd;
+        if (offset) *offset = 0;
+        if (nseg) *nseg = p->nseg;
+        return CDMT_OK;
+    }
+    const auto &q = p->groups[g];
+    if (dm_first) *dm_first = q.first;
+    if (ndm) *ndm = q.plan->ndm;
+    if (nd) *nd = q.plan->nd;
+    if (offset) *offset = q.off;
+    if (nseg) *nseg = q.kneed;
     return CDMT_OK;
 }
 
@@ -656,7 +750,25 @@ int cdmt_execute(cdmt_plan_t p, const void *d_in, float *d_out, const float *d_s
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int rc = CDMT_OK;
-    for (int64_t k0 = 0; k0 < p->nseg && rc == CDMT_OK; k0 += p->seg_chunk) {
+    // DM groups: each child reads the input from its offset on (subbands p->nsamp samples apart)
+    // and writes its DMs' rows of the common filterbank, only the segments that cover nout
+    const int64_t rows = (int64_t)p->nsub * p->nchan;
+    for (auto &g : p->groups) {
+        cdmt_plan_s *c = g.plan;
+        c->scale_dev = d_scale;
+        c->timing = p->timing;
+        const void *in = static_cast<const char *>(d_in) + g.off * (i8 ? 4 : 16);
+        float *out = d_out + (int64_t)g.first * rows * p->nout;
+        for (int64_t k0 = 0; k0 < g.kneed && rc == CDMT_OK; k0 += c->seg_chunk) {
+            const int kc = (int)std::min<int64_t>(c->seg_chunk, g.kneed - k0);
+            rc = enqueue_chunk(c, in, p->nsamp, k0, out, p->nout, k0, kc, st);
+        }
+        if (rc != CDMT_OK) {
+            p->last_error = c->last_error;
+            break;
+        }
+    }
+    for (int64_t k0 = 0; k0 < p->nseg && rc == CDMT_OK && p->groups.empty(); k0 += p->seg_chunk) {
         const int kc = (int)std::min<int64_t>(p->seg_chunk, p->nseg - k0);
         rc = enqueue_chunk(p, d_in, p->nsamp, k0, d_out, p->nout, k0, kc, st);
     }
@@ -819,6 +931,7 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    if (!p->groups.empty()) return fail(p, CDMT_ENOTSUP, "plans with DM groups run from device memory only");
     const int rc = host_pipeline(p, h_in, h_scale, h_out, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
@@ -832,6 +945,7 @@ int cdmt_execute_host_u8_ex(cdmt_plan_t p, const void *h_in, const float *h_scal
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
+    if (!p->groups.empty()) return fail(p, CDMT_ENOTSUP, "plans with DM groups run from device memory only");
     const int rc = host_pipeline(p, h_in, h_scale, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
@@ -849,8 +963,16 @@ int cdmt_device_status(cdmt_plan_t p)
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
     int flag = 0;
-    CK(p, cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) CK(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    for (auto &g : p->groups) {
+        int f = 0;
+        CK(p, cudaMemcpy(&f, g.plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (f) CK(p, cudaMemset(g.plan->d_status, 0, sizeof(int)));
+        flag |= f;
+    }
+    if (p->d_status) {
+        CK(p, cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) CK(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    }
     if (cur != p->device) cudaSetDevice(cur);
     if (flag) return fail(p, CDMT_ETIMEOUT, "a tensor-core wait gave up; outputs of that execute are incomplete");
     return CDMT_OK;
@@ -860,6 +982,7 @@ int cdmt_set_timing(cdmt_plan_t p, int on)
 {
     if (!p) return fail(nullptr, CDMT_EINVAL, "NULL plan");
     p->timing = on != 0;
+    for (auto &g : p->groups) g.plan->timing = p->timing;
     return CDMT_OK;
 }
 
@@ -868,6 +991,17 @@ int cdmt_stage_times(cdmt_plan_t p, double *ms, int64_t *launches)
     if (!p || !ms) return fail(p, CDMT_EINVAL, "NULL plan or ms");
     ms[0] = ms[1] = 0.0;
     int64_t n = 0;
+    for (auto &g : p->groups) {   // a grouped plan's stages are its children's
+        double cm[2];
+        int64_t cl[2];
+        if (cdmt_stage_times(g.plan, cm, cl) != CDMT_OK) {
+            p->last_error = g.plan->last_error;
+            return CDMT_ECUDA;
+        }
+        ms[0] += cm[0];
+        ms[1] += cm[1];
+        n += cl[1];
+    }
     for (size_t i = 0; i + 2 < p->ev_marks.size(); i += 3) {
         float a = 0.f, b = 0.f;
         CK(p, cudaEventSynchronize(p->ev_marks[i + 2]));

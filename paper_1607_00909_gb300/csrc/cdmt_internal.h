@@ -39,6 +39,7 @@ struct DedispArgs {
     // DM range: DMs dm_off .. dm_off + dm_cnt - 1 of every tile (dm_cnt 0: the whole tile); output
     // row of DM j of tile t's range: t * dm_cnt + j
     int dm_off = 0, dm_cnt = 0;
+    int64_t tlim = INT64_MAX;   // output positions (k0 + kk) * seglen + u >= tlim are not stored
 };
 
 struct TcArgs {
@@ -59,6 +60,7 @@ struct TcArgs {
     bool uniform;
     float scale;
     int dm_off = 0, dm_cnt = 0;   // DM range within every tile, as in DedispArgs
+    int64_t tlim = INT64_MAX;     // output positions >= tlim are not stored, as in DedispArgs
 };
 
 // one beam of a batch, as the persistent tensor-core kernel sees it

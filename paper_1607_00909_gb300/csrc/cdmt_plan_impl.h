@@ -59,12 +59,22 @@ struct cdmt_plan_s {
     int64_t bytes = 0;
     // host-execute pipeline
     int64_t host_chunk = 0, span_max = 0, host_block_opt = 0;
-    int64_t host_out_cap = 0;
+    int64_t host_out_cap = 0;      // floats per output slot of the host pipeline (u8 slots: bytes)
     double sk_nsigma = 0.0;        // spectral-kurtosis flagging of the 8-bit host output (0: off)
     const float *scale_dev = nullptr;  // int8 input: DEVICE per-subband scales of the current call
-    float *d_scale_buf = nullptr;      // int8 input from host memory: the scales on the device      // floats per output slot of the host pipeline (u8 slots: bytes)
+    float *d_scale_buf = nullptr;      // int8 input from host memory: the scales on the device
     cdmt::Staging stage[3];        // host pipeline: three blocks in flight (copy in, compute, copy out)
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    // DM groups (cdmt_opts.dm_groups > 1): one child plan per contiguous group of DMs, each with
+    // the overlap its own largest |DM| needs; this plan then holds no tables of its own
+    struct Group {
+        cdmt_plan_s *plan;   // DMs first .. first + plan->ndm - 1, input from sample `off` on
+        int first;
+        int64_t off;         // (nd - plan->nd) * nchan / 2 input samples
+        int64_t kneed;       // segments that cover this plan's nout
+    };
+    std::vector<Group> groups;
+    int64_t out_tlim = INT64_MAX;  // DM stage: output positions >= out_tlim are not stored
     // stage timing (cdmt_set_timing / cdmt_stage_times)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;

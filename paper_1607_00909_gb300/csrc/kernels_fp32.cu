@@ -155,7 +155,7 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
              const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
              float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
              int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg, int dm_off,
-             int dm_cnt)
+             int dm_cnt, int64_t tlim)
 {
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T, NT = 2 * T;
@@ -178,6 +178,10 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
     if (ndt <= 0) return;
     // batches: this chunk's segments start at round * kc; none past the end of the input
     if (round_dev && (int64_t)(*round_dev) * kc + kk >= nseg) return;
+    // output samples of this segment before the filterbank's end (position tlim on)
+    const int64_t room = tlim - (k0 + kk) * (int64_t)((M - nd) / nint);
+    const int ulim = room <= 0 ? 0 : (int)(room < (M - nd) / nint ? room : (M - nd) / nint);
+    if (ulim == 0) return;
 
     const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * M;
     float2 xr[16];
@@ -234,7 +238,7 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
         F::template pass_c1<+1>(exp_, t, [&](int m, float2 a) { ibp[m] = fmaf(a.x, a.x, a.y * a.y); });
         __syncthreads();
         float *orow = out + ((int64_t)tile * dm_cnt + d) * rows * nout + obase;
-        for (int u = tid; u < seglen; u += NT) {
+        for (int u = tid; u < ulim; u += NT) {
             const float *px = ib + half + u * nint;
             const float *py = px + M;
             float acc = 0.f;
@@ -343,7 +347,7 @@ template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStre
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
     k_dedisperse<R, U><<<(unsigned)nblk, 2 * Fft3<R>::T, smem_dedisp<R>(), st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
-        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile);
+        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile, a.tlim);
 }
 
 cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)

@@ -206,6 +206,8 @@ struct TcItem {
     float *out;            // output of the tile's first DM at this channel row and segment offset
     int64_t dm_stride;     // floats between the rows of consecutive DMs
     int nd, nint;
+    int ulim;              // output samples of this segment that are stored: (M - nd) / nint, less where
+                           // the segment reaches past the filterbank's last sample
     float scale_out;
 };
 
@@ -352,7 +354,7 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
     const int ndt = it.ndt;
     const int nd = it.nd, nint = it.nint;
     const int half = nd / 2;
-    const int seglen = (kM - nd) / nint;
+    const int ulim = it.ulim;
     const uint32_t id_a = tc::idesc(128, 2 * P, AB, 0, 0);   // pass A: data (K-major) x F_P (K-major)
     const uint32_t id_b = tc::idesc(128, 2 * P, AB, 0, 1);   // pass B: F_64^T (K-major) x data (MN-major)
     const uint32_t bm_addr = tc::smem_addr(bm), ab_addr = tc::smem_addr(ab);
@@ -542,12 +544,12 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             const uint32_t taddr = dcol + lane_off;
             const int m1 = t >> 1, ro = t & 1;
             switch (nint) {
-            case 1: tc_detect<1, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 2: tc_detect<2, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 4: tc_detect<4, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 8: tc_detect<8, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            case 16: tc_detect<16, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
-            default: tc_detect<32, P>(taddr, cg, m1, ro, orow, seglen, oscale); break;
+            case 1: tc_detect<1, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
+            case 2: tc_detect<2, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
+            case 4: tc_detect<4, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
+            case 8: tc_detect<8, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
+            case 16: tc_detect<16, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
+            default: tc_detect<32, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
             }
         }
     }
@@ -572,7 +574,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const uint4 *__restrict__ bmat64,
                 const float2 *__restrict__ twq, float *__restrict__ out, int *__restrict__ status, int nsub, int kc,
                 int64_t k0, int nchan, int ndm, int dm_tile, int nd, int nint, int64_t nout, float scale_out,
-                int64_t nitems, int dm_off, int dm_cnt)
+                int64_t nitems, int dm_off, int dm_cnt, int64_t tlim)
 {
     constexpr int kM = 1 << LM;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -599,6 +601,8 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         it.dm_stride = rows * nout;
         it.nd = nd;
         it.nint = nint;
+        const int64_t room = tlim - (k0 + kk) * seglen;
+        it.ulim = room <= 0 ? 0 : (int)(room < seglen ? room : seglen);
         it.scale_out = scale_out;
         return it;
     };
@@ -671,6 +675,7 @@ k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__
         it.dm_stride = rows * B.out_stride;
         it.nd = B.nd;
         it.nint = B.nint;
+        it.ulim = seglen;
         it.scale_out = B.scale;
         if (!tc_run_item<true, AB, 12>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
@@ -727,7 +732,8 @@ template <bool U, int AB, int LM> static void launch(const TcArgs &a, cudaStream
     const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
     k_dedisperse_tc<U, AB, LM><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.bmat64, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan,
-        a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile);
+        a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile,
+        a.tlim);
 }
 
 template <int LM> static void launch_lm(const TcArgs &a, cudaStream_t st)

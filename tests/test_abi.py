@@ -103,6 +103,18 @@ def test_null_handles_of_the_8bit_and_incoherent_entry_points(cdmt):
     assert lib.cdmt_redigitise_sk(None, None, None, None, 3.0, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_execute_host_u8(None, None, None, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_incoherent(None, None, 0.0, 0.0, 1, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_plan_group(None, 0, None, None, None, None, None) == cdmt.CDMT_EINVAL
+
+
+@pytest.mark.parametrize("groups", [-1, 3])
+def test_plan_rejects_dm_groups_outside_the_list(cdmt, groups):
+    # a group needs at least one DM trial; checked before any device call
+    o = cdmt.cdmt_opts()
+    o.dm_groups = groups
+    with pytest.raises(cdmt.CdmtError) as e:
+        cdmt.cdmt_plan_ex(1, 1 << 17, 135.0, 0.1953125, [0.0, 5.0], 8, 4, o)
+    assert e.value.status == cdmt.CDMT_EINVAL
+    assert "dm_groups" in str(e.value)
 
 
 def test_struct_layouts_match_the_header(cdmt, tmp_path):

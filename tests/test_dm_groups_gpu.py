@@ -1,0 +1,148 @@
+"""Plans with one overlap per DM group (cdmt_opts.dm_groups) against the oracle.
+
+Sec. 2 sizes the overlap for the largest |DM| of the list; digifil (Sec. 5)
+sizes it per DM.  A grouped plan gives each contiguous group of trials the
+overlap its own largest DM needs and keeps the ungrouped time axis and length.
+The layout (overlaps, input offsets) must equal the oracle's, every output
+sample must be written, and the values must match the oracle's grouped
+filterbank at the tolerances of the forms (FP32 1e-5, FP16 2e-3).
+"""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_filterbank, rel_errors
+
+pytestmark = pytest.mark.gpu
+BW = 0.1953125
+
+
+@pytest.fixture(scope="module")
+def cdmt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1607_00909_gb300 as m
+    return m
+
+
+def _case(chirp):
+    # a low band with the subband-wide chirp (overlaps of 54 % of M at the largest DM), or
+    # the per-channel chirp with an uneven DM list; several segments and a ragged tail
+    if chirp:
+        return dict(nsub=2, fc=60.0, dms=list(np.linspace(0.0, 6.0, 12)), nchan=8, nint=4, nbin=1 << 14,
+                    nsamp=54983)
+    return dict(nsub=3, fc=70.0, dms=[0.0, 1.5, 2.0, 4.0, 7.5, 9.0, 12.0, 20.0, 21.0], nchan=8, nint=4,
+                nbin=1 << 14, nsamp=5 * (1 << 14) + 333)
+
+
+def _plan(cdmt, c, groups, prec, chirp, **kw):
+    return cdmt.Plan(c["nsub"], c["nsamp"], c["fc"], BW, c["dms"], c["nchan"], c["nint"], nbin=c["nbin"],
+                     precision=prec, chirp=chirp, dm_groups=groups, **kw)
+
+
+@pytest.mark.parametrize("chirp", [0, 1])
+@pytest.mark.parametrize("groups", [2, 4])
+def test_grouped_layout_equals_the_oracle(cdmt, orc, chirp, groups):
+    c = _case(chirp)
+    plan = _plan(cdmt, c, groups, cdmt.CDMT_PREC_FP32, chirp)
+    plain = _plan(cdmt, c, 0, cdmt.CDMT_PREC_FP32, chirp)
+    layout, nd_max, nout = orc.grouped_layout(c["nsub"], c["nsamp"], c["fc"], BW, c["dms"], c["nchan"], c["nint"],
+                                              c["nbin"], groups, chirp)
+    assert plan.info["dm_groups"] == groups and plain.info["dm_groups"] == 1
+    assert plan.info["nd"] == nd_max == plain.info["nd"]
+    assert plan.info["nout"] == nout == plain.info["nout"]
+    assert plan.info["units"] == plain.info["units"]
+    got = plan.groups()
+    m = c["nbin"] // c["nchan"]
+    for g, (first, count, nd_g, off) in zip(got, layout):
+        assert (g["dm_first"], g["ndm"], g["nd"], g["offset"]) == (first, count, nd_g, off)
+        seglen = (m - nd_g) // c["nint"]
+        assert g["nseg"] == -(-nout // seglen)   # the segments that cover nout
+    assert got[0]["nd"] < nd_max
+    assert plain.groups() == [{"dm_first": 0, "ndm": len(c["dms"]), "nd": nd_max, "offset": 0,
+                               "nseg": plain.info["nseg"]}]
+    plan.close()
+    plain.close()
+
+
+@pytest.mark.parametrize("chirp", [0, 1])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-3)])
+def test_grouped_filterbank_matches_the_oracle(cdmt, orc, chirp, prec, tol):
+    c = _case(chirp)
+    x = synth.noise(40 + chirp, c["nsub"], c["nsamp"])
+    plan = _plan(cdmt, c, 4, prec, chirp)
+    g = gpu_filterbank(plan, x)   # NaN-filled first: every sample must be written
+    plan.device_status()
+    o = orc.filterbank_grouped(x, c["fc"], BW, c["dms"], c["nchan"], c["nint"], c["nbin"], 4, chirp=chirp)
+    assert g.shape == o.shape
+    assert np.all(np.isfinite(g))
+    emax, erms = rel_errors(g, o)
+    print(f"prec {prec} chirp {chirp} 4 groups: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert emax <= tol and erms <= tol
+    plan.close()
+
+
+def test_grouped_plan_chunked_and_int8(cdmt, orc):
+    # small workspace chunks and int8 input (offsets of 4-byte samples) give the same
+    # filterbank as the float32 grouped plan on the dequantised voltages, bit for bit
+    import torch
+    c = _case(1)
+    x = synth.noise(47, c["nsub"], c["nsamp"])
+    scale = (np.abs(x).reshape(c["nsub"], -1).max(axis=1) / 127.0).astype(np.float32)
+    q = np.clip(np.rint(x / scale[:, None, None]), -127, 127).astype(np.int8)
+    deq = q.astype(np.float32) * scale[:, None, None]
+    pf = _plan(cdmt, c, 3, cdmt.CDMT_PREC_FP32, 1)
+    want = gpu_filterbank(pf, deq)
+    pc = _plan(cdmt, c, 3, cdmt.CDMT_PREC_FP32, 1, seg_chunk=2)
+    assert np.array_equal(gpu_filterbank(pc, deq), want)
+    pi = _plan(cdmt, c, 3, cdmt.CDMT_PREC_FP32, 1, in_dtype=cdmt.CDMT_IN_I8)
+    got = cdmt.run(pi, torch.from_numpy(q).cuda(), scale=torch.from_numpy(scale).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), want)
+    o = orc.filterbank_grouped(deq, c["fc"], BW, c["dms"], c["nchan"], c["nint"], c["nbin"], 3, chirp=1)
+    emax, erms = rel_errors(want, o)
+    assert emax <= 1e-5 and erms <= 1e-5
+    for p in (pf, pc, pi):
+        p.close()
+
+
+def test_grouped_plan_stage_times_and_host_entry_points(cdmt):
+    # stage timing sums the groups' launches; the host pipelines refuse grouped plans
+    import torch
+    c = _case(1)
+    x = synth.noise(48, c["nsub"], c["nsamp"])
+    plan = _plan(cdmt, c, 4, cdmt.CDMT_PREC_FP16, 1)
+    cdmt.cdmt_set_timing(plan.handle, True)
+    cdmt.cdmt_stage_times(plan.handle)
+    gpu_filterbank(plan, x)
+    (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
+    assert dd_n == 4 and fwd_n == 8 and fwd_ms > 0 and dd_ms > 0
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.empty(plan.out_shape(), dtype=torch.float32).pin_memory()
+    with pytest.raises(cdmt.CdmtError) as e:
+        plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, 0)
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+    plan.close()
+
+
+def test_grouped_filterbank_feeds_redigitisation_and_the_incoherent_stage(cdmt, orc):
+    # the grouped plan's filterbank has the ungrouped geometry, so the 8-bit and
+    # incoherent stages take it as they take any plan's
+    import torch
+    c = _case(0)
+    x = synth.noise(49, c["nsub"], c["nsamp"])
+    plan = _plan(cdmt, c, 3, cdmt.CDMT_PREC_FP32, 0)
+    fb = torch.from_numpy(gpu_filterbank(plan, x)).cuda()
+    ndm, rows, nt = fb.shape
+    u8 = torch.empty((ndm, nt, rows), dtype=torch.uint8, device="cuda")
+    plan.redigitise(fb, u8)
+    torch.cuda.synchronize()
+    want, _ = orc.redigitise(fb.cpu().numpy())
+    assert np.abs(u8.cpu().numpy().astype(int) - want.astype(int)).max() <= 1
+    inc = plan.incoherent(fb, -0.5, 0.25, 5)
+    torch.cuda.synchronize()
+    o, _ = orc.incoherent(fb.cpu().numpy(), c["nsub"], c["nchan"], c["fc"], BW, c["nint"], c["dms"], -0.5, 0.25, 5)
+    emax, _ = rel_errors(inc.cpu().numpy(), o)
+    assert emax <= 1e-5
+    plan.close()
