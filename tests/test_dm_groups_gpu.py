@@ -26,12 +26,12 @@ def cdmt():
     return m
 
 
-def _case(chirp):
-    # a low band with the subband-wide chirp (overlaps of 54 % of M at the largest DM), or
-    # the per-channel chirp with an uneven DM list; several segments and a ragged tail
+def _case(chirp, nbin=1 << 14):
+    # a low band with the subband-wide chirp (overlaps of 54 % of M = 2048 at the largest DM, 27 % of
+    # M = 4096), or the per-channel chirp with an uneven DM list; several segments and a ragged tail
     if chirp:
-        return dict(nsub=2, fc=60.0, dms=list(np.linspace(0.0, 6.0, 12)), nchan=8, nint=4, nbin=1 << 14,
-                    nsamp=54983)
+        return dict(nsub=2, fc=60.0, dms=list(np.linspace(0.0, 6.0, 12)), nchan=8, nint=4, nbin=nbin,
+                    nsamp=54983 if nbin == 1 << 14 else 4 * nbin + 1999)
     return dict(nsub=3, fc=70.0, dms=[0.0, 1.5, 2.0, 4.0, 7.5, 9.0, 12.0, 20.0, 21.0], nchan=8, nint=4,
                 nbin=1 << 14, nsamp=5 * (1 << 14) + 333)
 
@@ -66,10 +66,11 @@ def test_grouped_layout_equals_the_oracle(cdmt, orc, chirp, groups):
     plain.close()
 
 
-@pytest.mark.parametrize("chirp", [0, 1])
-@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-3)])
-def test_grouped_filterbank_matches_the_oracle(cdmt, orc, chirp, prec, tol):
-    c = _case(chirp)
+@pytest.mark.parametrize("chirp,nbin", [(0, 1 << 14), (1, 1 << 14), (1, 1 << 15)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-3), (2, 2e-3)])
+def test_grouped_filterbank_matches_the_oracle(cdmt, orc, chirp, nbin, prec, tol):
+    # FP32, FP16 and BF16 hi/lo forms; M = 2048 and (subband chirp, N = 2^15) M = 4096
+    c = _case(chirp, nbin)
     x = synth.noise(40 + chirp, c["nsub"], c["nsamp"])
     plan = _plan(cdmt, c, 4, prec, chirp)
     g = gpu_filterbank(plan, x)   # NaN-filled first: every sample must be written
@@ -78,7 +79,7 @@ def test_grouped_filterbank_matches_the_oracle(cdmt, orc, chirp, prec, tol):
     assert g.shape == o.shape
     assert np.all(np.isfinite(g))
     emax, erms = rel_errors(g, o)
-    print(f"prec {prec} chirp {chirp} 4 groups: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    print(f"prec {prec} chirp {chirp} M {nbin // 8} 4 groups: rel_max {emax:.3e} rel_rms {erms:.3e}")
     assert emax <= tol and erms <= tol
     plan.close()
 
