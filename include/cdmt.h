@@ -112,7 +112,7 @@ typedef struct cdmt_info {
     int64_t nout;         /* output samples per channel = nseg * (M_bin - nd) / nint */
     int64_t seg_chunk;    /* segments per internal chunk */
     int64_t workspace_bytes; /* device memory the plan holds */
-    int64_t in_bytes;     /* bytes of one input block */
+    int64_t in_bytes;     /* bytes of one input block: 16 per sample, 4 for CDMT_IN_I8 */
     int64_t out_bytes;    /* bytes of one output filterbank */
     double units;         /* DM-trial x input samples consumed per execute = ndm * nsub * nseg * S */
     int32_t nsub, nchan, nint, ndm;

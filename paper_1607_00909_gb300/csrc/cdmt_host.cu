@@ -421,6 +421,7 @@ int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
         p->groups.push_back({child, first, off, (p->nout + seglen - 1) / seglen});
     }
     p->dm_tile = p->groups.back().plan->dm_tile;
+    p->seg_chunk = p->groups.back().plan->seg_chunk;
     p->ntile = 0;
     return CDMT_OK;
 }
@@ -696,7 +697,7 @@ int cdmt_plan_info(cdmt_plan_t p, cdmt_info *info)
     info->nout = p->nout;
     info->seg_chunk = p->seg_chunk;
     info->workspace_bytes = p->bytes;
-    info->in_bytes = (int64_t)p->nsub * p->nsamp * 16;
+    info->in_bytes = (int64_t)p->nsub * p->nsamp * (p->in_dtype == CDMT_IN_I8 ? 4 : 16);
     info->out_bytes = (int64_t)p->ndm * p->nsub * p->nchan * p->nout * 4;
     info->units = (double)p->ndm * p->nsub * p->nseg * p->nvalid;
     info->nsub = p->nsub;

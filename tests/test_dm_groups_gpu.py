@@ -53,6 +53,7 @@ def test_grouped_layout_equals_the_oracle(cdmt, orc, chirp, groups):
     assert plan.info["nd"] == nd_max == plain.info["nd"]
     assert plan.info["nout"] == nout == plain.info["nout"]
     assert plan.info["units"] == plain.info["units"]
+    assert plan.info["seg_chunk"] > 0 and plan.info["workspace_bytes"] > 0
     got = plan.groups()
     m = c["nbin"] // c["nchan"]
     for g, (first, count, nd_g, off) in zip(got, layout):

@@ -230,10 +230,12 @@ def test_int8_input_equals_dequantised_float(cdmt, prec):
     dms = [0.0, 3.0, 6.0]
     pf = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, precision=precision)
     want = gpu_filterbank(pf, deq)
+    pf_bytes = pf.info["in_bytes"]
     pf.close()
     pi = _plan(cdmt, nsub, nsamp, 140.0, dms, 8, 4, nbin=1 << 14, precision=precision, in_dtype=cdmt.CDMT_IN_I8,
                host_block=2)
     assert pi.info["in_dtype"] == cdmt.CDMT_IN_I8
+    assert pi.info["in_bytes"] == nsub * nsamp * 4 and pf_bytes == nsub * nsamp * 16
     qd, sd = torch.from_numpy(q).cuda(), torch.from_numpy(scale).cuda()
     got = cdmt.run(pi, qd, scale=sd)
     torch.cuda.synchronize()
