@@ -256,6 +256,27 @@ int cdmt_execute_host(cdmt_plan_t plan, const void *h_in, float *h_out, const fl
  * a CUDA error, CDMT_EINVAL for a NULL plan. */
 int cdmt_device_status(cdmt_plan_t plan);
 
+/* cdmt_selftest_wait - run the bounded wait of the tensor-core kernels (the
+ * wait between a GEMM's commit to an mbarrier and its read-out: a limit on the
+ * GPU's global timer plus a cap on polls) on a barrier that nothing arrives on,
+ * in a one-warp kernel of its own.  It must give up after limit_ms and leave the
+ * context usable; with arrive != 0 one arrival completes the barrier's phase
+ * first, and the wait must succeed at once.  No fault, trap or hang is involved.
+ *   limit_ms   the wait's time limit, in (0, 1000]
+ *   gave_up    out: 1 if the wait gave up, 0 if the phase completed
+ *   waited_ms  out: the wait's duration on the global timer
+ * Errors: CDMT_EINVAL (NULL outputs, limit out of range), CDMT_ENOMEM, CDMT_ECUDA. */
+int cdmt_selftest_wait(double limit_ms, int arrive, int *gave_up, double *waited_ms);
+
+/* cdmt_inject_timeout - mark the plan's device status word (every group's, for a
+ * plan with DM groups) as a tensor-core kernel does when one of its waits gives
+ * up: host-side injection for tests of the recovery path.  Until
+ * cdmt_device_status reports CDMT_ETIMEOUT and clears the word, every launch of
+ * the tensor-core DM stage of this plan returns at once, before it allocates
+ * tensor memory, and leaves its outputs unwritten; the FP32 form does not read
+ * the word.  Errors: CDMT_EINVAL for a NULL plan, CDMT_ECUDA. */
+int cdmt_inject_timeout(cdmt_plan_t plan);
+
 /* cdmt_set_timing - when on != 0, later executes record CUDA events on their
  * stream around the forward stage (Sec. 3 "forward FFT" and "swap halves per
  * subband": two kernels per chunk) and around the dedispersion kernel (chirp

@@ -114,6 +114,9 @@ def _load():
                               ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.cdmt_plan_ex.argtypes = lib.cdmt_plan.argtypes + [ctypes.POINTER(cdmt_opts)]
     lib.cdmt_plan_info.argtypes = [P, ctypes.POINTER(cdmt_info)]
+    lib.cdmt_selftest_wait.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.cdmt_inject_timeout.argtypes = [P]
     lib.cdmt_plan_group.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
@@ -169,7 +172,8 @@ def _load():
 
 _lib = _load()
 
-EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
+EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "cdmt_selftest_wait",
+            "cdmt_inject_timeout", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
             "cdmt_redigitise", "cdmt_redigitise_sk", "cdmt_incoherent_info", "cdmt_incoherent",
             "cdmt_execute_host_u8", "cdmt_execute_host_u8_ex", "cdmt_execute_static", "cdmt_batch_create", "cdmt_batch_info", "cdmt_batch_run_round", "cdmt_batch_run",
@@ -225,6 +229,19 @@ def cdmt_plan_group(plan, g: int) -> dict:
     _check(_lib.cdmt_plan_group(plan, g, ctypes.byref(first), ctypes.byref(n), ctypes.byref(nd), ctypes.byref(off),
                                 ctypes.byref(nseg)), plan)
     return {"dm_first": first.value, "ndm": n.value, "nd": nd.value, "offset": off.value, "nseg": nseg.value}
+
+
+def cdmt_selftest_wait(limit_ms: float, arrive: bool = False) -> tuple[bool, float]:
+    """The tensor-core kernels' bounded mbarrier wait on a barrier nothing arrives on
+    (arrive: one arrival first).  Returns (gave_up, waited_ms)."""
+    g, w = ctypes.c_int(), ctypes.c_double()
+    _check(_lib.cdmt_selftest_wait(limit_ms, 1 if arrive else 0, ctypes.byref(g), ctypes.byref(w)), None)
+    return bool(g.value), w.value
+
+
+def cdmt_inject_timeout(plan) -> None:
+    """Mark the plan's device status as a tensor-core wait that gave up (host-side injection)."""
+    _check(_lib.cdmt_inject_timeout(plan), plan)
 
 
 def cdmt_execute(plan, d_in: int, d_out: int, d_scale: int = 0, stream: int = 0):

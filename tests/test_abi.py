@@ -104,6 +104,16 @@ def test_null_handles_of_the_8bit_and_incoherent_entry_points(cdmt):
     assert lib.cdmt_execute_host_u8(None, None, None, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_incoherent(None, None, 0.0, 0.0, 1, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_plan_group(None, 0, None, None, None, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_inject_timeout(None) == cdmt.CDMT_EINVAL
+
+
+@pytest.mark.parametrize("limit_ms", [0.0, -1.0, 1001.0, float("nan")])
+def test_selftest_wait_rejects_limits_outside_range(cdmt, limit_ms):
+    # checked before any device call: the wait must stay short
+    import ctypes
+    g, w = ctypes.c_int(), ctypes.c_double()
+    assert cdmt.lib().cdmt_selftest_wait(limit_ms, 0, ctypes.byref(g), ctypes.byref(w)) == cdmt.CDMT_EINVAL
+    assert cdmt.lib().cdmt_selftest_wait(1.0, 0, None, None) == cdmt.CDMT_EINVAL
 
 
 @pytest.mark.parametrize("groups", [-1, 3])
