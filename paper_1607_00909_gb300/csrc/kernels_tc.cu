@@ -60,6 +60,7 @@ constexpr uint32_t kF64Sbo = 2048;               // F_64 in global memory: K-maj
 constexpr uint32_t kF64Bytes = 32768;
 constexpr uint32_t kWaitPolls = 1u << 26;          // backstop on polls
 constexpr uint64_t kWaitNs = 50ull * 1000 * 1000;  // a GEMM batch takes microseconds; give up after 50 ms
+constexpr uint64_t kDrainNs = 20ull * 1000 * 1000; // after giving up: a late GEMM's last chance, per phase
 constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;
 
 // Sizes, shared-memory map, tensor-memory map and thread organisation for
@@ -262,6 +263,20 @@ __device__ __forceinline__ uint32_t tc_cta_setup(uint8_t *smem, const uint4 *__r
     __syncthreads();
     tc::fence_after();
     return tmem;
+}
+
+// After an item's wait gave up (CTA-uniform): one more bounded wait for each
+// phase of every pipe's mbarrier, by one thread, so that a GEMM that is merely
+// late completes before the tensor memory it writes is freed.  A phase that is
+// not pending completed earlier or costs one bounded wait.
+template <int AB, int LM> __device__ __forceinline__ void tc_cta_drain(uint8_t *smem)
+{
+    if (threadIdx.x != 0) return;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TcLayout<AB, LM>::off_misc);
+    for (int p = 0; p < TcLayout<AB, LM>::npipe; p++) {
+        (void)tc::mbar_wait(&mbar[p], 0, kDrainNs, kWaitPolls);
+        (void)tc::mbar_wait(&mbar[p], 1, kDrainNs, kWaitPolls);
+    }
 }
 
 template <int AB, int LM> __device__ __forceinline__ void tc_cta_teardown(uint32_t tmem)
@@ -617,6 +632,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         }
         if (!tc_run_item<UNIFORM, AB, LM>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
+            tc_cta_drain<AB, LM>(smem);
             break;
         }
     }
@@ -679,6 +695,7 @@ k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__
         it.scale_out = B.scale;
         if (!tc_run_item<true, AB, 12>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
+            tc_cta_drain<AB, 12>(smem);
             break;
         }
     }
