@@ -288,8 +288,10 @@ template <int AB, int LM> __device__ __forceinline__ void tc_cta_teardown(uint32
 }
 
 // The DM stage of one item.  Must be called by every thread of the CTA;
-// returns false (for every thread) if a tensor-core wait gave up.
-template <bool UNIFORM, int AB, int LM>
+// returns false (for every thread) if a tensor-core wait gave up.  NI > 0: the
+// item's nint, fixed at compile time (one detection variant in the per-DM loop);
+// NI = 0: nint chosen per DM among the six variants.
+template <bool UNIFORM, int AB, int LM, int NI>
 __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uint32_t tmem)
 {
     using L = TcLayout<AB, LM>;
@@ -558,7 +560,9 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
             float *orow = it.out + (int64_t)d * it.dm_stride;
             const uint32_t taddr = dcol + lane_off;
             const int m1 = t >> 1, ro = t & 1;
-            switch (nint) {
+            if constexpr (NI > 0) {
+                tc_detect<NI, P>(taddr, cg, m1, ro, orow, ulim, oscale);
+            } else switch (nint) {
             case 1: tc_detect<1, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
             case 2: tc_detect<2, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
             case 4: tc_detect<4, P>(taddr, cg, m1, ro, orow, ulim, oscale); break;
@@ -582,8 +586,9 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
 // Persistent: one CTA per SM sets up once (DFT matrix and twiddles in shared
 // memory, F in tensor memory) and takes items (DM tile, subband, segment,
 // channel) blockIdx.x, + gridDim.x, ...; while it works on one item, the next
-// item's spectrum and phase words are prefetched into L2.
-template <bool UNIFORM, int AB, int LM>
+// item's spectrum and phase words are prefetched into L2.  NI: nint fixed at
+// compile time (8), or 0 for any nint dividing 32.
+template <bool UNIFORM, int AB, int LM, int NI>
 __global__ void __launch_bounds__(TcLayout<AB, LM>::nt, 1)
 k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
                 const double *__restrict__ dm_list, const uint4 *__restrict__ bmat, const uint4 *__restrict__ bmat64,
@@ -630,7 +635,7 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
             if (tid < kSrcChunks) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
             else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - kSrcChunks), 4096);
         }
-        if (!tc_run_item<UNIFORM, AB, LM>(it, smem, tmem)) {
+        if (!tc_run_item<UNIFORM, AB, LM, NI>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
             tc_cta_drain<AB, LM>(smem);
             break;
@@ -693,7 +698,7 @@ k_dedisperse_tc_batch(const TcBeam *__restrict__ beams, int nbeam, const int *__
         it.nint = B.nint;
         it.ulim = seglen;
         it.scale_out = B.scale;
-        if (!tc_run_item<true, AB, 12>(it, smem, tmem)) {
+        if (!tc_run_item<true, AB, 12, 0>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
             tc_cta_drain<AB, 12>(smem);
             break;
@@ -710,9 +715,9 @@ size_t tc_smem(int ab, int lm)
     return ab ? TcLayout<1, 12>::total : TcLayout<0, 12>::total;
 }
 
-template <bool U, int AB, int LM> static cudaError_t set_attr()
+template <bool U, int AB, int LM, int NI = 0> static cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute(k_dedisperse_tc<U, AB, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_dedisperse_tc<U, AB, LM, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TcLayout<AB, LM>::total);
 }
 
@@ -722,6 +727,12 @@ template <int AB> static cudaError_t prepare_ab()
     if (e == cudaSuccess) e = set_attr<false, AB, 12>();
     if (e == cudaSuccess) e = set_attr<true, AB, 11>();
     if (e == cudaSuccess) e = set_attr<false, AB, 11>();
+    if constexpr (AB == 0) {   // the FP16 form with nint = 8 fixed at compile time
+        if (e == cudaSuccess) e = set_attr<true, 0, 12, 8>();
+        if (e == cudaSuccess) e = set_attr<false, 0, 12, 8>();
+        if (e == cudaSuccess) e = set_attr<true, 0, 11, 8>();
+        if (e == cudaSuccess) e = set_attr<false, 0, 11, 8>();
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dedisperse_tc_batch<AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TcLayout<AB, 12>::total);
@@ -742,12 +753,12 @@ cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev
     return cudaGetLastError();
 }
 
-template <bool U, int AB, int LM> static void launch(const TcArgs &a, cudaStream_t st)
+template <bool U, int AB, int LM, int NI = 0> static void launch(const TcArgs &a, cudaStream_t st)
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nitems = ntile * a.nsub * a.kc * a.nchan;
     const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
-    k_dedisperse_tc<U, AB, LM><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
+    k_dedisperse_tc<U, AB, LM, NI><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.bmat64, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan,
         a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile,
         a.tlim);
@@ -755,11 +766,14 @@ template <bool U, int AB, int LM> static void launch(const TcArgs &a, cudaStream
 
 template <int LM> static void launch_lm(const TcArgs &a, cudaStream_t st)
 {
+    const bool n8 = a.nint == 8;
     if (a.uniform) {
         if (a.ab) launch<true, 1, LM>(a, st);
+        else if (n8) launch<true, 0, LM, 8>(a, st);
         else launch<true, 0, LM>(a, st);
     } else {
         if (a.ab) launch<false, 1, LM>(a, st);
+        else if (n8) launch<false, 0, LM, 8>(a, st);
         else launch<false, 0, LM>(a, st);
     }
 }
