@@ -189,9 +189,9 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent): 544.8 MB read + 2068.5 MB
-    # written for 4.253e9 units (ncu --set full, 4th launch)
-    "0815fca4fa86f43a:fp16": 0.6145,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 544.3 MB read +
+    # 2068.2 MB written for 4.253e9 units (ncu --set full, 4th launch)
+    "ce32fc6e6d3b0f63:fp16": 0.6143,
 }
 
 try:
