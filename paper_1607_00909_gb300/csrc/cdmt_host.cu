@@ -274,6 +274,7 @@ namespace cdmt {
 // The forward stage of kc segments (segment in_k0 of `in` first) into the plan's spectra.
 int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t in_k0, int kc, cudaStream_t st)
 {
+    const Range range("cdmt forward stage");
     ForwardArgs fa{};
     fa.in = in;
     fa.spec = p->spec;
@@ -300,6 +301,7 @@ int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t i
 int enqueue_dm(cdmt_plan_s *p, float *out, int64_t out_stride, int64_t out_k0, int kc, int dm_off, int dm_cnt,
                cudaStream_t st)
 {
+    const Range range("cdmt DM stage");
     if (p->precision != CDMT_PREC_FP32) {
         TcArgs ta{};
         ta.spec = p->spec;
@@ -886,6 +888,7 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, const float *h_scale, float 
         first = std::max<int64_t>(1, std::min<int64_t>(kcm, std::max<int64_t>(kcm / 4, fill)));
     }
     for (int64_t k0 = 0; k0 < p->nseg; k0 += (k0 == 0 ? first : kcm), bi = (bi + 1) % 3) {
+        const Range range("cdmt host block");
         Staging &si = p->stage[bi];
         const int kc = (int)std::min<int64_t>(k0 == 0 ? first : kcm, p->nseg - k0);
         const int64_t span = (kc - 1) * p->nvalid + p->nbin;

@@ -190,6 +190,7 @@ int cdmt_incoherent(cdmt_plan_t p, const float *d_fb, double ddm_lo, double ddm_
 {
     if (!p) return CDMT_EINVAL;
     if (!d_fb || !d_out || nk < 1) return ifail(p, CDMT_EINVAL, "NULL buffer or nk < 1");
+    const cdmt::Range range("cdmt incoherent stage");
     const int rows = p->nsub * p->nchan;
     const bool same = p->inc_key[0] == ddm_lo && p->inc_key[1] == ddm_step && p->inc_nk == nk;
     std::vector<int32_t> tab;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cmath>
@@ -12,6 +13,16 @@
 #include "cdmt_internal.h"
 
 namespace cdmt {
+
+// A named NVTX range over the host code that enqueues a stage, for tools that
+// trace (ncu --nvtx, Nsight Systems); without such a tool attached it costs a
+// branch.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 struct Staging {
     float4 *in = nullptr;   // [nsub][span_max] samples

@@ -353,6 +353,7 @@ int redig_reserve(cdmt_plan_s *p)
 int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride, uint8_t *d_u8, float *d_stats,
                   cudaStream_t st, double sk_nsigma, uint8_t *d_flags, int ndm_r)
 {
+    const cdmt::Range range("cdmt redigitisation");
     const int rows = p->nsub * p->nchan;
     const int ndm = ndm_r > 0 ? ndm_r : p->ndm;   // DMs in d_fb (a range of the plan's)
     if (nt < 1) return rfail(p, CDMT_EINVAL, "no samples to redigitise");
