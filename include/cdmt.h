@@ -618,6 +618,28 @@ int cdmt_server_wait(cdmt_server_t server, int64_t request_id, double timeout_s,
 /* cdmt_server_release - give a completed block's output slot back. */
 int cdmt_server_release(cdmt_server_t server, int64_t request_id);
 
+/* cdmt_server_save_beam - checkpoint of a beam's stream: the overlap tail that
+ * its next block is appended to (the last N_bin - S samples it has not yet
+ * completed into segments, Sec. 2), its segment and block counters, and the
+ * shape the beam was made with.  A stream restored from it into a beam of the
+ * same shape continues exactly: the next block's filterbank equals the one the
+ * original beam would have produced, at the same output position.
+ *   host   out: the checkpoint (host memory), or NULL to query its size
+ *   bytes  in: the size of host; out: the checkpoint's size
+ * Every block submitted to the beam must be done (waited for or not).
+ * Errors: CDMT_EINVAL (NULL server or bytes, no such beam, blocks queued or
+ * running, host smaller than the checkpoint), CDMT_ECUDA. */
+int cdmt_server_save_beam(cdmt_server_t srv, int beam, void *host, int64_t *bytes);
+
+/* cdmt_server_restore_beam - continue a stream from a checkpoint of
+ * cdmt_server_save_beam (host memory, `bytes` long) in a beam with the same
+ * subbands, block length, band, DM grid, channels, nint, N_bin and overlap (the
+ * precision, input and output types may differ).  The beam must have no block
+ * queued or running; its tail and counters are replaced.
+ * Errors: CDMT_EINVAL (NULL pointers, no such beam, blocks queued or running,
+ * not a checkpoint, another shape, truncated), CDMT_ECUDA. */
+int cdmt_server_restore_beam(cdmt_server_t srv, int beam, const void *host, int64_t bytes);
+
 /* cdmt_server_get_stats - latency percentiles, real-time factor and throughput of
  * the blocks completed since the start (or the last reset). */
 int cdmt_server_get_stats(cdmt_server_t server, cdmt_server_stats *stats);

@@ -133,6 +133,8 @@ def _load():
     lib.cdmt_server_release.argtypes = [P, ctypes.c_int64]
     lib.cdmt_server_get_stats.argtypes = [P, ctypes.POINTER(cdmt_server_stats)]
     lib.cdmt_server_reset_stats.argtypes = [P]
+    lib.cdmt_server_save_beam.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.cdmt_server_restore_beam.argtypes = [P, ctypes.c_int, P, ctypes.c_int64]
     lib.cdmt_server_last_error.argtypes = [P]
     lib.cdmt_server_last_error.restype = ctypes.c_char_p
     lib.cdmt_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(cdmt_beam),
@@ -180,7 +182,7 @@ EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "c
             "cdmt_batch_status", "cdmt_batch_last_error", "cdmt_batch_destroy", "cdmt_batch_copy_out",
             "cdmt_server_create", "cdmt_server_destroy", "cdmt_server_add_beam", "cdmt_server_submit",
             "cdmt_server_wait", "cdmt_server_release", "cdmt_server_get_stats", "cdmt_server_reset_stats",
-            "cdmt_server_last_error")
+            "cdmt_server_last_error", "cdmt_server_save_beam", "cdmt_server_restore_beam")
 
 
 def lib():
@@ -377,6 +379,23 @@ def cdmt_server_destroy(server):
     _scheck(_lib.cdmt_server_destroy(server))
 
 
+def cdmt_server_save_beam(server, beam: int):
+    """Checkpoint of a beam's stream (its overlap tail and counters) as a numpy uint8 array."""
+    import numpy as np
+    n = ctypes.c_int64()
+    _scheck(_lib.cdmt_server_save_beam(server, beam, None, ctypes.byref(n)), server)
+    buf = np.empty(n.value, dtype=np.uint8)
+    _scheck(_lib.cdmt_server_save_beam(server, beam, buf.ctypes.data, ctypes.byref(n)), server)
+    return buf[:n.value]
+
+
+def cdmt_server_restore_beam(server, beam: int, ckpt) -> None:
+    """Continue a beam's stream from a checkpoint of cdmt_server_save_beam."""
+    import numpy as np
+    buf = np.ascontiguousarray(ckpt, dtype=np.uint8)
+    _scheck(_lib.cdmt_server_restore_beam(server, beam, buf.ctypes.data, buf.size), server)
+
+
 def cdmt_server_add_beam(server, desc: cdmt_stream_desc) -> int:
     b = ctypes.c_int()
     _scheck(_lib.cdmt_server_add_beam(server, ctypes.byref(desc), ctypes.byref(b)), server)
@@ -436,6 +455,12 @@ class Server:
 
     def stats(self):
         return cdmt_server_get_stats(self.handle)
+
+    def save_beam(self, beam):
+        return cdmt_server_save_beam(self.handle, beam)
+
+    def restore_beam(self, beam, ckpt):
+        cdmt_server_restore_beam(self.handle, beam, ckpt)
 
     @staticmethod
     def block_view(res: cdmt_block_result, ndm: int, rows: int):

@@ -589,6 +589,101 @@ int cdmt_server_get_stats(cdmt_server_t v, cdmt_server_stats *st)
     return CDMT_OK;
 }
 
+namespace {
+
+// Checkpoint of a beam's stream: the shape it was made with, the counters, then
+// the overlap tail, nsub rows of `tail` float4 samples.
+struct BeamCheckpoint {
+    uint64_t magic;
+    int32_t version, nsub;
+    int64_t block_len, nbin, nd, tail, seg_total, next_index;
+    double f_centre, bw, dm_first, dm_step;
+    int32_t ndm, nchan, nint, reserved;
+};
+constexpr uint64_t kCheckpointMagic = 0x636d646d74626d31ull;   // marks a beam checkpoint
+
+// The beam's blocks are all done (none queued or running); called with the lock held.
+bool beam_idle(const cdmt_server_s *v, int beam)
+{
+    for (const auto &kv : v->reqs)
+        if (kv.second.beam == beam && kv.second.state < 2) return false;
+    return true;
+}
+
+}  // namespace
+
+int cdmt_server_save_beam(cdmt_server_t v, int beam, void *host, int64_t *bytes)
+{
+    if (!v || !bytes) return sfail(v, CDMT_EINVAL, "NULL server or size");
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (beam < 0 || beam >= (int)v->beams.size() || !v->beams[beam].active)
+        return sfail(v, CDMT_EINVAL, "no beam %d", beam);
+    if (!beam_idle(v, beam)) return sfail(v, CDMT_EINVAL, "beam %d has blocks queued or running", beam);
+    const Beam &b = v->beams[beam];
+    const int64_t need = (int64_t)sizeof(BeamCheckpoint) + (int64_t)b.d.nsub * b.tail * 16;
+    if (!host) {
+        *bytes = need;
+        return CDMT_OK;
+    }
+    if (*bytes < need) return sfail(v, CDMT_EINVAL, "checkpoint needs %lld bytes", (long long)need);
+    BeamCheckpoint h{};
+    h.magic = kCheckpointMagic;
+    h.version = 1;
+    h.nsub = b.d.nsub;
+    h.block_len = b.d.block_len;
+    h.nbin = b.N;
+    h.nd = b.nd;
+    h.tail = b.tail;
+    h.seg_total = b.seg_total;
+    h.next_index = b.next_index;
+    h.f_centre = b.d.f_centre_mhz;
+    h.bw = b.d.bw_sub_mhz;
+    h.dm_first = b.d.dm_first;
+    h.dm_step = b.d.dm_step;
+    h.ndm = b.d.ndm;
+    h.nchan = b.d.nchan;
+    h.nint = b.d.nint;
+    std::memcpy(host, &h, sizeof h);
+    cudaSetDevice(v->device);
+    if (b.tail > 0 && cudaMemcpy2D(static_cast<uint8_t *>(host) + sizeof h, (size_t)b.tail * 16, b.stage[b.cur],
+                                   (size_t)b.cap * 16, (size_t)b.tail * 16, b.d.nsub, cudaMemcpyDeviceToHost) !=
+                          cudaSuccess)
+        return sfail(v, CDMT_ECUDA, "copy of the overlap tail failed");
+    *bytes = need;
+    return CDMT_OK;
+}
+
+int cdmt_server_restore_beam(cdmt_server_t v, int beam, const void *host, int64_t bytes)
+{
+    if (!v || !host) return sfail(v, CDMT_EINVAL, "NULL server or checkpoint");
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (beam < 0 || beam >= (int)v->beams.size() || !v->beams[beam].active)
+        return sfail(v, CDMT_EINVAL, "no beam %d", beam);
+    if (!beam_idle(v, beam)) return sfail(v, CDMT_EINVAL, "beam %d has blocks queued or running", beam);
+    Beam &b = v->beams[beam];
+    BeamCheckpoint h;
+    if (bytes < (int64_t)sizeof h) return sfail(v, CDMT_EINVAL, "checkpoint too short");
+    std::memcpy(&h, host, sizeof h);
+    if (h.magic != kCheckpointMagic || h.version != 1) return sfail(v, CDMT_EINVAL, "not a beam checkpoint");
+    if (h.nsub != b.d.nsub || h.block_len != b.d.block_len || h.nbin != b.N || h.nd != b.nd || h.ndm != b.d.ndm ||
+        h.nchan != b.d.nchan || h.nint != b.d.nint || h.f_centre != b.d.f_centre_mhz || h.bw != b.d.bw_sub_mhz ||
+        h.dm_first != b.d.dm_first || h.dm_step != b.d.dm_step)
+        return sfail(v, CDMT_EINVAL, "checkpoint of a stream of another shape");
+    if (h.tail < 0 || h.tail >= b.N || bytes < (int64_t)sizeof h + (int64_t)h.nsub * h.tail * 16 ||
+        h.seg_total < 0 || h.next_index < 0)
+        return sfail(v, CDMT_EINVAL, "checkpoint corrupt or truncated");
+    cudaSetDevice(v->device);
+    if (cudaStreamSynchronize(b.st) != cudaSuccess) return sfail(v, CDMT_ECUDA, "beam stream failed");
+    if (h.tail > 0 && cudaMemcpy2D(b.stage[b.cur], (size_t)b.cap * 16, static_cast<const uint8_t *>(host) + sizeof h,
+                                   (size_t)h.tail * 16, (size_t)h.tail * 16, h.nsub, cudaMemcpyHostToDevice) !=
+                          cudaSuccess)
+        return sfail(v, CDMT_ECUDA, "copy of the overlap tail failed");
+    b.tail = h.tail;
+    b.seg_total = h.seg_total;
+    b.next_index = h.next_index;
+    return CDMT_OK;
+}
+
 int cdmt_server_reset_stats(cdmt_server_t v)
 {
     if (!v) return sfail(nullptr, CDMT_EINVAL, "NULL server");

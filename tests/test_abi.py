@@ -105,6 +105,8 @@ def test_null_handles_of_the_8bit_and_incoherent_entry_points(cdmt):
     assert lib.cdmt_incoherent(None, None, 0.0, 0.0, 1, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_plan_group(None, 0, None, None, None, None, None) == cdmt.CDMT_EINVAL
     assert lib.cdmt_inject_timeout(None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_server_save_beam(None, 0, None, None) == cdmt.CDMT_EINVAL
+    assert lib.cdmt_server_restore_beam(None, 0, None, 0) == cdmt.CDMT_EINVAL
 
 
 @pytest.mark.parametrize("limit_ms", [0.0, -1.0, 1001.0, float("nan")])

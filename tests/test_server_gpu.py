@@ -204,3 +204,57 @@ def test_u8_blocks_in_dm_ranges_under_a_small_budget(cdmt, orc):
     for srv in servers:
         srv.close()
     assert checked >= 4
+
+
+def test_checkpoint_resumes_a_stream_exactly(cdmt):
+    # blocks 0-3 on one server, a checkpoint of the beam, blocks 4-7 on a new server restored
+    # from it: the same filterbank at the same positions, bit for bit, as the stream served
+    # whole; block indices continue.  The blocks are shorter than N, so the checkpoint holds a
+    # partly filled tail.
+    import torch
+    b = BEAMS[1]
+    L = b["block_len"]
+    x = synth.noise(b["seed"] + 100, b["nsub"], NBLK * L)
+    blocks = [torch.from_numpy(np.ascontiguousarray(x[:, k * L:(k + 1) * L])).pin_memory() for k in range(NBLK)]
+
+    def beam(srv, block_len=L):
+        return srv.add_beam(b["nsub"], block_len, b["f_centre"], BW, b["dm_first"], b["dm_step"], b["ndm"],
+                            b["nchan"], b["nint"], precision=cdmt.CDMT_PREC_FP16, dm_tile=b["ndm"])
+
+    def serve(srv, bid, ks):
+        got = {}
+        for k in ks:
+            rid = srv.submit(bid, blocks[k].data_ptr())
+            res = srv.wait(rid, 120.0)
+            assert res.index == k
+            if res.samples > 0:
+                got[res.first_sample] = srv.block_view(res, b["ndm"], b["nsub"] * b["nchan"]).cpu().numpy()
+            srv.release(rid)
+        return got
+
+    srv = cdmt.Server()
+    ref = serve(srv, beam(srv), range(NBLK))
+    srv.close()
+    sa = cdmt.Server()
+    a = beam(sa)
+    part = serve(sa, a, range(4))
+    ck = sa.save_beam(a)
+    sa.close()
+    assert ck.size > 64
+    sb = cdmt.Server()
+    nb = beam(sb)
+    sb.restore_beam(nb, ck)
+    part.update(serve(sb, nb, range(4, NBLK)))
+    sb.close()
+    assert sorted(part) == sorted(ref)
+    for k in ref:
+        assert np.array_equal(part[k], ref[k])
+    # refused: another shape, a truncated checkpoint
+    sc = cdmt.Server()
+    other = beam(sc, block_len=2 * L)
+    same = beam(sc)
+    for bad, data in ((other, ck), (same, ck[:ck.size - 16])):
+        with pytest.raises(cdmt.CdmtError) as e:
+            sc.restore_beam(bad, data)
+        assert e.value.status == cdmt.CDMT_EINVAL
+    sc.close()
