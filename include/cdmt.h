@@ -223,7 +223,10 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * pageable memory works but the copies are then synchronous.  Blocks until
  * h_out holds the result.  h_scale is a host array of nsub floats for
  * CDMT_IN_I8 input (required then; the input is then 4 bytes per sample, so
- * its copy to the device is 4x smaller).
+ * its copy to the device is 4x smaller).  A plan with DM groups
+ * (cdmt_opts.dm_groups) copies the whole input in, runs cdmt_execute and copies
+ * the whole filterbank out, without overlapping copies and compute (its groups
+ * segment the input differently), on device buffers it keeps.
  * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_ECUDA.
  */
 /* cdmt_execute_host_u8 - the pipeline of Algorithm 1 up to "redigitize" and
@@ -235,7 +238,8 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * and copied back as 8-bit codes, 4x fewer bytes than float32.  h_u8: host
  * (pinned for overlap) uint8 [ndm][nout][nsub*nchan], spectra in decreasing
  * frequency.  *block_segments (may be NULL) receives the segments per block
- * (the last block may be shorter).  Errors as cdmt_execute_host (a
+ * (the last block may be shorter).  A plan with DM groups redigitises its whole
+ * filterbank as one block (*block_segments = nseg of cdmt_plan_info).  Errors as cdmt_execute_host (a
  * CDMT_IN_I8 plan needs cdmt_execute_host_u8_ex, which takes the scales). */
 int cdmt_execute_host_u8(cdmt_plan_t plan, const void *h_in, uint8_t *h_u8, int64_t *block_segments,
                          void *cuda_stream);

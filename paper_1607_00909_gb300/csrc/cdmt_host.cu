@@ -232,7 +232,7 @@ void release(cdmt_plan_s *p)
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
                     p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab,
-                    p->d_scale_buf};
+                    p->d_scale_buf, p->grp_in, p->grp_out, p->grp_u8};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &st : p->stage) {
@@ -855,6 +855,44 @@ int host_setup(cdmt_plan_s *p, int64_t kc, int64_t out_floats, cudaStream_t st)
 // compute (the first one is the pipeline's fill) while its rows stay long.
 // *kc_used receives the segments per block.
 int host_pipeline(cdmt_plan_s *p, const void *h_in, const float *h_scale, float *h_out, uint8_t *h_u8,
+                  int64_t *kc_used, cudaStream_t st);
+
+// Plans with DM groups from and to host memory: the whole input to the device, the grouped
+// execute, and the whole filterbank back, or its 8-bit codes with the whole input as one data
+// block (Sec. 3 statistics over all of it).  Copies and compute do not overlap: the groups
+// segment the input differently, so there is no common block of segments to pipeline.
+int grouped_host(cdmt_plan_s *p, const void *h_in, const float *h_scale, float *h_out, uint8_t *h_u8,
+                 int64_t *kc_used, cudaStream_t st)
+{
+    int rc;
+    const bool i8 = p->in_dtype == CDMT_IN_I8;
+    if (i8 && !h_scale) return fail(p, CDMT_EINVAL, "int8 input needs the per-subband scales");
+    const size_t in_bytes = (size_t)p->nsub * p->nsamp * (i8 ? 4 : 16);
+    const size_t fb = (size_t)p->ndm * p->nsub * p->nchan * p->nout;
+    if (!p->grp_in && (rc = dalloc(p, &p->grp_in, in_bytes)) != CDMT_OK) return rc;
+    if (!p->grp_out && (rc = dalloc(p, &p->grp_out, fb)) != CDMT_OK) return rc;
+    if (h_u8 && !p->grp_u8 && (rc = dalloc(p, &p->grp_u8, fb)) != CDMT_OK) return rc;
+    CK(p, cudaMemcpyAsync(p->grp_in, h_in, in_bytes, cudaMemcpyHostToDevice, st));
+    const float *d_scale = nullptr;
+    if (i8) {
+        if (!p->d_scale_buf && (rc = dalloc(p, &p->d_scale_buf, (size_t)p->nsub)) != CDMT_OK) return rc;
+        CK(p, cudaMemcpyAsync(p->d_scale_buf, h_scale, sizeof(float) * p->nsub, cudaMemcpyHostToDevice, st));
+        d_scale = p->d_scale_buf;
+    }
+    if ((rc = cdmt_execute(p, p->grp_in, p->grp_out, d_scale, st)) != CDMT_OK) return rc;
+    if (h_u8) {
+        if ((rc = redig_enqueue(p, p->grp_out, p->nout, p->nout, p->grp_u8, nullptr, st, p->sk_nsigma)) != CDMT_OK)
+            return rc;
+        CK(p, cudaMemcpyAsync(h_u8, p->grp_u8, fb, cudaMemcpyDeviceToHost, st));
+    } else {
+        CK(p, cudaMemcpyAsync(h_out, p->grp_out, fb * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    CK(p, cudaStreamSynchronize(st));
+    if (kc_used) *kc_used = p->nseg;
+    return CDMT_OK;
+}
+
+int host_pipeline(cdmt_plan_s *p, const void *h_in, const float *h_scale, float *h_out, uint8_t *h_u8,
                   int64_t *kc_used, cudaStream_t st)
 {
     int rc;
@@ -935,8 +973,9 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    if (!p->groups.empty()) return fail(p, CDMT_ENOTSUP, "plans with DM groups run from device memory only");
-    const int rc = host_pipeline(p, h_in, h_scale, h_out, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int rc = p->groups.empty() ? host_pipeline(p, h_in, h_scale, h_out, nullptr, nullptr, st)
+                                     : grouped_host(p, h_in, h_scale, h_out, nullptr, nullptr, st);
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }
@@ -949,8 +988,9 @@ int cdmt_execute_host_u8_ex(cdmt_plan_t p, const void *h_in, const float *h_scal
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) CK(p, cudaSetDevice(p->device));
-    if (!p->groups.empty()) return fail(p, CDMT_ENOTSUP, "plans with DM groups run from device memory only");
-    const int rc = host_pipeline(p, h_in, h_scale, nullptr, h_u8, block_segments, static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int rc = p->groups.empty() ? host_pipeline(p, h_in, h_scale, nullptr, h_u8, block_segments, st)
+                                     : grouped_host(p, h_in, h_scale, nullptr, h_u8, block_segments, st);
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }

@@ -86,6 +86,10 @@ struct cdmt_plan_s {
     };
     std::vector<Group> groups;
     int64_t out_tlim = INT64_MAX;  // DM stage: output positions >= out_tlim are not stored
+    // grouped plans from and to host memory: the whole input, filterbank and codes on the device
+    uint8_t *grp_in = nullptr;
+    float *grp_out = nullptr;
+    uint8_t *grp_u8 = nullptr;
     // stage timing (cdmt_set_timing / cdmt_stage_times)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;

@@ -110,21 +110,28 @@ def test_grouped_plan_chunked_and_int8(cdmt, orc):
 
 
 def test_grouped_plan_stage_times_and_host_entry_points(cdmt):
-    # stage timing sums the groups' launches; the host pipelines refuse grouped plans
+    # stage timing sums the groups' launches; from host memory a grouped plan gives the
+    # device execute's filterbank, and 8-bit codes of the whole input as one block, bit for bit
     import torch
     c = _case(1)
     x = synth.noise(48, c["nsub"], c["nsamp"])
     plan = _plan(cdmt, c, 4, cdmt.CDMT_PREC_FP16, 1)
     cdmt.cdmt_set_timing(plan.handle, True)
     cdmt.cdmt_stage_times(plan.handle)
-    gpu_filterbank(plan, x)
+    want = gpu_filterbank(plan, x)
     (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
     assert dd_n == 4 and fwd_n == 8 and fwd_ms > 0 and dd_ms > 0
+    cdmt.cdmt_set_timing(plan.handle, False)
     hin = torch.from_numpy(x).pin_memory()
-    hout = torch.empty(plan.out_shape(), dtype=torch.float32).pin_memory()
-    with pytest.raises(cdmt.CdmtError) as e:
-        plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, 0)
-    assert e.value.status == cdmt.CDMT_ENOTSUP
+    hout = torch.full(plan.out_shape(), float("nan"), dtype=torch.float32).pin_memory()
+    plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, 0)
+    assert np.array_equal(hout.numpy(), want)
+    ndm, rows, nt = plan.out_shape()
+    codes = plan.redigitise(torch.from_numpy(want).cuda())
+    torch.cuda.synchronize()
+    hu8 = torch.empty((ndm, nt, rows), dtype=torch.uint8).pin_memory()
+    assert plan.execute_host_u8(hin.data_ptr(), hu8.data_ptr(), 0) == plan.info["nseg"]
+    assert np.array_equal(hu8.numpy(), codes.cpu().numpy())
     plan.close()
 
 
