@@ -145,9 +145,10 @@ typedef struct cdmt_info {
  *   ndm           >= 1
  *   nchan         channels per subband n_c, a power of two 2..32
  *   nint          output integration factor, >= 1
- * Errors: CDMT_EINVAL (bad argument, N_bin <= n_d n_c, nsamp < N_bin),
- *         CDMT_ENOTSUP (M_bin outside 512..4096; tensor-core precisions need
- *         M_bin = 4096), CDMT_ENOMEM, CDMT_ECUDA.
+ * Errors: CDMT_EINVAL (bad argument, N_bin <= n_d n_c, nsamp < N_bin;
+ *         cdmt_opts.dm_groups outside 0..ndm), CDMT_ENOTSUP (M_bin outside
+ *         512..4096; tensor-core precisions need M_bin = 2048 or 4096 and nint
+ *         dividing 32), CDMT_ENOMEM, CDMT_EBUDGET (cdmt_opts.mem_budget), CDMT_ECUDA.
  * Allocates device memory (tables and workspace); the plan owns all of it.
  */
 int cdmt_plan(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz,
