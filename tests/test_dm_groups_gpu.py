@@ -105,6 +105,14 @@ def test_grouped_plan_chunked_and_int8(cdmt, orc):
     o = orc.filterbank_grouped(deq, c["fc"], BW, c["dms"], c["nchan"], c["nint"], c["nbin"], 3, chirp=1)
     emax, erms = rel_errors(want, o)
     assert emax <= 1e-5 and erms <= 1e-5
+    # int8 from host memory, the scales in host memory too
+    hin, hsc = torch.from_numpy(q).pin_memory(), torch.from_numpy(scale)
+    hout = torch.full(pi.out_shape(), float("nan"), dtype=torch.float32).pin_memory()
+    pi.execute_host(hin.data_ptr(), hout.data_ptr(), hsc.data_ptr(), 0)
+    assert np.array_equal(hout.numpy(), want)
+    with pytest.raises(cdmt.CdmtError) as e:
+        pi.execute_host(hin.data_ptr(), hout.data_ptr(), 0, 0)
+    assert e.value.status == cdmt.CDMT_EINVAL
     for p in (pf, pc, pi):
         p.close()
 
