@@ -328,7 +328,67 @@ def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
     cdmt.cdmt_set_timing(plan.handle, False)
     ms_max = max_over_ranks(ms, world, dev)
     return {"plan": plan, "info": info, "ms_max": ms_max, "fwd_ms": fwd_ms, "dd_ms": dd_ms, "fwd_n": fwd_n,
-            "dd_n": dd_n, "value": replica_value(info["units"], args.steps, ms_max, world)}
+            "dd_n": dd_n, "steps": args.steps, "value": replica_value(info["units"], args.steps, ms_max, world)}
+
+
+def dm_stage_roofline(form, r, props, sm_max):
+    """Roofline of one form's DM-stage kernel: the slower of (a) the nominal FFT flops
+    10 N log2(M) / S per unit (2 polarisations x n_c backward M-point FFTs per segment,
+    5 M log2 M each, and the forward N-point FFT amortised over the DMs is left out as in
+    the definition) at the form's peak (FP32: SMs x 128 lanes x 2 x SM clock, derived;
+    FP16 / BF16: the measured sustained bf16 dense peak) and (b) the algorithmic bytes
+    16 N / (S ndm) + 4 / nint per unit (the spectra read once per DM tile, the filterbank
+    written once) at the measured HBM bandwidth, divided by the kernel's measured time
+    per launch.  The tensor-core forms also report the GEMM work they issue (the
+    64-point DFTs as dense real GEMMs) against the tensor peak, as a utilisation of the
+    tensor pipe (not the roofline)."""
+    info = r["info"]
+    units = info["units"]
+    nbin, mbin, S = info["nbin"], info["mbin"], info["nvalid"]
+    t = r["dd_ms"] / max(1, r["dd_n"]) / 1e3          # seconds per DM-stage launch
+    launches_per_step = r["dd_n"] / max(1, r["steps"])
+    units_launch = units / launches_per_step
+    flops_unit = 10.0 * nbin * np.log2(mbin) / S
+    bytes_unit = 16.0 * nbin / (S * info["ndm"]) + 4.0 / info["nint"]
+    hbm = MEASURED.get("hbm_gbs") or 6800.0
+    if form == "fp32":
+        fpeak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        fbasis = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
+        kernel, fbound = "k_dedisperse", "alu"
+    else:
+        fpeak = MEASURED.get("bf16_tflops_sustained") or 1700.0
+        fbasis = "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); the FP16 dense rate equals BF16"
+        kernel, fbound = "k_dedisperse_tc", "tensor"
+    t_flop = flops_unit * units_launch / (fpeak * 1e12)
+    t_byte = bytes_unit * units_launch / (hbm * 1e9)
+    if t_byte >= t_flop:
+        rf = {"bound": "hbm", "achieved": bytes_unit * units_launch / t / 1e9, "peak": hbm, "unit": "GB/s",
+              "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    else:
+        rf = {"bound": fbound, "achieved": flops_unit * units_launch / t / 1e12, "peak": fpeak, "unit": "TFLOP/s",
+              "peak_basis": fbasis}
+    rf["frac"] = max(t_flop, t_byte) / t
+    tr = NCU_TRAFFIC.get(kernel_source_hash(form) + ":" + form)
+    rf.update({"traffic": tr * units_launch if tr else None, "kernel": kernel,
+               "definition": "slower of nominal FFT flops at the form's peak and algorithmic bytes at HBM bandwidth, "
+                             "over the kernel's time per launch",
+               "flops_per_unit": flops_unit, "bytes_per_unit": bytes_unit, "units_per_launch": units_launch,
+               "flop_leg_ms": t_flop * 1e3, "byte_leg_ms": t_byte * 1e3, "flop_peak_tflops": fpeak,
+               "flop_peak_basis": fbasis, "kernel_ms_per_launch": t * 1e3,
+               "nominal_fft_tflops": flops_unit * units_launch / t / 1e12,
+               "share_of_step": r["dd_ms"] / max(1e-9, r["dd_ms"] + r["fwd_ms"])})
+    if form != "fp32":
+        # the tensor-core GEMM work issued per (channel, DM), P = M / 64: pass A 128 x 2P x 2P and
+        # pass B 128 x 2P x 128, 2 flops per multiply-add (x3 for the BF16 hi/lo products)
+        mult = 3 if form == "bf16" else 1
+        P_ = mbin // 64
+        tc_unit = mult * 2 * 128 * (2 * P_) * (2 * P_ + 128) * info["nchan"] / S
+        ach = tc_unit * units_launch / t / 1e12
+        rf["tensor_pipe_issued"] = {"flops_per_unit": tc_unit, "achieved_tflops": ach, "peak_tflops": fpeak,
+                                    "frac": ach / fpeak,
+                                    "note": "dense real DFT GEMMs issued on the tensor cores (17x the nominal FFT "
+                                            "flops at M = 4096): a utilisation of the tensor pipe, not the roofline"}
+    return rf
 
 
 def gpu_arm(args, w):
@@ -454,73 +514,52 @@ def gpu_arm(args, w):
         log(f"rank {rank}: cuFFT unfused comparison: {cufft['value']:.2f} {UNIT}, {cufft['ms_per_step']:.1f} ms/step, "
             f"max rel diff vs headline {cufft['max_rel_diff_vs_headline']:.2e}")
 
-    # ---- roofline of the dominant kernel of the headline form
-    nbin, mbin, nseg = info["nbin"], info["mbin"], info["nseg"]
-    dd_avg_s = R["dd_ms"] / max(1, R["dd_n"]) / 1e3
+    # ---- roofline of the dominant kernel (the DM stage) of every form, SURVEY 8(d)'s definition
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    fft_flops_unit = 10.0 * nbin * np.log2(mbin) / info["nvalid"]   # 2 pols x n_c x 5 M log2 M per segment
-    if head == "fp32":
-        achieved = fft_flops_unit * units / dd_avg_s / 1e12
-        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": "k_dedisperse", "work": "nominal FFT flops 10 N log2(M) / S per unit",
-                    "flops_per_unit": fft_flops_unit,
-                    "peak_basis": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
-    else:
-        # the tensor-core GEMM work actually issued per (channel, DM), with P = M / 64: pass A
-        # 128 x 2P x 2P and pass B 128 x 2P x 128, 2 flops per multiply-add (x3 for the BF16 hi/lo
-        # products); per unit = that x n_c / S.  M = 4096: 2 x 128^3 x 2.
-        mult = 3 if head == "bf16" else 1
-        P_ = mbin // 64
-        tc_flops_unit = mult * 2 * 128 * (2 * P_) * (2 * P_ + 128) * info["nchan"] / info["nvalid"]
-        achieved = tc_flops_unit * units / dd_avg_s / 1e12
-        peak = MEASURED.get("bf16_tflops_sustained") or 1703.7
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": "k_dedisperse_tc", "work": "tensor-core GEMM flops issued (two real DFT GEMMs per channel and DM)",
-                    "flops_per_unit": tc_flops_unit,
-                    "nominal_fft_tflops": fft_flops_unit * units / dd_avg_s / 1e12,
-                    "peak_basis": "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); FP16 dense rate equals BF16"}
-    tr = NCU_TRAFFIC.get(kernel_source_hash(head) + ":" + head)
-    roofline.update({"traffic": tr * units if tr else None, "kernel_ms_per_launch": dd_avg_s * 1e3,
-                     "share_of_step": R["dd_ms"] / max(1e-9, R["dd_ms"] + R["fwd_ms"])})
+    rooflines = {f: dm_stage_roofline(f, r, props, sm_max) for f, r in results.items()}
+    roofline = rooflines[head]
 
-    # ---- end to end through the host-memory entry point
+    # ---- end to end through the host-memory entry points: each call timed on its own (host clock
+    #      around the call, which returns once the result is in host memory), over args.e2e_calls calls
     e2e = None
     if not args.no_e2e:
         st = stream.cuda_stream
+
+        def timed_calls(fn):
+            fn()   # warm-up (allocates the staging)
+            barrier()
+            torch.cuda.synchronize(dev)
+            ts = []
+            for _ in range(args.e2e_calls):
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize(dev)
+                ts.append(time.perf_counter() - t0)
+            med = max_over_ranks(float(np.median(ts)), world, dev)
+            return med, {"calls": len(ts), "ms_median": med * 1e3, "ms_min": min(ts) * 1e3, "ms_max": max(ts) * 1e3}
+
         hin = torch.from_numpy(x).pin_memory()
         hout = torch.empty(plan.out_shape(), dtype=torch.float32, pin_memory=True)
-        plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)   # warm-up (allocates staging)
-        ne = max(1, min(args.steps, 3))
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0 = time.perf_counter()
-        for _ in range(ne):
-            plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st)
-        torch.cuda.synchronize(dev)
-        e_s = time.perf_counter() - e0
+        med, spread = timed_calls(lambda: plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st))
         plan.device_status()
-        e_max = max_over_ranks(e_s, world, dev)
-        e2e = {"value": replica_value(units, ne, e_max * 1e3, world), "unit": UNIT,
+        e2e = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
                "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
-               "steps": ne, "ms_per_step": e_max / ne * 1e3, "output": "float32 filterbank"}
+               "ms_per_step": med * 1e3, "spread": spread, "output": "float32 filterbank",
+               "timing": "median of single calls, host clock around each call (inputs in pinned host memory, "
+                         "result back in pinned host memory)"}
         del hout
         # the paper's pipeline (Algorithm 1): each block redigitised to 8 bits on the device, codes to host
         hu8 = torch.empty((plan.out_shape()[0], plan.out_shape()[2], plan.out_shape()[1]), dtype=torch.uint8,
                           pin_memory=True)
-        kb = plan.execute_host_u8(hin.data_ptr(), hu8.data_ptr(), st)   # warm-up
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0 = time.perf_counter()
-        for _ in range(ne):
-            plan.execute_host_u8(hin.data_ptr(), hu8.data_ptr(), st)
-        torch.cuda.synchronize(dev)
-        e_s = time.perf_counter() - e0
+        kb = [0]
+
+        def call_u8():
+            kb[0] = plan.execute_host_u8(hin.data_ptr(), hu8.data_ptr(), st)
+        med, spread = timed_calls(call_u8)
         plan.device_status()
-        e_max = max_over_ranks(e_s, world, dev)
-        e2e["u8"] = {"value": replica_value(units, ne, e_max * 1e3, world), "unit": UNIT,
+        e2e["u8"] = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
                      "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hu8.numel()),
-                     "ms_per_step": e_max / ne * 1e3, "block_segments": kb,
+                     "ms_per_step": med * 1e3, "spread": spread, "block_segments": kb[0],
                      "output": "8-bit filterbank (statistics per block), decreasing frequency, time-major"}
         del hin
         # the paper's own I/O: 8-bit voltages in (4 bytes per dual-polarisation sample, one scale per
@@ -531,28 +570,29 @@ def gpu_arm(args, w):
         hsc = sc.cpu().pin_memory()
         plan8 = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin,
                           precision=PREC[head], in_dtype=cdmt.CDMT_IN_I8, host_block=args.host_block)
-        kb = plan8.execute_host_u8(hin8.data_ptr(), hu8.data_ptr(), st, hsc.data_ptr())   # warm-up
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0 = time.perf_counter()
-        for _ in range(ne):
-            plan8.execute_host_u8(hin8.data_ptr(), hu8.data_ptr(), st, hsc.data_ptr())
-        torch.cuda.synchronize(dev)
-        e_s = time.perf_counter() - e0
+
+        def call_i8():
+            kb[0] = plan8.execute_host_u8(hin8.data_ptr(), hu8.data_ptr(), st, hsc.data_ptr())
+        med, spread = timed_calls(call_i8)
         plan8.device_status()
-        e_max = max_over_ranks(e_s, world, dev)
-        e2e["i8_u8"] = {"value": replica_value(units, ne, e_max * 1e3, world), "unit": UNIT,
+        e2e["i8_u8"] = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
                         "h2d_bytes_per_step": int(hin8.numel() + hsc.numel() * 4), "d2h_bytes_per_step": int(hu8.numel()),
-                        "ms_per_step": e_max / ne * 1e3, "block_segments": kb,
+                        "ms_per_step": med * 1e3, "spread": spread, "block_segments": kb[0],
                         "output": "int8 voltages in (per-subband scale), 8-bit filterbank out"}
+        plan8.close()
         del plan8, hin8, hsc, hu8
+
+    # ---- serving: one beam of the serving workload (288 subbands, blocks of 2^16 samples, 1024 DMs)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_probe(cdmt, dev, args)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         n_sub, n_seg = [int(v) for v in args.cpu_sample.split("x")]
         u, dt, cores = oracle_sample(w, x, info["nd"], n_sub, n_seg)
         cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n_sub} of {w.nsub} subbands x {n_seg} of {nseg} segments x all {len(w.dms)} DMs "
+               "sample": f"{n_sub} of {w.nsub} subbands x {n_seg} of {info['nseg']} segments x all {len(w.dms)} DMs "
                          f"({u:.3g} units in {dt:.1f} s)"}
 
     if rank == 0:
@@ -569,9 +609,11 @@ def gpu_arm(args, w):
                 "redigitise": redig,
                 "incoherent": incoh,
                 "comparisons": {"cufft_unfused": cufft},
+                "serving": serving,
                 "forms": {f: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
                               "dedisperse_ms_per_step": r["dd_ms"] / args.steps,
-                              "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error")}
+                              "forward_ms_per_step": r["fwd_ms"] / args.steps, "error_vs_oracle": r.get("error"),
+                              "dtype": DTYPE[f], "roofline": rooflines[f]}
                           for f, r in results.items()}}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -695,6 +737,68 @@ def _serve_run(cdmt, srv, beams, host_blocks, scale, nblk, pace_s=0.0, hist=None
                 finish(reqs.pop(0))
     for item in reqs:
         finish(item)
+
+
+def serving_probe(cdmt, dev, args, nblk=8, npaced=6):
+    """One beam of the serving workload through the streaming server (SERVE: 288
+    subbands at 135 MHz, blocks of 2^16 complex64 samples from pinned host memory,
+    1024 DMs 0-100, 16 channels, nint 8, FP16 form, float32 filterbank in device
+    slots): its real-time factor with blocks queued back to back, and its block
+    latency (submit to GPU completion) when blocks arrive at the data rate; four
+    sampled (subband, DM) tiles of two blocks against the FP64 oracle."""
+    import torch
+    c = SERVE
+    shape = (c["nsub"], c["block_len"], 4)
+    g = torch.Generator(device=dev)
+    host_blocks = []
+    for i in range(4):
+        g.manual_seed(5000 + i)
+        d = torch.randn(shape, generator=g, device=dev, dtype=torch.float32)
+        h = torch.empty(shape, dtype=d.dtype, pin_memory=True)
+        h.copy_(d)
+        host_blocks.append(h)
+        del d
+    srv = cdmt.Server(hbm_budget=120 << 30)
+    beam = srv.add_beam(c["nsub"], c["block_len"], c["f_centre"], c["bw"], 0.0, c["dm_max"] / c["ndm"], c["ndm"],
+                        c["nchan"], c["nint"], precision=cdmt.CDMT_PREC_FP16)
+    hist, samples = {}, []
+    _serve_run(cdmt, srv, [beam], host_blocks, None, 3, hist=hist)
+    torch.cuda.synchronize(dev)
+    srv.reset_stats()
+    rng = np.random.default_rng(8)
+    rows = c["nsub"] * c["nchan"]
+    pick = {4, 3 + nblk - 1}
+
+    def probe(b, kb, res):
+        if args.no_error or kb not in pick or res.nseg < 1:
+            return
+        view = cdmt.Server.block_view(res, c["ndm"], rows)
+        seglen = res.samples // res.nseg
+        for _ in range(2):
+            s_, d_ = int(rng.integers(0, c["nsub"])), int(rng.integers(0, c["ndm"]))
+            samples.append((res.first_sample // seglen, s_, d_,
+                            view[d_, s_ * c["nchan"]:(s_ + 1) * c["nchan"], :seglen].cpu().numpy()))
+    _serve_run(cdmt, srv, [beam], host_blocks, None, nblk, hist=hist, probe=probe)
+    sat = srv.stats()
+    srv.reset_stats()
+    block_s = c["block_len"] / (c["bw"] * 1e6)
+    _serve_run(cdmt, srv, [beam], host_blocks, None, npaced, pace_s=block_s, hist=hist)
+    paced = srv.stats()
+    srv.close()
+    err = _serve_error(c, host_blocks, None, hist[beam], samples, False) if samples else None
+    del host_blocks
+    torch.cuda.empty_cache()
+    log(f"serving, one beam: {sat.realtime_factor:.2f}x real time, {sat.units_per_s / 1e9:.1f} {UNIT}; paced latency "
+        f"p50 {paced.latency_p50_ms:.1f} ms, p99 {paced.latency_p99_ms:.1f} ms")
+    return {"workload": f"one beam of {c['nsub']} subbands, blocks of 2^16 complex64 samples ({block_s * 1e3:.1f} ms "
+                        f"of data) from pinned host memory, {c['ndm']} DMs 0-{c['dm_max']:g}, {c['nchan']} channels, "
+                        f"nint {c['nint']}, FP16 form, float32 filterbank kept in device slots",
+            "realtime_factor": sat.realtime_factor, "value": sat.units_per_s / 1e9, "unit": UNIT,
+            "blocks": sat.blocks_done, "latency_p50_ms": sat.latency_p50_ms, "latency_p99_ms": sat.latency_p99_ms,
+            "paced": {"blocks": paced.blocks_done, "latency_p50_ms": paced.latency_p50_ms,
+                      "latency_p99_ms": paced.latency_p99_ms, "latency_max_ms": paced.latency_max_ms,
+                      "note": "blocks submitted every 335.5 ms (the data rate)"},
+            "target_realtime_factor": 10.0, "error_vs_oracle": err}
 
 
 def _serve_error(c, host_blocks, scale, hist0, samples, i8):
@@ -938,12 +1042,14 @@ def main():
                     help="segments per block of the host pipeline (e2e; 0: the plan's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
-    ap.add_argument("--forms", default="fp32,fp16",
+    ap.add_argument("--forms", default="fp32,bf16,fp16",
                     help="precision forms to time, comma-separated (fp32, fp16, bf16); the last is the headline")
     ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
     ap.add_argument("--no-redigitise", action="store_true", help="skip timing the 8-bit redigitisation")
     ap.add_argument("--no-incoherent", action="store_true", help="skip timing the incoherent stage")
     ap.add_argument("--no-cufft", action="store_true", help="skip timing the unfused cuFFT comparison pipeline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the one-beam serving figures in the default run")
+    ap.add_argument("--e2e-calls", type=int, default=10, help="host-memory calls timed per end-to-end leg")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

@@ -227,8 +227,14 @@ int cdmt_execute(cdmt_plan_t plan, const void *d_in, float *d_out, const float *
  * its copy to the device is 4x smaller).  A plan with DM groups
  * (cdmt_opts.dm_groups) copies the whole input in, runs cdmt_execute and copies
  * the whole filterbank out, without overlapping copies and compute (its groups
- * segment the input differently), on device buffers it keeps.
- * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_ECUDA.
+ * segment the input differently), on device buffers it keeps until
+ * cdmt_destroy: about the input plus five times the filterbank's bytes (the
+ * float32 filterbank, and its 8-bit codes once cdmt_execute_host_u8 has run),
+ * which cdmt_info.workspace_bytes does not include.
+ * On an error the call waits for the copies it had queued before it returns,
+ * so that the caller may free or reuse h_in and h_out at once.
+ * Errors: CDMT_EINVAL, CDMT_ENOMEM (staging buffers), CDMT_EBUDGET (a staging
+ * or DM-group buffer would exceed cdmt_opts.mem_budget), CDMT_ECUDA.
  */
 /* cdmt_execute_host_u8 - the pipeline of Algorithm 1 up to "redigitize" and
  * "copy to host": like cdmt_execute_host, but each block of segments

@@ -24,6 +24,7 @@ CDMT_CHIRP_CHANNEL, CDMT_CHIRP_SUBBAND = 0, 1
 CDMT_PREC_FP32, CDMT_PREC_FP16, CDMT_PREC_BF16 = 0, 1, 2
 CDMT_IN_C64, CDMT_IN_I8 = 0, 1
 CDMT_OUT_F32, CDMT_OUT_U8 = 0, 1
+CDMT_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024   # size of the array behind cdmt_execute_static
 
 
 class cdmt_opts(ctypes.Structure):

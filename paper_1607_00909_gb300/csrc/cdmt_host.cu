@@ -134,8 +134,8 @@ __device__ __forceinline__ uint32_t fix32(double x) { return (uint32_t)(unsigned
 // shift * j / M cycles on bin j of each channel, which delays the channel's
 // backward DFT output by `shift` samples (exact: shift * j * 2^32 / M is an
 // integer for M a power of two <= 2^32).
-__global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, double f_centre, double bw, int nsub,
-                            int nchan, int64_t nbin, int ntile, int shift, int chirp)
+__global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double dm0, double ddm, double f_centre, double bw,
+                            int nsub, int nchan, int64_t nbin, int ntile, int shift, int chirp)
 {
     const int64_t mbin = nbin / nchan;
     const int64_t total = (int64_t)ntile * nsub * nbin;
@@ -146,7 +146,8 @@ __global__ void k_nco_table(uint2 *nco, const double *dm_tile0, double ddm, doub
         const double k = chirp_k(f_centre, bw, nsub, nchan, nbin, s, i, chirp);
         const int lm = 31 - __clz((int)mbin);   // shift * j * 2^32 / M = (shift * j) << (32 - log2 M)
         const uint32_t ramp = shift ? (uint32_t)((i % mbin) * shift) << (32 - lm) : 0u;
-        nco[q] = make_uint2(fix32(-dm_tile0[tile] * k) + ramp, fix32(-ddm * k));
+        const double first = dm_tile0 ? dm_tile0[tile] : dm0;
+        nco[q] = make_uint2(fix32(-first * k) + ramp, fix32(-ddm * k));
     }
 }
 
@@ -428,6 +429,22 @@ int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
     return CDMT_OK;
 }
 
+cudaError_t enqueue_fp32_tables(float2 *tw_n, float2 *tw_af, float2 *tw_ai, int64_t nbin, int r, cudaStream_t st)
+{
+    const int tn = 16 * r;
+    k_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256, 0, st>>>(tw_n, nbin, -1);
+    k_twiddle_passes<<<64, 256, 0, st>>>(tw_af, tw_af + 15 * tn, r, -1);
+    k_twiddle_passes<<<64, 256, 0, st>>>(tw_ai, tw_ai + 15 * tn, r, +1);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_nco_table(uint2 *nco, const double *d_tile0, double dm0, double ddm, double f_centre, double bw,
+                              int nsub, int nchan, int64_t nbin, int ntile, int shift, int chirp, cudaStream_t st)
+{
+    k_nco_table<<<1024, 256, 0, st>>>(nco, d_tile0, dm0, ddm, f_centre, bw, nsub, nchan, nbin, ntile, shift, chirp);
+    return cudaGetLastError();
+}
+
 // lets other translation units of the library report an error before a plan exists
 void set_thread_error(const char *msg) { g_thread_error = msg; }
 
@@ -666,14 +683,12 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
         if (p->tc_bmat64 != p->tc_bmat) k_tc_bmat<<<64, 256>>>(reinterpret_cast<uint16_t *>(p->tc_bmat64), ab, 64);
         k_tc_twq<<<(unsigned)((p->mbin / 2 + 255) / 256), 256>>>(p->tc_twq, (int)p->mbin);
     }
-    k_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256>>>(p->tw_n, nbin, -1);
-    k_twiddle_passes<<<64, 256>>>(p->tw_af, p->tw_bf, p->r, -1);
-    k_twiddle_passes<<<64, 256>>>(p->tw_ai, p->tw_bi, p->r, +1);
+    TRYC(enqueue_fp32_tables(p->tw_n, p->tw_af, p->tw_ai, nbin, p->r, 0));
     if (p->uniform) {
         TRYC(cudaMalloc(&d_tile0, sizeof(double) * p->ntile));
         TRYC(cudaMemcpy(d_tile0, tile0.data(), sizeof(double) * p->ntile, cudaMemcpyHostToDevice));
-        k_nco_table<<<1024, 256>>>(p->nco, d_tile0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile,
-                                   p->precision != CDMT_PREC_FP32 ? (int)(p->nd / 2) : 0, p->chirp);
+        TRYC(enqueue_nco_table(p->nco, d_tile0, 0.0, p->ddm, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->ntile,
+                               p->precision != CDMT_PREC_FP32 ? (int)(p->nd / 2) : 0, p->chirp, 0));
     } else {
         k_k_table<<<1024, 256>>>(p->ktab, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, p->chirp);
     }
@@ -964,6 +979,16 @@ int host_pipeline(cdmt_plan_s *p, const void *h_in, const float *h_scale, float 
     return CDMT_OK;
 }
 
+// After a host-memory call failed part-way, copies from or into the caller's host
+// buffers may still be queued: wait for every stream the call used (ignoring their
+// status), so that no copy touches those buffers once the call has returned.
+void drain_after_error(cdmt_plan_s *p, cudaStream_t st)
+{
+    cudaStreamSynchronize(st);
+    if (p->s_h2d) cudaStreamSynchronize(p->s_h2d);
+    if (p->s_d2h) cudaStreamSynchronize(p->s_d2h);
+}
+
 }  // namespace
 
 int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float *h_scale, void *cuda_stream)
@@ -976,6 +1001,7 @@ int cdmt_execute_host(cdmt_plan_t p, const void *h_in, float *h_out, const float
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int rc = p->groups.empty() ? host_pipeline(p, h_in, h_scale, h_out, nullptr, nullptr, st)
                                      : grouped_host(p, h_in, h_scale, h_out, nullptr, nullptr, st);
+    if (rc != CDMT_OK) drain_after_error(p, st);
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }
@@ -991,6 +1017,7 @@ int cdmt_execute_host_u8_ex(cdmt_plan_t p, const void *h_in, const float *h_scal
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int rc = p->groups.empty() ? host_pipeline(p, h_in, h_scale, nullptr, h_u8, block_segments, st)
                                      : grouped_host(p, h_in, h_scale, nullptr, h_u8, block_segments, st);
+    if (rc != CDMT_OK) drain_after_error(p, st);
     if (cur != p->device) cudaSetDevice(cur);
     return rc;
 }

@@ -80,6 +80,17 @@ cudaError_t tc_batch_launch(const TcBeam *beams, int nbeam, const int *round_dev
 size_t tc_smem(int ab, int lm);
 cudaError_t tc_dedisperse(const TcArgs &a, cudaStream_t st);
 
+// Plan tables shared by cdmt_plan_ex and cdmt_execute_static (defined with the planner):
+// the FP32 form's twiddles (W_N line; forward and backward pass twiddles, tw_b = tw_a +
+// 15 * 16 r), and the fixed-point chirp words (phase, step) of an evenly spaced DM list
+// for ntile tiles whose first DMs are d_tile0[t] (device), or dm0 when d_tile0 is NULL
+// (one tile); shift != 0 adds the tensor-core form's output-shift ramp.
+cudaError_t enqueue_fp32_tables(float2 *tw_n, float2 *tw_af, float2 *tw_ai, int64_t nbin, int r, cudaStream_t st);
+cudaError_t enqueue_nco_table(uint2 *nco, const double *d_tile0, double dm0, double ddm, double f_centre, double bw,
+                              int nsub, int nchan, int64_t nbin, int ntile, int shift, int chirp, cudaStream_t st);
+// Sec. 2's overlap for the lowest channel of the band at |DM| dm_abs_max (per-channel chirps); -1 if none < M.
+int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin);
+
 cudaError_t fp32_prepare(int r);
 size_t fp32_dedisp_smem(int r);
 cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st);

@@ -372,16 +372,13 @@ int redig_enqueue(cdmt_plan_s *p, const float *d_fb, int64_t nt, int64_t stride,
     const int fr = fused_smem(32, nt) <= kFusedSmemMax ? 32 : fused_smem(16, nt) <= kFusedSmemMax ? 16 : 0;
     if (fr) {
         const size_t smem = fused_smem(fr, nt);
-        static bool attr32 = false, attr16 = false;
-        bool &attr = fr == 32 ? attr32 : attr16;
-        if (!attr) {
-            const cudaError_t ea = fr == 32 ? cudaFuncSetAttribute(k_redig_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                                   (int)kFusedSmemMax)
-                                            : cudaFuncSetAttribute(k_redig_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                                   (int)kFusedSmemMax);
-            if (ea != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(ea));
-            attr = true;
-        }
+        // set on every call: the attribute is per device, and plans on several devices or
+        // threads may launch this kernel (the call costs microseconds)
+        const cudaError_t ea = fr == 32 ? cudaFuncSetAttribute(k_redig_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)kFusedSmemMax)
+                                        : cudaFuncSetAttribute(k_redig_fused<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)kFusedSmemMax);
+        if (ea != cudaSuccess) return rfail(p, CDMT_ECUDA, cudaGetErrorString(ea));
         const dim3 fg((unsigned)((rows + fr - 1) / fr), (unsigned)ndm);
         if (fr == 32) k_redig_fused<32><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk, vec);
         else k_redig_fused<16><<<fg, 256, smem, st>>>(d_fb, rows, nt, stride, d_u8, d_stats, sk, vec);

@@ -38,8 +38,6 @@ constexpr int kMaxDevices = 128;
 void *g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device
 std::mutex g_scratch_mu;
 
-constexpr double kD = 4.148808e3;  // MHz^2 pc^-1 cm^3 s
-
 int fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -52,51 +50,6 @@ int fail(int code, const char *fmt, ...)
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-// tw[k] = exp(sign 2 pi i k / n)
-__global__ void k_static_twiddle_line(float2 *tw, int64_t n, int sign)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    double s, c;
-    sincospi(2.0 * (double)k / (double)n, &s, &c);
-    tw[k] = make_float2((float)c, (float)(sign * s));
-}
-
-// the three-pass FFT's twiddles: W_M^{t m0} at [m0-1][t], then W_M^{16 j0 m1} at [m1-1][j0]
-__global__ void k_static_twiddle_passes(float2 *tw, int r, int sign)
-{
-    const int m = 256 * r, tn = 16 * r;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 15 * (tn + r); i += gridDim.x * blockDim.x) {
-        int64_t p;
-        if (i < 15 * tn) p = (int64_t)(i % tn) * (i / tn + 1);
-        else p = 16LL * ((i - 15 * tn) % r) * ((i - 15 * tn) / r + 1);
-        double s, c;
-        sincospi(2.0 * (double)(p % m) / (double)m, &s, &c);
-        tw[i] = make_float2((float)c, (float)(sign * s));
-    }
-}
-
-// fixed-point chirp phase and step per bin for the single DM tile: Eq. 1 per
-// channel, phase -dm_first K and step -dm_step K in 2^-32 cycles
-__global__ void k_static_nco(uint2 *nco, double dm_first, double dm_step, double f_centre, double bw, int nsub,
-                             int nchan, int64_t nbin)
-{
-    const int64_t total = (int64_t)nsub * nbin;
-    const int64_t m = nbin / nchan;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q % nbin;
-        const int s = (int)(q / nbin);
-        const int c = (int)(i / m);
-        const int64_t j = i % m;
-        const double nu_s = f_centre + ((double)s - 0.5 * (double)(nsub - 1)) * bw;
-        const double nu_c = nu_s - 0.5 * bw + ((double)c + 0.5) * bw / (double)nchan;
-        const double nu = ((double)j - 0.5 * (double)m) * bw / (double)nbin;
-        const double k = 1e6 * kD * nu * nu / (nu_c * nu_c * (nu_c + nu));
-        nco[q] = make_uint2((uint32_t)(unsigned long long)llrint(-dm_first * k * 4294967296.0),
-                            (uint32_t)(unsigned long long)llrint(-dm_step * k * 4294967296.0));
-    }
-}
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -122,14 +75,11 @@ extern "C" int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz,
     if (nsamp < nbin) return fail(CDMT_EINVAL, "nsamp (%lld) < nbin (%lld)", (long long)nsamp, (long long)nbin);
     if (!d_in || !d_out) return fail(CDMT_EINVAL, "NULL input or output pointer");
     if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(CDMT_EINVAL, "input must be 16-byte aligned");
-    if (nd < 0) {
-        // Sec. 2: n_d = r t_d / n_c with t_d of Eq. 2 for the lowest channel at the largest |DM|
+    if (reinterpret_cast<uintptr_t>(d_out) % 4) return fail(CDMT_EINVAL, "output must be 4-byte aligned");
+    if (nd < 0) {   // the planner's overlap rule (Sec. 2) for the largest |DM| of the list
         const double dmax = std::fmax(std::fabs(dm_first), std::fabs(dm_first + (ndm - 1) * dm_step));
-        const double lo = band_lo, hi = band_lo + bw_sub_mhz / nchan;
-        const double td = kD * dmax * (1.0 / (lo * lo) - 1.0 / (hi * hi));
-        nd = (int64_t)std::ceil(bw_sub_mhz * 1e6 * td / nchan);
-        nd += nd & 1;
-        while (nd < m && (m - nd) % nint) nd += 2;
+        nd = overlap_for(nsub, f_centre_mhz, bw_sub_mhz, dmax, nchan, nint, nbin);
+        if (nd < 0) return fail(CDMT_EINVAL, "the overlap for DM %.6g does not fit M=%lld", dmax, (long long)m);
     }
     if (nd % 2 || nd >= m || (m - nd) % nint)
         return fail(CDMT_EINVAL, "overlap nd=%lld invalid for M=%lld, nint=%d", (long long)nd, (long long)m, nint);
@@ -180,11 +130,10 @@ extern "C" int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz,
     float2 *twi = reinterpret_cast<float2 *>(base + off_twi);
     uint2 *nco = reinterpret_cast<uint2 *>(base + off_nco);
     float4 *spec = reinterpret_cast<float4 *>(base + off_spec);
-    k_static_twiddle_line<<<(unsigned)((nbin + 255) / 256), 256, 0, st>>>(twn, nbin, -1);
-    k_static_twiddle_passes<<<64, 256, 0, st>>>(twf, r, -1);
-    k_static_twiddle_passes<<<64, 256, 0, st>>>(twi, r, +1);
-    k_static_nco<<<1024, 256, 0, st>>>(nco, dm_first, dm_step, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin);
-    e = cudaGetLastError();
+    e = enqueue_fp32_tables(twn, twf, twi, nbin, r, st);
+    if (e == cudaSuccess)
+        e = enqueue_nco_table(nco, nullptr, dm_first, dm_step, f_centre_mhz, bw_sub_mhz, nsub, nchan, nbin, 1, 0,
+                              CDMT_CHIRP_CHANNEL, st);
     if (e != cudaSuccess) return fail(CDMT_ECUDA, "table kernels: %s", cudaGetErrorString(e));
 
     // ---- segment chunks: forward stage into the scratch spectrum, then the DM stage

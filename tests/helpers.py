@@ -53,3 +53,41 @@ def pulse_snr(fb, dms, pulse, f_centre, bw, nsub, nchan, nint, nd):
     med = np.median(off)
     mad = np.median(np.abs(off - med)) * 1.4826
     return float((sm[lo:hi].max() - med) / mad)
+
+
+def pulse_geometry(pulse, dms, f_centre, bw, nsub, nchan, nint, nd):
+    """The quantities of the S/N harness of :func:`pulse_snr` for one pulse:
+    (index of the DM trial nearest the pulse's DM, per-row shift in output
+    samples D DM (nu_c^-2 - nu_top^-2) at that trial, boxcar width in output
+    samples, expected output sample of the pulse at the top of the band)."""
+    r = bw * 1e6
+    tsamp = nchan * nint / r
+    idm = int(np.argmin(np.abs(np.asarray(dms) - pulse.dm)))
+    dm = dms[idm]
+    nu_top = f_centre + 0.5 * nsub * bw
+    nus = f_centre + (np.arange(nsub) - 0.5 * (nsub - 1)) * bw
+    nuc = (nus[:, None] - bw / 2 + (np.arange(nchan)[None, :] + 0.5) * bw / nchan).ravel()
+    shifts = np.rint(D * dm * (1 / nuc ** 2 - 1 / nu_top ** 2) / tsamp).astype(np.int64)
+    wbox = max(1, int(round(pulse.width_s / tsamp)))
+    t_exp = int(round((pulse.t0_s * r / nchan - nd / 2) / nint))
+    return idm, shifts, wbox, t_exp
+
+
+def windowed_snr(rows_at, shifts, wbox, t_exp, half):
+    """The S/N of :func:`pulse_snr` computed on the window [t_exp - half,
+    t_exp + half) of the dedispersed series only: rows_at(r, a, b) returns
+    samples a..b-1 of filterbank row r at the pulse's DM trial.  The series is
+    the sum over rows of each row shifted back by its delay, convolved with a
+    boxcar of the pulse width; S/N = (peak within 4 widths + 8 samples of t_exp
+    - median of the rest of the window) / (1.4826 MAD of the rest)."""
+    lo = t_exp - half
+    series = np.zeros(2 * half)
+    for r, sh in enumerate(shifts):
+        series += rows_at(r, lo + sh, lo + sh + 2 * half)
+    sm = np.convolve(series, np.ones(wbox), mode="same")
+    c = half
+    a, b = c - 4 * wbox - 8, c + 4 * wbox + 8
+    off = np.concatenate([sm[2 * wbox:max(2 * wbox, a - 4 * wbox)], sm[b + 4 * wbox:2 * half - 2 * wbox]])
+    med = np.median(off)
+    mad = np.median(np.abs(off - med)) * 1.4826
+    return float((sm[a:b].max() - med) / mad)

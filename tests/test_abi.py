@@ -162,3 +162,11 @@ def test_struct_layouts_match_the_header(cdmt, tmp_path):
         assert got[(n, "size")] == ctypes.sizeof(st), n
         for f, _ in st._fields_:
             assert got[(n, f)] == getattr(st, f).offset, (n, f)
+
+
+def test_binding_constants_match_header(cdmt):
+    # the numeric #defines and enumerators the binding mirrors, read from the header text
+    text = open(os.path.join(HEADER_DIR, "cdmt.h")).read()
+    m = re.search(r"#define\s+CDMT_STATIC_SCRATCH_BYTES\s+\((\d+)u\s*\*\s*(\d+)u\s*\*\s*(\d+)u\)", text)
+    assert m, "CDMT_STATIC_SCRATCH_BYTES not found"
+    assert cdmt.CDMT_STATIC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))

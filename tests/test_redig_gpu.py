@@ -4,9 +4,11 @@ Both sides take each code in FP32 from the row's (mean, gain) rounded to FP32;
 the statistics differ only in their arithmetic (FP64 in the oracle; on the GPU
 FP32 partial sums per thread with an FP64 combination for long rows, and FP32
 two-pass mean and deviation for rows under 8192 samples), so a code may differ
-by one where the unrounded value sits on a rounding boundary.  The tests require identical codes
-everywhere else, at most 1e-4 of the samples on boundaries, and mean and sigma
-within 1e-5.
+by one where the unrounded value sits within 1e-3 of a rounding boundary.
+Every case uses fixed seeds, so the number of such codes is a property of the
+case: each test asserts the count measured on a GB300 for it (BOUNDARY_CODES;
+0 for most, 1 to 18 codes out of 10^5 to 10^7 for three of them), every other
+code identical, and mean and sigma within 1e-5.
 """
 import numpy as np
 import pytest
@@ -16,6 +18,10 @@ from helpers import gpu_filterbank
 
 pytestmark = pytest.mark.gpu
 BW = 0.1953125
+# codes that differ by one on a rounding boundary, as measured on a GB300 for the fixed-seed cases
+# that have any (the statistics' summation order decides them); every other case has none
+BOUNDARY_CODES = {"full_tiles_tensor_core_plan": 1, "block_choice_and_staging_growth": 18,
+                  "u8_blocks_in_dm_ranges": 1}
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +33,7 @@ def cdmt():
     return m
 
 
-def _check(orc, fb, codes, stats):
+def _check(orc, fb, codes, stats, boundary=0):
     fb = np.ascontiguousarray(fb, dtype=np.float32)
     ndm, rows, nt = fb.shape
     oc, ost = orc.redigitise(fb)
@@ -41,7 +47,7 @@ def _check(orc, fb, codes, stats):
     r = rows - 1 - p
     x = 128.0 + (fb[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / scale[d, r]
     assert np.all(np.abs(x - np.floor(x) - 0.5) < 1e-3), "a code differs away from a rounding boundary"
-    assert len(d) <= max(1, 1e-4 * codes.size)
+    assert len(d) <= boundary, f"{len(d)} codes differ on rounding boundaries (recorded: {boundary})"
     return len(d)
 
 
@@ -93,7 +99,7 @@ def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
     codes = plan.redigitise(fb, stats=stats)
     torch.cuda.synchronize()
     c = codes.cpu().numpy()
-    _check(orc, fb.cpu().numpy(), c, stats.cpu().numpy())
+    _check(orc, fb.cpu().numpy(), c, stats.cpu().numpy(), BOUNDARY_CODES["full_tiles_tensor_core_plan"])
     # detected noise: codes centred on 128 with 16 steps per sigma
     assert abs(c.mean() - 128.0) < 0.5 and abs(c.astype(np.float64).std() - 16.0) < 0.5
     plan.close()
@@ -136,7 +142,7 @@ def test_host_pipeline_8bit_blocks(cdmt, orc, host_block, sk_nsigma):
         xv = 128.0 + (block[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / ost[d, r, 1]
         assert np.all(np.abs(xv - np.floor(xv) - 0.5) < 1e-3)
         nbad += len(d)
-    assert nbad <= max(1, 1e-4 * codes.size)
+    assert nbad == 0, f"{nbad} codes differ on rounding boundaries"
     if sk_nsigma > 0:
         assert nflag >= 1   # a 2-sigma rule flags a few noise rows out of 3 blocks x 3 DMs x 16 rows
     plan.close()
@@ -194,11 +200,11 @@ def test_host_pipeline_block_choice_and_staging_growth(cdmt, orc):
         diff = np.abs(codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32))
         assert diff.max() <= 1
         nbad += int(np.count_nonzero(diff))
-    assert nbad <= max(1, 1e-4 * codes.size)
+    assert nbad <= BOUNDARY_CODES["block_choice_and_staging_growth"], f"{nbad} codes differ on rounding boundaries"
     plan.close()
 
 
-def _check_sk(orc, fb, codes, stats, flags, k, nsigma):
+def _check_sk(orc, fb, codes, stats, flags, k, nsigma, boundary=0):
     """Flags equal to the oracle's except where |SK - 1| lies within 1e-4 of the
     threshold (the two sides take SK from statistics rounded differently); codes
     of rows both sides flag are all 128, other rows as _check."""
@@ -219,7 +225,7 @@ def _check_sk(orc, fb, codes, stats, flags, k, nsigma):
         c2[d, :, rows - 1 - r] = 128
     st2 = stats.copy()
     st2[~keep] = (1.0, 0.0)
-    _check(orc, fb2, c2, st2)
+    _check(orc, fb2, c2, st2, boundary)
     return int(of.sum())
 
 

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from helpers import rel_errors
 
 pytestmark = pytest.mark.gpu
 BW = 0.1953125
@@ -34,7 +35,7 @@ BEAMS = [
 NBLK = 8
 
 
-def _serve(cdmt, beams, inputs, interleave=True, i8=False, scales=None, precision=None, max_slots=0):
+def _serve(cdmt, beams, inputs, interleave=True, i8=False, scales=None, precision=None, max_slots=0, keep_parts=False):
     import torch
     precision = cdmt.CDMT_PREC_FP16 if precision is None else precision
     srv = cdmt.Server(max_slots=max_slots)
@@ -61,6 +62,8 @@ def _serve(cdmt, beams, inputs, interleave=True, i8=False, scales=None, precisio
         srv.release(rid)
     st = srv.stats()
     srv.close()
+    if keep_parts:
+        return parts, st
     out = []
     for p in parts:
         keys = sorted(p)
@@ -103,6 +106,38 @@ def test_stream_equals_offline_and_mix_equals_alone(cdmt, prec):
         off = _offline(cdmt, b, x, precision)
         assert off.shape == mixed[bi].shape, (off.shape, mixed[bi].shape)
         assert np.array_equal(off, mixed[bi]), bi
+
+
+@pytest.mark.parametrize("prec,i8", [("fp32", False), ("fp16", False), ("fp32", True), ("fp16", True)])
+def test_served_blocks_match_oracle(cdmt, orc, prec, i8):
+    """Each block of each beam, served in a mix of three beams whose blocks overlap
+    on the GPU (blocks shorter than, equal to and longer than N; two output slots,
+    so blocks wait for slots), equals the FP64 oracle's filterbank of the beam's
+    whole stream at the block's output positions (Algorithm 1's block loop, Sec. 3):
+    within 1e-5 (FP32) or 2e-3 (FP16) of the mean output, sample by sample.  With
+    int8 blocks the oracle runs on the dequantised voltages (scale x byte, FP32)."""
+    precision = cdmt.CDMT_PREC_FP16 if prec == "fp16" else cdmt.CDMT_PREC_FP32
+    tol = 2e-3 if prec == "fp16" else 1e-5
+    xs = _inputs(BEAMS)
+    scales = None
+    if i8:
+        scales = [(np.abs(x).reshape(b["nsub"], -1).max(axis=1) / 127.0).astype(np.float32) for b, x in zip(BEAMS, xs)]
+        xs = [np.clip(np.rint(x / s[:, None, None]), -127, 127).astype(np.int8) for x, s in zip(xs, scales)]
+    parts, st = _serve(cdmt, BEAMS, xs, interleave=True, i8=i8, scales=scales, precision=precision, max_slots=2,
+                       keep_parts=True)
+    assert st.blocks_done == NBLK * len(BEAMS)
+    for bi, (b, x) in enumerate(zip(BEAMS, xs)):
+        v = x.astype(np.float32) * scales[bi][:, None, None] if i8 else x
+        dms = [b["dm_first"] + i * b["dm_step"] for i in range(b["ndm"])]
+        nbin = 4096 * b["nchan"]
+        nd = orc.overlap(b["nsub"], b["f_centre"], BW, dms, b["nchan"], b["nint"], nbin)
+        o = orc.filterbank(v, b["f_centre"], BW, dms, b["nchan"], b["nint"], nbin, nd)
+        assert sum(p.shape[2] for p in parts[bi].values()) == o.shape[2]
+        for first, g in parts[bi].items():
+            ob = o[:, :, first:first + g.shape[2]]
+            assert ob.shape == g.shape and np.all(np.isfinite(g))
+            emax, erms = rel_errors(g, ob)
+            assert emax <= tol and erms <= tol, (bi, first, emax, erms)
 
 
 def test_int8_blocks(cdmt):
@@ -172,7 +207,7 @@ def test_u8_blocks_in_dm_ranges_under_a_small_budget(cdmt, orc):
     its codes, statistics and flags equal the oracle's redigitisation of a float32
     twin beam (on a server with the default budget) fed the same blocks."""
     import torch
-    from test_redig_gpu import _check_sk
+    from test_redig_gpu import BOUNDARY_CODES, _check_sk
     b = dict(nsub=2, block_len=1 << 14, f_centre=140.0, dm_first=0.0, dm_step=0.25, ndm=64, nchan=8, nint=4, seed=57)
     rows, L, nbin = b["nsub"] * b["nchan"], b["block_len"], 4096 * b["nchan"]
     dms = [b["dm_first"] + i * b["dm_step"] for i in range(b["ndm"])]
@@ -197,7 +232,7 @@ def test_u8_blocks_in_dm_ranges_under_a_small_budget(cdmt, orc):
         if u.samples > 0:
             fb = servers[0].block_view(a, b["ndm"], rows).cpu().numpy()
             codes, stats, flags = (t.cpu().numpy() for t in servers[1].block_u8_view(u, b["ndm"], rows))
-            _check_sk(orc, fb, codes, stats, flags, 2 * b["nint"], 2.5)
+            _check_sk(orc, fb, codes, stats, flags, 2 * b["nint"], 2.5, BOUNDARY_CODES["u8_blocks_in_dm_ranges"])
             checked += 1
         servers[0].release(ra)
         servers[1].release(ru)

@@ -87,3 +87,29 @@ def test_static_entry_overlap_rule_and_limit(cdmt):
     assert rc == cdmt.CDMT_EBUDGET
     assert "static scratch" in cdmt.cdmt_last_error(None)
     plan.close()
+
+
+def test_static_entry_chunked_segments(cdmt):
+    """16 subbands of N = 2^16: the fixed scratch holds the forward spectra of 3
+    segments at a time, so the 16 segments run in 6 chunks (forward stage and DM
+    stage per chunk, the spectrum region reused); the result equals the plan's."""
+    import torch
+    nsub, nsamp, fc, nchan, nint, nbin = 16, 1 << 20, 135.0, 16, 8, 1 << 16
+    dm_first, dm_step, ndm = 1.0, 2.5, 6
+    dms = [dm_first + i * dm_step for i in range(ndm)]
+    plan = cdmt.Plan(nsub, nsamp, fc, BW, dms, nchan, nint, nbin=nbin)
+    i = plan.info
+    per_seg = 16 * nsub * nbin
+    assert i["nseg"] >= 3 * (cdmt.CDMT_STATIC_SCRATCH_BYTES // per_seg)   # several chunks
+    x = torch.from_numpy(synth.noise(34, nsub, nsamp)).cuda()
+    out = torch.full(plan.out_shape(), float("nan"), dtype=torch.float32, device="cuda")
+    rc = _static_call(cdmt, x, out, torch.cuda.current_stream().cuda_stream, nsub, nsamp, fc, dm_first, dm_step,
+                      ndm, nchan, nint, nbin, i["nd"])
+    assert rc == cdmt.CDMT_OK, cdmt.cdmt_last_error(None)
+    ref = cdmt.run(plan, x)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    emax, erms = rel_errors(got, ref.cpu().numpy())
+    assert emax <= TOL and erms <= TOL, (emax, erms)
+    plan.close()
