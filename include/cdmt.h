@@ -316,7 +316,9 @@ int cdmt_stage_times(cdmt_plan_t plan, double *ms, int64_t *launches);
  *   mu, sigma = mean and (population) standard deviation of the row's nout
  *               samples (sums of I and I^2; FP32 within a thread, FP64 across);
  *   code      = clamp(rint(fmaf(I - mu, g, 128)), 0, 255),  g = CDMT_REDIG_LEVELS / sigma
- *               (g = 0 for a constant row), in FP32 with mu and g rounded to FP32.
+ *               (g = 0 for a constant row), in FP32: mu and sigma rounded to FP32
+ *               (the values d_stats reports) and g divided in FP32, so that the
+ *               codes of a row follow from its reported (mu, sigma) alone.
  * The mapping is this library's choice (the paper leaves it open): 128 is the
  * mean and 16 code steps span one sigma, so -8 .. +7.9 sigma are kept.
  *

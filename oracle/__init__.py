@@ -90,6 +90,9 @@ def _load():
                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_redigitise.restype = None
+            lib.orc_codes.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+            lib.orc_codes.restype = None
             lib.orc_sk_sigma.argtypes = [i64, ctypes.c_int]
             lib.orc_sk_sigma.restype = ctypes.c_double
             lib.orc_spectral_kurtosis.argtypes = [fp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, ctypes.c_double,
@@ -273,6 +276,20 @@ def redigitise(fb) -> tuple[np.ndarray, np.ndarray]:
     st = np.empty((ndm, rows, 2), dtype=np.float64)
     _load().orc_redigitise(_fp(fb), ndm, rows, nt, out.ctypes.data, st.ctypes.data)
     return out, st
+
+
+def codes(fb, stats, flags=None) -> np.ndarray:
+    """The code step of the redigitisation (Sec. 3) given each row's statistics:
+    stats [ndm][rows][2] = (mean, standard deviation) taken as FP32, flags
+    [ndm][rows] (optional) marks rows coded 128.  Returns uint8 [ndm][nt][rows]
+    in decreasing frequency, as :func:`redigitise`."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    ndm, rows, nt = fb.shape
+    st = np.ascontiguousarray(stats, dtype=np.float32).reshape(ndm, rows, 2)
+    fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8).reshape(ndm, rows)
+    out = np.empty((ndm, nt, rows), dtype=np.uint8)
+    _load().orc_codes(_fp(fb), ndm, rows, nt, st.ctypes.data, None if fl is None else fl.ctypes.data, out.ctypes.data)
+    return out
 
 
 LEVELS = 16.0

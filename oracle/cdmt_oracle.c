@@ -370,8 +370,9 @@ int orc_max_threads(void)
  * channel statistics", "redigitize" of Algorithm 1).  For every DM trial and
  * every channel row of a float filterbank fb[ndm][rows][nt] (one data block):
  *   mu = (1/nt) sum_t I_t,  sigma = sqrt((1/nt) sum_t I_t^2 - mu^2)   (FP64);
- * the offset and scale of the row are mu and g = LEVELS / sigma (g = 0 when
- * sigma = 0), both rounded to FP32, and each sample becomes
+ * the offset and scale of the row are mu and sigma rounded to FP32 and the
+ * gain g = LEVELS / sigma divided in FP32 (g = 0 when sigma = 0), and each
+ * sample becomes (orc_codes)
  *   code = clamp(rint(fmaf(I - mu, g, 128)), 0, 255)
  * in FP32 (the paper leaves the mapping open: 128 is the mean and LEVELS = 16
  * code steps span one sigma).  Codes are written in the paper's filterbank
@@ -381,11 +382,36 @@ int orc_max_threads(void)
  */
 #define ORC_LEVELS 16.0f
 
-void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out, double *stats)
+/* The code step of the redigitisation alone, given each row's statistics:
+ * musig[2 i] = mu, musig[2 i + 1] = sigma (FP32) of row i = d rows + r, and
+ * (may be NULL) flags[i] != 0 for rows coded 128 whatever their samples.  The
+ * codes of a row are unique given these two numbers, so a redigitiser that
+ * reports the statistics it used can be checked code for code. */
+void orc_codes(const float *fb, int ndm, int rows, int64_t nt, const float *musig, const uint8_t *flags, uint8_t *out)
 {
     for (int d = 0; d < ndm; d++) {
         for (int r = 0; r < rows; r++) {
-            const float *row = fb + ((size_t)d * rows + r) * (size_t)nt;
+            const size_t i = (size_t)d * rows + r;
+            const float *row = fb + i * (size_t)nt;
+            const float muf = musig[2 * i], sgf = musig[2 * i + 1];
+            const float g = (flags && flags[i]) || !(sgf > 0.0f) ? 0.0f : ORC_LEVELS / sgf;
+            for (int64_t t = 0; t < nt; t++) {
+                float x = rintf(fmaf(row[t] - muf, g, 128.0f));
+                if (x < 0.0f) x = 0.0f;
+                if (x > 255.0f) x = 255.0f;
+                out[((size_t)d * (size_t)nt + (size_t)t) * rows + (size_t)(rows - 1 - r)] = (uint8_t)x;
+            }
+        }
+    }
+}
+
+void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out, double *stats)
+{
+    float *musig = (float *)malloc(sizeof(float) * 2 * (size_t)ndm * rows);
+    for (int d = 0; d < ndm; d++) {
+        for (int r = 0; r < rows; r++) {
+            const size_t i = (size_t)d * rows + r;
+            const float *row = fb + i * (size_t)nt;
             double s1 = 0.0, s2 = 0.0;
             for (int64_t t = 0; t < nt; t++) {
                 s1 += (double)row[t];
@@ -396,19 +422,15 @@ void orc_redigitise(const float *fb, int ndm, int rows, int64_t nt, uint8_t *out
             if (var < 0.0) var = 0.0;
             const double sigma = sqrt(var);
             if (stats) {
-                stats[2 * ((size_t)d * rows + r)] = mu;
-                stats[2 * ((size_t)d * rows + r) + 1] = sigma;
+                stats[2 * i] = mu;
+                stats[2 * i + 1] = sigma;
             }
-            const float muf = (float)mu;
-            const float g = sigma > 0.0 ? (float)(ORC_LEVELS / sigma) : 0.0f;
-            for (int64_t t = 0; t < nt; t++) {
-                float x = rintf(fmaf(row[t] - muf, g, 128.0f));
-                if (x < 0.0f) x = 0.0f;
-                if (x > 255.0f) x = 255.0f;
-                out[((size_t)d * (size_t)nt + (size_t)t) * rows + (size_t)(rows - 1 - r)] = (uint8_t)x;
-            }
+            musig[2 * i] = (float)mu;
+            musig[2 * i + 1] = (float)sigma;
         }
     }
+    orc_codes(fb, ndm, rows, nt, musig, NULL, out);
+    free(musig);
 }
 
 /*

@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(256) k_redig_stats(const float *__restrict__ f
         const double var = nt > 0 ? fmax(b / (double)nt - mu * mu, 0.0) : 0.0;
         const double sigma = sqrt(var);
         const bool flag = sk_flag(mu, sigma, nt, sk);
-        mg[row] = make_float2((float)mu, sigma > 0.0 && !flag ? (float)(CDMT_REDIG_LEVELS / sigma) : 0.f);
+        // the gain from sigma rounded to FP32, divided in FP32: the codes then follow from the
+        // reported (mu, sigma) alone
+        mg[row] = make_float2((float)mu, sigma > 0.0 && !flag ? (float)CDMT_REDIG_LEVELS / (float)sigma : 0.f);
         if (sk.flags) sk.flags[row] = flag;
         if (stats) {
             stats[2 * row] = (float)mu;

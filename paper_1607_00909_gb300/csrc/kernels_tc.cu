@@ -511,12 +511,19 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                     tc::f2_unpack(R, re[2 * i], re[2 * i + 1]);
                     tc::f2_unpack(I, im[2 * i], im[2 * i + 1]);
                 }
+                // Polarisation 0 stores its real parts in K row 2 j_lo and its imaginary parts in row
+                // 2 j_lo + 1.  Polarisation 1 stores i y instead: its real parts in row 2 j_lo + 1 and
+                // its negated imaginary parts (sign bits flipped) in row 2 j_lo.  Pass B is linear, so
+                // that polarisation's output is i times the true one, which detection does not see;
+                // the neighbouring lanes of the two polarisations then write different banks.
                 const uint32_t o = (uint32_t)((pol * P + m0b) / 8) * kSboB + (uint32_t)(2 * rjlo / 8) * kLboB +
                                    (uint32_t)((2 * rjlo) % 8) * 16;
-                *reinterpret_cast<uint4 *>(ab + o) =
+                const uint32_t flip = pol ? 0x80008000u : 0u, o_re = o + 16 * pol, o_im = o + 16 * (1 - pol);
+                *reinterpret_cast<uint4 *>(ab + o_re) =
                     make_uint4(pk<AB>(re[0], re[1]), pk<AB>(re[2], re[3]), pk<AB>(re[4], re[5]), pk<AB>(re[6], re[7]));
-                *reinterpret_cast<uint4 *>(ab + o + 16) =
-                    make_uint4(pk<AB>(im[0], im[1]), pk<AB>(im[2], im[3]), pk<AB>(im[4], im[5]), pk<AB>(im[6], im[7]));
+                *reinterpret_cast<uint4 *>(ab + o_im) =
+                    make_uint4(pk<AB>(im[0], im[1]) ^ flip, pk<AB>(im[2], im[3]) ^ flip, pk<AB>(im[4], im[5]) ^ flip,
+                               pk<AB>(im[6], im[7]) ^ flip);
                 if constexpr (AB) {
                     float lr[8], li[8];
                     #pragma unroll
@@ -524,10 +531,11 @@ __device__ __forceinline__ bool tc_run_item(const TcItem &it, uint8_t *smem, uin
                         lr[z] = re[z] - bf16_round(re[z]);
                         li[z] = im[z] - bf16_round(im[z]);
                     }
-                    *reinterpret_cast<uint4 *>(ab + kAbuf + o) = make_uint4(
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + o_re) = make_uint4(
                         pk<1>(lr[0], lr[1]), pk<1>(lr[2], lr[3]), pk<1>(lr[4], lr[5]), pk<1>(lr[6], lr[7]));
-                    *reinterpret_cast<uint4 *>(ab + kAbuf + o + 16) = make_uint4(
-                        pk<1>(li[0], li[1]), pk<1>(li[2], li[3]), pk<1>(li[4], li[5]), pk<1>(li[6], li[7]));
+                    *reinterpret_cast<uint4 *>(ab + kAbuf + o_im) = make_uint4(
+                        pk<1>(li[0], li[1]) ^ flip, pk<1>(li[2], li[3]) ^ flip, pk<1>(li[4], li[5]) ^ flip,
+                        pk<1>(li[6], li[7]) ^ flip);
                 }
             }
         }

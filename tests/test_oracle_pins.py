@@ -670,3 +670,23 @@ def test_grouped_impulse_at_the_closed_form_time(orc, dm_true):
         i0 = int(np.floor(t_exp))
         assert abs(np.argmax(row) - t_exp) <= 1.0, (c, np.argmax(row), t_exp)
         assert (row[i0] + row[i0 + 1]) / np.sum(row) >= 0.8
+
+
+def test_code_step_given_statistics(orc):
+    # the code step alone (oracle.codes), with statistics given by hand: gain 16 / sigma
+    # in FP32, rint rounding half to even, clipping to 0..255, flagged rows at 128, rows
+    # written in decreasing frequency
+    fb = np.array([[[14.0, 10.125, 10.375, 6.0, 100.0, -100.0],
+                    [5.0, 5.0, 5.0, 5.0, 5.0, 5.0]]], dtype=np.float32)
+    stats = np.array([[[10.0, 4.0], [5.0, 0.0]]], dtype=np.float32)
+    c = orc.codes(fb, stats)
+    # row 0: (I - 10) * 4 + 128 = 144, 128.5 -> 128, 129.5 -> 130, 112, 488 -> 255, -312 -> 0
+    assert list(c[0, :, 1]) == [144, 128, 130, 112, 255, 0]
+    assert list(c[0, :, 0]) == [128] * 6          # sigma 0: gain 0
+    flagged = orc.codes(fb, stats, np.array([[1, 0]], dtype=np.uint8))
+    assert list(flagged[0, :, 1]) == [128] * 6
+    # the redigitisation is the code step applied with its own statistics rounded to FP32
+    g = np.random.default_rng(14)
+    fb = g.gamma(6.0, 2.0, (2, 5, 300)).astype(np.float32)
+    codes, st = orc.redigitise(fb)
+    assert np.array_equal(codes, orc.codes(fb, st.astype(np.float32)))

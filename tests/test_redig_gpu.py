@@ -1,14 +1,17 @@
 """8-bit redigitisation of the filterbank (Sec. 3) against the oracle.
 
-Both sides take each code in FP32 from the row's (mean, gain) rounded to FP32;
-the statistics differ only in their arithmetic (FP64 in the oracle; on the GPU
-FP32 partial sums per thread with an FP64 combination for long rows, and FP32
-two-pass mean and deviation for rows under 8192 samples), so a code may differ
-by one where the unrounded value sits within 1e-3 of a rounding boundary.
-Every case uses fixed seeds, so the number of such codes is a property of the
-case: each test asserts the count measured on a GB300 for it (BOUNDARY_CODES;
-0 for most, 1 to 18 codes out of 10^5 to 10^7 for three of them), every other
-code identical, and mean and sigma within 1e-5.
+Both sides decide each code in FP32 from the row's mean and standard deviation
+rounded to FP32 and the gain 16 / sigma divided in FP32, so a row's codes are
+unique given its (mu, sigma): wherever the GPU reports the statistics it used
+(cdmt_redigitise, 8-bit served beams) its codes must equal, byte for byte, the
+oracle's code step (oracle.codes) applied with them, and the statistics must
+agree with the oracle's FP64 ones within 1e-5.  The statistics differ only in
+their arithmetic (FP64 sums in order in the oracle; on the GPU FP32 partial sums
+per thread with an FP64 combination for long rows, FP32 two-pass mean and
+deviation for short ones), so against the oracle's own codes a code may differ
+by one where the unrounded value sits within 1e-3 of a rounding boundary; the
+host pipeline, which does not report its per-block statistics, is held to that
+(at most 1e-4 of the codes).
 """
 import numpy as np
 import pytest
@@ -18,10 +21,6 @@ from helpers import gpu_filterbank
 
 pytestmark = pytest.mark.gpu
 BW = 0.1953125
-# codes that differ by one on a rounding boundary, as measured on a GB300 for the fixed-seed cases
-# that have any (the statistics' summation order decides them); every other case has none
-BOUNDARY_CODES = {"full_tiles_tensor_core_plan": 1, "block_choice_and_staging_growth": 18,
-                  "u8_blocks_in_dm_ranges": 1}
 
 
 @pytest.fixture(scope="module")
@@ -33,22 +32,35 @@ def cdmt():
     return m
 
 
-def _check(orc, fb, codes, stats, boundary=0):
+def _boundary_codes(orc, fb, codes):
+    """Codes that differ from the oracle's own redigitisation: each by one, on a
+    rounding boundary of the oracle's unrounded value.  Returns their number."""
     fb = np.ascontiguousarray(fb, dtype=np.float32)
-    ndm, rows, nt = fb.shape
+    rows = fb.shape[1]
     oc, ost = orc.redigitise(fb)
-    mu_g, sg_g = stats[..., 0].astype(np.float64), stats[..., 1].astype(np.float64)
     scale = np.maximum(ost[..., 1], 1e-30)
-    assert np.max(np.abs(mu_g - ost[..., 0]) / (np.abs(ost[..., 0]) + scale)) <= 1e-5
-    assert np.max(np.abs(sg_g - ost[..., 1]) / (np.abs(ost[..., 0]) + scale)) <= 1e-5
     diff = codes.astype(np.int32) - oc.astype(np.int32)
     assert np.all(np.abs(diff) <= 1)
     d, t, p = np.nonzero(diff)
     r = rows - 1 - p
     x = 128.0 + (fb[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / scale[d, r]
     assert np.all(np.abs(x - np.floor(x) - 0.5) < 1e-3), "a code differs away from a rounding boundary"
-    assert len(d) <= boundary, f"{len(d)} codes differ on rounding boundaries (recorded: {boundary})"
     return len(d)
+
+
+def _check(orc, fb, codes, stats, flags=None):
+    """Reported statistics within 1e-5 of the oracle's; codes byte for byte the
+    oracle's code step with the reported statistics (and flags)."""
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    _, ost = orc.redigitise(fb)
+    keep = np.ones(ost.shape[:2], dtype=bool) if flags is None else flags == 0
+    mu_g, sg_g = stats[..., 0].astype(np.float64), stats[..., 1].astype(np.float64)
+    scale = np.maximum(ost[..., 1], 1e-30)
+    assert np.max((np.abs(mu_g - ost[..., 0]) / (np.abs(ost[..., 0]) + scale))[keep], initial=0.0) <= 1e-5
+    assert np.max((np.abs(sg_g - ost[..., 1]) / (np.abs(ost[..., 0]) + scale))[keep], initial=0.0) <= 1e-5
+    exact = orc.codes(fb, stats, flags)
+    assert np.array_equal(codes, exact), f"{int(np.count_nonzero(codes != exact))} codes differ"
+    return _boundary_codes(orc, fb, codes) if flags is None else 0
 
 
 def test_redigitise_tiny_workload(cdmt, orc):
@@ -99,7 +111,7 @@ def test_redigitise_full_tiles_tensor_core_plan(cdmt, orc):
     codes = plan.redigitise(fb, stats=stats)
     torch.cuda.synchronize()
     c = codes.cpu().numpy()
-    _check(orc, fb.cpu().numpy(), c, stats.cpu().numpy(), BOUNDARY_CODES["full_tiles_tensor_core_plan"])
+    _check(orc, fb.cpu().numpy(), c, stats.cpu().numpy())
     # detected noise: codes centred on 128 with 16 steps per sigma
     assert abs(c.mean() - 128.0) < 0.5 and abs(c.astype(np.float64).std() - 16.0) < 0.5
     plan.close()
@@ -142,7 +154,7 @@ def test_host_pipeline_8bit_blocks(cdmt, orc, host_block, sk_nsigma):
         xv = 128.0 + (block[d, r, t].astype(np.float64) - ost[d, r, 0]) * 16.0 / ost[d, r, 1]
         assert np.all(np.abs(xv - np.floor(xv) - 0.5) < 1e-3)
         nbad += len(d)
-    assert nbad == 0, f"{nbad} codes differ on rounding boundaries"
+    assert nbad <= max(1, 1e-4 * codes.size), f"{nbad} codes differ on rounding boundaries"
     if sk_nsigma > 0:
         assert nflag >= 1   # a 2-sigma rule flags a few noise rows out of 3 blocks x 3 DMs x 16 rows
     plan.close()
@@ -200,32 +212,22 @@ def test_host_pipeline_block_choice_and_staging_growth(cdmt, orc):
         diff = np.abs(codes[:, t0:t1, :].astype(np.int32) - oc.astype(np.int32))
         assert diff.max() <= 1
         nbad += int(np.count_nonzero(diff))
-    assert nbad <= BOUNDARY_CODES["block_choice_and_staging_growth"], f"{nbad} codes differ on rounding boundaries"
+    assert nbad <= max(1, 1e-4 * codes.size), f"{nbad} codes differ on rounding boundaries"
     plan.close()
 
 
-def _check_sk(orc, fb, codes, stats, flags, k, nsigma, boundary=0):
+def _check_sk(orc, fb, codes, stats, flags, k, nsigma):
     """Flags equal to the oracle's except where |SK - 1| lies within 1e-4 of the
     threshold (the two sides take SK from statistics rounded differently); codes
-    of rows both sides flag are all 128, other rows as _check."""
+    byte for byte the oracle's code step with the reported statistics and flags
+    (flagged rows all 128); statistics of unflagged rows as _check."""
     fb = np.ascontiguousarray(fb, dtype=np.float32)
-    ndm, rows, nt = fb.shape
+    nt = fb.shape[2]
     sk, of = orc.spectral_kurtosis(fb, k, nsigma)
     thr = nsigma * orc.sk_sigma(nt, k)
     near = np.abs(np.abs(sk - 1.0) - thr) < 1e-4 * thr
     assert np.all((flags == of) | near)
-    both = (flags == 1) & (of == 1)
-    for d, r in zip(*np.nonzero(both)):
-        assert np.all(codes[d, :, rows - 1 - r] == 128)
-    keep = (flags == 0) & (of == 0)
-    fb2 = fb.copy()
-    c2 = codes.copy()
-    for d, r in zip(*np.nonzero(~keep)):   # compare the remaining rows only: blank the others
-        fb2[d, r, :] = 1.0
-        c2[d, :, rows - 1 - r] = 128
-    st2 = stats.copy()
-    st2[~keep] = (1.0, 0.0)
-    _check(orc, fb2, c2, st2, boundary)
+    _check(orc, fb, codes, stats, flags)
     return int(of.sum())
 
 
