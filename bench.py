@@ -10,6 +10,11 @@ per second (units = ndm * nsub * nseg * S).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cdmt|reference]
 
+Multi-GPU (torchrun, one rank per GPU): --shard replicas (default) runs one
+independent beam per rank (weak scaling); --shard subbands splits one beam's
+subbands across the ranks, each planning its slice with the whole band's
+overlap, no data exchanged (strong scaling).
+
 Timing: W untimed steps, then K steps between barrier + synchronize, CUDA
 events on the launching stream, max over ranks.  The inputs (4.3 GB) are larger
 than L2, so no flush is needed between steps.  --impl reference times the FP64
@@ -221,6 +226,35 @@ def max_over_ranks(v: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(v: float, world: int, device=None) -> float:
+    """The sum of v over the ranks of the process group (v itself on one rank)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def subband_slice(nsub: int, world: int, rank: int) -> tuple[int, int]:
+    """Subbands [lo, hi) of one rank when `world` ranks split one beam's nsub
+    subbands as evenly as possible (the first nsub % world ranks take one more).
+    Subbands are independent problems (Sec. 4 splits them across nodes), so the
+    split needs no exchange of data."""
+    base, extra = divmod(nsub, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def slice_view(w, lo: int, hi: int):
+    """The workload's description restricted to subbands [lo, hi): the same subband
+    frequencies (the centre moves to the slice's centre), DMs, channels and N."""
+    import dataclasses
+    fc = w.f_centre + (0.5 * (lo + hi - 1) - 0.5 * (w.nsub - 1)) * w.bw
+    return dataclasses.replace(w, nsub=hi - lo, f_centre=fc, name=f"{w.name}[subbands {lo}:{hi}]")
+
+
 def replica_value(units_per_rank: float, steps: int, ms_max: float, world: int) -> float:
     """Whole-job throughput of `world` independent replicas (one beam each, same
     shapes) in G units/s: every rank's units over the slowest rank's time."""
@@ -303,12 +337,13 @@ def time_cufft_unfused(w, xin, out, info, dev, stream, args):
                     "not the product path"}
 
 
-def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
-    """Plan one precision form, warm up, time args.steps executes; returns a dict."""
+def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world, nd=-1):
+    """Plan one precision form, warm up, time args.steps executes; returns a dict.
+    nd >= 0 fixes the overlap (a slice of a band keeps the whole band's)."""
     import torch
     import torch.distributed as dist
     plan = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, precision=PREC[prec],
-                     host_block=args.host_block)
+                     host_block=args.host_block, nd=nd)
     info = plan.info
     st = stream.cuda_stream
     for _ in range(args.warmup):
@@ -331,8 +366,10 @@ def time_form(cdmt, w, xin, out, prec, args, dev, stream, barrier, world):
     (fwd_ms, dd_ms), (fwd_n, dd_n) = cdmt.cdmt_stage_times(plan.handle)
     cdmt.cdmt_set_timing(plan.handle, False)
     ms_max = max_over_ranks(ms, world, dev)
+    units_all = sum_over_ranks(info["units"], world, dev)   # every rank's units (equal for replicas)
     return {"plan": plan, "info": info, "ms_max": ms_max, "fwd_ms": fwd_ms, "dd_ms": dd_ms, "fwd_n": fwd_n,
-            "dd_n": dd_n, "steps": args.steps, "value": replica_value(info["units"], args.steps, ms_max, world)}
+            "dd_n": dd_n, "steps": args.steps, "units_all": units_all,
+            "value": units_all * args.steps / (ms_max / 1e3) / 1e9}
 
 
 def dm_stage_roofline(form, r, props, sm_max):
@@ -415,9 +452,21 @@ def gpu_arm(args, w):
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     head = forms[-1]
+    shard = args.shard == "subbands" and world > 1
+    nd_band = -1
     log(f"rank {rank}: generating {w.name} ...")
     t0 = time.perf_counter()
-    x = w.voltages(threads=16, beam=rank)
+    if shard and w.nsub < world:
+        raise SystemExit(f"--shard subbands needs at least one subband per rank ({w.nsub} subbands, {world} ranks)")
+    if shard:   # one beam, its subbands split across the ranks; every rank keeps the band's overlap
+        probe = cdmt.Plan(w.nsub, w.nbin, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
+        nd_band = probe.info["nd"]
+        probe.close()
+        lo, hi = subband_slice(w.nsub, world, rank)
+        x = w.voltages(threads=16, sub=(lo, hi))
+        w = slice_view(w, lo, hi)
+    else:       # independent replicas: one beam per rank
+        x = w.voltages(threads=16, beam=rank)
     log(f"rank {rank}: inputs ready in {time.perf_counter() - t0:.1f}s ({x.nbytes / 1e9:.2f} GB)")
     xin = torch.from_numpy(x).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -433,15 +482,15 @@ def gpu_arm(args, w):
     clocks = None
     for f in forms:
         if out is None:
-            probe = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
+            probe = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, nd=nd_band)
             out = torch.empty(probe.out_shape(), dtype=torch.float32, device=dev)
             probe.close()
         if f == head:
             with ClockSampler(bus) as clk:
-                r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world)
+                r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world, nd_band)
             clocks = clk.summary()
         else:
-            r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world)
+            r = time_form(cdmt, w, xin, out, f, args, dev, stream, barrier, world, nd_band)
         if rank == 0 and not args.no_error:
             r["error"] = sampled_error(w, x, out, r["info"])
         results[f] = r
@@ -453,6 +502,7 @@ def gpu_arm(args, w):
     R = results[head]
     plan, info = R["plan"], R["info"]
     units = info["units"]
+    units_all = R["units_all"]   # all ranks' units (world x units for replicas)
 
     # 8-bit redigitisation of the headline form's filterbank (Sec. 3), timed on its own:
     # a statistics pass reads the filterbank, a code pass reads it again and writes one byte per sample
@@ -546,7 +596,7 @@ def gpu_arm(args, w):
         hout = torch.empty(plan.out_shape(), dtype=torch.float32, pin_memory=True)
         med, spread = timed_calls(lambda: plan.execute_host(hin.data_ptr(), hout.data_ptr(), 0, st))
         plan.device_status()
-        e2e = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
+        e2e = {"value": units_all / med / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
                "ms_per_step": med * 1e3, "spread": spread, "output": "float32 filterbank",
                "timing": "median of single calls, host clock around each call (inputs in pinned host memory, "
@@ -561,7 +611,7 @@ def gpu_arm(args, w):
             kb[0] = plan.execute_host_u8(hin.data_ptr(), hu8.data_ptr(), st)
         med, spread = timed_calls(call_u8)
         plan.device_status()
-        e2e["u8"] = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
+        e2e["u8"] = {"value": units_all / med / 1e9, "unit": UNIT,
                      "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hu8.numel()),
                      "ms_per_step": med * 1e3, "spread": spread, "block_segments": kb[0],
                      "output": "8-bit filterbank (statistics per block), decreasing frequency, time-major"}
@@ -573,13 +623,13 @@ def gpu_arm(args, w):
         hin8 = torch.clamp(torch.round(xs / sc[:, None]), -127, 127).to(torch.int8).view(xin.shape).cpu().pin_memory()
         hsc = sc.cpu().pin_memory()
         plan8 = cdmt.Plan(w.nsub, w.nsamp, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin,
-                          precision=PREC[head], in_dtype=cdmt.CDMT_IN_I8, host_block=args.host_block)
+                          precision=PREC[head], in_dtype=cdmt.CDMT_IN_I8, host_block=args.host_block, nd=nd_band)
 
         def call_i8():
             kb[0] = plan8.execute_host_u8(hin8.data_ptr(), hu8.data_ptr(), st, hsc.data_ptr())
         med, spread = timed_calls(call_i8)
         plan8.device_status()
-        e2e["i8_u8"] = {"value": replica_value(units, 1, med * 1e3, world), "unit": UNIT,
+        e2e["i8_u8"] = {"value": units_all / med / 1e9, "unit": UNIT,
                         "h2d_bytes_per_step": int(hin8.numel() + hsc.numel() * 4), "d2h_bytes_per_step": int(hu8.numel()),
                         "ms_per_step": med * 1e3, "spread": spread, "block_segments": kb[0],
                         "output": "int8 voltages in (per-subband scale), 8-bit filterbank out"}
@@ -602,12 +652,16 @@ def gpu_arm(args, w):
     if rank == 0:
         cfg = describe(w, info)
         cfg.update({"l2": f"inputs ({x.nbytes / 1e9:.2f} GB) larger than L2; no flush", "precision": head,
-                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"})
+                    "parallelism": (f"subbands split over {world} GPUs" if shard else f"replicas x{world}")
+                    if world > 1 else "single GPU"})
+        if shard:
+            cfg.update({"workload": describe(workload(args.workload))["workload"], "nsub": w.nsub * world,
+                        "subbands_per_rank": w.nsub, "nd": nd_band})
         launches = (R["fwd_n"] + R["dd_n"])
         line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": R["ms_max"] / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
-                "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": DTYPE[head],
+                "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "error_vs_oracle": R.get("error"),
                 "redigitise": redig,
@@ -1054,6 +1108,9 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip timing the unfused cuFFT comparison pipeline")
     ap.add_argument("--no-serving", action="store_true", help="skip the one-beam serving figures in the default run")
     ap.add_argument("--e2e-calls", type=int, default=10, help="host-memory calls timed per end-to-end leg")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "subbands"],
+                    help="N > 1: one beam per rank (replicas, weak scaling) or one beam's subbands split across "
+                         "the ranks (subbands, strong scaling)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

@@ -48,14 +48,16 @@ def _rng(seed: int, beam: int, sub: int, pol: int, stream: int = 0) -> np.random
 
 
 def noise(seed: int, nsub: int, nsamp: int, sigma2: float = 1.0, beam: int = 0,
-          threads: int = 8) -> np.ndarray:
-    """Complex Gaussian noise, float32 [nsub][nsamp][4]."""
+          threads: int = 8, sub0: int = 0) -> np.ndarray:
+    """Complex Gaussian noise, float32 [nsub][nsamp][4]: subbands sub0 .. sub0 + nsub - 1
+    of a band (each subband's stream is keyed by its own index, so a slice of the band
+    equals the same rows of the whole band)."""
     out = np.empty((nsub, nsamp, 4), dtype=np.float32)
     sc = np.float32(np.sqrt(sigma2 / 2.0))
 
     def one(s):
         for p in range(2):
-            g = _rng(seed, beam, s, p)
+            g = _rng(seed, beam, s + sub0, p)
             v = g.standard_normal(2 * nsamp, dtype=np.float32)
             v *= sc
             out[s, :, 2 * p] = v[0::2]
@@ -76,7 +78,7 @@ def ism_sweep(nu_lo: float, nu_hi: float, dm: float) -> float:
 
 
 def add_pulses(x: np.ndarray, pulses, f_centre: float, bw: float, seed: int,
-               sigma2: float = 1.0, beam: int = 0) -> None:
+               sigma2: float = 1.0, beam: int = 0, sub0: int = 0, nsub_band: int = 0) -> None:
     """Add dispersed pulses in place to float32 [nsub][nsamp][4] voltages.
 
     For each subband the pulse is drawn in a window long enough to hold its
@@ -85,11 +87,14 @@ def add_pulses(x: np.ndarray, pulses, f_centre: float, bw: float, seed: int,
     subband centre, i.e. exp(+2 pi i 1e6 D DM nu^2 / (nu_0^2 (nu_0 + nu))) for the
     numpy forward-FFT convention), and the result is added at the subband's
     arrival time t0 + D DM (nu_0^-2 - nu_ref^-2), nu_ref the top of the band.
+    x may hold subbands sub0 .. sub0 + len(x) - 1 of a band of nsub_band subbands
+    centred on f_centre (0: x is the whole band).
     """
     nsub, nsamp = x.shape[0], x.shape[1]
+    band = nsub_band if nsub_band > 0 else nsub
     r = bw * 1e6
-    nus = subband_centres(nsub, f_centre, bw)
-    nu_ref = f_centre + 0.5 * nsub * bw
+    nus = subband_centres(band, f_centre, bw)[sub0:sub0 + nsub]
+    nu_ref = f_centre + 0.5 * band * bw
     for ip, pu in enumerate(pulses):
         for s in range(nsub):
             nu0 = nus[s]
@@ -103,7 +108,7 @@ def add_pulses(x: np.ndarray, pulses, f_centre: float, bw: float, seed: int,
             f = np.fft.fftfreq(L, d=1.0 / r) / 1e6  # MHz offsets from nu0
             h = np.exp(2j * np.pi * 1e6 * D_MHZ * pu.dm * f ** 2 / (nu0 ** 2 * (nu0 + f)))
             for p in range(2):
-                g = _rng(seed, beam, s, p, stream=16 + ip)
+                g = _rng(seed, beam, s + sub0, p, stream=16 + ip)
                 w = np.zeros(L, dtype=np.complex128)
                 b0 = L // 2 - wn // 2
                 amp = pu.amp * np.sqrt(sigma2 / 2.0)
@@ -148,10 +153,13 @@ class Workload:
     seed: int
     pulses: tuple = ()
 
-    def voltages(self, threads: int = 8, beam: int = 0) -> np.ndarray:
-        x = noise(self.seed, self.nsub, self.nsamp, beam=beam, threads=threads)
+    def voltages(self, threads: int = 8, beam: int = 0, sub=None) -> np.ndarray:
+        """The workload's voltages, or subbands sub = (lo, hi) of them (equal to those rows
+        of the whole band)."""
+        lo, hi = (0, self.nsub) if sub is None else sub
+        x = noise(self.seed, hi - lo, self.nsamp, beam=beam, threads=threads, sub0=lo)
         if self.pulses:
-            add_pulses(x, self.pulses, self.f_centre, self.bw, self.seed, beam=beam)
+            add_pulses(x, self.pulses, self.f_centre, self.bw, self.seed, beam=beam, sub0=lo, nsub_band=self.nsub)
         return x
 
 
