@@ -52,16 +52,12 @@ k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T;
     extern __shared__ float4 smem[];
-    float4 *ex = smem;
-    float2 *ta = reinterpret_cast<float2 *>(ex + M);
-    float2 *tb = ta + F::NTA;
+    float4 *ex = smem;   // the exchange buffer; the pass twiddles are read through the cache
 
     const int t = threadIdx.x;
     const int n1 = blockIdx.x;
     const int kk = blockIdx.y;
     const int s = blockIdx.z;
-    for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
-    for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
 
     const int64_t s0 = (int64_t)s * nsamp + (k0 + kk) * nvalid + n1;
     float2 x[16], y[16];
@@ -85,10 +81,9 @@ k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale
             y[j2] = make_float2(v.z, v.w);
         }
     }
-    __syncthreads();  // twiddles in place
-    F::template pass_a<-1>(x, y, ex, ta, t);
+    F::template pass_a<-1>(x, y, ex, tw_a, t);
     __syncthreads();
-    F::template pass_b<-1>(x, y, ex, tb, t);
+    F::template pass_b<-1>(x, y, ex, tw_b, t);
     __syncthreads();
     float4 *dst = spec + (((int64_t)s * kc + kk) * nchan + n1) * M;
     F::template pass_c<-1>(ex, t, [&](int j, float2 a, float2 b) {
@@ -258,7 +253,7 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
 // ---------------------------------------------------------------------------
 // launchers
 
-template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>::M + sizeof(float2) * (Fft3<R>::NTA + Fft3<R>::NTB); }
+template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>::M; }
 template <int R> static size_t smem_dedisp()
 {
     using F = Fft3<R>;
