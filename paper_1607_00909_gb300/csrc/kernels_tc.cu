@@ -90,8 +90,8 @@ template <int AB, int LM> struct TcLayout {
     static constexpr uint32_t abytes = na * abuf;
     static constexpr uint32_t off_misc = off_a + npipe * abytes;
     // misc: mbarriers (one per pipe, <= 8) at +0, TMEM slot at +64, one float per
-    // warp (<= 32) at +128, queue ticket at +256
-    static constexpr uint32_t m_tslot = 64, m_red = 128, m_next = 256;
+    // warp (<= 32) at +128, queue ticket at +256, the CTA's work split (6 words) at +264
+    static constexpr uint32_t m_tslot = 64, m_red = 128, m_next = 256, m_book = 264;
     static constexpr uint32_t total = off_misc + 320;
     static_assert(npipe <= 8 && nt <= 1024, "misc area");
     static constexpr uint32_t tmem_cols = 512;
@@ -634,20 +634,92 @@ k_dedisperse_tc(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, 
         it.scale_out = scale_out;
         return it;
     };
-    const uint32_t tmem = tc_cta_setup<AB, LM>(smem, bmat, bmat64, twq);
+    // Work split: whole items round-robin (item blockIdx.x + k gridDim.x) for every full round of
+    // the grid, which keeps the items running at once neighbours (one subband's phase words and
+    // segments); then the (item, DM) pairs of the last, partial round split into equal shares, so
+    // that no CTA is left a whole item behind the others (a served block of 4608 items on 152 SMs
+    // had 48 CTAs working a 31st item while 104 idled).  A part of an item is computed exactly as
+    // the whole item would compute those DMs.  The split's bookkeeping is kept in shared memory, so
+    // that it holds no registers through the per-DM loop.
+    int64_t *book = reinterpret_cast<int64_t *>(smem + TcLayout<AB, LM>::off_misc + TcLayout<AB, LM>::m_book);
+    if (tid == 0) {
+        const int64_t tile_items = (int64_t)nsub * kc * nchan;
+        const int64_t ntile = nitems / tile_items;
+        const int64_t ndt_last = max(0, min(dm_cnt, ndm - ((int)(ntile - 1) * dm_tile + dm_off)));
+        const int64_t f_full = (ntile - 1) * tile_items * dm_cnt;   // pairs of the full tiles
+        const int64_t last0 = (ntile - 1) * tile_items;              // first item of the last tile
+        const int64_t total = f_full + tile_items * ndt_last;
+        const int64_t rounds = nitems / gridDim.x;                   // whole-item rounds
+        const int64_t i0 = rounds * gridDim.x;                       // first item of the partial round
+        const int64_t f0 = i0 <= last0 ? i0 * dm_cnt : f_full + (i0 - last0) * ndt_last;
+        const int64_t share = (total - f0 + gridDim.x - 1) / gridDim.x;
+        book[0] = f_full;
+        book[1] = ndt_last;
+        book[2] = last0;
+        book[3] = min(total, f0 + (int64_t)blockIdx.x * share);
+        book[4] = min(total, book[3] + share);
+        book[5] = rounds;
+    }
+    auto locate = [&](int64_t f, int64_t &item, int &off, int &ndt) {
+        const int64_t f_full = book[0];
+        if (f < f_full) {
+            item = f / dm_cnt;
+            off = (int)(f % dm_cnt);
+            ndt = dm_cnt;
+        } else {
+            const int64_t last = book[1];
+            item = book[2] + (f - f_full) / last;
+            off = (int)((f - f_full) % last);
+            ndt = (int)last;
+        }
+    };
+    const uint32_t tmem = tc_cta_setup<AB, LM>(smem, bmat, bmat64, twq);   // ends with a CTA barrier
     constexpr int kSrcChunks = kM / 256, kPhChunks = kM / 512;   // 4 KB chunks of 16 M and 8 M bytes
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const TcItem it = make(item);
-        if (tid < kSrcChunks + kPhChunks && item + gridDim.x < nitems) {
-            const TcItem nx = make(item + gridDim.x);
-            if (tid < kSrcChunks) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
-            else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - kSrcChunks), 4096);
+    // step k < rounds: whole item blockIdx.x + k gridDim.x; then parts of the partial round's items
+    int64_t k = 0, f = book[3];
+    for (;;) {
+        int64_t item;
+        int off = 0, n;
+        if (k < book[5]) {
+            item = blockIdx.x + k * gridDim.x;
+            n = -1;   // the whole item
+        } else {
+            if (f >= book[4]) break;
+            int ndt;
+            locate(f, item, off, ndt);
+            n = (int)min((int64_t)(ndt - off), book[4] - f);
+        }
+        TcItem it = make(item);
+        if (n >= 0) {
+            it.ndt = n;
+            it.dbase += off;
+            it.dms += off;
+            it.out += (int64_t)off * it.dm_stride;
+        }
+        if (tid < kSrcChunks + kPhChunks) {   // the next step's spectrum and phase words into L2
+            int64_t nitem = -1;
+            if (k + 1 < book[5]) {
+                nitem = blockIdx.x + (k + 1) * gridDim.x;
+            } else {
+                const int64_t fn = n >= 0 ? f + n : book[3];
+                if (fn < book[4]) {
+                    int noff, nndt;
+                    locate(fn, nitem, noff, nndt);
+                }
+            }
+            if (nitem >= 0) {
+                const TcItem nx = make(nitem);
+                if (tid < kSrcChunks) tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.src) + 4096 * tid, 4096);
+                else tc::prefetch_l2(reinterpret_cast<const uint8_t *>(nx.ph) + 4096 * (tid - kSrcChunks), 4096);
+            }
         }
         if (!tc_run_item<UNIFORM, AB, LM, NI>(it, smem, tmem)) {
             if (tid == 0) atomicExch(status, 1);
             tc_cta_drain<AB, LM>(smem);
             break;
         }
+        if (n >= 0) f += n;
+        else k++;
     }
     tc_cta_teardown<AB, LM>(tmem);
 }
@@ -765,7 +837,11 @@ template <bool U, int AB, int LM, int NI = 0> static void launch(const TcArgs &a
 {
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nitems = ntile * a.nsub * a.kc * a.nchan;
-    const int64_t nblk = std::min<int64_t>(nitems, std::max(1, a.nsm));
+    // one CTA per SM, none without a share of the (item, DM) pairs
+    const int cnt = a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile;
+    const int64_t last = std::max(0, std::min(cnt, a.ndm - ((int)(ntile - 1) * a.dm_tile + a.dm_off)));
+    const int64_t pairs = (int64_t)a.nsub * a.kc * a.nchan * ((ntile - 1) * cnt + last);
+    const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(pairs, std::max(1, a.nsm)));
     k_dedisperse_tc<U, AB, LM, NI><<<(unsigned)nblk, TcLayout<AB, LM>::nt, TcLayout<AB, LM>::total, st>>>(
         a.spec, a.nco, a.ktab, a.dm_list, a.bmat, a.bmat64, a.twq, a.out, a.status, a.nsub, a.kc, a.k0, a.nchan,
         a.ndm, a.dm_tile, a.nd, a.nint, a.nout, a.scale, nitems, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile,
