@@ -194,13 +194,13 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8, conflict-free
-    # pass-B operand stores): 544.3 MB read + 2068.6 MB written for 4.253e9 units (ncu --set full,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 543.6 MB read +
+    # 2067.7 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
-    "20ecb736271ea817:fp16": 0.6144,
-    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 547.1 MB read + 2069.1 MB
-    # written for 4.253e9 units (ncu --set full, 4th launch)
-    "95a66e1599de366f:fp32": 0.6151,
+    "3889bae55e20a28f:fp16": 0.6140,
+    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 543.1 MB read + 2067.5 MB
+    # written for 4.253e9 units (same capture command with the FP32 form)
+    "94a2ef83621ff4bf:fp32": 0.6138,
 }
 
 try:
