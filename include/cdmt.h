@@ -147,8 +147,10 @@ typedef struct cdmt_info {
  *   nint          output integration factor, >= 1
  * Errors: CDMT_EINVAL (bad argument, N_bin <= n_d n_c, nsamp < N_bin;
  *         cdmt_opts.dm_groups outside 0..ndm), CDMT_ENOTSUP (M_bin outside
- *         512..4096; tensor-core precisions need M_bin = 2048 or 4096 and nint
- *         dividing 32), CDMT_ENOMEM, CDMT_EBUDGET (cdmt_opts.mem_budget), CDMT_ECUDA.
+ *         512..8192 in the FP32 form, e.g. Sec. 4's N_bin = 65536 with n_c = 8;
+ *         tensor-core precisions need M_bin = 2048 or 4096 and nint dividing 32),
+ *         CDMT_ENOMEM, CDMT_EBUDGET (cdmt_opts.mem_budget), CDMT_ECUDA.  Without
+ *         cdmt_opts.nbin the plan picks M_bin in 512..4096.
  * Allocates device memory (tables and workspace); the plan owns all of it.
  */
 int cdmt_plan(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz,
@@ -406,7 +408,7 @@ int cdmt_incoherent(cdmt_plan_t plan, const float *d_fb, double ddm_lo, double d
  * later reads, so nothing carries over from a previous call, but all calls on a
  * device share the one array: calls whose work overlaps on the GPU (different
  * streams, or host threads racing) corrupt each other's results.
- * Errors: CDMT_EINVAL, CDMT_ENOTSUP (M_bin outside 512..4096), CDMT_EBUDGET,
+ * Errors: CDMT_EINVAL, CDMT_ENOTSUP (M_bin outside 512..8192), CDMT_EBUDGET,
  * CDMT_ECUDA; messages via cdmt_last_error(NULL).
  */
 int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz, double bw_sub_mhz, double dm_first,

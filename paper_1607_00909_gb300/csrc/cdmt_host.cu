@@ -556,10 +556,10 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     }
     p->nbin = nbin;
     p->mbin = nbin / nchan;
-    if (p->mbin < 512 || p->mbin > 4096) {
+    if (p->mbin < 512 || p->mbin > (p->precision == CDMT_PREC_FP32 ? 8192 : 4096)) {
         const long long mb = (long long)p->mbin;
         delete p;
-        return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", mb);
+        return fail(nullptr, CDMT_ENOTSUP, "M_bin = %lld outside 512..4096 (512..8192 in the FP32 form)", mb);
     }
     p->r = (int)(p->mbin / 256);
     if (p->precision != CDMT_PREC_FP32 && 32 % nint != 0) {

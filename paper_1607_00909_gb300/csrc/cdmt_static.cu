@@ -71,7 +71,7 @@ extern "C" int cdmt_execute_static(int nsub, int64_t nsamp, double f_centre_mhz,
     if (!(band_lo > 0)) return fail(CDMT_EINVAL, "lowest frequency %.6g MHz must be > 0", band_lo);
     if (!is_pow2(nbin) || nbin % nchan) return fail(CDMT_EINVAL, "nbin must be a power of two divisible by nchan");
     const int64_t m = nbin / nchan;
-    if (m < 512 || m > 4096) return fail(CDMT_ENOTSUP, "M_bin = %lld outside 512..4096", (long long)m);
+    if (m < 512 || m > 8192) return fail(CDMT_ENOTSUP, "M_bin = %lld outside 512..8192", (long long)m);
     if (nsamp < nbin) return fail(CDMT_EINVAL, "nsamp (%lld) < nbin (%lld)", (long long)nsamp, (long long)nbin);
     if (!d_in || !d_out) return fail(CDMT_EINVAL, "NULL input or output pointer");
     if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(CDMT_EINVAL, "input must be 16-byte aligned");

@@ -1,8 +1,8 @@
 // Device FFT machinery for the coherent-dedispersion kernels.
 //
-// An M-point DFT (M = 256 R, R in {2, 4, 8, 16}) is computed by T = M/16 threads
-// in three radix passes, P = 16, Q = 16 and R (a three-factor Cooley-Tukey
-// decomposition).  With input index j = j2 (16R) + j1 R + j0 and output index
+// An M-point DFT (M = 256 R, R in {2, 4, 8, 16, 32}) is computed by T = M/16
+// threads in three radix passes, P = 16, Q = 16 and R (a three-factor
+// Cooley-Tukey decomposition).  With input index j = j2 (16R) + j1 R + j0 and output index
 // m = m0 + 16 m1 + 256 m2:
 //   pass A  thread t = j1 R + j0:   a[m0]  = sum_j2 x[j2 T + t] W_16^{j2 m0},  a *= W_M^{t m0}
 //   pass B  thread u = m0 R + j0:   b[m1]  = sum_j1 a[m0; j1, j0] W_16^{j1 m1}, b *= W_M^{16 j0 m1}
@@ -13,7 +13,11 @@
 // between passes go through one shared-memory buffer of M elements.  The buffer
 // indices carry an XOR swizzle on their low four bits that makes every access
 // pattern of the passes free of bank conflicts (16-byte elements per
-// quarter-warp, 8-byte elements per half-warp).
+// quarter-warp, 8-byte elements per half-warp) for R <= 16.  With R = 32 each
+// radix-32 butterfly of pass C is shared by two neighbouring lanes: lane e of
+// the pair takes the 16 inputs j0 = 2a + e, runs their 16-point DFT, and one
+// radix-2 step with W_32^k, its operands swapped through lane shuffles, gives
+// outputs m2 = k + 16 e (decimation in time).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,6 +42,25 @@ template <int S> __device__ __forceinline__ float2 mul_cs(float2 a, float c, flo
     const float ss = S > 0 ? s : -s;
     return make_float2(fmaf(a.x, c, -a.y * ss), fmaf(a.x, ss, a.y * c));
 }
+
+// (cos, sin) of pi k / 16, k = 0..15: the radix-2 twiddles W_32^k of the R = 32 pass C
+static __device__ __constant__ float kW32[16][2] = {
+    {1.00000000000000000000f, 0.00000000000000000000f},
+    {0.98078528040323043058f, 0.19509032201612824808f},
+    {0.92387953251128673848f, 0.38268343236508978178f},
+    {0.83146961230254523567f, 0.55557023301960217765f},
+    {0.70710678118654757274f, 0.70710678118654746172f},
+    {0.55557023301960228867f, 0.83146961230254523567f},
+    {0.38268343236508983729f, 0.92387953251128673848f},
+    {0.19509032201612833135f, 0.98078528040323043058f},
+    {0.00000000000000000000f, 1.00000000000000000000f},
+    {-0.19509032201612819257f, 0.98078528040323043058f},
+    {-0.38268343236508972627f, 0.92387953251128673848f},
+    {-0.55557023301960195560f, 0.83146961230254545772f},
+    {-0.70710678118654746172f, 0.70710678118654757274f},
+    {-0.83146961230254534669f, 0.55557023301960217765f},
+    {-0.92387953251128673848f, 0.38268343236508989280f},
+    {-0.98078528040323043058f, 0.19509032201612860891f}};
 
 constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
 constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
@@ -121,7 +144,7 @@ template <int R> struct Fft3 {
     static constexpr int NTA = 15 * T;  // pass-A twiddles W_M^{t m0}, m0 = 1..15, layout [m0-1][t]
     static constexpr int NTB = 15 * R;  // pass-B twiddles W_M^{16 j0 m1}, m1 = 1..15, layout [m1-1][j0]
     static constexpr int GB = R >= 8 ? 1 : 8 / R;   // pass-B write swizzle step, 16-byte elements
-    static constexpr int GB1 = 16 / R;              // the same for 8-byte elements
+    static constexpr int GB1 = R >= 16 ? 1 : 16 / R;   // the same for 8-byte elements
 
     __device__ __forceinline__ static int ex1(int m0, int t) { return m0 * T + (t ^ ((m0 * R) & 15)); }
     __device__ __forceinline__ static int ex2(int j0, int beta) { return j0 * 256 + (beta ^ (j0 * GB)); }
@@ -152,18 +175,44 @@ template <int R> struct Fft3 {
         for (int m1 = 0; m1 < 16; m1++) ex[ex2s(j0, m0 + 16 * m1)] = x[m1];
     }
 
+    // R = 32: the radix-2 step joining the two 16-point halves of a butterfly held by lanes
+    // (2 beta, 2 beta + 1); v holds this lane's half (inputs j0 = 2a + e), leaves its outputs
+    // m2 = k + 16 e in v[k]
+    template <int S> __device__ __forceinline__ static void join32(float2 *v, int e)
+    {
+        #pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, v[k].x, 1), __shfl_xor_sync(0xffffffffu, v[k].y, 1));
+            const float2 ev = e ? other : v[k], od = e ? v[k] : other;
+            // W_32^k = exp(S 2 pi i k / 32)
+            const float2 w = cmul(od, make_float2(kW32[k][0], S > 0 ? kW32[k][1] : -kW32[k][1]));
+            v[k] = e ? csub(ev, w) : cadd(ev, w);
+        }
+    }
+
     template <int S, class Emit>
     __device__ __forceinline__ static void pass_c1(const float2 *ex, int t, Emit &&emit)
     {
-        #pragma unroll
-        for (int i = 0; i < 16 / R; i++) {
-            const int beta = t + T * i;
-            float2 x[R];
+        if constexpr (R == 32) {
+            const int beta = t >> 1, e = t & 1;
+            float2 x[16];
             #pragma unroll
-            for (int j0 = 0; j0 < R; j0++) x[j0] = ex[ex2s(j0, beta)];
-            dft_r<R, S>(x);
+            for (int a = 0; a < 16; a++) x[a] = ex[ex2s(2 * a + e, beta)];
+            dft16<S>(x);
+            join32<S>(x, e);
             #pragma unroll
-            for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2]);
+            for (int k = 0; k < 16; k++) emit(beta + 256 * (k + 16 * e), x[k]);
+        } else {
+            #pragma unroll
+            for (int i = 0; i < 16 / R; i++) {
+                const int beta = t + T * i;
+                float2 x[R];
+                #pragma unroll
+                for (int j0 = 0; j0 < R; j0++) x[j0] = ex[ex2s(j0, beta)];
+                dft_r<R, S>(x);
+                #pragma unroll
+                for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2]);
+            }
         }
     }
 
@@ -214,20 +263,37 @@ template <int R> struct Fft3 {
     template <int S, class Emit>
     __device__ __forceinline__ static void pass_c(const float4 *ex, int t, Emit &&emit)
     {
-        #pragma unroll
-        for (int i = 0; i < 16 / R; i++) {
-            const int beta = t + T * i;
-            float2 x[R], y[R];
+        if constexpr (R == 32) {
+            const int beta = t >> 1, e = t & 1;
+            float2 x[16], y[16];
             #pragma unroll
-            for (int j0 = 0; j0 < R; j0++) {
-                float4 v = ex[ex2(j0, beta)];
-                x[j0] = make_float2(v.x, v.y);
-                y[j0] = make_float2(v.z, v.w);
+            for (int a = 0; a < 16; a++) {
+                const float4 v = ex[ex2(2 * a + e, beta)];
+                x[a] = make_float2(v.x, v.y);
+                y[a] = make_float2(v.z, v.w);
             }
-            dft_r<R, S>(x);
-            dft_r<R, S>(y);
+            dft16<S>(x);
+            dft16<S>(y);
+            join32<S>(x, e);
+            join32<S>(y, e);
             #pragma unroll
-            for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2], y[m2]);
+            for (int k = 0; k < 16; k++) emit(beta + 256 * (k + 16 * e), x[k], y[k]);
+        } else {
+            #pragma unroll
+            for (int i = 0; i < 16 / R; i++) {
+                const int beta = t + T * i;
+                float2 x[R], y[R];
+                #pragma unroll
+                for (int j0 = 0; j0 < R; j0++) {
+                    float4 v = ex[ex2(j0, beta)];
+                    x[j0] = make_float2(v.x, v.y);
+                    y[j0] = make_float2(v.z, v.w);
+                }
+                dft_r<R, S>(x);
+                dft_r<R, S>(y);
+                #pragma unroll
+                for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2], y[m2]);
+            }
         }
     }
 };

@@ -61,7 +61,8 @@ def test_tiny_workload_full_parity(cdmt, orc):
 
 
 @pytest.mark.parametrize("nchan,mbin,nint", [(2, 512, 1), (4, 1024, 2), (8, 2048, 4), (16, 4096, 8),
-                                             (32, 512, 16), (32, 2048, 3), (16, 1024, 5)])
+                                             (32, 512, 16), (32, 2048, 3), (16, 1024, 5), (8, 8192, 4),
+                                             (2, 8192, 3)])
 def test_channel_and_fft_shapes(cdmt, orc, nchan, mbin, nint):
     nbin = nchan * mbin
     nsamp = 3 * nbin + 777          # several segments and a ragged tail
@@ -172,7 +173,10 @@ def test_plan_errors_on_device(cdmt):
         _plan(cdmt, 1, 1 << 14, 135.0, [0.0], 16, 4, nbin=1 << 16)         # nsamp < N
     assert e.value.status == cdmt.CDMT_EINVAL
     with pytest.raises(cdmt.CdmtError) as e:
-        _plan(cdmt, 1, 1 << 16, 135.0, [0.0], 8, 4, nbin=1 << 16)          # M = 8192 has no kernel yet
+        _plan(cdmt, 1, 1 << 17, 135.0, [0.0], 8, 4, nbin=1 << 17)          # M = 16384: no kernel
+    assert e.value.status == cdmt.CDMT_ENOTSUP
+    with pytest.raises(cdmt.CdmtError) as e:                              # M = 8192: FP32 form only
+        _plan(cdmt, 1, 1 << 16, 135.0, [0.0], 8, 4, nbin=1 << 16, precision=cdmt.CDMT_PREC_FP16)
     assert e.value.status == cdmt.CDMT_ENOTSUP
     with pytest.raises(cdmt.CdmtError) as e:
         _plan(cdmt, 64, 1 << 20, 135.0, [0.0], 16, 8, nbin=1 << 16, mem_budget=1 << 20)
