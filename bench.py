@@ -47,7 +47,14 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def workload(name):
+def workload(name, nsamp=0):
+    """The named workload; nsamp > 0 shortens (or lengthens) its input, for profiling small cases."""
+    import dataclasses
+    w = _workload(name)
+    return dataclasses.replace(w, nsamp=nsamp, name=f"{w.name}[nsamp {nsamp}]") if nsamp > 0 else w
+
+
+def _workload(name):
     import synth
     if name == "lofar64":
         return synth.lofar64()
@@ -57,6 +64,8 @@ def workload(name):
         return synth.lofar64(nchan=32)
     if name == "tiny":
         return synth.tiny()
+    if name == "paper":
+        return synth.paper()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -153,7 +162,7 @@ def reference_arm(args, w):
         return 0
     import oracle
     oracle.build()
-    nd = oracle.overlap(w.nsub, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin)
+    nd = w.nd if w.nd >= 0 else oracle.overlap(w.nsub, w.f_centre, w.bw, w.dms, w.nchan, w.nint, w.nbin)
     n_sub, n_seg = [int(v) for v in args.cpu_sample.split("x")]
     log(f"reference arm: FP64 oracle, {n_sub} subbands x {n_seg} segments x {len(w.dms)} DMs per step")
     x = w.voltages(threads=16)
@@ -194,13 +203,16 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 543.6 MB read +
-    # 2067.7 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 543.9 MB read +
+    # 2068.0 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
-    "3889bae55e20a28f:fp16": 0.6140,
-    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 543.1 MB read + 2067.5 MB
+    "ca8ecf5fa754f2a2:fp16": 0.6141,
+    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 543.9 MB read + 2067.6 MB
     # written for 4.253e9 units (same capture command with the FP32 form)
-    "94a2ef83621ff4bf:fp32": 0.6138,
+    "a06535e10a1edf95:fp32": 0.6140,
+    # the paper's setup at 2^20 samples, one launch of k_dedisperse_pol (FP32, 8 channels of 8192
+    # bins, nint 1): 239.1 MB read + 3241.6 MB written for 8.258e8 units
+    "a06535e10a1edf95:fp32:m8192": 4.2152,
 }
 
 try:
@@ -395,7 +407,7 @@ def dm_stage_roofline(form, r, props, sm_max):
     if form == "fp32":
         fpeak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
         fbasis = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
-        kernel, fbound = "k_dedisperse", "alu"
+        kernel, fbound = ("k_dedisperse_pol" if mbin == 8192 else "k_dedisperse"), "alu"
     else:
         fpeak = MEASURED.get("bf16_tflops_sustained") or 1700.0
         fbasis = "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); the FP16 dense rate equals BF16"
@@ -409,7 +421,7 @@ def dm_stage_roofline(form, r, props, sm_max):
         rf = {"bound": fbound, "achieved": flops_unit * units_launch / t / 1e12, "peak": fpeak, "unit": "TFLOP/s",
               "peak_basis": fbasis}
     rf["frac"] = max(t_flop, t_byte) / t
-    tr = NCU_TRAFFIC.get(kernel_source_hash(form) + ":" + form)
+    tr = NCU_TRAFFIC.get(kernel_source_hash(form) + ":" + form + (":m8192" if mbin == 8192 else ""))
     rf.update({"traffic": tr * units_launch if tr else None, "kernel": kernel,
                "definition": "slower of nominal FFT flops at the form's peak and algorithmic bytes at HBM bandwidth, "
                              "over the kernel's time per launch",
@@ -453,13 +465,13 @@ def gpu_arm(args, w):
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     head = forms[-1]
     shard = args.shard == "subbands" and world > 1
-    nd_band = -1
+    nd_band = w.nd
     log(f"rank {rank}: generating {w.name} ...")
     t0 = time.perf_counter()
     if shard and w.nsub < world:
         raise SystemExit(f"--shard subbands needs at least one subband per rank ({w.nsub} subbands, {world} ranks)")
     if shard:   # one beam, its subbands split across the ranks; every rank keeps the band's overlap
-        probe = cdmt.Plan(w.nsub, w.nbin, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin)
+        probe = cdmt.Plan(w.nsub, w.nbin, w.f_centre, w.bw, w.dms, w.nchan, w.nint, nbin=w.nbin, nd=w.nd)
         nd_band = probe.info["nd"]
         probe.close()
         lo, hi = subband_slice(w.nsub, world, rank)
@@ -1088,7 +1100,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cdmt", choices=["cdmt", "reference"])
-    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "lofar64c32", "tiny", "batch4", "serve8",
+    ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "lofar64c32", "tiny", "paper", "batch4", "serve8",
                                                               "groups", "groups-long"])
     ap.add_argument("--dm-groups", default="1,2,4,8", help="groups: DM group counts to time")
     ap.add_argument("--beams", type=int, default=8, help="serve8: beams served at once")
@@ -1100,6 +1112,7 @@ def main():
                     help="segments per block of the host pipeline (e2e; 0: the plan's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default="4x8", help="oracle sample: SUBBANDSxSEGMENTS")
+    ap.add_argument("--nsamp", type=int, default=0, help="input samples per subband (0: the workload's own)")
     ap.add_argument("--forms", default="fp32,bf16,fp16",
                     help="precision forms to time, comma-separated (fp32, fp16, bf16); the last is the headline")
     ap.add_argument("--no-error", action="store_true", help="skip the sampled error check against the oracle")
@@ -1120,7 +1133,10 @@ def main():
         return serve_arm(args)
     if args.workload in ("groups", "groups-long") and args.impl != "reference":
         return groups_arm(args)
-    w = workload(args.workload)
+    w = workload(args.workload, args.nsamp)
+    if args.workload == "paper" and args.forms != "fp32":
+        log("paper workload: channels of 8192 bins run in the FP32 form only (--forms fp32)")
+        args.forms = "fp32"
     if args.impl == "reference":
         return reference_arm(args, w)
     return gpu_arm(args, w)

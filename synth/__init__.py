@@ -152,6 +152,7 @@ class Workload:
     nbin: int
     seed: int
     pulses: tuple = ()
+    nd: int = -1        # overlap n_d fixed by the setup (-1: the planner's rule)
 
     def voltages(self, threads: int = 8, beam: int = 0, sub=None) -> np.ndarray:
         """The workload's voltages, or subbands sub = (lo, hi) of them (equal to those rows
@@ -168,6 +169,20 @@ def tiny() -> Workload:
     DMs {0, 5, 10, 15}, 8 channels, integrate 4."""
     return Workload("tiny-1sub-2^17", 1, 1 << 17, 135.0, 0.1953125, (0.0, 5.0, 10.0, 15.0), 8, 4,
                     1 << 14, 1, (Pulse(0.30, 10.0, 1e-3, 0.5),))
+
+
+def paper(nsamp: int = 1 << 22) -> Workload:
+    """The paper's own application setup (Sec. 4): 10 contiguous subbands
+    114.93-116.88 MHz, N = 2^16 with n_c = 8 channels (M = 8192 bins) and an
+    overlap of n_d = 2048, 80 DMs 0.5..79.5 step 1, no averaging (nint 1); 2^22
+    samples (21.5 s) instead of the paper's 20 minutes, 3 pulses at DM ~ U(5, 75),
+    widths U(0.2, 2) ms."""
+    g = np.random.default_rng(103)
+    T = nsamp / 195312.5
+    pulses = tuple(Pulse(float(g.uniform(1.0, max(1.5, T - 3.0))), float(g.uniform(5, 75)),
+                         float(g.uniform(0.2e-3, 2e-3)), 0.5) for _ in range(3))
+    return Workload(f"paper-10sub-2^{int(np.log2(nsamp))}-M8192", 10, nsamp, 114.93 + 5 * 0.1953125, 0.1953125,
+                    tuple(0.5 + i for i in range(80)), 8, 1, 1 << 16, 3, pulses, 2048)
 
 
 def lofar64(nsamp: int = 1 << 22, nsub: int = 64, nchan: int = 16) -> Workload:
