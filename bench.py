@@ -910,8 +910,8 @@ GROUPS_LONG = dict(GROUPS, nsub=72, nsamp=1 << 21, f_centre=135.0 - 108 * 0.1953
 
 
 def groups_arm(args):
-    """DM groups with their own overlap (cdmt_opts.dm_groups) against one overlap for
-    the whole list, FP16 form.  A step = one execute over the whole input; units are
+    """DM groups with their own overlap (cdmt_opts.dm_groups; with --group-nbin 1 also
+    their own FFT length) against one overlap for the whole list, in the last of --forms.  A step = one execute over the whole input; units are
     those of the ungrouped plan (the same filterbank is delivered).  One sampled
     (subband, segment, DM) tile per group is checked against the oracle."""
     import torch
@@ -934,10 +934,12 @@ def groups_arm(args):
     except AttributeError:
         pass
     rng = np.random.default_rng(7001)
+    form = [f.strip() for f in args.forms.split(",") if f.strip()][-1]
     out, res, clocks = None, {}, None
     for ng in [int(v) for v in args.dm_groups.split(",")]:
         plan = cdmt.Plan(c["nsub"], c["nsamp"], c["f_centre"], c["bw"], dms, c["nchan"], c["nint"], nbin=c["nbin"],
-                         precision=cdmt.CDMT_PREC_FP16, chirp=cdmt.CDMT_CHIRP_SUBBAND, dm_groups=ng)
+                         precision=PREC[form], chirp=cdmt.CDMT_CHIRP_SUBBAND, dm_groups=ng,
+                         group_nbin=args.group_nbin)
         if out is None:
             out = torch.empty(plan.out_shape(), dtype=torch.float32, device=dev)
         st = stream.cuda_stream
@@ -957,15 +959,16 @@ def groups_arm(args):
         ms = ev0.elapsed_time(ev1) / args.steps
         info, layout = plan.info, plan.groups()
         errs = []
-        m = c["nbin"] // c["nchan"]
         for gr in layout:
+            nb = gr["nbin"]
+            m = nb // c["nchan"]
             s = int(rng.integers(c["nsub"]))
             k = int(rng.integers(gr["nseg"]))
             di = gr["dm_first"] + int(rng.integers(gr["ndm"]))
-            sv = c["nbin"] - gr["nd"] * c["nchan"]
-            xs = x[s:s + 1, gr["offset"] + k * sv:gr["offset"] + k * sv + c["nbin"]].cpu().numpy()
+            sv = nb - gr["nd"] * c["nchan"]
+            xs = x[s:s + 1, gr["offset"] + k * sv:gr["offset"] + k * sv + nb].cpu().numpy()
             fc_s = c["f_centre"] + (s - 0.5 * (c["nsub"] - 1)) * c["bw"]
-            o = oracle.tiles(xs, fc_s, c["bw"], [dms[di]], c["nchan"], c["nint"], c["nbin"], gr["nd"], [0], [0],
+            o = oracle.tiles(xs, fc_s, c["bw"], [dms[di]], c["nchan"], c["nint"], nb, gr["nd"], [0], [0],
                              [0], chirp=1)[0]
             seglen = (m - gr["nd"]) // c["nint"]
             t0, t1 = k * seglen, min((k + 1) * seglen, info["nout"])
@@ -973,18 +976,20 @@ def groups_arm(args):
             errs.append(float(np.max(np.abs(gv - o[:, :t1 - t0])) / np.mean(o[:, :t1 - t0])))
         res[ng] = {"value": info["units"] / (ms / 1e3) / 1e9, "ms_per_step": ms,
                    "overlaps": [gr["nd"] for gr in layout], "segments": [gr["nseg"] for gr in layout],
+                   "channel_lengths": [gr["nbin"] // c["nchan"] for gr in layout],
                    "workspace_gb": info["workspace_bytes"] / 1e9, "sampled_rel_max_vs_oracle": max(errs),
                    "clocks": clocks}
         log(f"dm_groups {ng}: {res[ng]['value']:.1f} G/s, {ms:.1f} ms/step, overlaps {res[ng]['overlaps']}, "
-            f"sampled error {max(errs):.2e}")
+            f"lengths {res[ng]['channel_lengths']}, sampled error {max(errs):.2e}")
         plan.close()
     best = max(res, key=lambda k: res[k]["value"])
     line = {"metric": METRIC, "value": res[best]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res[best]["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f16 (FP32 accumulate)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[form], "data": "synthetic",
             "config": {"workload": f"{c['nsub']} subbands x {c['nsamp']} samples at {c['f_centre']} MHz, {c['ndm']} DMs "
                                    f"0-{c['dm_max']:g}, {c['nchan']} channels, nint {c['nint']}, N 2^16, one "
                                    f"transfer function per subband", "dm_groups": best,
+                       "group_lengths": bool(args.group_nbin),
                        "l2": f"inputs ({x.numel() * 4 / 1e9:.1f} GB) larger than L2; no flush"},
             "dm_groups": {str(k): v for k, v in res.items()}, "roofline": None, "clocks": clocks,
             "gpu_launches": 3 * best * args.steps}
@@ -1103,6 +1108,7 @@ def main():
     ap.add_argument("--workload", default="lofar64", choices=["lofar64", "lofar8", "lofar64c32", "tiny", "paper", "batch4", "serve8",
                                                               "groups", "groups-long"])
     ap.add_argument("--dm-groups", default="1,2,4,8", help="groups: DM group counts to time")
+    ap.add_argument("--group-nbin", type=int, default=0, help="groups: 1 = each group picks its own FFT length")
     ap.add_argument("--beams", type=int, default=8, help="serve8: beams served at once")
     ap.add_argument("--int8", action="store_true", help="serve8: int8 blocks (4 bytes per sample)")
     ap.add_argument("--u8", action="store_true", help="serve8: blocks redigitised to 8 bits on the device")

@@ -97,7 +97,9 @@ typedef struct cdmt_opts {
                             largest |DM| needs (the per-DM overlap of Sec. 5, taken per group), the
                             ungrouped time axis and length kept (see cdmt_plan_group); 0 or 1 = one
                             overlap for the whole list */
-    int32_t reserved32;
+    int32_t group_nbin;  /* with dm_groups > 1: 1 = each group also picks its own N_bin (Sec. 5: digifil
+                            chooses the FFT size per DM; see cdmt_plan_group_nbin); 0 = every group
+                            uses the plan's N_bin */
     int64_t reserved[3];
 } cdmt_opts;
 
@@ -190,6 +192,27 @@ int cdmt_plan_info(cdmt_plan_t plan, cdmt_info *info);
  * Errors: CDMT_EINVAL for a NULL plan or g out of range. */
 int cdmt_plan_group(cdmt_plan_t plan, int g, int *dm_first, int *ndm, int64_t *nd, int64_t *offset,
                     int64_t *nseg);
+
+/* cdmt_plan_group_nbin - the forward FFT length N_g of DM group g (the plan's
+ * N_bin unless the plan was made with cdmt_opts.group_nbin = 1).
+ *
+ * Sec. 5 notes that digifil chooses the FFT size as well as the overlap for the
+ * DM and frequency at hand, which pays at low DMs.  With group_nbin = 1 group g
+ * takes, among the channel lengths M = N / nchan its precision runs (512..8192
+ * in the FP32 form, 2048 and 4096 in the tensor-core forms) for which an
+ * overlap nd_g <= n_d exists as in cdmt_plan_group (the group's own rule at
+ * that M, grown until its segments cover the ungrouped output length) and one
+ * segment fits the input from off_g on, the M with the least nominal FFT work
+ * per DM-trial x input sample, 10 N log2(M) / S_g = 10 nchan M log2(M) /
+ * (nchan (M - nd_g)), the plan's own M on a tie.  The time axis and off_g do not
+ * depend on N_g (channel samples keep their rate), so the filterbank layout is
+ * that of cdmt_plan_group.  The rule counts flops only: a length whose kernel
+ * runs at a lower rate can make the plan slower (measured on GB300: FP32 groups
+ * that take M = 8192, or FP16 groups that take M = 2048, lose more to the
+ * kernels' rate than they save in work).
+ *   nbin  out: N_g
+ * Errors: CDMT_EINVAL for a NULL plan or nbin, or g out of range. */
+int cdmt_plan_group_nbin(cdmt_plan_t plan, int g, int64_t *nbin);
 
 /*
  * cdmt_execute - compute the whole filterbank of one input block.

@@ -194,7 +194,8 @@ def dm_groups(ndm: int, groups: int) -> list[tuple[int, int]]:
     return [(g * ndm // groups, (g + 1) * ndm // groups - g * ndm // groups) for g in range(groups)]
 
 
-def grouped_layout(nsub, nsamp, f_centre, bw, dm_list, nchan, nint, nbin, groups, chirp: int = 0, nd: int = -1):
+def grouped_layout(nsub, nsamp, f_centre, bw, dm_list, nchan, nint, nbin, groups, chirp: int = 0, nd: int = -1,
+                   lengths=None):
     """Overlap per DM group (digifil's per-DM overlap, Sec. 5, taken per group of
     trials).  nd_max is Sec. 2's overlap for the whole list (or `nd`), and the
     grouped filterbank keeps its time axis and length nout: a group whose
@@ -204,42 +205,73 @@ def grouped_layout(nsub, nsamp, f_centre, bw, dm_list, nchan, nint, nbin, groups
     nd_g is the smallest overlap that is at least Sec. 2's overlap for the
     group's own largest |DM|, satisfies the rule's parity and nint conditions and
     whose segments still cover nout (nd_max always does).
-    Returns ([(first, count, nd_g, off_g)], nd_max, nout)."""
+
+    lengths: channel lengths M the groups may take besides nbin / nchan (Sec. 5:
+    digifil also picks the FFT size for the DM at hand).  A group then takes the M
+    whose overlap, found as above with N = n_c M, stays within nd_max and lets one
+    segment fit the input from off_g, and whose nominal FFT work per unit
+    10 N log2(M) / S_g = 10 M log2(M) / (M - nd_g) is least; nbin / nchan on a tie.
+    The channel sample rate, hence the time axis and off_g, do not depend on M.
+    Returns ([(first, count, nd_g, off_g, nbin_g)], nd_max, nout)."""
     dm = np.ascontiguousarray(dm_list, dtype=np.float64)
     nd_max = nd if nd >= 0 else overlap(nsub, f_centre, bw, dm, nchan, nint, nbin, chirp)
     if nd_max < 0:
         raise ValueError("no overlap < M")
     nout = grid(nsamp, nbin, nchan, nd_max, nint)[2]
-    m = nbin // nchan
+    m_plan = nbin // nchan
 
-    def covers(nd_g):
+    def segments_cover(n, nd_g):
         off = (nd_max - nd_g) * nchan // 2
-        return nsamp - off >= nbin and grid(nsamp - off, nbin, nchan, nd_g, nint)[2] >= nout
+        return nsamp - off >= n and grid(nsamp - off, n, nchan, nd_g, nint)[2] >= nout
 
-    out = []
-    for first, count in dm_groups(len(dm), groups):
-        nd_g = min(overlap(nsub, f_centre, bw, dm[first:first + count], nchan, nint, nbin, chirp), nd_max)
-        while not covers(nd_g):
+    def group_overlap(dms, m):
+        # the group's overlap at channel length m, or None where it would exceed nd_max
+        n = m * nchan
+        nd_g = overlap(nsub, f_centre, bw, dms, nchan, nint, n, chirp)
+        if nd_g < 0 or nd_g > nd_max:
+            if m != m_plan:
+                return None
+            nd_g = nd_max
+        while not segments_cover(n, nd_g):
             nd_g += 2
             while (m - nd_g) % nint:
                 nd_g += 2
-        out.append((first, count, nd_g, (nd_max - nd_g) * nchan // 2))
+            if nd_g > nd_max:
+                return None
+        return nd_g
+
+    out = []
+    for first, count in dm_groups(len(dm), groups):
+        dms = dm[first:first + count]
+        m_g, nd_g = m_plan, group_overlap(dms, m_plan)
+        work = m_g * np.log2(m_g) / (m_g - nd_g)
+        for m in (lengths or ()):
+            if m == m_plan:
+                continue
+            v = group_overlap(dms, m)
+            if v is None:
+                continue
+            w = m * np.log2(m) / (m - v)
+            if w < work * (1 - 1e-12):
+                m_g, nd_g, work = m, v, w
+        out.append((first, count, nd_g, (nd_max - nd_g) * nchan // 2, m_g * nchan))
     return out, nd_max, nout
 
 
 def filterbank_grouped(x, f_centre, bw, dm_list, nchan, nint, nbin, groups, nthreads: int = 0, chirp: int = 0,
-                       nd: int = -1) -> np.ndarray:
-    """The filterbank of :func:`filterbank` with each DM group's own overlap
-    (:func:`grouped_layout`): group g's rows are the filterbank of the input from
-    sample off_g on, with overlap nd_g, cut to the ungrouped length nout.
-    float64 [ndm][nsub*nchan][nout], on the ungrouped time axis."""
+                       nd: int = -1, lengths=None) -> np.ndarray:
+    """The filterbank of :func:`filterbank` with each DM group's own overlap (and,
+    with `lengths`, its own FFT length) (:func:`grouped_layout`): group g's rows are
+    the filterbank of the input from sample off_g on, with overlap nd_g and N_g,
+    cut to the ungrouped length nout.  float64 [ndm][nsub*nchan][nout], on the
+    ungrouped time axis."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     nsub, nsamp = x.shape[0], x.shape[1]
     dm = np.ascontiguousarray(dm_list, dtype=np.float64)
-    layout, _, nout = grouped_layout(nsub, nsamp, f_centre, bw, dm, nchan, nint, nbin, groups, chirp, nd)
+    layout, _, nout = grouped_layout(nsub, nsamp, f_centre, bw, dm, nchan, nint, nbin, groups, chirp, nd, lengths)
     out = np.empty((len(dm), nsub * nchan, nout), dtype=np.float64)
-    for first, count, nd_g, off in layout:
-        fb = filterbank(x[:, off:], f_centre, bw, dm[first:first + count], nchan, nint, nbin, nd_g, nthreads, chirp)
+    for first, count, nd_g, off, nbin_g in layout:
+        fb = filterbank(x[:, off:], f_centre, bw, dm[first:first + count], nchan, nint, nbin_g, nd_g, nthreads, chirp)
         out[first:first + count] = fb[:, :, :nout]
     return out
 

@@ -31,7 +31,7 @@ class cdmt_opts(ctypes.Structure):
     _fields_ = [("nbin", ctypes.c_int64), ("nd", ctypes.c_int64), ("dm_tile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("chirp", ctypes.c_int32),
                 ("seg_chunk", ctypes.c_int64), ("mem_budget", ctypes.c_int64), ("host_block", ctypes.c_int64),
-                ("sk_nsigma", ctypes.c_double), ("dm_groups", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("sk_nsigma", ctypes.c_double), ("dm_groups", ctypes.c_int32), ("group_nbin", ctypes.c_int32),
                 ("reserved", ctypes.c_int64 * 3)]
 
 
@@ -121,6 +121,7 @@ def _load():
     lib.cdmt_plan_group.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.cdmt_plan_group_nbin.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
     lib.cdmt_execute.argtypes = [P, P, P, P, P]
     lib.cdmt_execute_host.argtypes = [P, P, P, P, P]
     lib.cdmt_destroy.argtypes = [P]
@@ -175,7 +176,8 @@ def _load():
 
 _lib = _load()
 
-EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "cdmt_selftest_wait",
+EXPORTED = ("cdmt_plan", "cdmt_plan_ex", "cdmt_plan_info", "cdmt_plan_group", "cdmt_plan_group_nbin",
+            "cdmt_selftest_wait",
             "cdmt_inject_timeout", "cdmt_execute", "cdmt_execute_host", "cdmt_destroy",
             "cdmt_strerror", "cdmt_last_error", "cdmt_set_timing", "cdmt_stage_times", "cdmt_device_status",
             "cdmt_redigitise", "cdmt_redigitise_sk", "cdmt_incoherent_info", "cdmt_incoherent",
@@ -231,7 +233,15 @@ def cdmt_plan_group(plan, g: int) -> dict:
     nd, off, nseg = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.cdmt_plan_group(plan, g, ctypes.byref(first), ctypes.byref(n), ctypes.byref(nd), ctypes.byref(off),
                                 ctypes.byref(nseg)), plan)
-    return {"dm_first": first.value, "ndm": n.value, "nd": nd.value, "offset": off.value, "nseg": nseg.value}
+    return {"dm_first": first.value, "ndm": n.value, "nd": nd.value, "offset": off.value, "nseg": nseg.value,
+            "nbin": cdmt_plan_group_nbin(plan, g)}
+
+
+def cdmt_plan_group_nbin(plan, g: int) -> int:
+    """Forward FFT length N_g of DM group g (cdmt_opts.group_nbin)."""
+    nbin = ctypes.c_int64()
+    _check(_lib.cdmt_plan_group_nbin(plan, g, ctypes.byref(nbin)), plan)
+    return nbin.value
 
 
 def cdmt_selftest_wait(limit_ms: float, arrive: bool = False) -> tuple[bool, float]:
@@ -574,11 +584,11 @@ class Plan:
 
     def __init__(self, nsub, nsamp, f_centre, bw_sub, dm_list, nchan, nint, *, nbin=0, nd=-1, dm_tile=0,
                  seg_chunk=0, mem_budget=0, precision=CDMT_PREC_FP32, in_dtype=CDMT_IN_C64, chirp=0, host_block=0,
-                 sk_nsigma=0.0, dm_groups=0):
+                 sk_nsigma=0.0, dm_groups=0, group_nbin=0):
         o = cdmt_opts()
         o.nbin, o.nd, o.dm_tile, o.seg_chunk, o.mem_budget = nbin, nd, dm_tile, seg_chunk, mem_budget
         o.precision, o.in_dtype, o.chirp, o.host_block, o.sk_nsigma = precision, in_dtype, chirp, host_block, sk_nsigma
-        o.dm_groups = dm_groups
+        o.dm_groups, o.group_nbin = dm_groups, group_nbin
         self.handle = cdmt_plan_ex(nsub, nsamp, f_centre, bw_sub, list(dm_list), nchan, nint, o)
         self.info = cdmt_plan_info(self.handle)
 
@@ -597,7 +607,7 @@ class Plan:
         cdmt_device_status(self.handle)
 
     def groups(self) -> list[dict]:
-        """Layout of the plan's DM groups: dm_first, ndm, nd, offset (input samples), nseg."""
+        """Layout of the plan's DM groups: dm_first, ndm, nd, offset (input samples), nseg, nbin."""
         return [cdmt_plan_group(self.handle, g) for g in range(self.info["dm_groups"])]
 
     def out_shape(self):

@@ -384,12 +384,36 @@ int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
 {
     const int G = o.dm_groups;
     const int64_t ndm = p->ndm;
-    auto covers = [&](int64_t ndg) {
-        const int64_t off = (p->nd - ndg) * p->nchan / 2;
-        if (p->nsamp - off < p->nbin) return false;
-        const int64_t nseg = (p->nsamp - off - p->nbin) / (p->nbin - ndg * p->nchan) + 1;
-        return nseg * ((p->mbin - ndg) / p->nint) >= p->nout;
+    // A group's overlap at channel length m: its own rule at N = nchan m, grown (even, (m - ndg)
+    // divisible by nint) until its segments from offset (nd - ndg) nchan / 2 cover nout.  At the
+    // plan's own m the whole list's nd always covers; at another m, -1 when that needs more than nd
+    // or one segment does not fit the input.
+    auto fit = [&](const cdmt_plan_s &part, int64_t m) -> int64_t {
+        const int64_t n = m * p->nchan;
+        int64_t ndg = overlap_rule(part, n);
+        if (ndg < 0 || ndg > p->nd) {
+            if (m != p->mbin) return -1;
+            ndg = p->nd;
+        }
+        for (;;) {
+            if (ndg > p->nd) return -1;
+            const int64_t off = (p->nd - ndg) * p->nchan / 2;
+            if (p->nsamp - off >= n) {
+                const int64_t nseg = (p->nsamp - off - n) / (n - ndg * p->nchan) + 1;
+                if (nseg * ((m - ndg) / p->nint) >= p->nout) return ndg;
+            }
+            ndg += 2;
+            while ((m - ndg) % p->nint) ndg += 2;
+        }
     };
+    // channel lengths a group may take: the plan's, or (group_nbin) every length its precision runs
+    std::vector<int64_t> lengths;
+    if (o.group_nbin) {
+        for (int64_t m = 512; m <= (p->precision == CDMT_PREC_FP32 ? 8192 : 4096); m *= 2)
+            if (p->precision == CDMT_PREC_FP32 || m == 2048 || m == 4096) lengths.push_back(m);
+    } else {
+        lengths.push_back(p->mbin);
+    }
     for (int g = 0; g < G; g++) {
         const int first = (int)(g * ndm / G), count = (int)((g + 1) * ndm / G) - first;
         cdmt_plan_s part;
@@ -400,15 +424,24 @@ int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
         part.nint = p->nint;
         part.chirp = p->chirp;
         part.dms.assign(dm_list + first, dm_list + first + count);
-        int64_t ndg = overlap_rule(part, p->nbin);
-        if (ndg < 0 || ndg > p->nd) ndg = p->nd;
-        while (!covers(ndg)) {
-            ndg += 2;
-            while ((p->mbin - ndg) % p->nint) ndg += 2;
+        // the length with the least nominal FFT work per unit, 10 N log2(M) / S_g (Sec. 5: digifil
+        // picks the FFT size per DM); the plan's own length on a tie
+        int64_t mg = p->mbin, ndg = fit(part, p->mbin);
+        double best = (double)mg * std::log2((double)mg) / (double)(mg - ndg);
+        for (int64_t m : lengths) {
+            if (m == p->mbin) continue;
+            const int64_t nd_m = fit(part, m);
+            if (nd_m < 0) continue;
+            const double cost = (double)m * std::log2((double)m) / (double)(m - nd_m);
+            if (cost < best * (1.0 - 1e-12)) {
+                best = cost;
+                mg = m;
+                ndg = nd_m;
+            }
         }
         const int64_t off = (p->nd - ndg) * p->nchan / 2;
         cdmt_opts co = o;
-        co.nbin = p->nbin;
+        co.nbin = mg * p->nchan;
         co.nd = ndg;
         co.dm_groups = 0;
         co.mem_budget = o.mem_budget > 0 ? o.mem_budget / G : 0;
@@ -419,7 +452,7 @@ int make_groups(cdmt_plan_s *p, const cdmt_opts &o, const double *dm_list)
             p->last_error = g_thread_error;
             return rc;
         }
-        const int64_t seglen = (p->mbin - ndg) / p->nint;
+        const int64_t seglen = (mg - ndg) / p->nint;
         child->out_tlim = p->nout;
         p->groups.push_back({child, first, off, (p->nout + seglen - 1) / seglen});
     }
@@ -750,6 +783,15 @@ int cdmt_plan_group(cdmt_plan_t p, int g, int *dm_first, int *ndm, int64_t *nd, 
     if (nd) *nd = q.plan->nd;
     if (offset) *offset = q.off;
     if (nseg) *nseg = q.kneed;
+    return CDMT_OK;
+}
+
+int cdmt_plan_group_nbin(cdmt_plan_t p, int g, int64_t *nbin)
+{
+    if (!p || !nbin) return fail(p, CDMT_EINVAL, "NULL plan or nbin");
+    const int ng = p->groups.empty() ? 1 : (int)p->groups.size();
+    if (g < 0 || g >= ng) return fail(p, CDMT_EINVAL, "group %d outside 0..%d", g, ng - 1);
+    *nbin = p->groups.empty() ? p->nbin : p->groups[g].plan->nbin;
     return CDMT_OK;
 }
 

@@ -56,13 +56,14 @@ def test_grouped_layout_equals_the_oracle(cdmt, orc, chirp, groups):
     assert plan.info["seg_chunk"] > 0 and plan.info["workspace_bytes"] > 0
     got = plan.groups()
     m = c["nbin"] // c["nchan"]
-    for g, (first, count, nd_g, off) in zip(got, layout):
-        assert (g["dm_first"], g["ndm"], g["nd"], g["offset"]) == (first, count, nd_g, off)
+    for g, (first, count, nd_g, off, nbin_g) in zip(got, layout):
+        assert (g["dm_first"], g["ndm"], g["nd"], g["offset"], g["nbin"]) == (first, count, nd_g, off, nbin_g)
+        assert nbin_g == c["nbin"]
         seglen = (m - nd_g) // c["nint"]
         assert g["nseg"] == -(-nout // seglen)   # the segments that cover nout
     assert got[0]["nd"] < nd_max
     assert plain.groups() == [{"dm_first": 0, "ndm": len(c["dms"]), "nd": nd_max, "offset": 0,
-                               "nseg": plain.info["nseg"]}]
+                               "nseg": plain.info["nseg"], "nbin": c["nbin"]}]
     plan.close()
     plain.close()
 
@@ -81,6 +82,42 @@ def test_grouped_filterbank_matches_the_oracle(cdmt, orc, chirp, nbin, prec, tol
     assert np.all(np.isfinite(g))
     emax, erms = rel_errors(g, o)
     print(f"prec {prec} chirp {chirp} M {nbin // 8} 4 groups: rel_max {emax:.3e} rel_rms {erms:.3e}")
+    assert emax <= tol and erms <= tol
+    plan.close()
+
+
+# channel lengths each precision runs (cdmt_plan_group_nbin)
+LENGTHS = {0: [512, 1024, 2048, 4096, 8192], 1: [2048, 4096], 2: [2048, 4096]}
+
+
+@pytest.mark.parametrize("chirp", [0, 1])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-3)])
+def test_grouped_lengths_match_the_oracle(cdmt, orc, chirp, prec, tol):
+    """cdmt_opts.group_nbin: each group also takes its own FFT length (Sec. 5, digifil's
+    per-DM FFT size).  The layout, lengths included, equals the oracle's with the
+    lengths the precision runs; the filterbank matches the oracle's grouped filterbank
+    at the same layout, every sample written."""
+    c = _case(chirp)
+    plan = _plan(cdmt, c, 4, prec, chirp, group_nbin=1)
+    layout, nd_max, nout = orc.grouped_layout(c["nsub"], c["nsamp"], c["fc"], BW, c["dms"], c["nchan"], c["nint"],
+                                              c["nbin"], 4, chirp, lengths=LENGTHS[prec])
+    assert plan.info["nd"] == nd_max and plan.info["nout"] == nout
+    got = plan.groups()
+    for g, (first, count, nd_g, off, nbin_g) in zip(got, layout):
+        assert (g["dm_first"], g["ndm"], g["nd"], g["offset"], g["nbin"]) == (first, count, nd_g, off, nbin_g)
+        seglen = (nbin_g // c["nchan"] - nd_g) // c["nint"]
+        assert g["nseg"] == -(-nout // seglen)
+    print("lengths", [g["nbin"] // c["nchan"] for g in got], "overlaps", [g["nd"] for g in got])
+    if prec == 0:
+        assert any(g["nbin"] != c["nbin"] for g in got)
+    x = synth.noise(60 + chirp, c["nsub"], c["nsamp"])
+    fb = gpu_filterbank(plan, x)
+    plan.device_status()
+    o = orc.filterbank_grouped(x, c["fc"], BW, c["dms"], c["nchan"], c["nint"], c["nbin"], 4, chirp=chirp,
+                               lengths=LENGTHS[prec])
+    assert fb.shape == o.shape and np.all(np.isfinite(fb))
+    emax, erms = rel_errors(fb, o)
+    print(f"prec {prec} chirp {chirp} group lengths: rel_max {emax:.3e} rel_rms {erms:.3e}")
     assert emax <= tol and erms <= tol
     plan.close()
 

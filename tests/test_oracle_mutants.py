@@ -101,10 +101,15 @@ MUTANTS_PY = [
     ("grouped_no_offset", "off = (nd_max - nd_g) * nchan // 2", "off = 0", None),
     ("grouped_offset_sign", "(nd_max - nd_g) * nchan // 2", "(nd_g - nd_max) * nchan // 2", None),
     ("grouped_offset_not_halved", "(nd_max - nd_g) * nchan // 2", "(nd_max - nd_g) * nchan", None),
-    ("grouped_no_coverage_step", "while not covers(nd_g):", "while False:", None),
-    ("grouped_overlap_of_first_dm", "dm[first:first + count], nchan, nint, nbin, chirp), nd_max)",
-     "dm[first:first + 1], nchan, nint, nbin, chirp), nd_max)", None),
-    ("grouped_all_nd_max", "nd_g = min(overlap(", "nd_g = max(overlap(", None),
+    ("grouped_no_coverage_step", "while not segments_cover(n, nd_g):", "while False:", None),
+    ("grouped_overlap_of_first_dm", "dms = dm[first:first + count]", "dms = dm[first:first + 1]", None),
+    ("grouped_all_nd_max", "if nd_g < 0 or nd_g > nd_max:", "if True:", None),
+    # per-group FFT lengths
+    ("grouped_lengths_plan_grid", "grid(nsamp - off, n, nchan, nd_g, nint)", "grid(nsamp - off, nbin, nchan, nd_g, nint)",
+     None),
+    ("grouped_lengths_most_work", "if w < work * (1 - 1e-12):", "if w > work * (1 + 1e-12):", None),
+    ("grouped_lengths_overlap_at_plan_n", "nd_g = overlap(nsub, f_centre, bw, dms, nchan, nint, n, chirp)",
+     "nd_g = overlap(nsub, f_centre, bw, dms, nchan, nint, nbin, chirp)", None),
 ]
 
 GROUPED_PIN_CALLS = [
@@ -114,6 +119,11 @@ GROUPED_PIN_CALLS = [
     lambda o: pins.test_grouped_filterbank_keeps_the_ungrouped_time_axis(o),
     lambda o: pins.test_grouped_impulse_at_the_closed_form_time(o, 5.0),
     lambda o: pins.test_grouped_impulse_at_the_closed_form_time(o, 10.0),
+    lambda o: pins.test_grouped_lengths_cover_and_save_work(o, 0),
+    lambda o: pins.test_grouped_lengths_cover_and_save_work(o, 1),
+    lambda o: pins.test_grouped_lengths_keep_the_time_axis(o),
+    lambda o: pins.test_grouped_lengths_impulse_at_the_closed_form_time(o, 5.0),
+    lambda o: pins.test_grouped_lengths_impulse_at_the_closed_form_time(o, 10.0),
 ]
 
 

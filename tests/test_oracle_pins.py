@@ -614,7 +614,8 @@ def test_grouped_overlaps_cover_their_group_and_are_minimal(orc, chirp, groups):
         sv = nbin - nd_g * nchan
         return nsamp - off >= nbin and ((nsamp - off - nbin) // sv + 1) * ((m - nd_g) // nint) >= nout
 
-    for first, count, nd_g, off in layout:
+    for first, count, nd_g, off, nbin_g in layout:
+        assert nbin_g == nbin
         need = _grouped_need(orc, nsub, fc, nchan, np.abs(dms[first:first + count]).max(), chirp)
         assert nd_g % 2 == 0 and (m - nd_g) % nint == 0 and nd_g <= nd_max
         assert nd_g >= need and covers(nd_g)
@@ -660,9 +661,93 @@ def test_grouped_impulse_at_the_closed_form_time(orc, dm_true):
     x = _physical_impulse(nsamp, fc, dm_true, t0)
     dms = [0.0, 5.0, 10.0, 15.0, 40.0, 45.0]
     layout, nd_max, _ = orc.grouped_layout(1, nsamp, fc, BW, dms, nchan, 1, nbin, 3)
-    gi = [g for g, (first, count, _, _) in enumerate(layout) if first <= dms.index(dm_true) < first + count][0]
+    gi = [g for g, (first, count, _, _, _) in enumerate(layout) if first <= dms.index(dm_true) < first + count][0]
     assert layout[gi][3] > 0   # the DM's group starts its segments later
     fb = orc.filterbank_grouped(x, fc, BW, dms, nchan, 1, nbin, 3)
+    for c in range(nchan):
+        nuc = fc - BW / 2 + (c + 0.5) * BW / nchan
+        t_exp = t0 / nchan + D * dm_true * (1 / nuc ** 2 - 1 / fc ** 2) * r / nchan - nd_max / 2
+        row = fb[dms.index(dm_true), c]
+        i0 = int(np.floor(t_exp))
+        assert abs(np.argmax(row) - t_exp) <= 1.0, (c, np.argmax(row), t_exp)
+        assert (row[i0] + row[i0 + 1]) / np.sum(row) >= 0.8
+
+
+LENGTHS = [512, 1024, 2048, 4096, 8192]
+
+
+@pytest.mark.parametrize("chirp", [0, 1])
+def test_grouped_lengths_cover_and_save_work(orc, chirp):
+    # With FFT lengths per group (Sec. 5: digifil picks the FFT size per DM): every group's
+    # length is one offered, its overlap satisfies the rule's conditions at that length,
+    # holds the group's Eq. 2 sweep, stays within the whole list's and lets its segments
+    # cover the ungrouped length from the same offset (which does not depend on the
+    # length); the group of the largest |DM| keeps nd_max and no offset; some group does
+    # take another length; and the total nominal FFT work, sum over DMs of
+    # M log2(M) / (M - nd) (10 N log2 M / S per unit, over 10 n_c), is no more than that of
+    # the same grouping at the plan's length.
+    nsub, fc, nchan, nint, nbin = 2, 60.0, 8, 2, 1 << 14
+    nsamp = 6 * nbin + 1000
+    dms = np.linspace(0.0, 4.2, 8) if chirp else np.linspace(0.0, 30.0, 8)
+    layout, nd_max, nout = orc.grouped_layout(nsub, nsamp, fc, BW, dms, nchan, nint, nbin, 4, chirp, lengths=LENGTHS)
+    fixed, _, _ = orc.grouped_layout(nsub, nsamp, fc, BW, dms, nchan, nint, nbin, 4, chirp)
+    m_plan = nbin // nchan
+    work = work_fixed = 0.0
+    for (first, count, nd_g, off, nbin_g), fx in zip(layout, fixed):
+        m = nbin_g // nchan
+        assert m in LENGTHS and nbin_g == m * nchan
+        need = _grouped_need(orc, nsub, fc, nchan, np.abs(dms[first:first + count]).max(), chirp)
+        assert nd_g % 2 == 0 and (m - nd_g) % nint == 0 and need <= nd_g <= nd_max
+        assert off == (nd_max - nd_g) * nchan // 2
+        sv = nbin_g - nd_g * nchan
+        assert nsamp - off >= nbin_g and ((nsamp - off - nbin_g) // sv + 1) * ((m - nd_g) // nint) >= nout
+        work += count * m * np.log2(m) / (m - nd_g)
+        work_fixed += count * m_plan * np.log2(m_plan) / (m_plan - fx[2])
+    assert layout[-1][2] == nd_max and layout[-1][3] == 0
+    assert any(g[4] != nbin for g in layout)
+    assert work <= work_fixed * (1 + 1e-12)
+
+
+def test_grouped_lengths_keep_the_time_axis(orc):
+    # Noise in, groups of the subband-wide chirp with their own FFT lengths: every row stays
+    # within the wrap-around leakage of the ungrouped rows (about 1 % rms; rows of a group at
+    # the plan's length and overlap, exactly), while one output sample of misalignment would
+    # differ by about 60 %.
+    nsub, fc, nchan, nint, nbin = 2, 60.0, 8, 2, 1 << 13
+    nsamp = 6 * nbin + 1000
+    dms = np.linspace(0.0, 4.2, 8)
+    x = np.random.default_rng(5).standard_normal((nsub, nsamp, 4)).astype(np.float32)
+    nd = orc.overlap(nsub, fc, BW, dms, nchan, nint, nbin, 1)
+    plain = orc.filterbank(x, fc, BW, dms, nchan, nint, nbin, nd, chirp=1)
+    layout, _, _ = orc.grouped_layout(nsub, nsamp, fc, BW, dms, nchan, nint, nbin, 4, 1, lengths=LENGTHS)
+    assert any(g[4] != nbin for g in layout)
+    g = orc.filterbank_grouped(x, fc, BW, dms, nchan, nint, nbin, 4, chirp=1, lengths=LENGTHS)
+    assert g.shape == plain.shape
+    for first, count, nd_g, off, nbin_g in layout:
+        for i in range(first, first + count):
+            if nd_g == nd and nbin_g == nbin:
+                assert np.array_equal(g[i], plain[i])
+                continue
+            rel = np.sqrt(np.mean((g[i] - plain[i]) ** 2) / np.mean(plain[i] ** 2))
+            assert rel < 0.03, (i, rel)
+            shifted = np.sqrt(np.mean((g[i][:, 1:] - plain[i][:, :-1]) ** 2) / np.mean(plain[i] ** 2))
+            assert shifted > 0.3, (i, shifted)
+
+
+@pytest.mark.parametrize("dm_true", [5.0, 10.0])
+def test_grouped_lengths_impulse_at_the_closed_form_time(orc, dm_true):
+    # A physical impulse dispersed at dm_true, in a group whose FFT length (and overlap and
+    # offset) differ from the plan's: at its DM row, channel c peaks at the closed-form time of
+    # the ungrouped axis, t0 / n_c + D DM (nu_c^-2 - nu_s^-2) r / n_c - nd_max / 2, with
+    # >= 0.8 of the row's energy in the two nearest samples.
+    fc, nchan, nbin = 135.0, 8, 1 << 14
+    nsamp, t0, r = 1 << 15, 20000, BW * 1e6
+    x = _physical_impulse(nsamp, fc, dm_true, t0)
+    dms = [0.0, 5.0, 10.0, 15.0, 40.0, 45.0]
+    layout, nd_max, _ = orc.grouped_layout(1, nsamp, fc, BW, dms, nchan, 1, nbin, 3, lengths=LENGTHS)
+    gi = [g for g, (first, count, _, _, _) in enumerate(layout) if first <= dms.index(dm_true) < first + count][0]
+    assert layout[gi][4] != nbin and layout[gi][3] > 0
+    fb = orc.filterbank_grouped(x, fc, BW, dms, nchan, 1, nbin, 3, lengths=LENGTHS)
     for c in range(nchan):
         nuc = fc - BW / 2 + (c + 0.5) * BW / nchan
         t_exp = t0 / nchan + D * dm_true * (1 / nuc ** 2 - 1 / fc ** 2) * r / nchan - nd_max / 2
