@@ -258,8 +258,8 @@ template <int R> struct Fft3 {
         for (int m1 = 0; m1 < 16; m1++) ex[ex2(j0, m0 + 16 * m1)] = pack(x[m1], y[m1]);
     }
 
-    // Final radix-R butterflies; emit(m, xm, ym) receives output m of both
-    // polarisations.
+    // Final radix-R butterflies; emit(beta, m2, xm, ym) receives output
+    // m = beta + 256 m2 (beta < 256) of both polarisations.
     template <int S, class Emit>
     __device__ __forceinline__ static void pass_c(const float4 *ex, int t, Emit &&emit)
     {
@@ -277,7 +277,7 @@ template <int R> struct Fft3 {
             join32<S>(x, e);
             join32<S>(y, e);
             #pragma unroll
-            for (int k = 0; k < 16; k++) emit(beta + 256 * (k + 16 * e), x[k], y[k]);
+            for (int k = 0; k < 16; k++) emit(beta, k + 16 * e, x[k], y[k]);
         } else {
             #pragma unroll
             for (int i = 0; i < 16 / R; i++) {
@@ -292,7 +292,7 @@ template <int R> struct Fft3 {
                 dft_r<R, S>(x);
                 dft_r<R, S>(y);
                 #pragma unroll
-                for (int m2 = 0; m2 < R; m2++) emit(beta + 256 * m2, x[m2], y[m2]);
+                for (int m2 = 0; m2 < R; m2++) emit(beta, m2, x[m2], y[m2]);
             }
         }
     }
