@@ -292,6 +292,7 @@ int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t i
     fa.r = p->r;
     fa.i8 = p->in_dtype == CDMT_IN_I8;
     fa.scale = p->scale_dev;
+    fa.status = p->d_status;
     CK(p, fp32_forward(fa, st));
     return CDMT_OK;
 }

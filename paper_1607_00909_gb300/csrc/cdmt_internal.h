@@ -20,6 +20,7 @@ struct ForwardArgs {
     int64_t nseg = 0;                // batches: segments of the whole input
     bool i8 = false;                 // int8 samples (X re, X im, Y re, Y im) ...
     const float *scale = nullptr;    // ... times a DEVICE per-subband scale
+    int *status = nullptr;           // set to 1 by a CTA whose input copy (TMA) did not complete in time
 };
 
 struct DedispArgs {

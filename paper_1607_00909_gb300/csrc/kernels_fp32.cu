@@ -30,22 +30,38 @@
 // phase a + d b exactly modulo 2^32.  Lists that are not evenly spaced use the
 // FP64 product DM K per bin and DM instead.
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "cdmt_internal.h"
 #include "fft_core.cuh"
+#include "tc_ptx.cuh"
 
 namespace cdmt {
 
 constexpr float kTwoPiOver2p32 = 1.46291807926715968e-9f;  // 2 pi / 2^32
 
+constexpr uint64_t kTmaWaitNs = 50ull * 1000 * 1000;   // a CTA's input copy takes microseconds
+constexpr uint32_t kTmaWaitPolls = 1u << 26;
+
 // ---------------------------------------------------------------------------
 // I8: char4 samples (X re, X im, Y re, Y im) times the subband's scale, in FP32.
-template <int R, bool I8>
+// TMA (float4 samples): the decimated series x[n1 + nchan n2], n2 < M, comes into
+// the exchange buffer by TMA instead of per-thread loads: the input is a 3-D
+// tensor map of rows of nchan samples ([subband][row][nchan x 4 floats]), and
+// each of M / 256 boxes takes one 16-byte sample (column n1) of 256 rows, so one
+// thread issues the whole gather and the threads read their points from shared
+// memory.  A wait that gives up (never expected) sets *status.
+template <int R, bool I8, bool TMA = false>
 __global__ void __launch_bounds__(16 * R)
-k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale, float4 *__restrict__ spec,
-                    const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n,
-                    int64_t nsamp, int64_t nvalid, int nchan, int64_t k0, int kc, const int *__restrict__ round_dev,
-                    int64_t nseg)
+k_forward_decimated(const __grid_constant__ CUtensorMap tmap, const void *__restrict__ in,
+                    const float *__restrict__ scale, float4 *__restrict__ spec, const float2 *__restrict__ tw_a,
+                    const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n, int64_t nsamp, int64_t nvalid,
+                    int nchan, int64_t k0, int kc, const int *__restrict__ round_dev, int64_t nseg,
+                    int *__restrict__ status)
 {
     // batches: the chunk's first segment is round * kc, read from device memory;
     // segments past the end of the input are skipped
@@ -53,7 +69,7 @@ k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale
     if (k0 + (int64_t)blockIdx.y >= nseg) return;
     using F = Fft3<R>;
     constexpr int M = F::M, T = F::T;
-    extern __shared__ float4 smem[];
+    extern __shared__ __align__(128) float4 smem[];
     float4 *ex = smem;   // the exchange buffer; the pass twiddles are read through the cache
 
     const int t = threadIdx.x;
@@ -63,7 +79,30 @@ k_forward_decimated(const void *__restrict__ in, const float *__restrict__ scale
 
     const int64_t s0 = (int64_t)s * nsamp + (k0 + kk) * nvalid + n1;
     float2 x[16], y[16];
-    if constexpr (I8) {
+    if constexpr (TMA) {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + M);
+        if (t == 0) {
+            tc::mbar_init(bar, 1);
+            tc::fence_mbar_init();
+        }
+        __syncthreads();
+        if (t == 0) {
+            tc::mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float4) * M));
+            const int row0 = (int)(((k0 + kk) * nvalid) / nchan);   // segments start on whole rows
+            for (int b = 0; b < M / 256; b++) tc::tma_load_3d(ex + 256 * b, &tmap, 4 * n1, row0 + 256 * b, s, bar);
+        }
+        if (!tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls)) {
+            if (status) atomicExch(status, 1);
+            (void)tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls);   // a late copy lands before the CTA leaves
+        }
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            const float4 v = ex[j2 * T + t];
+            x[j2] = make_float2(v.x, v.y);
+            y[j2] = make_float2(v.z, v.w);
+        }
+        __syncthreads();   // every thread holds its points before pass A writes the buffer
+    } else if constexpr (I8) {
         const char4 *src = static_cast<const char4 *>(in) + s0;
         const float sc = __ldg(scale + s);
         #pragma unroll
@@ -379,6 +418,7 @@ k_dedisperse_pol(const float4 *__restrict__ spec, const uint2 *__restrict__ nco,
 // launchers
 
 template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>::M; }
+template <int R> static size_t smem_forward_tma() { return sizeof(float4) * Fft3<R>::M + 16; }   // + mbarrier
 template <int R> static size_t smem_dedisp()
 {
     using F = Fft3<R>;
@@ -399,6 +439,9 @@ template <int R> static cudaError_t set_attrs()
     e = cudaFuncSetAttribute(k_forward_decimated<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_forward<R>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_forward_decimated<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_forward_tma<R>());
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
@@ -411,6 +454,9 @@ static cudaError_t set_attrs_8k()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_forward_decimated<kR8k, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_forward<kR8k>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_forward_decimated<kR8k, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_forward_tma<kR8k>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dedisperse_pol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_dedisp_pol());
@@ -444,16 +490,57 @@ size_t fp32_dedisp_smem(int r)
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up once per process)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The float4 input as the forward kernel's TMA sees it: [nsub][nsamp / nchan rows][nchan samples
+// x 4 floats], row pitch nchan samples, subband pitch nsamp samples; boxes of one sample of 256 rows.
+// Rows past nsamp / nchan are never read: a segment ends at or before sample nsamp of its subband.
+static bool input_tmap(CUtensorMap &tm, const ForwardArgs &a)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    if (!fn || reinterpret_cast<uintptr_t>(a.in) % 16 || a.nsamp / a.nchan < 1) return false;
+    cuuint64_t dims[3] = {4ull * (cuuint64_t)a.nchan, (cuuint64_t)(a.nsamp / a.nchan), (cuuint64_t)a.nsub};
+    cuuint64_t strides[2] = {16ull * (cuuint64_t)a.nchan, 16ull * (cuuint64_t)a.nsamp};
+    cuuint32_t box[3] = {4, 256, 1}, es[3] = {1, 1, 1};
+    return fn(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.in), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t st)
 {
     dim3 g(a.nchan, a.kc, a.nsub);
     const int64_t nseg = a.round_dev ? a.nseg : INT64_MAX;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
     if (a.i8)
         k_forward_decimated<R, true><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(
-            a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev, nseg);
+            tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
+            nseg, a.status);
+    else if (input_tmap(tm, a))
+        k_forward_decimated<R, false, true><<<g, Fft3<R>::T, smem_forward_tma<R>(), st>>>(
+            tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
+            nseg, a.status);
     else
         k_forward_decimated<R, false><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(
-            a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev, nseg);
+            tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
+            nseg, a.status);
 }
 
 template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t st)
