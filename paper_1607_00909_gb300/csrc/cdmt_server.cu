@@ -99,6 +99,9 @@ struct Beam {
     float *d_scale[2] = {nullptr, nullptr};
     cudaStream_t cp = nullptr;
     cudaEvent_t blk_ready[2] = {nullptr, nullptr}, blk_free[2] = {nullptr, nullptr};
+    // stage_free[x]: the last block that used staging buffer x has finished with it (complex64 blocks
+    // from host memory are copied straight into the staging buffer behind the tail)
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};
     int cb = 0;                 // block buffer of the next block
     int64_t fb_bytes = 0;       // float32 filterbank of one block (8-bit beams: of one DM range of a block)
     int nq = 1, qdm = 0;        // 8-bit beams: DM ranges per block and DMs per range
@@ -220,12 +223,24 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
     cudaPointerAttributes pa{};
     const bool on_device = cudaPointerGetAttributes(&pa, r.block) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
     cudaGetLastError();
-    // the block (and its int8 scales) into block buffer i on the copy stream, once the block that used
-    // the buffer before has been appended; the beam's stream waits for the copy
+    // Complex64 blocks from host memory go straight into the staging buffer; int8 blocks (and their
+    // scales) into block buffer i on the copy stream, once the block that used the buffer before has
+    // been appended, and k_append dequantises them behind the tail (it also appends blocks that are
+    // already in device memory); the beam's stream waits for the copy
     const int i = b.cb;
     b.cb ^= 1;
     const bool i8 = b.d.in_dtype == CDMT_IN_I8;
-    if (!on_device || i8) {
+    float4 *stage = b.stage[b.cur];
+    if (!on_device && !i8) {
+        // complex64 from host memory: one 2-D copy (rows of block_len samples) straight behind the tail
+        // of this block's staging buffer, once the block before last has finished with that buffer
+        if (cudaStreamWaitEvent(b.cp, b.stage_free[b.cur], 0) != cudaSuccess) return false;
+        if (cudaMemcpy2DAsync(stage + b.tail, (size_t)b.cap * 16, r.block, (size_t)b.d.block_len * 16,
+                              (size_t)b.d.block_len * 16, b.d.nsub, cudaMemcpyHostToDevice, b.cp) != cudaSuccess)
+            return false;
+        if (cudaEventRecord(b.blk_ready[i], b.cp) != cudaSuccess) return false;
+        if (cudaStreamWaitEvent(b.st, b.blk_ready[i], 0) != cudaSuccess) return false;
+    } else if (i8) {
         if (cudaStreamWaitEvent(b.cp, b.blk_free[i], 0) != cudaSuccess) return false;
         if (!on_device) {
             if (cudaMemcpyAsync(b.d_blk[i], r.block, bytes, cudaMemcpyHostToDevice, b.cp) != cudaSuccess) return false;
@@ -237,10 +252,11 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
         if (cudaEventRecord(b.blk_ready[i], b.cp) != cudaSuccess) return false;
         if (cudaStreamWaitEvent(b.st, b.blk_ready[i], 0) != cudaSuccess) return false;
     }
-    float4 *stage = b.stage[b.cur];
-    k_append<<<512, 256, 0, b.st>>>(stage, b.cap, b.tail, src, b.d_scale[i], b.d.block_len, b.d.nsub, i8);
-    if (cudaGetLastError() != cudaSuccess) return false;
-    if (cudaEventRecord(b.blk_free[i], b.st) != cudaSuccess) return false;
+    if (on_device || i8) {
+        k_append<<<512, 256, 0, b.st>>>(stage, b.cap, b.tail, src, b.d_scale[i], b.d.block_len, b.d.nsub, i8);
+        if (cudaGetLastError() != cudaSuccess) return false;
+        if (cudaEventRecord(b.blk_free[i], b.st) != cudaSuccess) return false;
+    }
     const int64_t avail = b.tail + b.d.block_len;
     int64_t nseg = avail >= b.N ? (avail - b.N) / b.S + 1 : 0;
     nseg = std::min(nseg, b.max_seg);
@@ -275,6 +291,7 @@ bool dispatch(cdmt_server_s *v, Beam &b, Req &r)
         cudaMemcpy2DAsync(b.stage[b.cur ^ 1], (size_t)b.cap * 16, stage + used, (size_t)b.cap * 16, (size_t)tail * 16,
                           b.d.nsub, cudaMemcpyDeviceToDevice, b.st) != cudaSuccess)
         return false;
+    if (cudaEventRecord(b.stage_free[b.cur], b.st) != cudaSuccess) return false;
     b.cur ^= 1;
     b.tail = tail;
     r.nseg = nseg;
@@ -365,6 +382,7 @@ void free_beam(Beam &b)
         if (b.d_scale[i]) cudaFree(b.d_scale[i]);
         if (b.blk_ready[i]) cudaEventDestroy(b.blk_ready[i]);
         if (b.blk_free[i]) cudaEventDestroy(b.blk_free[i]);
+        if (b.stage_free[i]) cudaEventDestroy(b.stage_free[i]);
     }
     if (b.cp) cudaStreamDestroy(b.cp);
     if (b.st) cudaStreamDestroy(b.st);
@@ -474,6 +492,7 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
         if (e == cudaSuccess) e = cudaMalloc((void **)&b.d_scale[i], sizeof(float) * d->nsub);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_ready[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_free[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.stage_free[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b.cp, cudaStreamNonBlocking);
     if (e == cudaSuccess && u8 && redig_reserve(b.plan) != CDMT_OK) e = cudaErrorMemoryAllocation;
