@@ -551,9 +551,11 @@ int cdmt_batch_destroy(cdmt_batch_t batch);
  * Streaming server: real-time blocks of several beams, continuously batched.
  *
  * Each beam added to a server keeps its plan, its overlap tail (the input
- * samples that do not yet complete an overlap-save segment, Sec. 2) and two
- * block buffers resident on the device (a block's copy to the device, on its
- * own stream, overlaps the compute of the block before).  Submitted blocks are
+ * samples that do not yet complete an overlap-save segment, Sec. 2) in two
+ * staging buffers, and for int8 blocks two block buffers, resident on the device
+ * (a block's copy to the device, on its own stream, overlaps the compute of the
+ * block before; complex64 blocks from host memory are copied straight behind
+ * the tail).  Submitted blocks are
  * queued; a
  * scheduler thread dispatches them in arrival order across beams whenever an
  * output slot is free (blocks of one beam stay in order on that beam's CUDA

@@ -459,7 +459,9 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     b.codes_bytes = ((int64_t)d->ndm * b.rows * b.max_seg * b.seglen + 15) / 16 * 16;
     b.stats_bytes = (int64_t)sizeof(float) * 2 * d->ndm * b.rows;
     b.out_bytes = u8 ? b.codes_bytes + b.stats_bytes + (int64_t)d->ndm * b.rows : b.fb_bytes;
-    b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + 2 * (int64_t)es * d->nsub * d->block_len +
+    // block buffers only for int8 blocks (complex64 blocks are copied straight into the staging buffer)
+    const int64_t blk_bytes = d->in_dtype == CDMT_IN_I8 ? (int64_t)es * d->nsub * d->block_len : 0;
+    b.bytes = inf.workspace_bytes + 2 * (int64_t)d->nsub * b.cap * 16 + 2 * blk_bytes +
               2 * (int64_t)sizeof(float) * d->nsub + (u8 ? (int64_t)sizeof(float) * 2 * d->ndm * b.rows : 0);
     // admission: resident state of every beam + the slots held + the slots one block of this beam
     // needs (an output slot; 8-bit beams also a float32 scratch slot) unless the pool has them
@@ -488,7 +490,7 @@ int cdmt_server_add_beam(cdmt_server_t v, const cdmt_stream_desc *d, int *beam_i
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaMalloc((void **)&b.stage[i], (size_t)d->nsub * b.cap * 16);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
-        e = cudaMalloc(&b.d_blk[i], es * (size_t)d->nsub * (size_t)d->block_len);
+        if (blk_bytes > 0) e = cudaMalloc(&b.d_blk[i], (size_t)blk_bytes);
         if (e == cudaSuccess) e = cudaMalloc((void **)&b.d_scale[i], sizeof(float) * d->nsub);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_ready[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.blk_free[i], cudaEventDisableTiming);

@@ -49,12 +49,13 @@ constexpr uint32_t kTmaWaitPolls = 1u << 26;
 
 // ---------------------------------------------------------------------------
 // I8: char4 samples (X re, X im, Y re, Y im) times the subband's scale, in FP32.
-// TMA (float4 samples): the decimated series x[n1 + nchan n2], n2 < M, comes into
-// the exchange buffer by TMA instead of per-thread loads: the input is a 3-D
-// tensor map of rows of nchan samples ([subband][row][nchan x 4 floats]), and
-// each of M / 256 boxes takes one 16-byte sample (column n1) of 256 rows, so one
-// thread issues the whole gather and the threads read their points from shared
-// memory.  A wait that gives up (never expected) sets *status.  With no loads in
+// TMA: the decimated series x[n1 + nchan n2], n2 < M, comes into the exchange
+// buffer by TMA instead of per-thread loads: the input is a 3-D tensor map of
+// rows of nchan samples ([subband][row][nchan samples]), and each of M / 256
+// boxes takes 16 bytes of 256 rows, so one thread issues the whole gather and the
+// threads read their points from shared memory.  Float samples: the box is the
+// sample of column n1.  int8 samples (4 bytes, nchan >= 4): the box is the four
+// samples of columns 4 (n1 / 4) .. + 3, of which the CTA keeps column n1.  A wait that gives up (never expected) sets *status.  With no loads in
 // flight in registers the M = 4096 form fits three CTAs per SM (80 registers,
 // a few bytes of spill): 3.12 against 3.48 ms per 64-subband step at two.
 template <int R, bool I8, bool TMA = false>
@@ -91,17 +92,30 @@ k_forward_decimated(const __grid_constant__ CUtensorMap tmap, const void *__rest
         if (t == 0) {
             tc::mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float4) * M));
             const int row0 = (int)(((k0 + kk) * nvalid) / nchan);   // segments start on whole rows
-            for (int b = 0; b < M / 256; b++) tc::tma_load_3d(ex + 256 * b, &tmap, 4 * n1, row0 + 256 * b, s, bar);
+            const int c0 = I8 ? 16 * (n1 / 4) : 4 * n1;                 // bytes of int8, floats of float4
+            for (int b = 0; b < M / 256; b++) tc::tma_load_3d(ex + 256 * b, &tmap, c0, row0 + 256 * b, s, bar);
         }
         if (!tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls)) {
             if (status) atomicExch(status, 1);
             (void)tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls);   // a late copy lands before the CTA leaves
         }
-        #pragma unroll
-        for (int j2 = 0; j2 < 16; j2++) {
-            const float4 v = ex[j2 * T + t];
-            x[j2] = make_float2(v.x, v.y);
-            y[j2] = make_float2(v.z, v.w);
+        if constexpr (I8) {
+            const float sc = __ldg(scale + s);
+            const char4 *q = reinterpret_cast<const char4 *>(ex) + (n1 & 3);
+            #pragma unroll
+            for (int j2 = 0; j2 < 16; j2++) {
+                // products rounded on their own, as in the per-thread loads below
+                const char4 v = q[4 * (j2 * T + t)];
+                x[j2] = make_float2(__fmul_rn((float)v.x, sc), __fmul_rn((float)v.y, sc));
+                y[j2] = make_float2(__fmul_rn((float)v.z, sc), __fmul_rn((float)v.w, sc));
+            }
+        } else {
+            #pragma unroll
+            for (int j2 = 0; j2 < 16; j2++) {
+                const float4 v = ex[j2 * T + t];
+                x[j2] = make_float2(v.x, v.y);
+                y[j2] = make_float2(v.z, v.w);
+            }
         }
         __syncthreads();   // every thread holds its points before pass A writes the buffer
     } else if constexpr (I8) {
@@ -444,6 +458,9 @@ template <int R> static cudaError_t set_attrs()
     e = cudaFuncSetAttribute(k_forward_decimated<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_forward_tma<R>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_forward_decimated<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_forward_tma<R>());
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
@@ -458,6 +475,9 @@ static cudaError_t set_attrs_8k()
                                  (int)smem_forward<kR8k>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_forward_decimated<kR8k, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_forward_tma<kR8k>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_forward_decimated<kR8k, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_forward_tma<kR8k>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dedisperse_pol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -510,19 +530,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
     return fn;
 }
 
-// The float4 input as the forward kernel's TMA sees it: [nsub][nsamp / nchan rows][nchan samples
-// x 4 floats], row pitch nchan samples, subband pitch nsamp samples; boxes of one sample of 256 rows.
-// Rows past nsamp / nchan are never read: a segment ends at or before sample nsamp of its subband.
+// The input as the forward kernel's TMA sees it: [nsub][nsamp / nchan rows][nchan samples], row
+// pitch nchan samples, subband pitch nsamp samples; boxes of 16 bytes of 256 rows (one float4
+// sample, or four int8 samples).  Rows past nsamp / nchan are never read: a segment ends at or
+// before sample nsamp of its subband.  int8 rows need nchan >= 4 (16-byte row pitch).
 static bool input_tmap(CUtensorMap &tm, const ForwardArgs &a)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    const uint64_t es_bytes = a.i8 ? 4 : 16;
     if (!fn || reinterpret_cast<uintptr_t>(a.in) % 16 || a.nsamp / a.nchan < 1) return false;
-    cuuint64_t dims[3] = {4ull * (cuuint64_t)a.nchan, (cuuint64_t)(a.nsamp / a.nchan), (cuuint64_t)a.nsub};
-    cuuint64_t strides[2] = {16ull * (cuuint64_t)a.nchan, 16ull * (cuuint64_t)a.nsamp};
-    cuuint32_t box[3] = {4, 256, 1}, es[3] = {1, 1, 1};
-    return fn(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.in), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (a.i8 && (a.nchan < 4 || (a.nsamp * 4) % 16)) return false;
+    cuuint64_t dims[3] = {a.i8 ? 4ull * (cuuint64_t)a.nchan : 4ull * (cuuint64_t)a.nchan,
+                          (cuuint64_t)(a.nsamp / a.nchan), (cuuint64_t)a.nsub};
+    cuuint64_t strides[2] = {es_bytes * (cuuint64_t)a.nchan, es_bytes * (cuuint64_t)a.nsamp};
+    cuuint32_t box[3] = {a.i8 ? 16u : 4u, 256, 1}, es[3] = {1, 1, 1};
+    return fn(&tm, a.i8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.in),
+              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t st)
@@ -531,11 +555,16 @@ template <int R> static void launch_forward(const ForwardArgs &a, cudaStream_t s
     const int64_t nseg = a.round_dev ? a.nseg : INT64_MAX;
     CUtensorMap tm;
     std::memset(&tm, 0, sizeof tm);
-    if (a.i8)
+    const bool tma = input_tmap(tm, a);
+    if (a.i8 && tma)
+        k_forward_decimated<R, true, true><<<g, Fft3<R>::T, smem_forward_tma<R>(), st>>>(
+            tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
+            nseg, a.status);
+    else if (a.i8)
         k_forward_decimated<R, true><<<g, Fft3<R>::T, smem_forward<R>(), st>>>(
             tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
             nseg, a.status);
-    else if (input_tmap(tm, a))
+    else if (tma)
         k_forward_decimated<R, false, true><<<g, Fft3<R>::T, smem_forward_tma<R>(), st>>>(
             tm, a.in, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nsamp, a.nvalid, a.nchan, a.k0, a.kc, a.round_dev,
             nseg, a.status);
