@@ -203,16 +203,16 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 543.9 MB read +
-    # 2068.0 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 544.8 MB read +
+    # 2069.0 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
-    "ca8ecf5fa754f2a2:fp16": 0.6141,
-    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 543.9 MB read + 2067.6 MB
+    "5d99fe1feac20d3b:fp16": 0.6146,
+    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 542.9 MB read + 2067.5 MB
     # written for 4.253e9 units (same capture command with the FP32 form)
-    "a06535e10a1edf95:fp32": 0.6140,
+    "640e95462c5f3a03:fp32": 0.6138,
     # the paper's setup at 2^20 samples, one launch of k_dedisperse_pol (FP32, 8 channels of 8192
-    # bins, nint 1): 239.1 MB read + 3241.6 MB written for 8.258e8 units
-    "a06535e10a1edf95:fp32:m8192": 4.2152,
+    # bins, nint 1): 239.0 MB read + 3241.4 MB written for 8.258e8 units
+    "640e95462c5f3a03:fp32:m8192": 4.2149,
 }
 
 try:
