@@ -232,7 +232,7 @@ void release(cdmt_plan_s *p)
     cudaDeviceSynchronize();
     // tw_bf / tw_bi point inside the tw_af / tw_ai allocations
     void *ptrs[] = {p->tw_n, p->tw_af, p->tw_ai, p->nco, p->ktab, p->d_dm, p->spec, p->tc_bmat, p->tc_twq,
-                    p->d_status, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab,
+                    p->d_status, p->fwd_sync, p->redig_mg, p->tc_bmat64 != p->tc_bmat ? p->tc_bmat64 : nullptr, p->inc_tab,
                     p->d_scale_buf, p->grp_in, p->grp_out, p->grp_u8};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -293,6 +293,9 @@ int enqueue_forward(cdmt_plan_s *p, const void *in, int64_t in_stride, int64_t i
     fa.i8 = p->in_dtype == CDMT_IN_I8;
     fa.scale = p->scale_dev;
     fa.status = p->d_status;
+    fa.sync = p->fwd_sync;
+    fa.sync_n = p->fwd_sync_n;
+    fa.nsm = p->nsm;
     CK(p, fp32_forward(fa, st));
     return CDMT_OK;
 }
@@ -687,6 +690,8 @@ int cdmt_plan_ex(cdmt_plan_t *plan, int nsub, int64_t nsamp, double f_centre_mhz
     else TRY(dalloc(p, &p->ktab, (size_t)nsub * nbin));
     TRY(dalloc(p, &p->spec, (size_t)p->seg_chunk * nsub * nbin));
     TRY(dalloc(p, &p->d_status, 1));
+    p->fwd_sync_n = 1 + (nsub * p->seg_chunk + 1) / 2;
+    TRY(dalloc(p, &p->fwd_sync, (size_t)p->fwd_sync_n));
     if (p->precision != CDMT_PREC_FP32) {
         const int P = (int)(p->mbin / 64), planes = p->precision == CDMT_PREC_BF16 ? 2 : 1;
         TRY(dalloc(p, &p->tc_bmat, (size_t)planes * P * P / 2));   // (2P)^2 halves per plane, 8 per uint4

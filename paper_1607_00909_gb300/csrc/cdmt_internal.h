@@ -21,6 +21,10 @@ struct ForwardArgs {
     bool i8 = false;                 // int8 samples (X re, X im, Y re, Y im) ...
     const float *scale = nullptr;    // ... times a DEVICE per-subband scale
     int *status = nullptr;           // set to 1 by a CTA whose input copy (TMA) did not complete in time
+    // the one-launch forward stage's work queue: 1 + ceil(nsub * kc / 2) words (none: two launches)
+    int *sync = nullptr;
+    int64_t sync_n = 0;
+    int nsm = 0;                     // SMs of the device
 };
 
 struct DedispArgs {

@@ -60,6 +60,8 @@ struct cdmt_plan_s {
     uint4 *tc_bmat64 = nullptr;   // F_64 (the same buffer when M = 4096)
     float2 *tc_twq = nullptr;
     int *d_status = nullptr;
+    int *fwd_sync = nullptr;      // the one-launch forward stage's work queue (1 + chunks words)
+    int64_t fwd_sync_n = 0;
     float2 *redig_mg = nullptr;   // redigitisation: (mean, levels / sigma) per (DM, channel)
     int32_t *inc_tab = nullptr;   // incoherent stage: shifts [ndm][nk][rows] of the last trial grid
     size_t inc_bytes = 0;

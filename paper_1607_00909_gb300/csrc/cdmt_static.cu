@@ -12,8 +12,9 @@
 // loads this part of the library and keeps until the process exits.
 //
 // The computation is the same as cdmt_plan + cdmt_execute in the FP32 form with
-// an evenly spaced DM list (the same kernels; only the location of the scratch
-// differs).
+// an evenly spaced DM list (the same arithmetic, bit for bit; the forward stage
+// runs as two launches, which need no work queue, and the scratch lives in a
+// different place).
 #include <cuda_runtime.h>
 
 #include <algorithm>

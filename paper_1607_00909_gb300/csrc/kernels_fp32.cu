@@ -11,6 +11,10 @@
 //     place with the halves of the spectrum swapped: unshifted channel c' lands
 //     in channel slot c = (c' + nchan/2) mod nchan, so that slot c holds bins of
 //     increasing frequency of channel c.
+//   k_forward_fused: both steps in one persistent launch (M = 4096, nchan <= 16),
+//     the column DFTs of a chunk of segments run soon after its transforms, so
+//     their intermediate spectra stay in L2; the two launches above serve the
+//     other sizes, the batch rounds and the allocation-free entry point.
 //
 // DM stage (Sec. 3: "complex multiplication with transfer function", "swap
 // halves per channel", "backward FFT", "transpose, unpad and detect"), fused in
@@ -33,6 +37,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -58,6 +63,63 @@ constexpr uint32_t kTmaWaitPolls = 1u << 26;
 // samples of columns 4 (n1 / 4) .. + 3, of which the CTA keeps column n1.  A wait that gives up (never expected) sets *status.  With no loads in
 // flight in registers the M = 4096 form fits three CTAs per SM (80 registers,
 // a few bytes of spill): 3.12 against 3.48 ms per 64-subband step at two.
+// This thread's 16 points of each polarisation of the decimated series staged in ex by TMA.
+template <int R, bool I8>
+__device__ __forceinline__ void fwd_read_staged(const float4 *ex, int n1, float sc, float2 *x, float2 *y, int t)
+{
+    constexpr int T = Fft3<R>::T;
+    if constexpr (I8) {
+        const char4 *q = reinterpret_cast<const char4 *>(ex) + (n1 & 3);
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            // products rounded on their own, as in the per-thread loads
+            const char4 v = q[4 * (j2 * T + t)];
+            x[j2] = make_float2(__fmul_rn((float)v.x, sc), __fmul_rn((float)v.y, sc));
+            y[j2] = make_float2(__fmul_rn((float)v.z, sc), __fmul_rn((float)v.w, sc));
+        }
+    } else {
+        #pragma unroll
+        for (int j2 = 0; j2 < 16; j2++) {
+            const float4 v = ex[j2 * T + t];
+            x[j2] = make_float2(v.x, v.y);
+            y[j2] = make_float2(v.z, v.w);
+        }
+    }
+}
+
+// One thread issues the TMA gather of the decimated series of phase n1 (rows row0 .. row0 + M - 1
+// of subband s) into ex, completing on bar.
+template <int R, bool I8>
+__device__ __forceinline__ void fwd_issue_gather(float4 *ex, uint64_t *bar, const CUtensorMap *tmap, int n1, int row0,
+                                                 int s)
+{
+    constexpr int M = Fft3<R>::M;
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float4) * M));
+    const int c0 = I8 ? 16 * (n1 / 4) : 4 * n1;   // bytes of int8, floats of float4
+    for (int b = 0; b < M / 256; b++) tc::tma_load_3d(ex + 256 * b, tmap, c0, row0 + 256 * b, s, bar);
+}
+
+// The M-point transform of a decimated series (x, y: this thread's points), times W_N^{n1 j},
+// stored at dst.  ex is free on entry.
+template <int R>
+__device__ __forceinline__ void fwd_transform_store(float2 *x, float2 *y, float4 *ex, const float2 *__restrict__ tw_a,
+                                                    const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n,
+                                                    int n1, float4 *__restrict__ dst, int t)
+{
+    using F = Fft3<R>;
+    F::template pass_a<-1>(x, y, ex, tw_a, t);
+    __syncthreads();
+    F::template pass_b<-1>(x, y, ex, tw_b, t);
+    __syncthreads();
+    // W_N^{n1 j} for j = beta + 256 m2 as W_N^{n1 beta} W_N^{256 n1 m2}: one scattered table read per
+    // beta (16 / R per thread) and warp-uniform ones for the second factor, instead of 16 scattered
+    // reads that each use 8 bytes of a 32-byte sector
+    F::template pass_c<-1>(ex, t, [&](int beta, int m2, float2 a, float2 b) {
+        const float2 w = cmul(__ldg(tw_n + n1 * beta), __ldg(tw_n + 256 * n1 * m2));
+        dst[beta + 256 * m2] = pack(cmul(a, w), cmul(b, w));
+    });
+}
+
 template <int R, bool I8, bool TMA = false>
 __global__ void __launch_bounds__(16 * R, (R == 16 && TMA) ? 3 : 1)   // TMA, M = 4096: 3 CTAs per SM
 k_forward_decimated(const __grid_constant__ CUtensorMap tmap, const void *__restrict__ in,
@@ -89,34 +151,13 @@ k_forward_decimated(const __grid_constant__ CUtensorMap tmap, const void *__rest
             tc::fence_mbar_init();
         }
         __syncthreads();
-        if (t == 0) {
-            tc::mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float4) * M));
-            const int row0 = (int)(((k0 + kk) * nvalid) / nchan);   // segments start on whole rows
-            const int c0 = I8 ? 16 * (n1 / 4) : 4 * n1;                 // bytes of int8, floats of float4
-            for (int b = 0; b < M / 256; b++) tc::tma_load_3d(ex + 256 * b, &tmap, c0, row0 + 256 * b, s, bar);
-        }
+        // segments start on whole rows
+        if (t == 0) fwd_issue_gather<R, I8>(ex, bar, &tmap, n1, (int)(((k0 + kk) * nvalid) / nchan), s);
         if (!tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls)) {
             if (status) atomicExch(status, 1);
             (void)tc::mbar_wait(bar, 0, kTmaWaitNs, kTmaWaitPolls);   // a late copy lands before the CTA leaves
         }
-        if constexpr (I8) {
-            const float sc = __ldg(scale + s);
-            const char4 *q = reinterpret_cast<const char4 *>(ex) + (n1 & 3);
-            #pragma unroll
-            for (int j2 = 0; j2 < 16; j2++) {
-                // products rounded on their own, as in the per-thread loads below
-                const char4 v = q[4 * (j2 * T + t)];
-                x[j2] = make_float2(__fmul_rn((float)v.x, sc), __fmul_rn((float)v.y, sc));
-                y[j2] = make_float2(__fmul_rn((float)v.z, sc), __fmul_rn((float)v.w, sc));
-            }
-        } else {
-            #pragma unroll
-            for (int j2 = 0; j2 < 16; j2++) {
-                const float4 v = ex[j2 * T + t];
-                x[j2] = make_float2(v.x, v.y);
-                y[j2] = make_float2(v.z, v.w);
-            }
-        }
+        fwd_read_staged<R, I8>(ex, n1, I8 ? __ldg(scale + s) : 1.f, x, y, t);
         __syncthreads();   // every thread holds its points before pass A writes the buffer
     } else if constexpr (I8) {
         const char4 *src = static_cast<const char4 *>(in) + s0;
@@ -138,32 +179,19 @@ k_forward_decimated(const __grid_constant__ CUtensorMap tmap, const void *__rest
             y[j2] = make_float2(v.z, v.w);
         }
     }
-    F::template pass_a<-1>(x, y, ex, tw_a, t);
-    __syncthreads();
-    F::template pass_b<-1>(x, y, ex, tw_b, t);
-    __syncthreads();
-    float4 *dst = spec + (((int64_t)s * kc + kk) * nchan + n1) * M;
-    // W_N^{n1 j} for j = beta + 256 m2 as W_N^{n1 beta} W_N^{256 n1 m2}: one scattered table read per
-    // beta (16 / R per thread) and warp-uniform ones for the second factor, instead of 16 scattered
-    // reads that each use 8 bytes of a 32-byte sector
-    F::template pass_c<-1>(ex, t, [&](int beta, int m2, float2 a, float2 b) {
-        const float2 w = cmul(__ldg(tw_n + n1 * beta), __ldg(tw_n + 256 * n1 * m2));
-        dst[beta + 256 * m2] = pack(cmul(a, w), cmul(b, w));
-    });
+    fwd_transform_store<R>(x, y, ex, tw_a, tw_b, tw_n, n1, spec + (((int64_t)s * kc + kk) * nchan + n1) * M, t);
 }
 
-// nchan-point DFT over n1 (stride M) for every bin j; in place.
-template <int NC>
-__global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ spec, const float2 *__restrict__ tw_n,
-                                                         int m, int64_t nbin)
+// The nchan-point DFT over n1 (stride m) of one bin j, col = &spec[segment][n1 = 0][j], in place,
+// with the halves swapped: unshifted channel c' goes to slot (c' + NC / 2) mod NC.  CG: the loads
+// go through L2 only (spectra that other CTAs of the same launch have just stored).
+template <int NC, bool CG = false>
+__device__ __forceinline__ void column_dft(float4 *col, const float2 *__restrict__ tw_n, int m, int64_t nbin)
 {
-    const int j = blockIdx.x * 256 + threadIdx.x;
-    if (j >= m) return;
-    float4 *col = spec + ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * nbin + j;
     float2 x[NC], y[NC];
     #pragma unroll
     for (int n1 = 0; n1 < NC; n1++) {
-        float4 v = col[(int64_t)n1 * m];
+        const float4 v = CG ? __ldcg(col + (int64_t)n1 * m) : col[(int64_t)n1 * m];
         x[n1] = make_float2(v.x, v.y);
         y[n1] = make_float2(v.z, v.w);
     }
@@ -192,6 +220,153 @@ __global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ sp
     for (int cp = 0; cp < NC; cp++) {
         const int c = (cp + NC / 2) % NC;
         col[(int64_t)c * m] = pack(x[cp], y[cp]);
+    }
+}
+
+// nchan-point DFT over n1 (stride M) for every bin j; in place.
+template <int NC>
+__global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ spec, const float2 *__restrict__ tw_n,
+                                                         int m, int64_t nbin)
+{
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    if (j >= m) return;
+    column_dft<NC>(spec + ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * nbin + j, tw_n, m, nbin);
+}
+
+// ---------------------------------------------------------------------------
+// The forward stage in one persistent launch (TMA gather, M = 4096, nchan <= 16).  CTAs take
+// work items from a queue whose tickets sync[0] hands out in order: D items are the decimated
+// transforms of k_forward_decimated (segment, n1), C items the column DFTs of k_forward_columns
+// (segment, block of 256 bins).  The segments, subband by subband, form chunks of kFwdChunk; the
+// queue puts the D items of chunk i + kFwdLag before the C items of chunk i, and a C item first
+// waits until all D items of its chunk have stored their spectra (sync[1 + i] counts them).  So
+// the transforms' output is read back from L2 shortly after it was written, and the stage moves
+// its input once from HBM and its output once to HBM, where the two launches move the spectra
+// through HBM three times.
+// Each CTA holds two tickets, the item it works on and the next one (fetched while it works), and
+// runs its items in ticket order.  A C item waits only on D items with smaller tickets, and D items
+// wait on nothing but their own copy, so every wait ends: of the waiting items take the one with
+// the smallest ticket.  Each D item it waits on has a smaller ticket, so it has been handed out
+// (tickets go out in order), and it is not the next item of a CTA whose current item waits (that
+// item's ticket would be smaller still): it is done, running, or next after an item that runs.
+// The waits are bounded all the same: one that gives up (never expected) sets *status and skips
+// its item.
+constexpr int kFwdChunk = 2;   // segments per chunk
+constexpr int kFwdLag = 16;    // chunks between a chunk's D items and its C items in the queue
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// bounded wait until *p >= need (one thread)
+__device__ __forceinline__ int wait_count(const int *p, int need)
+{
+    const uint64_t t0 = tc::globaltimer_ns();
+    for (uint32_t it = 0; it < kTmaWaitPolls; it++) {
+        if (ld_acquire_gpu(p) >= need) return 1;
+        if ((it & 15) == 15 && tc::globaltimer_ns() - t0 > kTmaWaitNs) return 0;
+        __nanosleep(64);
+    }
+    return 0;
+}
+
+template <int R, bool I8>
+__global__ void __launch_bounds__(16 * R, 3)
+k_forward_fused(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ scale, float4 *__restrict__ spec,
+                const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b, const float2 *__restrict__ tw_n,
+                int64_t nvalid, int nchan, int64_t k0, int kc, int nsub, int *__restrict__ sync,
+                int *__restrict__ status)
+{
+    constexpr int M = Fft3<R>::M;
+    extern __shared__ __align__(128) float4 smem[];
+    float4 *ex = smem;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + M);
+    int *shared_word = reinterpret_cast<int *>(bar + 1);   // [0] the CTA's ticket, [1] a C item's wait result
+    const int t = threadIdx.x;
+    const int nsegs = nsub * kc;
+    const int nchunk = (nsegs + kFwdChunk - 1) / kFwdChunk;
+    const int nd_items = kFwdChunk * nchan, nc_items = kFwdChunk * (M / 256);   // per chunk
+    const int lag = min(kFwdLag, nchunk);
+    const int64_t head = (int64_t)lag * nd_items;                              // D items of chunks 0 .. lag - 1
+    const int64_t mid = (int64_t)(nchunk - lag) * (nd_items + nc_items);     // D(k), then C(k - lag)
+    const int64_t total = (int64_t)nchunk * (nd_items + nc_items);
+    if (t == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    uint32_t nd_run = 0;   // D items this CTA has run: the parity of the mbarrier's phase
+    int next = t == 0 ? atomicAdd(sync, 1) : 0;   // thread 0 holds the ticket after the current one
+    for (;;) {
+        __syncthreads();   // the previous item is done with ex and the shared words
+        if (t == 0) {
+            shared_word[0] = next;
+            next = atomicAdd(sync, 1);   // in flight while the CTA works on this item
+        }
+        __syncthreads();
+        const int64_t tk = shared_word[0];
+        if (tk >= total) break;
+        bool is_d;
+        int chunk, idx;
+        if (tk < head) {
+            is_d = true;
+            chunk = (int)(tk / nd_items);
+            idx = (int)(tk % nd_items);
+        } else if (tk - head < mid) {
+            const int64_t u = tk - head;
+            const int k = lag + (int)(u / (nd_items + nc_items)), r = (int)(u % (nd_items + nc_items));
+            is_d = r < nd_items;
+            chunk = is_d ? k : k - lag;
+            idx = is_d ? r : r - nd_items;
+        } else {
+            const int64_t u = tk - head - mid;
+            is_d = false;
+            chunk = nchunk - lag + (int)(u / nc_items);
+            idx = (int)(u % nc_items);
+        }
+        if (is_d) {
+            const int g = chunk * kFwdChunk + idx / nchan, n1 = idx % nchan;
+            if (g < nsegs) {   // the last chunk's missing segment counts as done
+                const int s = g / kc, kk = g % kc;
+                if (t == 0) {
+                    tc::fence_async_smem();   // the previous item's accesses to ex before the copy into it
+                    fwd_issue_gather<R, I8>(ex, bar, &tmap, n1, (int)(((k0 + kk) * nvalid) / nchan), s);
+                }
+                if (!tc::mbar_wait(bar, nd_run & 1, kTmaWaitNs, kTmaWaitPolls)) {
+                    if (status) atomicExch(status, 1);
+                    (void)tc::mbar_wait(bar, nd_run & 1, kTmaWaitNs, kTmaWaitPolls);
+                }
+                nd_run++;
+                float2 x[16], y[16];
+                fwd_read_staged<R, I8>(ex, n1, I8 ? __ldg(scale + s) : 1.f, x, y, t);
+                __syncthreads();   // every thread holds its points before pass A writes the buffer
+                fwd_transform_store<R>(x, y, ex, tw_a, tw_b, tw_n, n1, spec + ((int64_t)g * nchan + n1) * M, t);
+            }
+            __syncthreads();   // all of the item's stores precede its count
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(sync + 1 + chunk, 1);
+            }
+        } else {
+            const int g = chunk * kFwdChunk + idx / (M / 256), jb = idx % (M / 256);
+            if (g >= nsegs) continue;
+            if (t == 0) shared_word[1] = wait_count(sync + 1 + chunk, nd_items);
+            __syncthreads();
+            if (!shared_word[1]) {
+                if (t == 0 && status) atomicExch(status, 1);
+                continue;
+            }
+            float4 *col = spec + (int64_t)g * nchan * M + 256 * jb + t;
+            const int64_t nbin = (int64_t)nchan * M;
+            switch (nchan) {
+            case 2: column_dft<2, true>(col, tw_n, M, nbin); break;
+            case 4: column_dft<4, true>(col, tw_n, M, nbin); break;
+            case 8: column_dft<8, true>(col, tw_n, M, nbin); break;
+            default: column_dft<16, true>(col, tw_n, M, nbin); break;
+            }
+        }
     }
 }
 
@@ -435,6 +610,7 @@ k_dedisperse_pol(const float4 *__restrict__ spec, const uint2 *__restrict__ nco,
 
 template <int R> static size_t smem_forward() { return sizeof(float4) * Fft3<R>::M; }
 template <int R> static size_t smem_forward_tma() { return sizeof(float4) * Fft3<R>::M + 16; }   // + mbarrier
+template <int R> static size_t smem_forward_fused() { return sizeof(float4) * Fft3<R>::M + 16; }   // + mbarrier, 2 words
 template <int R> static size_t smem_dedisp()
 {
     using F = Fft3<R>;
@@ -461,6 +637,14 @@ template <int R> static cudaError_t set_attrs()
     e = cudaFuncSetAttribute(k_forward_decimated<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_forward_tma<R>());
     if (e != cudaSuccess) return e;
+    if constexpr (R == 16) {
+        e = cudaFuncSetAttribute(k_forward_fused<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_forward_fused<R>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_forward_fused<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_forward_fused<R>());
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
@@ -581,8 +765,47 @@ template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t 
     k_forward_columns<NC><<<g, 256, 0, st>>>(a.spec, a.tw_n, m, a.nbin);
 }
 
+// The one-launch forward stage where it applies (M = 4096, nchan 2..16, the TMA gather, a queue
+// buffer of 1 + chunks words, no batch rounds); cudaErrorNotSupported where it does not.  A
+// cooperative launch of at most the CTAs that fit on the device at once.
+static cudaError_t launch_forward_fused(const ForwardArgs &a, cudaStream_t st)
+{
+    if (!a.sync || a.r != 16 || a.round_dev || a.nchan < 2 || a.nchan > 16 || a.nsm < 1) return cudaErrorNotSupported;
+    const int64_t nsegs = (int64_t)a.nsub * a.kc;
+    const int64_t nchunk = (nsegs + kFwdChunk - 1) / kFwdChunk;
+    if (nsegs < 1 || 1 + nchunk > a.sync_n || nsegs * (a.nchan + 16) > INT32_MAX) return cudaErrorNotSupported;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    if (!input_tmap(tm, a)) return cudaErrorNotSupported;
+    const void *fn = a.i8 ? reinterpret_cast<const void *>(k_forward_fused<16, true>)
+                          : reinterpret_cast<const void *>(k_forward_fused<16, false>);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, Fft3<16>::T, smem_forward_fused<16>());
+    if (e != cudaSuccess || occ < 1) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    const int64_t total = nchunk * (int64_t)kFwdChunk * (a.nchan + 16);
+    const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)occ * a.nsm);
+    if ((e = cudaMemsetAsync(a.sync, 0, sizeof(int) * (size_t)(1 + nchunk), st)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(Fft3<16>::T);
+    cfg.dynamicSmemBytes = smem_forward_fused<16>();
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (a.i8)
+        return cudaLaunchKernelEx(&cfg, k_forward_fused<16, true>, tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n,
+                                  a.nvalid, a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
+    return cudaLaunchKernelEx(&cfg, k_forward_fused<16, false>, tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nvalid,
+                              a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
+}
+
 cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st)
 {
+    const cudaError_t ef = launch_forward_fused(a, st);
+    if (ef != cudaErrorNotSupported) return ef;
     switch (a.r) {
     case 2: launch_forward<2>(a, st); break;
     case 4: launch_forward<4>(a, st); break;
