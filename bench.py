@@ -203,16 +203,16 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 544.8 MB read +
-    # 2069.0 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 546.8 MB read +
+    # 2068.8 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
-    "5d99fe1feac20d3b:fp16": 0.6146,
-    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 542.9 MB read + 2067.5 MB
+    "78c9c93b50e440c0:fp16": 0.6150,
+    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 545.1 MB read + 2067.9 MB
     # written for 4.253e9 units (same capture command with the FP32 form)
-    "640e95462c5f3a03:fp32": 0.6138,
+    "1450598587c9369d:fp32": 0.6144,
     # the paper's setup at 2^20 samples, one launch of k_dedisperse_pol (FP32, 8 channels of 8192
-    # bins, nint 1): 239.0 MB read + 3241.4 MB written for 8.258e8 units
-    "640e95462c5f3a03:fp32:m8192": 4.2149,
+    # bins, nint 1): 238.9 MB read + 3241.5 MB written for 8.258e8 units
+    "1450598587c9369d:fp32:m8192": 4.2148,
 }
 
 try:
