@@ -273,7 +273,7 @@ def replica_value(units_per_rank: float, steps: int, ms_max: float, world: int) 
     return world * units_per_rank * steps / (ms_max / 1e3) / 1e9
 
 
-def sampled_error(w, x, out, info, ntile=8, seed=5):
+def sampled_error(w, x, out, info, ntile=32, seed=5):
     """max |gpu - oracle| / mean(oracle) and the RMS ratio on ntile random
     (subband, segment, DM) tiles of this run's output."""
     import oracle

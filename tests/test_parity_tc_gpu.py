@@ -170,7 +170,7 @@ def test_tc_lofar64_full_size_sampled_tiles(cdmt, orc):
     assert bool(torch.isfinite(out).all())
     del xt
     g = np.random.default_rng(77)
-    ntile = 24
+    ntile = 32
     sub = g.integers(0, w.nsub, ntile)
     seg = g.integers(0, i["nseg"], ntile)
     seg[:2] = [0, i["nseg"] - 1]
