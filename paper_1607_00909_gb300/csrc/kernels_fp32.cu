@@ -766,11 +766,17 @@ template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t 
 }
 
 // The one-launch forward stage where it applies (M = 4096, nchan 2..16, the TMA gather, a queue
-// buffer of 1 + chunks words, no batch rounds); cudaErrorNotSupported where it does not.  A
-// cooperative launch of at most the CTAs that fit on the device at once.
+// buffer of 1 + chunks words, no batch rounds, a stream that is not being captured into a graph);
+// cudaErrorNotSupported where it does not.  A cooperative launch of at most the CTAs that fit on
+// the device at once.
 static cudaError_t launch_forward_fused(const ForwardArgs &a, cudaStream_t st)
 {
     if (!a.sync || a.r != 16 || a.round_dev || a.nchan < 2 || a.nchan > 16 || a.nsm < 1) return cudaErrorNotSupported;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return cudaErrorNotSupported;
+    }
     const int64_t nsegs = (int64_t)a.nsub * a.kc;
     const int64_t nchunk = (nsegs + kFwdChunk - 1) / kFwdChunk;
     if (nsegs < 1 || 1 + nchunk > a.sync_n || nsegs * (a.nchan + 16) > INT32_MAX) return cudaErrorNotSupported;
