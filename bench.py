@@ -190,7 +190,8 @@ def reference_arm(args, w):
 
 def kernel_source_hash(form="fp16"):
     """Hash of the sources the form's DM-stage kernel is compiled from (the key of its traffic figure)."""
-    files = ("kernels_fp32.cu", "fft_core.cuh", "cdmt_internal.h") if form == "fp32" else \
+    files = ("kernels_fp32.cu", "kernels_fp32_pair.cu", "fft_core.cuh", "tc_ptx.cuh", "cdmt_internal.h") \
+        if form == "fp32" else \
         ("kernels_tc.cu", "fft_core.cuh", "tc_ptx.cuh", "cdmt_internal.h")
     h = hashlib.sha256()
     for f in files:
@@ -407,7 +408,7 @@ def dm_stage_roofline(form, r, props, sm_max):
     if form == "fp32":
         fpeak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
         fbasis = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
-        kernel, fbound = ("k_dedisperse_pol" if mbin == 8192 else "k_dedisperse"), "alu"
+        kernel, fbound = {8192: "k_dedisperse_pol", 4096: "k_dedisperse_pair"}.get(mbin, "k_dedisperse"), "alu"
     else:
         fpeak = MEASURED.get("bf16_tflops_sustained") or 1700.0
         fbasis = "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); the FP16 dense rate equals BF16"

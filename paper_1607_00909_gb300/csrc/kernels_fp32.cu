@@ -645,9 +645,15 @@ template <int R> static cudaError_t set_attrs()
                                  (int)smem_forward_fused<R>());
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dedisp<R>());
+    if constexpr (R == 16) {
+        return fp32_pair_prepare();   // the DM stage at M = 4096 is k_dedisperse_pair
+    } else {
+        e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_dedisp<R>());
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_dedisperse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_dedisp<R>());
+    }
 }
 
 static cudaError_t set_attrs_8k()
@@ -690,7 +696,7 @@ size_t fp32_dedisp_smem(int r)
     case 2: return smem_dedisp<2>();
     case 4: return smem_dedisp<4>();
     case 8: return smem_dedisp<8>();
-    case 16: return smem_dedisp<16>();
+    case 16: return fp32_pair_smem();
     case kR8k: return smem_dedisp_pol();
     default: return 0;
     }
@@ -865,8 +871,8 @@ cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)
     case 8: launch_dedisp<4, false>(a, st); break;
     case 16 + 1: launch_dedisp<8, true>(a, st); break;
     case 16: launch_dedisp<8, false>(a, st); break;
-    case 32 + 1: launch_dedisp<16, true>(a, st); break;
-    case 32: launch_dedisp<16, false>(a, st); break;
+    case 32 + 1:
+    case 32: return fp32_dedisperse_pair(a, st);   // M = 4096: both polarisations per thread
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
