@@ -74,11 +74,15 @@ struct P2 {
 __device__ __forceinline__ P2 padd(P2 a, P2 b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
 __device__ __forceinline__ P2 psub(P2 a, P2 b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
 
-// a * (c + S i s) for constants, rounded as mul_cs rounds: (re c - im s', re s' + im c), s' = S s
+// a * (c + S i s) for constants, rounded as mul_cs rounds: (re c - im s', re s' + im c), s' = S s.
+// Scalar multiplies take the constants as immediates; packed ones would need them as register pairs.
 template <int S> __device__ __forceinline__ P2 pmul_cs(P2 a, float c, float s)
 {
     const float ss = S > 0 ? s : -s;
-    return {fma2(a.re, pk2(c, c), mul2(a.im, pk2(-ss, -ss))), fma2(a.re, pk2(ss, ss), mul2(a.im, pk2(c, c)))};
+    float xr, yr, xi, yi;
+    up2(a.re, xr, yr);
+    up2(a.im, xi, yi);
+    return {pk2(fmaf(xr, c, -xi * ss), fmaf(yr, c, -yi * ss)), pk2(fmaf(xr, ss, xi * c), fmaf(yr, ss, yi * c))};
 }
 // a * (S i), exact
 template <int S> __device__ __forceinline__ P2 pmul_i(P2 a)
@@ -128,13 +132,12 @@ template <int S> __device__ __forceinline__ void pdft16(P2 *v)
     t = v[11]; v[11] = v[14]; v[14] = t;
 }
 
-// a * w for one twiddle w shared by both polarisations, rounded as cmul rounds
+// a * w for one twiddle w shared by both polarisations, rounded as cmul rounds:
+// (re wx + im (-wy), re wy + im wx) with the products of im rounded first
 __device__ __forceinline__ P2 ptwiddle(P2 a, float2 w)
 {
-    float xr, yr, xi, yi;
-    up2(a.re, xr, yr);
-    up2(a.im, xi, yi);
-    return {pk2(fmaf(xr, w.x, -xi * w.y), fmaf(yr, w.x, -yi * w.y)), pk2(fmaf(xr, w.y, xi * w.x), fmaf(yr, w.y, yi * w.x))};
+    const u64 WX = pk2(w.x, w.x), WY = pk2(w.y, w.y), NWY = pk2(-w.y, -w.y);
+    return {fma2(a.re, WX, mul2(a.im, NWY)), fma2(a.re, WY, mul2(a.im, WX))};
 }
 
 __device__ __forceinline__ void st_pair(float4 *p, P2 a)
