@@ -408,7 +408,7 @@ def dm_stage_roofline(form, r, props, sm_max):
     if form == "fp32":
         fpeak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
         fbasis = f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
-        kernel, fbound = {8192: "k_dedisperse_pol", 4096: "k_dedisperse_pair"}.get(mbin, "k_dedisperse"), "alu"
+        kernel, fbound = ("k_dedisperse_pair" if mbin >= 4096 else "k_dedisperse"), "alu"
     else:
         fpeak = MEASURED.get("bf16_tflops_sustained") or 1700.0
         fbasis = "measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json); the FP16 dense rate equals BF16"

@@ -97,10 +97,10 @@ cudaError_t enqueue_nco_table(uint2 *nco, const double *d_tile0, double dm0, dou
 int64_t overlap_for(int nsub, double f_centre, double bw, double dm_abs_max, int nchan, int nint, int64_t nbin);
 
 cudaError_t fp32_prepare(int r);
-// the DM stage at M = 4096 (r = 16): both polarisations per thread in packed f32x2 arithmetic,
-// the channel's spectrum and phase words in tensor memory (kernels_fp32_pair.cu)
-cudaError_t fp32_pair_prepare();
-size_t fp32_pair_smem();
+// the DM stage at M = 4096 and 8192 (r = 16, 32): both polarisations per thread in packed f32x2
+// arithmetic, the channel's spectrum and phase words in tensor memory (kernels_fp32_pair.cu)
+cudaError_t fp32_pair_prepare(int r);
+size_t fp32_pair_smem(int r);
 cudaError_t fp32_dedisperse_pair(const DedispArgs &a, cudaStream_t st);
 size_t fp32_dedisp_smem(int r);
 cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st);

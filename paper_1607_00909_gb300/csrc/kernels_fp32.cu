@@ -18,14 +18,15 @@
 //
 // DM stage (Sec. 3: "complex multiplication with transfer function", "swap
 // halves per channel", "backward FFT", "transpose, unpad and detect"), fused in
-// k_dedisperse: one CTA per (DM tile, subband, segment, channel) keeps the
-// channel's M spectral bins of both polarisations in registers (one
-// polarisation per half of the CTA) and, for each DM of its tile, multiplies
-// them by the chirp, runs the M-point backward FFT, forms |X|^2 + |Y|^2, drops
-// nd/2 samples at each edge, sums nint samples and stores the filterbank row
-// segment.  The per-channel swap of halves is a
-// factor (-1)^m on the time series, which the detection removes, so it is not
-// performed.  Spectra never leave the chip between chirp and detection.
+// k_dedisperse (M = 512 .. 2048; M = 4096 and 8192 run k_dedisperse_pair of
+// kernels_fp32_pair.cu, the same steps with both polarisations per thread): one
+// CTA per (DM tile, subband, segment, channel) keeps the channel's M spectral
+// bins of both polarisations in registers (one polarisation per half of the CTA)
+// and, for each DM of its tile, multiplies them by the chirp, runs the M-point
+// backward FFT, forms |X|^2 + |Y|^2, drops nd/2 samples at each edge, sums nint
+// samples and stores the filterbank row segment.  The per-channel swap of halves
+// is a factor (-1)^m on the time series, which the detection removes, so it is
+// not performed.  Spectra never leave the chip between chirp and detection.
 //
 // Chirp (Eq. 1, conjugated for dedispersion): bin j of channel c has
 // exp(-2 pi i DM K), K = 1e6 D nu^2 / (nu_c^2 (nu_c + nu)).  The planner stores,
@@ -33,7 +34,6 @@
 // b = -dDM K (in cycles, computed in FP64); DM number d of the tile then has
 // phase a + d b exactly modulo 2^32.  Lists that are not evenly spaced use the
 // FP64 product DM K per bin and DM instead.
-#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -485,125 +485,8 @@ k_dedisperse(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, con
     }
 }
 
-// ---------------------------------------------------------------------------
-// M = 8192 (R = 32): the same steps with one polarisation per CTA, so that each
-// of its 512 threads keeps 16 bins in registers (two polarisations would need
-// 1024 threads and more registers than an SM gives them).  The two CTAs of an
-// item form a cluster: each integrates its own polarisation's powers, and after
-// a cluster barrier each adds the pair's sums (X first, then Y) for half of the
-// item's output samples, reading the other CTA's sums from its shared memory.
-// Shared memory: one exchange buffer (reused for the integrated sums), the phase
-// words, the twiddles and one detected-power row.
+// M = 8192: R = 32 (k_forward_decimated; the DM stage is k_dedisperse_pair)
 constexpr int kR8k = 32;
-template <bool UNIFORM>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(16 * kR8k, 1)
-k_dedisperse_pol(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
-                 const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
-                 float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
-                 int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg, int dm_off,
-                 int dm_cnt, int64_t tlim)
-{
-    namespace cg = cooperative_groups;
-    using F = Fft3<kR8k>;
-    constexpr int M = F::M, T = F::T;
-    extern __shared__ float4 smem[];
-    float2 *ex = reinterpret_cast<float2 *>(smem);   // [M] exchange buffer, then the integrated sums
-    uint2 *ph = reinterpret_cast<uint2 *>(ex + M);    // M phase words (a, b) or K as double
-    float2 *ta = reinterpret_cast<float2 *>(ph + M);
-    float2 *tb = ta + F::NTA;
-    float *ib = reinterpret_cast<float *>(tb + F::NTB);   // [M] detected powers
-    float *sums = reinterpret_cast<float *>(ex);
-    cg::cluster_group cluster = cg::this_cluster();
-
-    const int t = threadIdx.x;
-    const int pol = (int)cluster.block_rank();   // 0: X, 1: Y (the grid's x extent is twice the items)
-    int64_t item = blockIdx.x >> 1;
-    const int c = (int)(item % nchan); item /= nchan;
-    const int kk = (int)(item % kc); item /= kc;
-    const int s = (int)(item % nsub); item /= nsub;
-    const int tile = (int)item;
-    const int dm0 = tile * dm_tile + dm_off;
-    const int ndt = min(dm_cnt, ndm - dm0);
-    // the early returns depend on the item only, so both CTAs of the cluster take them
-    if (ndt <= 0) return;
-    if (round_dev && (int64_t)(*round_dev) * kc + kk >= nseg) return;
-    const int64_t room = tlim - (k0 + kk) * (int64_t)((M - nd) / nint);
-    const int ulim = room <= 0 ? 0 : (int)(room < (M - nd) / nint ? room : (M - nd) / nint);
-    if (ulim == 0) return;
-
-    const float4 *src = spec + (((int64_t)s * kc + kk) * nchan + c) * M;
-    float2 xr[16];
-    #pragma unroll
-    for (int j2 = 0; j2 < 16; j2++) {
-        float4 v = __ldg(src + j2 * T + t);
-        xr[j2] = pol ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-    }
-    if constexpr (UNIFORM) {
-        const uint2 *p = nco + ((int64_t)tile * nsub + s) * (int64_t)nchan * M + (int64_t)c * M;
-        for (int i = t; i < M; i += T) ph[i] = p[i];
-    } else {
-        const uint2 *p = reinterpret_cast<const uint2 *>(ktab + ((int64_t)s * nchan + c) * M);
-        for (int i = t; i < M; i += T) ph[i] = p[i];
-    }
-    for (int i = t; i < F::NTA; i += T) ta[i] = tw_a[i];
-    for (int i = t; i < F::NTB; i += T) tb[i] = tw_b[i];
-    __syncthreads();
-
-    const int half = nd / 2;
-    const int seglen = (M - nd) / nint;
-    const int64_t rows = (int64_t)nsub * nchan;
-    const int64_t obase = (int64_t)(s * nchan + c) * nout + (k0 + kk) * seglen;
-    const bool pow2 = (nint & (nint - 1)) == 0 && nint <= 32;
-    const int rot = pow2 ? (((t & 31) * nint) >> 5) : 0;
-    const float *other = cluster.map_shared_rank(sums, pol ^ 1);
-    const int uhalf = (ulim + 1) / 2;
-
-    for (int d = 0; d < ndt; d++) {
-        float2 x[16];
-        double dmv = 0.0;
-        if constexpr (!UNIFORM) dmv = dm_list[dm0 + d];
-        #pragma unroll
-        for (int j2 = 0; j2 < 16; j2++) {
-            const int j = j2 * T + t;
-            float sn, cs;
-            if constexpr (UNIFORM) {
-                uint2 ab = ph[j];
-                int32_t p = (int32_t)(ab.x + (uint32_t)(dm_off + d) * ab.y);
-                __sincosf((float)p * kTwoPiOver2p32, &sn, &cs);
-            } else {
-                double kj = __hiloint2double((int)ph[j].y, (int)ph[j].x);
-                double cyc = dmv * kj;
-                cyc -= rint(cyc);
-                __sincosf(-6.283185307179586f * (float)cyc, &sn, &cs);
-            }
-            x[j2] = make_float2(xr[j2].x * cs - xr[j2].y * sn, xr[j2].x * sn + xr[j2].y * cs);
-        }
-        F::template pass_a1<+1>(x, ex, ta, t);
-        __syncthreads();
-        F::template pass_b1<+1>(x, ex, tb, t);
-        __syncthreads();
-        F::template pass_c1<+1>(ex, t, [&](int m, float2 a) { ib[m] = fmaf(a.x, a.x, a.y * a.y); });
-        __syncthreads();
-        for (int u = t; u < ulim; u += T) {   // this polarisation's nint-sample sums
-            const float *pp = ib + half + u * nint;
-            float acc = 0.f;
-            if (pow2) {
-                for (int q = 0; q < nint; q++) acc += pp[(q + rot) & (nint - 1)];
-            } else {
-                for (int q = 0; q < nint; q++) acc += pp[q];
-            }
-            sums[u] = acc;
-        }
-        cluster.sync();   // both polarisations' sums are ready
-        float *orow = out + ((int64_t)tile * dm_cnt + d) * rows * nout + obase;
-        const int u0 = pol * uhalf, u1 = min(ulim, u0 + uhalf);
-        for (int u = u0 + t; u < u1; u += T) {
-            const float mine = sums[u], theirs = other[u];
-            orow[u] = (pol ? theirs + mine : mine + theirs) * scale;
-        }
-        cluster.sync();   // the other CTA has read these sums before the next DM overwrites them
-    }
-}
 
 // ---------------------------------------------------------------------------
 // launchers
@@ -617,11 +500,6 @@ template <int R> static size_t smem_dedisp()
     return sizeof(float2) * 2 * F::M + sizeof(uint2) * F::M + sizeof(float2) * (F::NTA + F::NTB) + sizeof(float) * 2 * F::M;
 }
 
-static size_t smem_dedisp_pol()
-{
-    using F = Fft3<kR8k>;
-    return sizeof(float2) * F::M + sizeof(uint2) * F::M + sizeof(float2) * (F::NTA + F::NTB) + sizeof(float) * F::M;
-}
 
 template <int R> static cudaError_t set_attrs()
 {
@@ -646,7 +524,7 @@ template <int R> static cudaError_t set_attrs()
         if (e != cudaSuccess) return e;
     }
     if constexpr (R == 16) {
-        return fp32_pair_prepare();   // the DM stage at M = 4096 is k_dedisperse_pair
+        return fp32_pair_prepare(16);   // the DM stage at M = 4096 is k_dedisperse_pair
     } else {
         e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_dedisp<R>());
@@ -669,12 +547,7 @@ static cudaError_t set_attrs_8k()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_forward_decimated<kR8k, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_forward_tma<kR8k>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dedisperse_pol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_dedisp_pol());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dedisperse_pol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_dedisp_pol());
+    if (e == cudaSuccess) e = fp32_pair_prepare(kR8k);
     return e;
 }
 
@@ -696,8 +569,8 @@ size_t fp32_dedisp_smem(int r)
     case 2: return smem_dedisp<2>();
     case 4: return smem_dedisp<4>();
     case 8: return smem_dedisp<8>();
-    case 16: return fp32_pair_smem();
-    case kR8k: return smem_dedisp_pol();
+    case 16: return fp32_pair_smem(16);
+    case kR8k: return fp32_pair_smem(kR8k);
     default: return 0;
     }
 }
@@ -848,22 +721,9 @@ template <int R, bool U> static void launch_dedisp(const DedispArgs &a, cudaStre
         a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile, a.tlim);
 }
 
-template <bool U> static void launch_dedisp_pol(const DedispArgs &a, cudaStream_t st)
-{
-    const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
-    const int64_t nblk = 2 * ntile * a.nsub * a.kc * a.nchan;   // a cluster of two CTAs per item
-    k_dedisperse_pol<U><<<(unsigned)nblk, Fft3<kR8k>::T, smem_dedisp_pol(), st>>>(
-        a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
-        a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile, a.tlim);
-}
-
 cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)
 {
-    if (a.r == kR8k) {
-        if (a.uniform) launch_dedisp_pol<true>(a, st);
-        else launch_dedisp_pol<false>(a, st);
-        return cudaGetLastError();
-    }
+    if (a.r == kR8k) return fp32_dedisperse_pair(a, st);
     switch (a.r * 2 + (a.uniform ? 1 : 0)) {
     case 4 + 1: launch_dedisp<2, true>(a, st); break;
     case 4: launch_dedisp<2, false>(a, st); break;

@@ -1,5 +1,6 @@
-// FP32 form of the DM stage for channels of M = 4096 bins, with both polarisations
-// in every thread and their arithmetic paired in packed f32x2 instructions.
+// FP32 form of the DM stage for channels of M = 4096 and 8192 bins, with both
+// polarisations in every thread and their arithmetic paired in packed f32x2
+// instructions.
 //
 // The steps are those of k_dedisperse (Sec. 3: "complex multiplication with
 // transfer function", "backward FFT", "transpose, unpad and detect"; Eq. 1 for the
@@ -7,18 +8,23 @@
 // chirp the channel's M bins, run the M-point backward FFT in three radix-16 passes,
 // form |X|^2 + |Y|^2, drop nd/2 samples at each edge, integrate nint samples and
 // store.  What differs is the mapping onto the machine:
-// - Each of the CTA's 256 threads carries 16 bins of BOTH polarisations.  The two
+// - Each of the CTA's T = M / 16 threads (256, or 512 at M = 8192) carries 16 bins of
+//   BOTH polarisations.  The two
 //   polarisations go through exactly the same operations with the same twiddles, so
 //   the radix-16 butterflies run on pairs (X re, Y re) and (X im, Y im) in packed
 //   add/sub/mul/fma.rn.f32x2 instructions: one instruction does the work of two.  The
 //   f32x2 instructions round each lane as the scalar ones do, so every lane computes
 //   what the one-polarisation kernel computes, in the same order.
-// - The channel's spectrum (64 KB) and its chirp-phase words (32 KB) live in tensor
-//   memory, 192 of the CTA's 256 columns: thread t holds its bins j = j2 * 256 + t in
-//   TMEM lane t mod 128, columns 64 (t / 128) + 4 j2 + (X re, Y re, X im, Y im) and
-//   128 + 32 (t / 128) + 2 j2 + (phase word pair).  Shared memory keeps the exchange
-//   buffer, the pass twiddles and one detected-power row (112 KB), so two CTAs share
-//   an SM, as two 256-thread halves of the one-polarisation kernel's CTA did.
+// - The channel's spectrum (16 M bytes) and its chirp-phase words (8 M bytes) live in
+//   tensor memory: thread t holds its bins j = j2 T + t in TMEM lane t mod 128, columns
+//   64 (t / 128) + 4 j2 + (X re, Y re, X im, Y im) and 64 T / 128 + 32 (t / 128) + 2 j2 +
+//   (phase word pair); 192 of 256 columns at M = 4096, 384 of 512 at M = 8192.  Shared
+//   memory keeps the exchange buffer, the pass twiddles and one detected-power row
+//   (112 KB at M = 4096, so two CTAs share an SM; 224 KB at M = 8192, one CTA).
+// - M = 8192 (R = 32): the radix-32 butterflies of the last pass are shared by lane
+//   pairs as in fft_core.cuh (a 16-point DFT each, then one radix-2 step through lane
+//   shuffles), so one CTA carries both polarisations of a channel: no cluster and no
+//   exchange of sums between CTAs.
 // - The detected powers of both polarisations are summed per bin before they are
 //   stored, so integration reads one row.
 #include "cdmt_internal.h"
@@ -29,9 +35,16 @@ namespace cdmt {
 
 namespace {
 
-constexpr int kM = 4096, kT = 256, kR = 16;
 constexpr float kPhaseScale = 1.46291807926715968e-9f;   // 2 pi / 2^32
-constexpr uint32_t kTmemCols = 256;
+
+// M = 256 R bins per channel, T = 16 R threads; tensor memory: T / 128 column groups of 64
+// spectrum words, then as many groups of 32 phase words (192 columns of 256 at R = 16, 384 of
+// 512 at R = 32)
+template <int R> struct PairLayout {
+    static constexpr int M = 256 * R, T = 16 * R, NG = T / 128;
+    static constexpr uint32_t tmem_cols = R == 16 ? 256 : 512;
+    static constexpr int ctas_per_sm = R == 16 ? 2 : 1;
+};
 
 using u64 = uint64_t;
 
@@ -132,6 +145,20 @@ template <int S> __device__ __forceinline__ void pdft16(P2 *v)
     t = v[11]; v[11] = v[14]; v[14] = t;
 }
 
+// The radix-2 step of a radix-32 butterfly shared by lanes (2 beta, 2 beta + 1), as join32 of
+// fft_core.cuh does it, on pairs: v holds this lane's 16-point half (inputs j0 = 2a + e) and
+// leaves its outputs m2 = k + 16 e in v[k]
+template <int S> __device__ __forceinline__ void pjoin32(P2 *v, int e)
+{
+    #pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const P2 other = {__shfl_xor_sync(0xffffffffu, v[k].re, 1), __shfl_xor_sync(0xffffffffu, v[k].im, 1)};
+        const P2 ev = e ? other : v[k], od = e ? v[k] : other;
+        const P2 w = pmul_cs<S>(od, kW32[k][0], kW32[k][1]);   // W_32^k
+        v[k] = e ? psub(ev, w) : padd(ev, w);
+    }
+}
+
 // a * w for one twiddle w shared by both polarisations, rounded as cmul rounds:
 // (re wx + im (-wy), re wy + im wx) with the products of im rounded first
 __device__ __forceinline__ P2 ptwiddle(P2 a, float2 w)
@@ -155,16 +182,23 @@ __device__ __forceinline__ P2 ld_pair(const float4 *p)
 // Shared memory: exchange buffer [M] float4 (X re, Y re, X im, Y im), pass-A twiddles
 // W_M^{t m0} [15][T], pass-B twiddles W_M^{16 j0 m1} [15][R], detected powers [M], and the
 // TMEM base address.
-static size_t smem_pair() { return 16u * kM + 8u * 15u * (kT + kR) + 4u * kM + 16u; }
+template <int R> static size_t smem_pair()
+{
+    using L = PairLayout<R>;
+    return 16u * L::M + 8u * 15u * (L::T + R) + 4u * L::M + 16u;
+}
 
-template <bool UNIFORM>
-__global__ void __launch_bounds__(kT, 2)
+template <int R, bool UNIFORM>
+__global__ void __launch_bounds__(PairLayout<R>::T, PairLayout<R>::ctas_per_sm)
 k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco, const double *__restrict__ ktab,
                   const double *__restrict__ dm_list, const float2 *__restrict__ tw_a, const float2 *__restrict__ tw_b,
                   float *__restrict__ out, int nsub, int kc, int64_t k0, int nchan, int ndm, int dm_tile, int nd,
                   int nint, int64_t nout, float scale, const int *__restrict__ round_dev, int64_t nseg, int dm_off,
                   int dm_cnt, int64_t tlim)
 {
+    using L = PairLayout<R>;
+    constexpr int kM = L::M, kT = L::T, kR = R;
+    constexpr uint32_t kTmemCols = L::tmem_cols;
     extern __shared__ __align__(16) float4 smem[];
     float4 *ex = smem;
     float2 *ta = reinterpret_cast<float2 *>(ex + kM);
@@ -194,8 +228,8 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
     __syncthreads();
     tc::fence_after();
     const uint32_t lane = *tslot + ((uint32_t)(32 * (warp & 3)) << 16);
-    const uint32_t col_s = lane + 64u * (uint32_t)(t >> 7);         // spectrum words of this thread's bins
-    const uint32_t col_p = lane + 128u + 32u * (uint32_t)(t >> 7);  // phase words
+    const uint32_t col_s = lane + 64u * (uint32_t)(t >> 7);                   // spectrum words of this thread's bins
+    const uint32_t col_p = lane + 64u * L::NG + 32u * (uint32_t)(t >> 7);     // phase words
 
     // the thread's 16 bins j2 * T + t of both polarisations, and their phase words, into tensor memory
     {
@@ -281,15 +315,29 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
             for (int m1 = 0; m1 < 16; m1++) st_pair(ex + j0 * 256 + ((m0 + 16 * m1) ^ j0), x[m1]);
         }
         __syncthreads();
-        // ---- pass C: 16-point DFTs over j0 for beta = t; output m = t + 256 m2; detection
-        #pragma unroll
-        for (int j0 = 0; j0 < 16; j0++) x[j0] = ld_pair(ex + j0 * 256 + (t ^ j0));
-        pdft16<+1>(x);
-        #pragma unroll
-        for (int m2 = 0; m2 < 16; m2++) {
-            float px, py;
-            up2(fma2(x[m2].re, x[m2].re, mul2(x[m2].im, x[m2].im)), px, py);
-            pw[t + 256 * m2] = px + py;
+        // ---- pass C: radix-R butterflies over j0, output m = beta + 256 m2; detection
+        if constexpr (R == 16) {   // beta = t
+            #pragma unroll
+            for (int j0 = 0; j0 < 16; j0++) x[j0] = ld_pair(ex + j0 * 256 + (t ^ j0));
+            pdft16<+1>(x);
+            #pragma unroll
+            for (int m2 = 0; m2 < 16; m2++) {
+                float px, py;
+                up2(fma2(x[m2].re, x[m2].re, mul2(x[m2].im, x[m2].im)), px, py);
+                pw[t + 256 * m2] = px + py;
+            }
+        } else {   // R = 32: lanes 2 beta + e share beta's butterfly, inputs j0 = 2a + e
+            const int beta = t >> 1, e = t & 1;
+            #pragma unroll
+            for (int a = 0; a < 16; a++) x[a] = ld_pair(ex + (2 * a + e) * 256 + (beta ^ (2 * a + e)));
+            pdft16<+1>(x);
+            pjoin32<+1>(x, e);
+            #pragma unroll
+            for (int k = 0; k < 16; k++) {
+                float px, py;
+                up2(fma2(x[k].re, x[k].re, mul2(x[k].im, x[k].im)), px, py);
+                pw[beta + 256 * (k + 16 * e)] = px + py;
+            }
         }
         __syncthreads();
         float *orow = out + ((int64_t)tile * dm_cnt + d) * rows * nout + obase;
@@ -310,30 +358,42 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
     if (warp == 0) tc::tmem_free(*tslot, kTmemCols);
 }
 
-cudaError_t fp32_pair_prepare()
+template <int R> static cudaError_t prepare_pair()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_dedisperse_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_pair());
+    cudaError_t e = cudaFuncSetAttribute(k_dedisperse_pair<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_pair<R>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_dedisperse_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pair());
+    return cudaFuncSetAttribute(k_dedisperse_pair<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_pair<R>());
 }
 
-size_t fp32_pair_smem() { return smem_pair(); }
-
-cudaError_t fp32_dedisperse_pair(const DedispArgs &a, cudaStream_t st)
+cudaError_t fp32_pair_prepare(int r)
 {
-    if (a.r != kR) return cudaErrorInvalidValue;
+    return r == 16 ? prepare_pair<16>() : r == 32 ? prepare_pair<32>() : cudaErrorInvalidValue;
+}
+
+size_t fp32_pair_smem(int r) { return r == 16 ? smem_pair<16>() : r == 32 ? smem_pair<32>() : 0; }
+
+template <int R> static void launch_pair(const DedispArgs &a, cudaStream_t st)
+{
     const int64_t ntile = (a.ndm + a.dm_tile - 1) / a.dm_tile;
     const int64_t nblk = ntile * a.nsub * a.kc * a.nchan;
     const int cnt = a.dm_cnt > 0 ? a.dm_cnt : a.dm_tile;
     if (a.uniform)
-        k_dedisperse_pair<true><<<(unsigned)nblk, kT, smem_pair(), st>>>(
+        k_dedisperse_pair<R, true><<<(unsigned)nblk, PairLayout<R>::T, smem_pair<R>(), st>>>(
             a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
             a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, cnt, a.tlim);
     else
-        k_dedisperse_pair<false><<<(unsigned)nblk, kT, smem_pair(), st>>>(
+        k_dedisperse_pair<R, false><<<(unsigned)nblk, PairLayout<R>::T, smem_pair<R>(), st>>>(
             a.spec, a.nco, a.ktab, a.dm_list, a.tw_a, a.tw_b, a.out, a.nsub, a.kc, a.k0, a.nchan, a.ndm, a.dm_tile,
             a.nd, a.nint, a.nout, a.scale, a.round_dev, a.nseg, a.dm_off, cnt, a.tlim);
+}
+
+cudaError_t fp32_dedisperse_pair(const DedispArgs &a, cudaStream_t st)
+{
+    if (a.r == 16) launch_pair<16>(a, st);
+    else if (a.r == 32) launch_pair<32>(a, st);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -5,8 +5,8 @@ n_d = 2048, no averaging, 195.31-kHz subbands at the bottom of the 114.93 -
 
 Tolerance as in the other FP32 parity tests: max |gpu - oracle| / mean(oracle)
 <= 1e-5 and ||gpu - oracle|| / ||oracle|| <= 1e-5; an injected pulse keeps its
-S/N to 1 %.  At M = 8192 each CTA carries one polarisation and a cluster of two
-adds the polarisations, so every path through the DM stage is checked at this
+S/N to 1 %.  At M = 8192 the DM stage runs 512 threads per channel, the last
+radix-32 pass shared by lane pairs, so every path through it is checked at this
 size too: uneven DM lists (FP64 phase), int8 input, the host pipeline's DM
 ranges and the allocation-free entry point."""
 import ctypes
