@@ -208,12 +208,12 @@ NCU_TRAFFIC = {
     # 2068.8 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
     "78c9c93b50e440c0:fp16": 0.6150,
-    # 8-subband workload, one launch of k_dedisperse (FP32, 16 channels): 545.1 MB read + 2067.9 MB
-    # written for 4.253e9 units (same capture command with the FP32 form)
-    "1450598587c9369d:fp32": 0.6144,
-    # the paper's setup at 2^20 samples, one launch of k_dedisperse_pol (FP32, 8 channels of 8192
-    # bins, nint 1): 238.9 MB read + 3241.5 MB written for 8.258e8 units
-    "1450598587c9369d:fp32:m8192": 4.2148,
+    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 543.2 MB read +
+    # 2067.2 MB written for 4.253e9 units (same capture command with the FP32 form)
+    "205c289feff7d96a:fp32": 0.6138,
+    # the paper's setup at 2^20 samples, one launch of k_dedisperse_pair at M = 8192 (FP32, 8
+    # channels, nint 1): 234.6 MB read + 3242.4 MB written for 8.258e8 units
+    "205c289feff7d96a:fp32:m8192": 4.2106,
 }
 
 try:
