@@ -177,6 +177,18 @@ __device__ __forceinline__ P2 ld_pair(const float4 *p)
     return {v.x, v.y};
 }
 
+// Exchange-buffer swizzle of the second re-ordering (row j0, column beta ^ sw(j0)).  R = 32: the
+// low three bits of j0 rotated (bit 0 to bit 2), so that the lane pairs of pass C, which read rows
+// 2a and 2a + 1 at four neighbouring beta, meet eight different bank groups; the rows of one
+// quarter-warp's pass-B stores stay distinct.
+template <int R> __device__ __forceinline__ int sw_col(int j0)
+{
+    return R == 32 ? (j0 & 24) | ((j0 & 1) << 2) | ((j0 >> 1) & 3) : j0;
+}
+// Index of output m in the detected-power row.  R = 32: the upper half (m >= 4096) shifted by 16
+// words, so that the two lanes of a pass-C pair, whose outputs are 4096 apart, store to different banks.
+template <int R> __device__ __forceinline__ int pw_idx(int m) { return R == 32 ? m + ((m >> 12) << 4) : m; }
+
 }  // namespace
 
 // Shared memory: exchange buffer [M] float4 (X re, Y re, X im, Y im), pass-A twiddles
@@ -185,7 +197,7 @@ __device__ __forceinline__ P2 ld_pair(const float4 *p)
 template <int R> static size_t smem_pair()
 {
     using L = PairLayout<R>;
-    return 16u * L::M + 8u * 15u * (L::T + R) + 4u * L::M + 16u;
+    return 16u * L::M + 8u * 15u * (L::T + R) + 4u * (L::M + (R == 32 ? 16 : 0)) + 16u;
 }
 
 template <int R, bool UNIFORM>
@@ -204,7 +216,7 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
     float2 *ta = reinterpret_cast<float2 *>(ex + kM);
     float2 *tb = ta + 15 * kT;
     float *pw = reinterpret_cast<float *>(tb + 15 * kR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(pw + kM);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(pw + kM + (R == 32 ? 16 : 0));
 
     const int t = threadIdx.x, warp = t >> 5;
     int64_t item = blockIdx.x;
@@ -312,7 +324,7 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
             #pragma unroll
             for (int m1 = 1; m1 < 16; m1++) x[m1] = ptwiddle(x[m1], tb[(m1 - 1) * kR + j0]);
             #pragma unroll
-            for (int m1 = 0; m1 < 16; m1++) st_pair(ex + j0 * 256 + ((m0 + 16 * m1) ^ j0), x[m1]);
+            for (int m1 = 0; m1 < 16; m1++) st_pair(ex + j0 * 256 + ((m0 + 16 * m1) ^ sw_col<R>(j0)), x[m1]);
         }
         __syncthreads();
         // ---- pass C: radix-R butterflies over j0, output m = beta + 256 m2; detection
@@ -329,25 +341,25 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
         } else {   // R = 32: lanes 2 beta + e share beta's butterfly, inputs j0 = 2a + e
             const int beta = t >> 1, e = t & 1;
             #pragma unroll
-            for (int a = 0; a < 16; a++) x[a] = ld_pair(ex + (2 * a + e) * 256 + (beta ^ (2 * a + e)));
+            for (int a = 0; a < 16; a++) x[a] = ld_pair(ex + (2 * a + e) * 256 + (beta ^ sw_col<R>(2 * a + e)));
             pdft16<+1>(x);
             pjoin32<+1>(x, e);
             #pragma unroll
             for (int k = 0; k < 16; k++) {
                 float px, py;
                 up2(fma2(x[k].re, x[k].re, mul2(x[k].im, x[k].im)), px, py);
-                pw[beta + 256 * (k + 16 * e)] = px + py;
+                pw[pw_idx<R>(beta + 256 * (k + 16 * e))] = px + py;
             }
         }
         __syncthreads();
         float *orow = out + ((int64_t)tile * dm_cnt + d) * rows * nout + obase;
         for (int u = t; u < ulim; u += kT) {
-            const float *pp = pw + half + u * nint;
+            const int m = half + u * nint;
             float acc = 0.f;
             if (pow2) {
-                for (int q = 0; q < nint; q++) acc += pp[(q + rot) & (nint - 1)];
+                for (int q = 0; q < nint; q++) acc += pw[pw_idx<R>(m + ((q + rot) & (nint - 1)))];
             } else {
-                for (int q = 0; q < nint; q++) acc += pp[q];
+                for (int q = 0; q < nint; q++) acc += pw[pw_idx<R>(m + q)];
             }
             orow[u] = acc * scale;
         }
