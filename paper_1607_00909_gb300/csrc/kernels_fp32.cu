@@ -18,7 +18,7 @@
 //
 // DM stage (Sec. 3: "complex multiplication with transfer function", "swap
 // halves per channel", "backward FFT", "transpose, unpad and detect"), fused in
-// k_dedisperse (M = 512 .. 2048; M = 4096 and 8192 run k_dedisperse_pair of
+// k_dedisperse (M = 512, 1024; M = 2048 .. 8192 run k_dedisperse_pair of
 // kernels_fp32_pair.cu, the same steps with both polarisations per thread): one
 // CTA per (DM tile, subband, segment, channel) keeps the channel's M spectral
 // bins of both polarisations in registers (one polarisation per half of the CTA)
@@ -523,8 +523,8 @@ template <int R> static cudaError_t set_attrs()
                                  (int)smem_forward_fused<R>());
         if (e != cudaSuccess) return e;
     }
-    if constexpr (R == 16) {
-        return fp32_pair_prepare(16);   // the DM stage at M = 4096 is k_dedisperse_pair
+    if constexpr (R == 8 || R == 16) {
+        return fp32_pair_prepare(R);   // the DM stage at M = 2048 and 4096 is k_dedisperse_pair
     } else {
         e = cudaFuncSetAttribute(k_dedisperse<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_dedisp<R>());
@@ -568,7 +568,7 @@ size_t fp32_dedisp_smem(int r)
     switch (r) {
     case 2: return smem_dedisp<2>();
     case 4: return smem_dedisp<4>();
-    case 8: return smem_dedisp<8>();
+    case 8: return fp32_pair_smem(8);
     case 16: return fp32_pair_smem(16);
     case kR8k: return fp32_pair_smem(kR8k);
     default: return 0;
@@ -729,10 +729,10 @@ cudaError_t fp32_dedisperse(const DedispArgs &a, cudaStream_t st)
     case 4: launch_dedisp<2, false>(a, st); break;
     case 8 + 1: launch_dedisp<4, true>(a, st); break;
     case 8: launch_dedisp<4, false>(a, st); break;
-    case 16 + 1: launch_dedisp<8, true>(a, st); break;
-    case 16: launch_dedisp<8, false>(a, st); break;
+    case 16 + 1:
+    case 16:
     case 32 + 1:
-    case 32: return fp32_dedisperse_pair(a, st);   // M = 4096: both polarisations per thread
+    case 32: return fp32_dedisperse_pair(a, st);   // M = 2048, 4096: both polarisations per thread
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -1,4 +1,4 @@
-// FP32 form of the DM stage for channels of M = 4096 and 8192 bins, with both
+// FP32 form of the DM stage for channels of M = 2048, 4096 and 8192 bins, with both
 // polarisations in every thread and their arithmetic paired in packed f32x2
 // instructions.
 //
@@ -8,7 +8,7 @@
 // chirp the channel's M bins, run the M-point backward FFT in three radix-16 passes,
 // form |X|^2 + |Y|^2, drop nd/2 samples at each edge, integrate nint samples and
 // store.  What differs is the mapping onto the machine:
-// - Each of the CTA's T = M / 16 threads (256, or 512 at M = 8192) carries 16 bins of
+// - Each of the CTA's T = M / 16 threads (128, 256 or 512) carries 16 bins of
 //   BOTH polarisations.  The two
 //   polarisations go through exactly the same operations with the same twiddles, so
 //   the radix-16 butterflies run on pairs (X re, Y re) and (X im, Y im) in packed
@@ -18,9 +18,10 @@
 // - The channel's spectrum (16 M bytes) and its chirp-phase words (8 M bytes) live in
 //   tensor memory: thread t holds its bins j = j2 T + t in TMEM lane t mod 128, columns
 //   64 (t / 128) + 4 j2 + (X re, Y re, X im, Y im) and 64 T / 128 + 32 (t / 128) + 2 j2 +
-//   (phase word pair); 192 of 256 columns at M = 4096, 384 of 512 at M = 8192.  Shared
-//   memory keeps the exchange buffer, the pass twiddles and one detected-power row
-//   (112 KB at M = 4096, so two CTAs share an SM; 224 KB at M = 8192, one CTA).
+//   (phase word pair); 96 of 128 columns at M = 2048, 192 of 256 at 4096, 384 of 512 at
+//   8192.  Shared memory keeps the exchange buffer, the pass twiddles and one
+//   detected-power row: 56 KB at M = 2048 (four CTAs per SM), 112 KB at 4096 (two),
+//   224 KB at 8192 (one).
 // - M = 8192 (R = 32): the radix-32 butterflies of the last pass are shared by lane
 //   pairs as in fft_core.cuh (a 16-point DFT each, then one radix-2 step through lane
 //   shuffles), so one CTA carries both polarisations of a channel: no cluster and no
@@ -38,12 +39,12 @@ namespace {
 constexpr float kPhaseScale = 1.46291807926715968e-9f;   // 2 pi / 2^32
 
 // M = 256 R bins per channel, T = 16 R threads; tensor memory: T / 128 column groups of 64
-// spectrum words, then as many groups of 32 phase words (192 columns of 256 at R = 16, 384 of
-// 512 at R = 32)
+// spectrum words, then as many groups of 32 phase words (96 columns of 128 at R = 8, 192 of 256
+// at R = 16, 384 of 512 at R = 32)
 template <int R> struct PairLayout {
     static constexpr int M = 256 * R, T = 16 * R, NG = T / 128;
-    static constexpr uint32_t tmem_cols = R == 16 ? 256 : 512;
-    static constexpr int ctas_per_sm = R == 16 ? 2 : 1;
+    static constexpr uint32_t tmem_cols = R == 8 ? 128 : R == 16 ? 256 : 512;
+    static constexpr int ctas_per_sm = R == 8 ? 4 : R == 16 ? 2 : 1;
 };
 
 using u64 = uint64_t;
@@ -143,6 +144,22 @@ template <int S> __device__ __forceinline__ void pdft16(P2 *v)
     t = v[6]; v[6] = v[9]; v[9] = t;
     t = v[7]; v[7] = v[13]; v[13] = t;
     t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+// dft8 of fft_core.cuh on pairs (radix-2 decimation in time over two dft4)
+template <int S> __device__ __forceinline__ void pdft8(P2 *v)
+{
+    P2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    P2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    pdft4<S>(e0, e1, e2, e3);
+    pdft4<S>(o0, o1, o2, o3);
+    o1 = pmul_cs<S>(o1, kC8, kC8);    // W8^1
+    o2 = pmul_i<S>(o2);               // W8^2
+    o3 = pmul_cs<S>(o3, -kC8, kC8);   // W8^3
+    v[0] = padd(e0, o0); v[4] = psub(e0, o0);
+    v[1] = padd(e1, o1); v[5] = psub(e1, o1);
+    v[2] = padd(e2, o2); v[6] = psub(e2, o2);
+    v[3] = padd(e3, o3); v[7] = psub(e3, o3);
 }
 
 // The radix-2 step of a radix-32 butterfly shared by lanes (2 beta, 2 beta + 1), as join32 of
@@ -312,13 +329,13 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
         #pragma unroll
         for (int m0 = 1; m0 < 16; m0++) x[m0] = ptwiddle(x[m0], ta[(m0 - 1) * kT + t]);
         #pragma unroll
-        for (int m0 = 0; m0 < 16; m0++) st_pair(ex + m0 * kT + t, x[m0]);
+        for (int m0 = 0; m0 < 16; m0++) st_pair(ex + m0 * kT + (t ^ ((m0 * kR) & 15)), x[m0]);
         __syncthreads();
         // ---- pass B: thread (m0, j0), 16-point DFTs over j1, twiddles W_M^{16 j0 m1}
         {
             const int m0 = t / kR, j0 = t % kR;
             #pragma unroll
-            for (int j1 = 0; j1 < 16; j1++) x[j1] = ld_pair(ex + m0 * kT + j1 * kR + j0);
+            for (int j1 = 0; j1 < 16; j1++) x[j1] = ld_pair(ex + m0 * kT + ((j1 * kR + j0) ^ ((m0 * kR) & 15)));
             __syncthreads();
             pdft16<+1>(x);
             #pragma unroll
@@ -328,7 +345,22 @@ k_dedisperse_pair(const float4 *__restrict__ spec, const uint2 *__restrict__ nco
         }
         __syncthreads();
         // ---- pass C: radix-R butterflies over j0, output m = beta + 256 m2; detection
-        if constexpr (R == 16) {   // beta = t
+        if constexpr (R == 8) {   // beta = t, t + T; inputs j0 < 8
+            #pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int beta = t + kT * i;
+                P2 y[8];
+                #pragma unroll
+                for (int j0 = 0; j0 < 8; j0++) y[j0] = ld_pair(ex + j0 * 256 + (beta ^ j0));
+                pdft8<+1>(y);
+                #pragma unroll
+                for (int m2 = 0; m2 < 8; m2++) {
+                    float px, py;
+                    up2(fma2(y[m2].re, y[m2].re, mul2(y[m2].im, y[m2].im)), px, py);
+                    pw[beta + 256 * m2] = px + py;
+                }
+            }
+        } else if constexpr (R == 16) {   // beta = t
             #pragma unroll
             for (int j0 = 0; j0 < 16; j0++) x[j0] = ld_pair(ex + j0 * 256 + (t ^ j0));
             pdft16<+1>(x);
@@ -381,10 +413,14 @@ template <int R> static cudaError_t prepare_pair()
 
 cudaError_t fp32_pair_prepare(int r)
 {
-    return r == 16 ? prepare_pair<16>() : r == 32 ? prepare_pair<32>() : cudaErrorInvalidValue;
+    return r == 8 ? prepare_pair<8>() : r == 16 ? prepare_pair<16>() : r == 32 ? prepare_pair<32>()
+                                                                          : cudaErrorInvalidValue;
 }
 
-size_t fp32_pair_smem(int r) { return r == 16 ? smem_pair<16>() : r == 32 ? smem_pair<32>() : 0; }
+size_t fp32_pair_smem(int r)
+{
+    return r == 8 ? smem_pair<8>() : r == 16 ? smem_pair<16>() : r == 32 ? smem_pair<32>() : 0;
+}
 
 template <int R> static void launch_pair(const DedispArgs &a, cudaStream_t st)
 {
@@ -403,7 +439,8 @@ template <int R> static void launch_pair(const DedispArgs &a, cudaStream_t st)
 
 cudaError_t fp32_dedisperse_pair(const DedispArgs &a, cudaStream_t st)
 {
-    if (a.r == 16) launch_pair<16>(a, st);
+    if (a.r == 8) launch_pair<8>(a, st);
+    else if (a.r == 16) launch_pair<16>(a, st);
     else if (a.r == 32) launch_pair<32>(a, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
