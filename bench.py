@@ -204,16 +204,16 @@ def kernel_source_hash(form="fp16"):
 # dram__bytes_write.sum per launch / units per launch), valid for the sources of that form's kernel
 # whose hash is recorded (kernel_source_hash); null otherwise.
 NCU_TRAFFIC = {
-    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 546.8 MB read +
-    # 2068.8 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # 8-subband workload, one launch of k_dedisperse_tc (FP16, persistent, nint 8): 547.4 MB read +
+    # 2069.1 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
-    "78c9c93b50e440c0:fp16": 0.6150,
-    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 543.2 MB read +
-    # 2067.2 MB written for 4.253e9 units (same capture command with the FP32 form)
-    "205c289feff7d96a:fp32": 0.6138,
+    "d561d216c3f24e5d:fp16": 0.6152,
+    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 546.7 MB read +
+    # 2067.7 MB written for 4.253e9 units (same capture command with the FP32 form)
+    "c39ffd8e7205f266:fp32": 0.6147,
     # the paper's setup at 2^20 samples, one launch of k_dedisperse_pair at M = 8192 (FP32, 8
-    # channels, nint 1): 234.6 MB read + 3242.4 MB written for 8.258e8 units
-    "205c289feff7d96a:fp32:m8192": 4.2106,
+    # channels, nint 1): 232.5 MB read + 3241.8 MB written for 8.258e8 units
+    "c39ffd8e7205f266:fp32:m8192": 4.2074,
 }
 
 try:
