@@ -83,6 +83,20 @@ def test_uneven_dm_list_uses_fp64_products(cdmt, orc):
     assert emax <= TOL_MAX and erms <= TOL_RMS, (emax, erms)
 
 
+@pytest.mark.parametrize("mbin", [2048, 4096])
+def test_uneven_dm_list_paired_kernel(cdmt, orc, mbin):
+    """Uneven DM lists (the FP64 phase per bin and DM) at the sizes the FP32 form runs with both
+    polarisations per thread, several segments and a ragged tail."""
+    dms = [0.0, 3.7, -5.0, 12.1, 40.0, 39.99, 7.25]
+    nbin = 8 * mbin
+    nsamp = 3 * nbin + 1234
+    x = synth.noise(41, 2, nsamp)
+    plan = _plan(cdmt, 2, nsamp, 125.0, dms, 8, 4, nbin=nbin)
+    assert plan.info["uniform_dm"] == 0 and plan.info["mbin"] == mbin
+    g, o, (emax, erms) = _compare(orc, plan, x, 125.0, dms, 8, 4)
+    assert emax <= TOL_MAX and erms <= TOL_RMS, (emax, erms)
+
+
 def test_dm_zero_only_needs_no_overlap(cdmt, orc):
     x = synth.noise(5, 1, 1 << 14)
     plan = _plan(cdmt, 1, 1 << 14, 135.0, [0.0], 8, 4, nbin=1 << 12)
