@@ -5,16 +5,16 @@
 // The steps are those of k_dedisperse (Sec. 3: "complex multiplication with
 // transfer function", "backward FFT", "transpose, unpad and detect"; Eq. 1 for the
 // chirp): per (DM tile, subband, segment, channel) item, for every DM of the tile,
-// chirp the channel's M bins, run the M-point backward FFT in three radix-16 passes,
-// form |X|^2 + |Y|^2, drop nd/2 samples at each edge, integrate nint samples and
-// store.  What differs is the mapping onto the machine:
-// - Each of the CTA's T = M / 16 threads (128, 256 or 512) carries 16 bins of
-//   BOTH polarisations.  The two
-//   polarisations go through exactly the same operations with the same twiddles, so
-//   the radix-16 butterflies run on pairs (X re, Y re) and (X im, Y im) in packed
-//   add/sub/mul/fma.rn.f32x2 instructions: one instruction does the work of two.  The
-//   f32x2 instructions round each lane as the scalar ones do, so every lane computes
-//   what the one-polarisation kernel computes, in the same order.
+// chirp the channel's M bins, run the M-point backward FFT in three passes (radix 16,
+// 16 and R, M = 256 R), form |X|^2 + |Y|^2, drop nd/2 samples at each edge, integrate
+// nint samples and store.  What differs is the mapping onto the machine:
+// - Each of the CTA's T = M / 16 threads (128, 256 or 512) carries 16 bins of BOTH
+//   polarisations.  The two polarisations go through exactly the same operations with
+//   the same twiddles, so the butterflies run on pairs (X re, Y re) and (X im, Y im) in
+//   packed add/sub/mul/fma.rn.f32x2 instructions: one instruction does the work of two.
+//   The f32x2 instructions round each lane as the scalar ones do, and the butterflies
+//   and twiddle products take fft_core.cuh's operations in its order, so each lane's FFT
+//   rounds as the one-polarisation kernel's does.
 // - The channel's spectrum (16 M bytes) and its chirp-phase words (8 M bytes) live in
 //   tensor memory: thread t holds its bins j = j2 T + t in TMEM lane t mod 128, columns
 //   64 (t / 128) + 4 j2 + (X re, Y re, X im, Y im) and 64 T / 128 + 32 (t / 128) + 2 j2 +
