@@ -208,12 +208,12 @@ NCU_TRAFFIC = {
     # 2069.1 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
     "d561d216c3f24e5d:fp16": 0.6152,
-    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 546.7 MB read +
-    # 2067.7 MB written for 4.253e9 units (same capture command with the FP32 form)
-    "c39ffd8e7205f266:fp32": 0.6147,
+    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 542.6 MB read +
+    # 2067.2 MB written for 4.253e9 units (same capture command with the FP32 form)
+    "9138821633f26fff:fp32": 0.6136,
     # the paper's setup at 2^20 samples, one launch of k_dedisperse_pair at M = 8192 (FP32, 8
-    # channels, nint 1): 232.5 MB read + 3241.8 MB written for 8.258e8 units
-    "c39ffd8e7205f266:fp32:m8192": 4.2074,
+    # channels, nint 1): 232.4 MB read + 3241.3 MB written for 8.258e8 units
+    "9138821633f26fff:fp32:m8192": 4.2067,
 }
 
 try:
