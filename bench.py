@@ -442,6 +442,21 @@ def dm_stage_roofline(form, r, props, sm_max):
                                     "frac": ach / fpeak,
                                     "note": "dense real DFT GEMMs issued on the tensor cores (17x the nominal FFT "
                                             "flops at M = 4096): a utilisation of the tensor pipe, not the roofline"}
+        # the multi-pipe bound of the form as built: the slowest of its pipes at their peaks -- the
+        # issued GEMM flops (with the dense-DFT tax) on the tensor cores, the FP32 work around the
+        # GEMMs (per bin and DM, both polarisations: chirp 12, twiddle 12, detection 7 flops) on the
+        # FP32 lanes, and the algorithmic bytes on HBM; the chirp phase needs no FP64 per DM (the
+        # fixed-point words are computed in FP64 once per plan)
+        alu_unit = 31.0 * nbin / S
+        alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        legs = {"tensor": tc_unit * units_launch / (fpeak * 1e12) * 1e3,
+                "fp32_alu": alu_unit * units_launch / (alu_peak * 1e12) * 1e3,
+                "hbm": t_byte * 1e3}
+        slow = max(legs, key=legs.get)
+        rf["multi_pipe"] = {"bound": slow, "frac": legs[slow] / (t * 1e3), "legs_ms": legs,
+                            "fp32_flops_per_unit": alu_unit, "fp32_peak_tflops": alu_peak,
+                            "note": "the slowest pipe of the form as built at its peak over the kernel's time; "
+                                    "the nominal roofline above counts the method's FFT flops only"}
     return rf
 
 
