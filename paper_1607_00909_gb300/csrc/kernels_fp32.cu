@@ -249,8 +249,9 @@ __global__ void __launch_bounds__(256) k_forward_columns(float4 *__restrict__ sp
 // the smallest ticket.  Each D item it waits on has a smaller ticket, so it has been handed out
 // (tickets go out in order), and it is not the next item of a CTA whose current item waits (that
 // item's ticket would be smaller still): it is done, running, or next after an item that runs.
-// The waits are bounded all the same: one that gives up (never expected) sets *status and skips
-// its item.
+// This holds however many of the grid's CTAs are resident at a time, since only running CTAs take
+// tickets.  The waits are bounded all the same: one that gives up (never expected) sets *status
+// and skips its item.
 constexpr int kFwdChunk = 2;   // segments per chunk
 constexpr int kFwdLag = 16;    // chunks between a chunk's D items and its C items in the queue
 
@@ -646,8 +647,10 @@ template <int NC> static void launch_columns(const ForwardArgs &a, cudaStream_t 
 
 // The one-launch forward stage where it applies (M = 4096, nchan 2..16, the TMA gather, a queue
 // buffer of 1 + chunks words, no batch rounds, a stream that is not being captured into a graph);
-// cudaErrorNotSupported where it does not.  A cooperative launch of at most the CTAs that fit on
-// the device at once.
+// cudaErrorNotSupported where it does not.  A grid of at most the CTAs that fit on the device at
+// once, launched as an ordinary kernel: its waits end whichever of its CTAs are resident (see
+// k_forward_fused), and a cooperative launch, which needs the whole grid resident, would hold the
+// stage back until other streams' kernels (a server's other beams) have left the GPU.
 static cudaError_t launch_forward_fused(const ForwardArgs &a, cudaStream_t st)
 {
     if (!a.sync || a.r != 16 || a.round_dev || a.nchan < 2 || a.nchan > 16 || a.nsm < 1) return cudaErrorNotSupported;
@@ -670,21 +673,13 @@ static cudaError_t launch_forward_fused(const ForwardArgs &a, cudaStream_t st)
     const int64_t total = nchunk * (int64_t)kFwdChunk * (a.nchan + 16);
     const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)occ * a.nsm);
     if ((e = cudaMemsetAsync(a.sync, 0, sizeof(int) * (size_t)(1 + nchunk), st)) != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(Fft3<16>::T);
-    cfg.dynamicSmemBytes = smem_forward_fused<16>();
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
     if (a.i8)
-        return cudaLaunchKernelEx(&cfg, k_forward_fused<16, true>, tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n,
-                                  a.nvalid, a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
-    return cudaLaunchKernelEx(&cfg, k_forward_fused<16, false>, tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nvalid,
-                              a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
+        k_forward_fused<16, true><<<grid, Fft3<16>::T, smem_forward_fused<16>(), st>>>(
+            tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nvalid, a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
+    else
+        k_forward_fused<16, false><<<grid, Fft3<16>::T, smem_forward_fused<16>(), st>>>(
+            tm, a.scale, a.spec, a.tw_a, a.tw_b, a.tw_n, a.nvalid, a.nchan, a.k0, a.kc, a.nsub, a.sync, a.status);
+    return cudaGetLastError();
 }
 
 cudaError_t fp32_forward(const ForwardArgs &a, cudaStream_t st)
