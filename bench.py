@@ -208,12 +208,12 @@ NCU_TRAFFIC = {
     # 2069.1 MB written for 4.253e9 units (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # 4th launch)
     "d561d216c3f24e5d:fp16": 0.6152,
-    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 542.6 MB read +
-    # 2067.2 MB written for 4.253e9 units (same capture command with the FP32 form)
-    "9138821633f26fff:fp32": 0.6136,
+    # 8-subband workload, one launch of k_dedisperse_pair (FP32, 16 channels): 543.2 MB read +
+    # 2066.9 MB written for 4.253e9 units (same capture command with the FP32 form)
+    "11fe8e4f74697758:fp32": 0.6137,
     # the paper's setup at 2^20 samples, one launch of k_dedisperse_pair at M = 8192 (FP32, 8
-    # channels, nint 1): 232.4 MB read + 3241.3 MB written for 8.258e8 units
-    "9138821633f26fff:fp32:m8192": 4.2067,
+    # channels, nint 1): 232.3 MB read + 3241.0 MB written for 8.258e8 units
+    "11fe8e4f74697758:fp32:m8192": 4.2062,
 }
 
 try:
