@@ -596,7 +596,8 @@ def gpu_arm(args, w):
         log(f"rank {rank}: cuFFT unfused comparison: {cufft['value']:.2f} {UNIT}, {cufft['ms_per_step']:.1f} ms/step, "
             f"max rel diff vs headline {cufft['max_rel_diff_vs_headline']:.2e}")
 
-    # ---- roofline of the dominant kernel (the DM stage) of every form, SURVEY 8(d)'s definition
+    # ---- roofline of the dominant kernel (the DM stage) of every form: the slower of the nominal
+    #      FFT flops at the form's peak and the algorithmic bytes at HBM bandwidth
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     rooflines = {f: dm_stage_roofline(f, r, props, sm_max) for f, r in results.items()}
     roofline = rooflines[head]
