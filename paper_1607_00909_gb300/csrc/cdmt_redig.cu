@@ -251,14 +251,18 @@ __global__ void __launch_bounds__(256) k_redig_fused(const float *__restrict__ f
     uint8_t *dst = out + (int64_t)dm * nt * rows + (rows - r0 - nr);
     if (nr == R && (rows & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 3) == 0) {
         constexpr int W = R / 4;    // 4-byte words of the R rows in one spectrum
-        for (int64_t i = threadIdx.x; i < nt * W; i += blockDim.x) {
-            const int t = (int)(i / W), wd = (int)(i % W);
-            const int rr = R - 1 - 4 * wd;   // rows rr, rr-1, rr-2, rr-3 at positions 4wd .. 4wd+3
+        // a thread keeps one word position (the block's threads are a multiple of W): its four
+        // rows' (mean, gain) stay in registers
+        const int wd = (int)(threadIdx.x % W);
+        const int rr = R - 1 - 4 * wd;   // rows rr, rr-1, rr-2, rr-3 at positions 4wd .. 4wd+3
+        float2 mg[4];
+        #pragma unroll
+        for (int b = 0; b < 4; b++) mg[b] = make_float2(mus[rr - b], gs[rr - b]);
+        for (int64_t t = threadIdx.x / W; t < nt; t += blockDim.x / W) {
             uint32_t v = 0;
             #pragma unroll
-            for (int b = 0; b < 4; b++)
-                v |= (uint32_t)code8(tile[at(rr - b, t)], make_float2(mus[rr - b], gs[rr - b])) << (8 * b);
-            *reinterpret_cast<uint32_t *>(dst + (int64_t)t * rows + 4 * wd) = v;
+            for (int b = 0; b < 4; b++) v |= (uint32_t)code8(tile[at(rr - b, (int)t)], mg[b]) << (8 * b);
+            *reinterpret_cast<uint32_t *>(dst + t * rows + 4 * wd) = v;
         }
     } else {
         for (int64_t i = threadIdx.x; i < nt * nr; i += blockDim.x) {
